@@ -1,0 +1,488 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+No test here compares the oracle with itself: each check uses a value
+printed in a paper or library (known-answer vectors), a closed form, an
+invariant, a special case that reduces to a library routine, or brute force
+on tiny inputs.
+"""
+import json
+import math
+import os
+
+import numpy as np
+import pytest
+from scipy import special, stats
+
+from paper_2608_28514_gb300 import analytic as A
+from paper_2608_28514_gb300 import workloads as W
+
+GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
+
+
+# --------------------------------------------------------------------------
+# Philox4x32-10 (Salmon et al., SC'11) known-answer vectors
+# --------------------------------------------------------------------------
+def test_philox_known_answers(oracle):
+    rows = [l.split() for l in open(os.path.join(GOLDEN, "philox4x32_10_kat.txt"))
+            if l.strip() and not l.startswith("#")]
+    assert len(rows) == 3
+    for r in rows:
+        v = [int(x, 16) for x in r]
+        out = oracle.philox(v[0:4], v[4:6])[0]
+        assert list(out) == v[6:10]
+
+
+def test_stream_layout(oracle):
+    """Draw n of a stream is word n % 4 of the Philox block n // 4 with
+    counter (block, purpose, walker, t)."""
+    seed = 0x1234_5678_9ABC_DEF0
+    key = [seed & 0xFFFFFFFF, seed >> 32]
+    d = oracle.stream_draws(seed, 7, 3, 5, 0, 12)
+    for n in range(12):
+        blk = oracle.philox([n // 4, 5, 3, 7], key)[0]
+        assert d[n] == blk[n % 4]
+
+
+# --------------------------------------------------------------------------
+# Likelihoods: independent routes to the same value
+# --------------------------------------------------------------------------
+def _theta_to_unit(p, th):
+    return (np.asarray(th) - p.lo) / (p.hi - p.lo)
+
+
+def test_gauss_iso_matches_scipy_logpdf(oracle):
+    p = W.gauss_iso(3, 0.7, -5, 5, mean=0.3)
+    lik = oracle.Lik(p)
+    rng = np.random.default_rng(1)
+    th = rng.uniform(-5, 5, size=(20, 3))
+    got = oracle.loglike(lik, _theta_to_unit(p, th))
+    want = stats.norm.logpdf(th, loc=0.3, scale=0.7).sum(1) + 1.5 * math.log(2 * math.pi * 0.49)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-12)
+
+
+def test_gauss_corr_matches_linear_solve(oracle):
+    p = W.gauss_corr(6, seed=11)
+    lik = oracle.Lik(p)
+    rng = np.random.default_rng(2)
+    th = rng.uniform(-10, 10, size=(25, 6))
+    got = oracle.loglike(lik, _theta_to_unit(p, th))
+    y = th - p.mean
+    want = -0.5 * np.einsum("ij,ij->i", y, np.linalg.solve(p.cov, y.T).T)
+    np.testing.assert_allclose(got, want, rtol=1e-9)
+
+
+def test_rosenbrock_textbook_values(oracle):
+    p = W.rosenbrock(2)
+    lik = oracle.Lik(p)
+    pts = {(1.0, 1.0): 0.0, (0.0, 0.0): -1.0, (-1.0, 1.0): -4.0, (2.0, 0.0): -1601.0}
+    for th, want in pts.items():
+        assert oracle.loglike(lik, _theta_to_unit(p, th))[0] == pytest.approx(want, abs=1e-9)
+    p3 = W.rosenbrock(3)
+    l3 = oracle.Lik(p3)
+    assert oracle.loglike(l3, _theta_to_unit(p3, [1, 1, 1]))[0] == pytest.approx(0.0, abs=1e-12)
+    # chained: x = (0, 0, 0) has two unit terms
+    assert oracle.loglike(l3, _theta_to_unit(p3, [0, 0, 0]))[0] == pytest.approx(-2.0, abs=1e-9)
+
+
+def test_mixture_matches_logsumexp(oracle):
+    p = W.mixture(5, seed=3)
+    lik = oracle.Lik(p)
+    rng = np.random.default_rng(3)
+    th = np.vstack([p.centres + 0.05 * rng.standard_normal(p.centres.shape),
+                    rng.uniform(-5, 5, size=(10, 5))])
+    got = oracle.loglike(lik, _theta_to_unit(p, th))
+    sq = ((th[:, None, :] - p.centres[None]) ** 2).sum(-1)
+    want = special.logsumexp(-sq / (2 * p.sigma ** 2), axis=1) - math.log(4)
+    np.testing.assert_allclose(got, want, rtol=1e-12, atol=1e-9)
+
+
+def test_mlp_matches_torch_float64(oracle):
+    torch = pytest.importorskip("torch")
+    p = W.mlp_emulator(seed=1, widths=(5, 16, 16, 7))
+    lik = oracle.Lik(p)
+    rng = np.random.default_rng(4)
+    x = rng.uniform(0, 1, size=(8, 5))
+    got = oracle.loglike(lik, x)
+    h = torch.tensor(x, dtype=torch.float64)
+    for i, (Wt, Bt) in enumerate(zip(p.mlp.weights, p.mlp.biases)):
+        h = torch.nn.functional.linear(h, torch.tensor(Wt, dtype=torch.float64),
+                                       torch.tensor(Bt, dtype=torch.float64))
+        if i + 1 < len(p.mlp.weights):
+            h = torch.nn.functional.silu(h)
+    chi = ((h.numpy() - p.mlp.data) / p.mlp.sigma_out) ** 2
+    np.testing.assert_allclose(got, -0.5 * chi.sum(1), rtol=1e-11)
+
+
+# --------------------------------------------------------------------------
+# a2: selection by brute force
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N,m", [(7, 1), (10, 3), (33, 5), (64, 32), (200, 20)])
+def test_select_bruteforce(oracle, N, m):
+    rng = np.random.default_rng(N * 100 + m)
+    logl = np.round(rng.normal(size=N), 1)  # many ties
+    worst, seeds = oracle.select(logl, m, seed=99, t=4)
+    order = sorted(range(N), key=lambda j: (logl[j], j))
+    assert list(worst) == order[:m]
+    surv = sorted(order[m:])
+    for i in range(m):
+        w = int(oracle.stream_draws(99, 4, i, oracle.PURPOSE_SEED, 0, 1)[0])
+        assert seeds[i] == surv[(w * (N - m)) >> 32]
+
+
+# --------------------------------------------------------------------------
+# a4-a7: slice sampling
+# --------------------------------------------------------------------------
+def test_slice_step_is_uniform_on_a_1d_slice(oracle):
+    """From a fixed point, one stepping-out + shrinkage step on a unimodal
+    1-D slice returns a point uniform on the slice (Neal 2003)."""
+    p = W.gauss_iso(1, 1.0, -5, 5)
+    lik = oracle.Lik(p)
+    o = oracle.opts(1, 1)
+    thr = -0.5 * 1.5 ** 2  # slice theta in (-1.5, 1.5): x in (0.35, 0.65)
+    xs = []
+    for wk in range(3000):
+        r = oracle.slice_walker(lik, o, 1, 5, 0, wk, [0.5], 0.0, [[0.1]], thr, thr)
+        assert r["l"] > thr
+        xs.append(r["x"][0])
+    xs = np.array(xs)
+    assert xs.min() > 0.35 and xs.max() < 0.65
+    assert stats.kstest((xs - 0.35) / 0.3, "uniform").pvalue > 1e-3
+
+
+def test_slice_walker_invariants(oracle):
+    p = W.gauss_corr(4, seed=5)
+    lik = oracle.Lik(p)
+    o = oracle.opts(4, 8)
+    rng = np.random.default_rng(6)
+    x0 = _theta_to_unit(p, p.mean + 0.1 * rng.standard_normal(4))
+    l0 = oracle.loglike(lik, x0)[0]
+    chol = np.linalg.cholesky(np.diag([0.01] * 4))
+    for wk in range(20):
+        thr_out, thr_in = l0 - 20.0, l0 - 5.0
+        r = oracle.slice_walker(lik, o, 20, 8, 3, wk, x0, l0, chol, thr_out, thr_in)
+        assert r["l"] > thr_in
+        assert np.all((r["x"] >= 0) & (r["x"] <= 1))
+        assert r["l"] == pytest.approx(oracle.loglike(lik, r["x"])[0], abs=1e-12)
+        # the history of the last step ends with the accepted point
+        assert r["hist_len"] >= 1
+        assert r["hist_l"][-1] == r["l"]
+        np.testing.assert_array_equal(r["hist_x"][-1], r["x"])
+        # earlier history samples were all rejected against thr_in
+        assert np.all(~(r["hist_l"][:-1] > thr_in))
+        assert r["flags"] == 0
+
+
+def _disc_square_area(r, half):
+    """Area of the disc of radius r centred in the square [-half, half]^2."""
+    if r <= half:
+        return math.pi * r * r
+    if r >= half * math.sqrt(2):
+        return 4 * half * half
+    seg = r * r * math.acos(half / r) - half * math.sqrt(r * r - half * half)
+    return math.pi * r * r - 4 * seg
+
+
+def _x_of_l_gauss2d(l, sigma=0.5, half=5.0):
+    r = sigma * math.sqrt(max(-2.0 * l, 0.0))
+    return _disc_square_area(r, half) / (2 * half) ** 2
+
+
+@pytest.mark.slow
+def test_shrinkage_law_sequential(oracle):
+    """Sequential nested sampling: t_k = X_k / X_{k-1} are iid Beta(N, 1),
+    so t_k^N ~ U(0, 1) and E[log X_k] = -k/N (Skilling 2006).  X(logL) is
+    exact for the centred 2-D Gaussian (disc area, box-clipped)."""
+    p = W.gauss2d_sigma05()
+    N = 100
+    us, lx = [], []
+    for seed in range(1, 31):
+        r = oracle.run(p, N, 1, 10, 1e-3, seed, sequential=True)
+        n_dead = r["n_iter"]
+        X = np.array([_x_of_l_gauss2d(l) for l in r["dead_l"][:n_dead]])
+        prev = np.concatenate([[1.0], X[:-1]])
+        us.append((X / prev) ** N)
+        lx.append(np.log(X[:600]))
+    u = np.concatenate(us)
+    assert stats.kstest(u, "uniform").pvalue > 1e-3
+    lx = np.array(lx)
+    k = np.arange(1, 601)
+    mean = lx.mean(0)
+    se = np.sqrt(k) / N / math.sqrt(lx.shape[0])
+    z = (mean + k / N) / se
+    assert np.all(np.abs(z[[99, 299, 599]]) < 4.0)
+
+
+# --------------------------------------------------------------------------
+# a8-a9: Algorithms 1 and 2
+# --------------------------------------------------------------------------
+def _pad_hist(hist):
+    t = max(len(h) for h in hist)
+    H = np.full((len(hist), t), -np.inf)
+    for i, h in enumerate(hist):
+        H[i, :len(h)] = h
+    return H, np.array([len(h) for h in hist], dtype=np.int32)
+
+
+def test_alg12_hand_cases(oracle):
+    cases = json.load(open(os.path.join(GOLDEN, "alg12_hand_cases.json")))["cases"]
+    for c in cases:
+        H, hl = _pad_hist(c["hist"])
+        out = oracle.batch_correct(np.array(c["W"]), np.array(c["new"]), H, hl, K=c["K"], correction=2)
+        got_acc = [[int(out["acc_src"][j]), int(out["acc_hpos"][j]), out["acc_l"][j], out["acc_P"][j]]
+                   for j in range(len(c["W"]))]
+        got_rej = [[int(out["rej_src"][j]), int(out["rej_hpos"][j]), out["rej_l"][j], out["rej_P"][j]]
+                   for j in range(len(c["W"]))]
+        assert got_acc == c["acc"], c["name"]
+        assert got_rej == c["rej"], c["name"]
+        assert out["n_relaxed"] == c["n_relaxed"], c["name"]
+
+
+def _alg12_restated(W_, new, hist, K):
+    """Algorithms 1-2 restated from the paper's text, entry by entry."""
+    m = len(W_)
+    C = [dict(l=W_[i], P=-1.0, H=-1, src=i, hpos=-1) for i in range(m)]
+    C += [dict(l=new[i], P=W_[i], H=i, src=m + i, hpos=-1) for i in range(m)]
+    key = lambda e: (e["l"], e["src"])
+    C.sort(key=key)
+    rel = 0
+    for _ in range(K):
+        r, a = C[:m], C[m:]
+        faulty = [e for e in a if e["H"] >= 0 and e["P"] >= a[0]["l"]]
+        if not faulty:
+            break
+        inst = [e["l"] for e in r if e["H"] >= 0]
+        for e, thr in zip(faulty, inst):
+            h = hist[e["H"]]
+            for pos, hv in enumerate(h):
+                if hv > thr:
+                    e["l"], e["hpos"], e["P"] = hv, pos, thr
+                    rel += 1
+                    break
+        C = sorted(r + a, key=key)
+    return C[m:], C[:m], rel
+
+
+@pytest.mark.parametrize("trial", range(40))
+def test_alg12_random_vs_restatement(oracle, trial):
+    rng = np.random.default_rng(1000 + trial)
+    m = int(rng.integers(1, 9))
+    K = int(rng.integers(1, 4))
+    Wv = np.sort(np.round(rng.normal(size=m), 1))
+    new, hist = [], []
+    for i in range(m):
+        h = list(np.round(rng.normal(size=int(rng.integers(0, 5))), 1))
+        v = round(Wv[i] + abs(rng.normal()) + 0.05, 1)  # accepted: above its threshold
+        h.append(v)
+        new.append(v)
+        hist.append(h)
+    H, hl = _pad_hist(hist)
+    out = oracle.batch_correct(Wv, np.array(new), H, hl, K=K, correction=2)
+    acc, rej, rel = _alg12_restated(list(Wv), new, hist, K)
+    assert [e["src"] for e in acc] == list(out["acc_src"])
+    assert [e["src"] for e in rej] == list(out["rej_src"])
+    assert [e["l"] for e in acc] == list(out["acc_l"])
+    assert [e["hpos"] for e in rej] == list(out["rej_hpos"])
+    assert rel == out["n_relaxed"]
+    # invariants: the m dead are no better than the m live, and the dead
+    # include the m-th smallest removed value's bound
+    assert max(out["rej_l"]) <= min(out["acc_l"])
+    assert max(out["rej_l"]) <= Wv[-1]
+
+
+def test_sorting_only_and_naive(oracle):
+    Wv = np.array([1.0, 2.0])
+    new = np.array([1.5, 3.0])
+    H, hl = _pad_hist([[1.5], [0.5, 1.7, 3.0]])
+    s = oracle.batch_correct(Wv, new, H, hl, K=1, correction=1)
+    assert list(s["rej_l"]) == [1.0, 1.5] and list(s["acc_l"]) == [2.0, 3.0]
+    n = oracle.batch_correct(Wv, new, H, hl, K=1, correction=0)
+    assert list(n["rej_l"]) == [1.0, 2.0] and list(n["acc_l"]) == [1.5, 3.0]
+
+
+# --------------------------------------------------------------------------
+# a11: evidence
+# --------------------------------------------------------------------------
+def test_evidence_constant_likelihood(oracle):
+    """L = e^c everywhere: Z = e^c exactly and H = 0, for any number of
+    deaths (the rectangle weights and the live tail sum to X_0 = 1)."""
+    for N, K in [(1, 5), (10, 0), (100, 1234)]:
+        e = oracle.Evidence(N)
+        for _ in range(K):
+            e.add_dead(-3.25)
+        for _ in range(N):
+            e.add_live(-3.25)
+        assert e.logz == pytest.approx(-3.25, abs=1e-12)
+        assert abs(e.info) < 1e-9
+
+
+def test_evidence_matches_mpmath(oracle):
+    mpmath = pytest.importorskip("mpmath")
+    mpmath.mp.dps = 50
+    rng = np.random.default_rng(7)
+    N, K = 37, 500
+    ls = np.cumsum(np.abs(rng.normal(size=K))) * 0.1 - 30
+    live = ls[-1] + np.sort(np.abs(rng.normal(size=N)))
+    e = oracle.Evidence(N)
+    for l in ls:
+        e.add_dead(l)
+    for l in live:
+        e.add_live(l)
+    Z = mpmath.mpf(0)
+    terms = []
+    for k, l in enumerate(ls, start=1):
+        w = mpmath.e ** mpmath.mpf(l) * (mpmath.e ** (-mpmath.mpf(k - 1) / N) - mpmath.e ** (-mpmath.mpf(k) / N))
+        terms.append((w, l))
+    for l in live:
+        terms.append((mpmath.e ** mpmath.mpf(l) * mpmath.e ** (-mpmath.mpf(K) / N) / N, l))
+    Z = sum(t[0] for t in terms)
+    Hinfo = sum(t[0] / Z * mpmath.mpf(t[1]) for t in terms) - mpmath.log(Z)
+    assert e.logz == pytest.approx(float(mpmath.log(Z)), abs=1e-11)
+    assert e.info == pytest.approx(float(Hinfo), rel=1e-9)
+
+
+def test_stop_rule(oracle):
+    e = oracle.Evidence(10)
+    e.add_dead(0.0)  # Z = 1 - e^{-0.1}
+    logz = math.log(1 - math.exp(-0.1))
+    lmax_stop = math.log(1e-3) + 0.1 + logz - 1e-9
+    assert e.should_stop(lmax_stop, 1e-3)
+    assert not e.should_stop(lmax_stop + 2e-9, 1e-3)
+
+
+# --------------------------------------------------------------------------
+# a3: clustering
+# --------------------------------------------------------------------------
+def test_cholesky_of_root_matches_numpy(oracle):
+    rng = np.random.default_rng(8)
+    x = rng.uniform(0.2, 0.7, size=(300, 4)) @ np.array(
+        [[1, 0.3, 0, 0], [0, 1, 0.2, 0], [0, 0, 1, 0.1], [0, 0, 0, 1]]) * 0.8
+    o = oracle.opts(4, 1, depth=0)
+    out = oracle.cluster(x, o, 1, 0)
+    cov = np.cov(x.T, bias=True)
+    want = np.linalg.cholesky(cov + 1e-10 * np.trace(cov) / 4 * np.eye(4))
+    np.testing.assert_allclose(out["chol"][0], want, rtol=1e-10, atol=1e-14)
+    np.testing.assert_allclose(out["centres"][0], x.mean(0), rtol=1e-12)
+    assert out["mask"][0] == 1 and np.all(out["assign"] == 0)
+
+
+def test_eigen_clip_branch_matches_eigh(oracle):
+    """A covariance that rounding has made slightly indefinite fails the
+    plain Cholesky; its eigenvalues are clipped at 1e-10 lambda_max and the
+    result regularised (section 2.1).  A merely singular one is handled by
+    the jitter alone."""
+    rng = np.random.default_rng(12)
+    Q, _ = np.linalg.qr(rng.normal(size=(3, 3)))
+    cov = (Q * np.array([1.0, 0.5, -1e-6])) @ Q.T
+    L, flag = oracle.reg_cholesky(cov)
+    assert flag == 1
+    lam, V = np.linalg.eigh(cov)
+    lam = np.maximum(lam, 1e-10 * lam.max())
+    want = (V * lam) @ V.T + 1e-10 * np.trace(cov) / 3 * np.eye(3)
+    np.testing.assert_allclose(L @ L.T, want, rtol=1e-9, atol=1e-15)
+    v = np.array([1.0, 2.0, -1.0])
+    L1, flag1 = oracle.reg_cholesky(np.outer(v, v) * 0.01)
+    assert flag1 == 0
+    np.testing.assert_allclose(L1 @ L1.T, np.outer(v, v) * 0.01 + 1e-10 * 0.06 / 3 * np.eye(3), atol=1e-15)
+
+
+def test_two_blobs_split_at_depth_one(oracle):
+    rng = np.random.default_rng(9)
+    a = rng.normal([0.25, 0.3, 0.3], 0.03, size=(150, 3))
+    b = rng.normal([0.75, 0.7, 0.6], 0.03, size=(120, 3))
+    x = np.vstack([a, b])
+    o = oracle.opts(3, 1, depth=1)
+    out = oracle.cluster(x, o, 3, 0)
+    assert out["split"][0] == 1 and out["n_leaves"] == 2
+    assert list(out["mask"]) == [0, 1, 1]
+    labels = out["assign"]
+    assert len(set(labels[:150])) == 1 and len(set(labels[150:])) == 1
+    assert labels[0] != labels[-1]
+    assert sorted(out["count"][1:]) == [120, 150]
+    # new points join the nearest accepted centre
+    assert oracle.nearest_leaf(out["centres"], out["mask"], np.array([0.26, 0.3, 0.29])) == labels[0]
+
+
+def test_single_ball_is_not_split(oracle):
+    rng = np.random.default_rng(10)
+    g = rng.normal(size=(2000, 3))
+    x = 0.5 + 0.2 * g / np.linalg.norm(g, axis=1, keepdims=True) * rng.uniform(0, 1, (2000, 1)) ** (1 / 3)
+    o = oracle.opts(3, 1, depth=2)
+    out = oracle.cluster(x, o, 4, 0)
+    assert out["split"][0] == 0 and out["n_leaves"] == 1 and out["mask"][0] == 1
+
+
+def test_four_modes_found_at_depth_three(oracle):
+    p = W.mixture4_d5(1)
+    rng = np.random.default_rng(11)
+    th = np.vstack([c + p.sigma * rng.standard_normal((200, 5)) for c in p.centres])
+    x = (th - p.lo) / (p.hi - p.lo)
+    o = oracle.opts(5, 1, depth=3)
+    out = oracle.cluster(x, o, 5, 0)
+    labels = out["assign"]
+    # every mode maps to exactly one leaf and distinct modes to distinct leaves
+    leaf_of_mode = [set(labels[200 * k:200 * (k + 1)]) for k in range(4)]
+    assert all(len(s) == 1 for s in leaf_of_mode)
+    assert len(set.union(*leaf_of_mode)) == 4
+    assert out["n_leaves"] == 4
+
+
+# --------------------------------------------------------------------------
+# whole runs
+# --------------------------------------------------------------------------
+def test_batched_m1_equals_sequential(oracle):
+    """At m = 1 Algorithm 1 keeps the new point (logL > W[0]) and Algorithm
+    2 finds no faulty point (P = W[0] < logL), so the batched sampler is the
+    textbook sequential one, bit for bit (section 3.2)."""
+    for p, N in [(W.gauss2d_sigma05(), 100), (W.mixture4_d5(2), 150)]:
+        o1 = oracle.opts(p.d, 1, depth=1 if p.kind == W.MIXTURE else 0)
+        o2 = oracle.opts(p.d, 1, depth=1 if p.kind == W.MIXTURE else 0)
+        a = oracle.run(p, N, 1, 2 * p.d, 1e-2, 17, o=o1)
+        b = oracle.run(p, N, 1, 2 * p.d, 1e-2, 17, o=o2, sequential=True)
+        assert a["n_dead"] == b["n_dead"]
+        np.testing.assert_array_equal(a["dead_l"], b["dead_l"])
+        np.testing.assert_array_equal(a["dead_x"], b["dead_x"])
+        assert a["logz"] == b["logz"]
+
+
+@pytest.mark.slow
+def test_gauss2d_logz_over_50_seeds(oracle):
+    p = W.gauss2d_sigma05()
+    truth = A.logz(p)
+    assert truth == pytest.approx(-4.1535875, abs=1e-7)
+    z, err = [], []
+    for seed in range(1, 51):
+        r = oracle.run(p, 100, 1, 10, 1e-3, seed)
+        assert r["status"] == 0
+        z.append(r["logz"])
+        err.append(r["logz_err"])
+    z = np.array(z)
+    assert abs(z.mean() - truth) < 3 * z.std(ddof=1) / math.sqrt(len(z))
+    # the per-run sqrt(H/N) error agrees with the scatter over seeds
+    assert 0.6 < np.mean(err) / z.std(ddof=1) < 1.6
+
+
+@pytest.mark.slow
+def test_batched_runs_recover_analytic_logz(oracle):
+    cases = [
+        (W.corr_gauss10(1), 1000, 100, 50, 0, 2),
+        (W.rosenbrock(2), 1000, 50, 10, 0, 3),
+        (W.mixture4_d5(1), 2000, 200, 25, 3, 2),
+    ]
+    for p, N, m, ns, depth, nseeds in cases:
+        truth = A.logz(p)
+        o = oracle.opts(p.d, m, depth=depth)
+        for seed in range(1, nseeds + 1):
+            r = oracle.run(p, N, m, ns, 1e-3, seed, o=o)
+            assert r["status"] == 0, p.name
+            assert abs(r["logz"] - truth) < 3.5 * r["logz_err"] + 0.02, (p.name, r["logz"], truth)
+            assert np.all(np.diff(r["dead_l"][: r["n_iter"] * m]) >= 0), p.name
+
+
+def test_rosenbrock_quadratures_agree():
+    """The 2-D Rosenbrock pin: erf-quadrature and the 4096^2 midpoint grid."""
+    a = A.logz_rosenbrock_2d(1.0, 100.0, -5.0, 5.0)
+    b = A.logz_rosenbrock_grid2d(1.0, 100.0, -5.0, 5.0)
+    assert a == pytest.approx(-5.8041324, abs=2e-7)
+    assert abs(a - b) < 1e-7
+    c = A.logz_rosenbrock_chain(2, 1.0, 100.0, -5.0, 5.0, h=0.002)
+    assert abs(a - c) < 1e-7
