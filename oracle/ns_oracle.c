@@ -71,7 +71,6 @@ void orc_stream_draws(const uint32_t key[2], uint32_t t, uint32_t walker, uint32
 /* 24-bit uniforms: exactly representable in FP32 and FP64. */
 static double u24(uint32_t w) { return (double)(w >> 8) * (1.0 / 16777216.0); }          /* [0,1) */
 static double u24_open0(uint32_t w) { return ((double)(w >> 8) + 1.0) * (1.0 / 16777216.0); } /* (0,1] */
-static double u24_mid(uint32_t w) { return ((double)(w >> 8) + 0.5) * (1.0 / 16777216.0); }  /* (0,1) */
 /* Uniform integer in [0, n) by the high word of w*n. */
 static int u_index(uint32_t w, int n) { return (int)(((uint64_t)w * (uint64_t)n) >> 32); }
 
@@ -858,13 +857,14 @@ static void live_free(orc_live* s)
     free(s->count); free(s->split); free(s->mask); free(s->assign);
 }
 
-/* Initial live set: N uniform draws in the prior box (unit cube). */
+/* Initial live set: N uniform draws in the prior box (unit cube), each
+ * coordinate a 24-bit uniform on [0, 1). */
 static void live_init(orc_live* s, const orc_lik* L, const uint32_t key[2], long long* n_evals)
 {
     const int d = s->d;
     for (int j = 0; j < s->N; ++j) {
         for (int i = 0; i < d; ++i)
-            s->x[(size_t)j * d + i] = u24_mid(orc_draw_at(key, ORC_T_INIT, (uint32_t)j, 0, (uint32_t)i));
+            s->x[(size_t)j * d + i] = u24(orc_draw_at(key, ORC_T_INIT, (uint32_t)j, 0, (uint32_t)i));
         s->l[j] = orc_loglike(L, s->x + (size_t)j * d);
     }
     *n_evals += s->N;
