@@ -1,0 +1,351 @@
+#!/usr/bin/env python3
+"""Throughput benchmark of the GB300 batched nested sampler.
+
+Workload: the 10-D correlated Gaussian (covariance R diag(lambda) R^T, R a
+seeded Haar-orthogonal matrix, lambda log-uniform in [0.01, 1], mean
+uniform in [-2, 2]^10, prior [-10, 10]^10), N_live = 1000, m = 100 live
+points replaced per iteration, 5 d = 50 slice steps, stop at a remaining-
+evidence fraction of 1e-3.  Each GPU runs R independent runs (one seed and
+one seeded covariance each), all in one persistent launch.  A step is the
+whole job: every run from its initial live set to its stopping rule.
+
+Reported (one JSON line from rank 0):
+  value     likelihood evaluations per second over all GPUs, device time of
+            ns_run with the problem already resident (L2 flushed between
+            steps);
+  e2e       the same metric through the C ABI from host buffers:
+            ns_create (host->device) + ns_run + ns_result for every run
+            (device->host of all samples) + ns_destroy;
+  roofline  the run kernel against the FP32 ALU peak;
+  cpu_baseline  the CPU oracle on the host cores, on a bounded sample.
+
+``--impl reference`` times the CPU oracle as the reference arm instead.
+"""
+import argparse
+import json
+import math
+import multiprocessing as mp
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "likelihood evals/s and wall-time to log Z at |ΔlogZ|<0.1; BF16 vs FP32 path"
+UNIT = "evals/s"
+D, N_LIVE, M, N_STEPS, STOP = 10, 1000, 100, 50, 1e-3
+# algorithmic FP32 work of one correlated-Gaussian evaluation at d = 10:
+# candidate x + t v (d FMA), y = theta - mean (d FMA), z = L^T y
+# (d(d+1)/2 FMA), |z|^2 (d FMA)
+FLOP_PER_EVAL = 2 * (3 * D + D * (D + 1) // 2)
+# FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (maximum SM clock)
+SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--runs", type=int, default=304, help="independent runs per GPU")
+    ap.add_argument("--m", type=int, default=M)
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--chunk", type=int, default=1000)
+    return ap.parse_args()
+
+
+def workload_config(args, runs):
+    return {"workload": f"10-D correlated Gaussian, prior [-10,10]^10, N_live={N_LIVE}, m={args.m}, "
+                        f"{N_STEPS} slice steps, stop 1e-3; {runs} independent seeded runs per GPU",
+            "d": D, "n_live": N_LIVE, "m": args.m, "slice_steps": N_STEPS, "stop_frac": STOP,
+            "runs_per_gpu": runs, "correction": "sorting + history (K=1)",
+            "l2": "flushed between timed steps (256 MiB write)"}
+
+
+# --------------------------------------------------------------------------
+# CPU oracle (baseline and reference arm): one full run per process
+# --------------------------------------------------------------------------
+def _oracle_one(seed_m):
+    seed, m = seed_m
+    sys.path.insert(0, ROOT)
+    from oracle import oracle as O
+    from paper_2608_28514_gb300 import workloads as W
+    t0 = time.perf_counter()
+    r = O.run(W.corr_gauss10(seed), N_LIVE, m, N_STEPS, STOP, seed)
+    return r["n_evals"], time.perf_counter() - t0, r["logz"]
+
+
+def oracle_sample(n_proc, seeds, m):
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(n_proc) as pool:
+        out = pool.map(_oracle_one, [(s, m) for s in seeds])
+    wall = time.perf_counter() - t0
+    evals = sum(o[0] for o in out)
+    return evals, wall, out
+
+
+def host_cores():
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+# --------------------------------------------------------------------------
+# clocks during the timed region
+# --------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+        self.thread = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.gpu}", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-lms", "200"], stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+            return
+        self.thread = threading.Thread(target=self._read, daemon=True)
+        self.thread.start()
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        if self.thread:
+            self.thread.join(timeout=2)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() in ("active", "1", "yes"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# reference arm: the CPU oracle
+# --------------------------------------------------------------------------
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    cores = host_cores()
+    n_proc = max(1, min(cores, 16))
+    times, evals_all = [], 0
+    seed = 1
+    for step in range(args.warmup + args.steps):
+        seeds = list(range(seed, seed + n_proc))
+        seed += n_proc
+        ev, wall, _ = oracle_sample(n_proc, seeds, args.m)
+        if step >= args.warmup:
+            times.append(wall)
+            evals_all += ev
+    total = sum(times)
+    value = evals_all / total
+    sample = (f"each step: {n_proc} full runs of the workload (one seeded run per process, "
+              f"{n_proc} processes), FP64 oracle")
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(args, n_proc), "impl": "reference",
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_proc, "kind": "oracle", "sample": sample},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# --------------------------------------------------------------------------
+# the GB300 arm
+# --------------------------------------------------------------------------
+def main():
+    args = parse()
+    if args.impl == "reference":
+        run_reference(args)
+        return
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+
+    # the CPU baseline pool starts before the first GPU call (spawned workers)
+    cpu = None
+    if rank == 0 and world == 1 and not args.no_cpu:
+        cores = host_cores()
+        n_proc = max(1, min(cores, 16))
+        ev, wall, _ = oracle_sample(n_proc, list(range(10001, 10001 + n_proc)), args.m)
+        cpu = {"value": ev / wall, "unit": UNIT, "cores": n_proc, "kind": "oracle",
+               "sample": f"{n_proc} full runs of the workload (seeds 10001..{10000 + n_proc}), one per process, "
+                         f"{wall:.1f} s wall"}
+
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    from paper_2608_28514_gb300 import _native as nat
+    from paper_2608_28514_gb300 import analytic
+    from paper_2608_28514_gb300 import workloads as W
+
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl")
+    R = args.runs
+    seeds = [1 + rank * R + r for r in range(R)]
+    probs = [W.corr_gauss10(s) for s in seeds]
+    truths = np.array([analytic.logz(p) for p in probs])
+    runs = [(p, N_LIVE, args.m, N_STEPS, STOP, s) for p, s in zip(probs, seeds)]
+    opt = nat.ns_default_options(chunk_iters=args.chunk)
+    h = nat.ns_create_batch(runs, opt)
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def one_step():
+        nat.ns_reset(h, stream)
+        flush.zero_()
+        torch.cuda.synchronize()
+        nat.ns_run(h, stream)
+        st = nat.ns_get_stats(h)
+        res = [nat.ns_summary(h, r) for r in range(R)]
+        return st, res
+
+    for _ in range(args.warmup):
+        one_step()
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    sampler = ClockSampler(local)
+    sampler.start()
+    barrier()
+    dev_ms, ker_ms, launches, evals, wall_first = 0.0, 0.0, 0, 0, None
+    last_res = None
+    for k in range(args.steps):
+        st, res = one_step()
+        dev_ms += st["run_ms"]
+        ker_ms += st["kernel_ms"]
+        launches += st["launches"]
+        evals += sum(r["n_evals"] for r in res)
+        last_res = res
+    barrier()
+    clocks = sampler.stop()
+
+    t_dev = dev_ms / 1e3
+    if world > 1:
+        tt = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        ee = torch.tensor([float(evals)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(ee, op=dist.ReduceOp.SUM)
+        t_dev, evals_all = float(tt.item()), float(ee.item())
+    else:
+        evals_all = float(evals)
+    value = evals_all / t_dev
+
+    phase = {k: 0 for k in nat.PHASES}
+    for r in range(R):
+        for k, v in nat.ns_phase_cycles(h, r).items():
+            phase[k] += v
+    tot_c = max(1, sum(phase.values()))
+    phase_frac = {k: round(v / tot_c, 4) for k, v in phase.items()}
+    status = [r["status"] for r in last_res]
+    logz = np.array([r["log_z"] for r in last_res])
+    err = np.array([r["log_z_err"] for r in last_res])
+    dz = logz - truths
+    acc = {"mean_dlogz": float(np.mean(dz)), "mean_abs_dlogz": float(np.mean(np.abs(dz))),
+           "frac_abs_dlogz_lt_0.1": float(np.mean(np.abs(dz) < 0.1)),
+           "frac_within_2sigma": float(np.mean(np.abs(dz) < 2 * err)), "mean_logz_err": float(np.mean(err)),
+           "all_status_ok": all(s == 0 for s in status)}
+
+    # roofline of the run kernel (the only kernel of the timed region)
+    avg_launch_s = (ker_ms / 1e3) / max(1, launches)
+    flops_per_launch = FLOP_PER_EVAL * evals / max(1, launches)
+    achieved = flops_per_launch / avg_launch_s / 1e12
+    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    traffic = None
+    tf = os.path.join(ROOT, "profiles", "traffic_k_run.json")
+    if os.path.exists(tf):
+        try:
+            tj = json.load(open(tf))
+            if tj.get("runs") and tj.get("bytes_per_run_per_launch"):
+                traffic = tj["bytes_per_run_per_launch"] * R
+        except (ValueError, KeyError):
+            traffic = None
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                "traffic": traffic, "kernel": "k_run<16>",
+                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (recipe unit counts, max clock)",
+                "flop_per_eval": FLOP_PER_EVAL}
+
+    # end to end through the C ABI from host buffers
+    e2e = None
+    if not args.no_e2e:
+        e2e_t, e2e_evals, h2d, d2h = 0.0, 0, 0, 0
+        for k in range(args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            h2 = nat.ns_create_batch(runs, opt)
+            nat.ns_run(h2, stream)
+            res = [nat.ns_result(h2, r) for r in range(R)]
+            st2 = nat.ns_get_stats(h2)
+            nat.ns_destroy(h2)
+            torch.cuda.synchronize()
+            e2e_t += time.perf_counter() - t0
+            e2e_evals += sum(r["n_evals"] for r in res)
+            h2d, d2h = st2["h2d_bytes"], st2["d2h_bytes"]
+            del res
+        if world > 1:
+            tt = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
+            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+            ee = torch.tensor([float(e2e_evals)], dtype=torch.float64, device="cuda")
+            dist.all_reduce(ee, op=dist.ReduceOp.SUM)
+            e2e_t, e2e_evals = float(tt.item()), float(ee.item())
+        e2e = {"value": e2e_evals / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": int(d2h), "includes": "ns_create + ns_run + ns_result(all runs) + ns_destroy"}
+
+    nat.ns_destroy(h)
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": dict(workload_config(args, R), parallelism=f"replicas x{world} (runs sharded by seed)"),
+                "wall_time_to_logz_s": t_dev / args.steps, "accuracy": acc, "clocks": clocks,
+                "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
+                "phase_cycle_share": phase_frac}
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,284 @@
+/*
+ * ns_gb300.h -- C ABI of the GB300 (sm_103a) batched nested sampler.
+ *
+ * The library computes the Bayesian evidence
+ *     Z = integral_0^1 L(X) dX                       (section 1, eq. 1.1)
+ * of a likelihood over a uniform prior box by nested sampling with batched
+ * live-point replacement: each iteration removes the m worst live points,
+ * draws m replacements by slice sampling in parallel (section 2.2), and
+ * repairs the ordering with batch sorting (Algorithm 1) and the history
+ * correction (Algorithm 2) of section 3.1.  Clustering of the live points
+ * (section 2.1) shapes the slice directions.
+ *
+ * Conventions shared by every entry point
+ *  - Every function returns ns_status (NS_OK = 0, negative on error).  No
+ *    entry point aborts, traps or throws.  A device loop that runs out of
+ *    its iteration budget reports NS_ERR_BUDGET instead of spinning.
+ *  - "host" pointers are read during the call only, unless stated; the
+ *    caller keeps ownership.  "device" pointers are CUDA global-memory
+ *    pointers on the current device; the caller owns them and they must stay
+ *    valid until the work queued on `stream` has finished.
+ *  - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *    default stream.  The step-level calls (ns_philox4x32_10 ... ns_cluster)
+ *    are asynchronous on `stream` and allocate nothing.
+ *  - Points are stored in unit-cube coordinates x in [0,1]^d; the likelihood
+ *    is evaluated at theta = lo + (hi - lo) * x.
+ *  - Random numbers: Philox4x32-10 (Salmon et al., SC'11) with key
+ *    (seed & 0xffffffff, seed >> 32) and counter (block, purpose, walker, t);
+ *    draw n of a stream is word n % 4 of block n / 4.  Purposes: slice step
+ *    s (0..0xffff) of walker w at iteration t; NS_PURPOSE_SEED for the
+ *    choice of a walker's start point; NS_PURPOSE_KMEANS (walker = tree node)
+ *    for the first k-means centre; iteration NS_T_INIT (walker = live slot)
+ *    for the initial live points.
+ *  - Log-likelihoods are unnormalised (section 3.2).  A NaN likelihood counts
+ *    as -infinity (outside every constraint).
+ */
+#ifndef NS_GB300_H
+#define NS_GB300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define NS_MAX_DIM 32          /* largest d a run may have */
+#define NS_MAX_MODES 8         /* mixture components */
+#define NS_MAX_DEPTH 3         /* cluster tree depth: up to 8 leaves, 15 nodes */
+#define NS_MAX_BATCH 256       /* m, walkers per run (one thread each) */
+#define NS_MAX_LIVE 65536      /* N_live per run */
+#define NS_MAX_HISTORY 64      /* history slots per walker */
+#define NS_PURPOSE_SEED 0x10000u
+#define NS_PURPOSE_KMEANS 0x20000u
+#define NS_T_INIT 0xFFFFFFFFu
+
+typedef enum {
+    NS_OK = 0,
+    NS_ERR_ARG = -1,      /* an argument is out of range; nothing was queued */
+    NS_ERR_CUDA = -2,     /* a CUDA call failed; see ns_last_error */
+    NS_ERR_OOM = -3,      /* device allocation failed */
+    NS_ERR_BUDGET = -4,   /* a capped loop gave up (step-out, shrink, iterations, dead buffer) */
+    NS_ERR_STATE = -5,    /* call out of order (e.g. ns_result before ns_run) */
+    NS_ERR_UNSUPPORTED = -6
+} ns_status;
+
+typedef enum {
+    NS_LIK_GAUSS_ISO = 0,   /* -1/2 sum ((theta-mean)/sigma)^2            (section 3.2) */
+    NS_LIK_GAUSS_CORR = 1,  /* -1/2 |L^T (theta-mean)|^2, L L^T = Sigma^-1 */
+    NS_LIK_ROSENBROCK = 2,  /* -sum_i (a-theta_i)^2 + b (theta_{i+1}-theta_i^2)^2 (section 4.2) */
+    NS_LIK_MIXTURE = 3,     /* log (1/K) sum_k exp(-|theta-c_k|^2 / (2 sigma^2)) (eq. array form) */
+    NS_LIK_MLP = 4          /* -1/2 sum_k ((MLP(theta)_k - data_k)/sigma_k)^2 (section 5 stand-in) */
+} ns_lik_kind;
+
+/* Likelihood description; host pointers, copied by ns_create*. */
+typedef struct {
+    int kind;                  /* ns_lik_kind */
+    const double* mean;        /* [d]   GAUSS_ISO, GAUSS_CORR */
+    const double* prec_chol;   /* [d*d] GAUSS_CORR: row-major lower L with L L^T = Sigma^-1 */
+    double sigma;              /*       GAUSS_ISO, MIXTURE (> 0) */
+    int n_modes;               /*       MIXTURE, 1..NS_MAX_MODES */
+    const double* centres;     /* [n_modes*d] MIXTURE */
+    double a, b;               /*       ROSENBROCK */
+    int n_layers;              /*       MLP: affine layers */
+    const int* widths;         /* [n_layers+1], widths[0] = d */
+    const float* weights;      /* concatenated [out][in] row-major blocks */
+    const float* biases;       /* concatenated [out] blocks */
+    const float* data;         /* [widths[n_layers]] */
+    const float* sigma_out;    /* [widths[n_layers]] (> 0) */
+} ns_likelihood;
+
+typedef struct {
+    int depth;            /* cluster tree depth, 0..NS_MAX_DEPTH (default 0: one cluster) */
+    int recluster_every;  /* iterations between re-clusterings; 0 = max(1, 100/m) (section 2.3) */
+    int n_min;            /* a child cluster needs more than n_min points; 0 = d + 1 */
+    double vol_frac;      /* children must be this much smaller than the parent (0.5) */
+    int kmeans_iters;     /* Lloyd iterations per 2-means split (10) */
+    int correction;       /* 0 naive, 1 batch sorting, 2 sorting + history (default), 3 best-of-worst */
+    int history_iters;    /* K of Algorithm 2 (1) */
+    int t_max;            /* history slots per walker, 1..NS_MAX_HISTORY (64) */
+    int e_max;            /* step-out expansions per side (64) */
+    int s_max;            /* shrink draws per slice step (128) */
+    double width;         /* initial bracket width along the direction (1.0) */
+    long long max_iter;   /* iterations before NS_ERR_BUDGET (1000000) */
+    long long dead_cap;   /* dead-point capacity per run; 0 = 400 * N + 4 * m */
+    int chunk_iters;      /* iterations per persistent launch (1000) */
+    int precision;        /* MLP only: 0 FP32, 1 BF16 with FP32 re-evaluation */
+    double reeval_margin; /* MLP only: re-evaluate in FP32 when |logL - threshold| < margin */
+} ns_options;
+
+/* One run of a batch. */
+typedef struct {
+    const ns_likelihood* lik;
+    const double* lo;     /* [d] prior box, lo < hi */
+    const double* hi;     /* [d] */
+    int d;                /* 1..NS_MAX_DIM */
+    int n_live;           /* N, 2..NS_MAX_LIVE */
+    int m;                /* batch size, 1 <= m <= N/2, m <= NS_MAX_BATCH */
+    int n_slice_steps;    /* slice steps per replacement (5 d in the paper, section 4) */
+    double stop_frac;     /* stop when L_max X_k < stop_frac Z, 0 < stop_frac < 1 */
+    uint64_t seed;        /* Philox key */
+} ns_problem;
+
+typedef struct ns_handle ns_handle;
+
+typedef struct {
+    double log_z;         /* log evidence (dead points + final live tail) */
+    double log_z_err;     /* sqrt(H / N) (Skilling 2006) */
+    double info_h;        /* information H in nats */
+    long long n_dead;     /* samples returned: dead points then the final live points */
+    long long n_evals;    /* likelihood evaluations, initial draws included */
+    long long n_iter;     /* iterations of the batched loop */
+    long long n_relaxed;  /* points replaced by Algorithm 2 */
+    long long n_reeval;   /* FP32 re-evaluations (MLP precision 1) */
+    long long n_capped;   /* walker steps that hit the step-out or shrink cap */
+    int status;           /* ns_status of this run */
+    int d;
+    /* samples: the dead points in death order (ascending logL), then the
+     * final live points in slot order */
+    const float* dead_x;     /* [n_dead*d] host, owned by the handle */
+    const float* dead_logl;  /* [n_dead]   host, owned by the handle */
+    const double* dead_logw; /* [n_dead]   host, owned by the handle: log weight (prior mass times L) */
+} ns_result_t;
+
+/* ---- whole runs ------------------------------------------------------- */
+
+/* Fill `opt` with the defaults listed above. */
+ns_status ns_default_options(ns_options* opt);
+
+/* One run.  Validates every argument (NS_ERR_ARG, nothing allocated, on the
+ * first bad one), copies the likelihood to the device, allocates the run's
+ * device state (live set, dead buffer, history, cluster table) with
+ * cudaMalloc on the current device, and returns a handle.  `opt` NULL means
+ * defaults. */
+ns_status ns_create(const ns_likelihood* lik, const double* lo, const double* hi, int d,
+                    int n_live, int m, int n_slice_steps, double stop_frac, uint64_t seed,
+                    const ns_options* opt, ns_handle** out);
+
+/* Several independent runs (any mix of d, N, m and likelihood) sampled
+ * together: one persistent thread block per run. */
+ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* opt,
+                          ns_handle** out);
+
+/* Runs every run of the handle to its stopping rule (or budget), queued on
+ * `stream`, and waits for it.  Per-chunk host/device traffic is one status
+ * word per run. */
+ns_status ns_run(ns_handle* h, void* stream);
+
+/* Returns every run of the handle to its initial state (same seeds) so that
+ * ns_run can be repeated on the allocated memory; asynchronous on `stream`. */
+ns_status ns_reset(ns_handle* h, void* stream);
+
+/* Result of run `run` (0-based).  Copies that run's samples to host memory
+ * owned by the handle on first call; pointers stay valid until ns_destroy. */
+ns_status ns_result(ns_handle* h, int run, ns_result_t* out);
+
+/* The scalars of ns_result (log Z, error, H, counts, status) without
+ * copying any sample to the host; the three sample pointers are NULL. */
+ns_status ns_summary(const ns_handle* h, int run, ns_result_t* out);
+
+/* Tracing: SM cycles spent by run `run` in each step of its iterations,
+ * accumulated over all its iterations since creation or ns_reset, as seen
+ * by thread 0 of its block between barriers.  out[0..5] = clustering,
+ * selection, slice walkers, Algorithms 1-2, live/dead update, evidence and
+ * stop test; out[6..7] = 0.  Valid after ns_run. */
+ns_status ns_phase_cycles(const ns_handle* h, int run, long long* out);
+
+/* Number of runs in the handle, or -1 for NULL. */
+int ns_n_runs(const ns_handle* h);
+
+/* Device time of the last ns_run in milliseconds (CUDA events). */
+ns_status ns_last_run_ms(const ns_handle* h, double* ms);
+
+/* Counters of the last ns_run (and of ns_create / ns_result for the byte
+ * counts): run_ms = device time of the whole call; kernel_ms = summed
+ * device time of the run-kernel launches (CUDA events around each launch
+ * group, on the run's stream); launches = run-kernel launches; h2d_bytes =
+ * bytes copied host->device by ns_create; d2h_bytes = bytes copied
+ * device->host by the last ns_run plus every ns_result since. */
+typedef struct {
+    double run_ms;
+    double kernel_ms;
+    long long launches;
+    long long h2d_bytes;
+    long long d2h_bytes;
+} ns_stats;
+ns_status ns_get_stats(const ns_handle* h, ns_stats* out);
+
+/* Last error message of the handle (or of the library if h is NULL). */
+const char* ns_last_error(const ns_handle* h);
+
+/* Frees every device and host resource of the handle.  NULL is ignored. */
+void ns_destroy(ns_handle* h);
+
+/* ---- step-level calls (device buffers, asynchronous, no allocation) ----
+ * These run the same device code as ns_run, one step at a time, on caller
+ * buffers.  Layouts: live_x is structure-of-arrays [d][n_pad] (n_pad >= N);
+ * everything else is dense row-major as written. */
+
+/* Raw generator: out[4i..4i+3] = Philox4x32-10(ctr[4i..4i+3], key). */
+ns_status ns_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, int n,
+                           uint32_t* out, void* stream);
+
+/* FP32 log-likelihood of n points x [n][d] (device) -> logl [n] (device). */
+ns_status ns_loglike(const ns_likelihood* lik, const double* lo, const double* hi, int d,
+                     int n, const float* x, float* logl, void* stream);
+
+/* a1-a2 (Algorithm 1 "sorted", S_W, "RNG.choose"): for each of n_runs runs
+ * with N live log-likelihoods logl [n_runs][N] (device), the m lowest by
+ * (logL, slot) in ascending order -> worst [n_runs][m] (device), their
+ * values -> W [n_runs][m], and each walker's start slot, drawn uniformly from
+ * the N - m survivors in ascending slot order with stream
+ * (t, walker, NS_PURPOSE_SEED) -> seed_slot [n_runs][m].  seeds [n_runs]
+ * (host) are the runs' Philox seeds. */
+ns_status ns_select_worst(int n_runs, int N, int m, const float* logl, const uint64_t* seeds,
+                          uint32_t t, int* worst, float* W, int* seed_slot, void* stream);
+
+/* a4-a7 (section 2.2 and 3.1): one run's m walkers, each n_steps slice
+ * steps from live point seed_slot[i] with direction chol[cid[seed]] z/|z|
+ * (chol: [n_nodes][d][d] row-major lower, device FP32), expansion against
+ * W[0] and shrinkage against W[i] (W[m-1] for both under correction 3).
+ * Outputs (device): new_x [m][d], new_l [m], the last step's shrink history
+ * hist_l [m][t_max], hist_x [m][t_max][d], hist_len [m], evals [m] and
+ * flags [m] (bit0 step-out cap, bit1 shrink cap). */
+ns_status ns_slice_replace(const ns_likelihood* lik, const double* lo, const double* hi, int d,
+                           int N, int n_pad, int m, int n_steps, const ns_options* opt,
+                           uint64_t seed, uint32_t t, const float* live_x, const float* live_l,
+                           const int* seed_slot, const float* W, const float* chol, const int* cid,
+                           float* new_x, float* new_l, float* hist_l, float* hist_x, int* hist_len,
+                           long long* evals, int* flags, void* stream);
+
+/* a8-a9 (Algorithms 1 and 2): 2m candidates -- the removed points W [m]
+ * (candidates 0..m-1) and the new points new_l [m] of walkers 0..m-1
+ * (candidates m..2m-1, parent threshold W[i]) -- sorted by (logL,
+ * candidate); the m lowest die, the m highest live; then up to K history
+ * iterations.  Outputs (device, ascending): acc_* [m] and rej_* [m] with the
+ * candidate index (src), history slot used (hpos, -1 none), logL and parent
+ * threshold (P, -1 for removed points); n_relaxed [1]. */
+ns_status ns_batch_correct(int m, int K, int correction, const float* W, const float* new_l,
+                           const float* hist_l, const int* hist_len, int t_max,
+                           int* acc_src, int* acc_hpos, float* acc_l, float* acc_P,
+                           int* rej_src, int* rej_hpos, float* rej_l, float* rej_P,
+                           int* n_relaxed, void* stream);
+
+/* a11 (eq. 1.1 as a sum): FP64 evidence update with n dead points of
+ * ascending logL dead_l [n] (device) for N live points.  state [3] (device,
+ * FP64) holds (log Z, H, k) and is updated in place; logw [n] (device)
+ * receives each point's log weight.  live = 1 treats the points as the final
+ * live tail (each gets X_k / N) instead of dead points. */
+ns_status ns_evidence_update(int N, int n, const float* dead_l, double* state, double* logw,
+                             int live, void* stream);
+
+/* a3 (section 2.1): cluster tree of one live set live_x [d][n_pad] (device)
+ * at iteration t: node centres [n_nodes][d], Cholesky factors chol
+ * [n_nodes][d][d] (FP32) and chol64 (FP64), log volumes [n_nodes],
+ * counts [n_nodes], split flags [n_nodes], accepted-leaf mask [n_nodes]
+ * and each point's leaf cid [N] (all device).  n_nodes = 2^(depth+1) - 1. */
+ns_status ns_cluster(int N, int n_pad, int d, const float* live_x, const ns_options* opt,
+                     uint64_t seed, uint32_t t, float* centres, float* chol, double* chol64,
+                     float* logvol, int* count, int* split, int* mask, int* cid, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* NS_GB300_H */

@@ -1,0 +1,996 @@
+// ns_device.cuh -- device building blocks of the batched nested sampler
+// (arXiv 2608.28514) for sm_103a.  Every step of one iteration is a
+// __device__ function operating on one run with one thread block; the
+// persistent run kernel chains them, and the step-level kernels call them one
+// at a time on caller buffers, so both paths execute the same code.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+#include <math_constants.h>
+
+namespace nsd {
+
+constexpr int kMaxDim = 32;
+constexpr int kMaxModes = 8;
+constexpr int kMaxDepth = 3;
+constexpr int kMaxNodes = 15;
+constexpr int kMaxHistory = 64;
+constexpr uint32_t kPurposeSeed = 0x10000u;
+constexpr uint32_t kPurposeKmeans = 0x20000u;
+constexpr uint32_t kTInit = 0xFFFFFFFFu;
+constexpr unsigned kFull = 0xFFFFFFFFu;
+
+enum LikKind { kIso = 0, kCorr = 1, kRosen = 2, kMix = 3, kMlp = 4 };
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64 multiplications, key bumped by the Weyl constants each round.
+// ---------------------------------------------------------------------------
+struct U4 {
+  uint32_t x, y, z, w;
+};
+
+__device__ __forceinline__ U4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                     uint32_t k0, uint32_t k1) {
+#pragma unroll
+  for (int r = 0; r < 10; ++r) {
+    const uint32_t hi0 = __umulhi(0xD2511F53u, c0), lo0 = 0xD2511F53u * c0;
+    const uint32_t hi1 = __umulhi(0xCD9E8D57u, c2), lo1 = 0xCD9E8D57u * c2;
+    const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+    c0 = n0;
+    c1 = lo1;
+    c2 = n2;
+    c3 = lo0;
+    k0 += 0x9E3779B9u;
+    k1 += 0xBB67AE85u;
+  }
+  return U4{c0, c1, c2, c3};
+}
+
+// Draw n of stream (t, walker, purpose) = word n%4 of block (n/4, purpose,
+// walker, t); the last block is cached.
+struct Stream {
+  uint32_t k0, k1, t, walker, purpose, n, blk;
+  uint32_t c0, c1, c2, c3;
+  __device__ __forceinline__ void init(uint32_t key0, uint32_t key1, uint32_t tt, uint32_t w,
+                                       uint32_t p) {
+    k0 = key0;
+    k1 = key1;
+    t = tt;
+    walker = w;
+    purpose = p;
+    n = 0;
+    blk = 0xFFFFFFFFu;
+  }
+  __device__ __forceinline__ uint32_t next() {
+    const uint32_t b = n >> 2;
+    if (b != blk) {
+      const U4 r = philox(b, purpose, walker, t, k0, k1);
+      c0 = r.x;
+      c1 = r.y;
+      c2 = r.z;
+      c3 = r.w;
+      blk = b;
+    }
+    const uint32_t q = n & 3u;
+    ++n;
+    return q == 0 ? c0 : (q == 1 ? c1 : (q == 2 ? c2 : c3));
+  }
+};
+
+__device__ __forceinline__ uint32_t draw_at(uint32_t k0, uint32_t k1, uint32_t t, uint32_t w,
+                                            uint32_t purpose, uint32_t n) {
+  const U4 r = philox(n >> 2, purpose, w, t, k0, k1);
+  const uint32_t q = n & 3u;
+  return q == 0 ? r.x : (q == 1 ? r.y : (q == 2 ? r.z : r.w));
+}
+
+// 24-bit uniforms, exact in FP32.
+__device__ __forceinline__ float u24(uint32_t w) { return (float)(w >> 8) * 5.9604644775390625e-8f; }
+__device__ __forceinline__ float u24_open0(uint32_t w) {
+  return (float)((w >> 8) + 1u) * 5.9604644775390625e-8f;
+}
+// Uniform integer in [0, n).
+__device__ __forceinline__ int u_index(uint32_t w, int n) { return (int)__umulhi(w, (uint32_t)n); }
+
+// ---------------------------------------------------------------------------
+// Likelihoods (FP32).  theta_i = lo_i + span_i * u_i; constants folded so
+// that each coordinate costs one FMA: c_i = lo_i - mean_i (Gaussians),
+// cm_ki = lo_i - centre_ki (mixture).
+// ---------------------------------------------------------------------------
+struct LikParams {
+  int kind, d, n_modes, pad0;
+  float inv2s2;   // 1 / (2 sigma^2)
+  float a, b;     // Rosenbrock
+  float log_k;    // log n_modes
+  float lo[kMaxDim];
+  float span[kMaxDim];
+  float c[kMaxDim];
+  float Lp[kMaxDim * kMaxDim];     // [i*d + j], lower, inverse covariance = L L^T
+  float cm[kMaxModes * kMaxDim];   // [k*d + i]
+};
+
+// logL at u = x + tp * v (u computed per coordinate with one FMA).
+template <int DMAX>
+__device__ __forceinline__ float loglike(const LikParams& P, const float (&x)[DMAX],
+                                         const float (&v)[DMAX], float tp, int d) {
+  float ll;
+  switch (P.kind) {
+    case kIso: {
+      float s = 0.f;
+#pragma unroll
+      for (int i = 0; i < DMAX; ++i)
+        if (i < d) {
+          const float y = fmaf(P.span[i], fmaf(tp, v[i], x[i]), P.c[i]);
+          s = fmaf(y, y, s);
+        }
+      ll = -s * P.inv2s2;
+      break;
+    }
+    case kCorr: {
+      float y[DMAX];
+#pragma unroll
+      for (int i = 0; i < DMAX; ++i) y[i] = (i < d) ? fmaf(P.span[i], fmaf(tp, v[i], x[i]), P.c[i]) : 0.f;
+      float s = 0.f;
+#pragma unroll
+      for (int j = 0; j < DMAX; ++j)
+        if (j < d) {
+          float z = 0.f;
+#pragma unroll
+          for (int i = j; i < DMAX; ++i)
+            if (i < d) z = fmaf(P.Lp[i * d + j], y[i], z);
+          s = fmaf(z, z, s);
+        }
+      ll = -0.5f * s;
+      break;
+    }
+    case kRosen: {
+      float s = 0.f;
+      float th_prev = 0.f;
+#pragma unroll
+      for (int i = 0; i < DMAX; ++i)
+        if (i < d) {
+          const float th = fmaf(P.span[i], fmaf(tp, v[i], x[i]), P.lo[i]);
+          if (i > 0) {
+            const float p = P.a - th_prev;
+            const float q = fmaf(-th_prev, th_prev, th);
+            s = fmaf(p, p, s);
+            s = fmaf(P.b * q, q, s);
+          }
+          th_prev = th;
+        }
+      ll = -s;
+      break;
+    }
+    case kMix: {
+      float u[DMAX];
+#pragma unroll
+      for (int i = 0; i < DMAX; ++i) u[i] = (i < d) ? fmaf(tp, v[i], x[i]) : 0.f;
+      float e[kMaxModes];
+      float emax = -CUDART_INF_F;
+#pragma unroll
+      for (int k = 0; k < kMaxModes; ++k) {
+        e[k] = -CUDART_INF_F;
+        if (k < P.n_modes) {
+          float s = 0.f;
+#pragma unroll
+          for (int i = 0; i < DMAX; ++i)
+            if (i < d) {
+              const float y = fmaf(P.span[i], u[i], P.cm[k * d + i]);
+              s = fmaf(y, y, s);
+            }
+          e[k] = -s * P.inv2s2;
+          emax = fmaxf(emax, e[k]);
+        }
+      }
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < kMaxModes; ++k)
+        if (k < P.n_modes) acc += expf(e[k] - emax);
+      ll = emax + logf(acc) - P.log_k;
+      break;
+    }
+    default:
+      ll = -CUDART_INF_F;
+  }
+  return (ll != ll) ? -CUDART_INF_F : ll;
+}
+
+// ---------------------------------------------------------------------------
+// Block helpers (blockDim.x a multiple of 32, <= 1024)
+// ---------------------------------------------------------------------------
+struct BlockScratch {
+  int iw[33];
+  double dw[33];
+  float fw[33];
+  long long lw[33];
+};
+
+// Exclusive prefix sum of v over threads in thread order; *total = sum.
+__device__ __forceinline__ int block_exclusive_scan(int v, BlockScratch& S, int* total) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  int x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const int y = __shfl_up_sync(kFull, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) S.iw[wid] = x;
+  __syncthreads();
+  if (wid == 0) {
+    int w = lane < nw ? S.iw[lane] : 0;
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const int y = __shfl_up_sync(kFull, w, o);
+      if (lane >= o) w += y;
+    }
+    if (lane < nw) S.iw[lane] = w;  // inclusive warp totals
+  }
+  __syncthreads();
+  const int base = wid > 0 ? S.iw[wid - 1] : 0;
+  const int tot = S.iw[nw - 1];
+  __syncthreads();
+  *total = tot;
+  return base + x - v;
+}
+
+__device__ __forceinline__ double block_sum_d(double v, BlockScratch& S) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  if (lane == 0) S.dw[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double w = lane < nw ? S.dw[lane] : 0.0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(kFull, w, o);
+    if (lane == 0) S.dw[32] = w;
+  }
+  __syncthreads();
+  const double r = S.dw[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ double block_max_d(double v, BlockScratch& S) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(kFull, v, o));
+  if (lane == 0) S.dw[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double w = lane < nw ? S.dw[lane] : -CUDART_INF;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w = fmax(w, __shfl_down_sync(kFull, w, o));
+    if (lane == 0) S.dw[32] = w;
+  }
+  __syncthreads();
+  const double r = S.dw[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ float block_max_f(float v, BlockScratch& S) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmaxf(v, __shfl_down_sync(kFull, v, o));
+  if (lane == 0) S.fw[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    float w = lane < nw ? S.fw[lane] : -CUDART_INF_F;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w = fmaxf(w, __shfl_down_sync(kFull, w, o));
+    if (lane == 0) S.fw[32] = w;
+  }
+  __syncthreads();
+  const float r = S.fw[32];
+  __syncthreads();
+  return r;
+}
+
+__device__ __forceinline__ long long block_sum_ll(long long v, BlockScratch& S) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(kFull, v, o);
+  if (lane == 0) S.lw[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    long long w = lane < nw ? S.lw[lane] : 0;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) w += __shfl_down_sync(kFull, w, o);
+    if (lane == 0) S.lw[32] = w;
+  }
+  __syncthreads();
+  const long long r = S.lw[32];
+  __syncthreads();
+  return r;
+}
+
+// ---------------------------------------------------------------------------
+// a1-a2: the m worst live points (radix select on an order-preserving key,
+// ties by slot) and the walkers' start slots.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t order_key(float f) {
+  const uint32_t b = __float_as_uint(f);
+  return (b & 0x80000000u) ? ~b : (b | 0x80000000u);
+}
+
+struct SelectScratch {
+  unsigned hist[256];
+  int found[4];
+};
+
+// sel_slot/sel_key: smem [m] scratch.  Outputs (any address space): worst[m]
+// ascending by (logL, slot), W[m], seed_slot[m].
+inline __device__ void select_worst(const float* __restrict__ logl, int N, int m, uint32_t k0, uint32_t k1,
+                             uint32_t t, int* sel_slot, uint32_t* sel_key, int* worst, float* W,
+                             int* seed_slot, SelectScratch& X, BlockScratch& S) {
+  const int tid = threadIdx.x, B = blockDim.x;
+  uint32_t prefix = 0, pmask = 0;
+  int k = m;  // rank (1-based) still to find among keys matching the prefix
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 24 - 8 * pass;
+    for (int i = tid; i < 256; i += B) X.hist[i] = 0;
+    __syncthreads();
+    for (int j = tid; j < N; j += B) {
+      const uint32_t key = order_key(logl[j]);
+      if ((key & pmask) == prefix) atomicAdd(&X.hist[(key >> shift) & 255u], 1u);
+    }
+    __syncthreads();
+    if (tid < 32) {
+      unsigned c[8];
+      unsigned loc = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        c[q] = X.hist[tid * 8 + q];
+        loc += c[q];
+      }
+      unsigned incl = loc;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const unsigned y = __shfl_up_sync(kFull, incl, o);
+        if (tid >= o) incl += y;
+      }
+      const unsigned excl = incl - loc;
+      // the lane whose range holds the k-th key
+      if (excl < (unsigned)k && incl >= (unsigned)k) {
+        unsigned run = excl;
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+          if (run < (unsigned)k && run + c[q] >= (unsigned)k) {
+            X.found[0] = tid * 8 + q;
+            X.found[1] = (int)run;
+          }
+          run += c[q];
+        }
+      }
+    }
+    __syncthreads();
+    const int digit = X.found[0];
+    k -= X.found[1];
+    prefix |= (uint32_t)digit << shift;
+    pmask |= 255u << shift;
+    __syncthreads();
+  }
+  const uint32_t T = prefix;  // key of the m-th smallest; k of the equal keys are taken
+  // ordered compaction over slot chunks
+  const int C = (N + B - 1) / B;
+  const int j0 = min(N, tid * C), j1 = min(N, j0 + C);
+  int n_eq = 0;
+  for (int j = j0; j < j1; ++j) n_eq += (order_key(logl[j]) == T);
+  int tot;
+  int eq_base = block_exclusive_scan(n_eq, S, &tot);
+  int n_sel = 0;
+  {
+    int e = eq_base;
+    for (int j = j0; j < j1; ++j) {
+      const uint32_t key = order_key(logl[j]);
+      if (key < T || (key == T && e < k)) ++n_sel;
+      if (key == T) ++e;
+    }
+  }
+  int sel_base = block_exclusive_scan(n_sel, S, &tot);
+  {
+    int e = eq_base, p = sel_base;
+    for (int j = j0; j < j1; ++j) {
+      const uint32_t key = order_key(logl[j]);
+      if (key < T || (key == T && e < k)) {
+        sel_slot[p] = j;
+        sel_key[p] = key;
+        ++p;
+      }
+      if (key == T) ++e;
+    }
+  }
+  __syncthreads();
+  // sort the m selected by (key, slot): rank by counting
+  for (int e = tid; e < m; e += B) {
+    const uint32_t ke = sel_key[e];
+    const int se = sel_slot[e];
+    int r = 0;
+    for (int q = 0; q < m; ++q) {
+      const uint32_t kq = sel_key[q];
+      r += (kq < ke) || (kq == ke && sel_slot[q] < se);
+    }
+    worst[r] = se;
+    W[r] = logl[se];
+  }
+  // start slots: the idx-th survivor in ascending slot order; sel_slot is in
+  // ascending slot order, so skip every selected slot at or below the index.
+  for (int i = tid; i < m; i += B) {
+    int s = u_index(draw_at(k0, k1, t, (uint32_t)i, kPurposeSeed, 0), N - m);
+    for (int q = 0; q < m; ++q) {
+      if (sel_slot[q] <= s) ++s;
+      else break;
+    }
+    seed_slot[i] = s;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// a4-a7: one walker per thread.  A round evaluates one candidate per active
+// walker; the walker's state machine moves through expansion to the left,
+// expansion to the right, and shrinkage, n_steps times (section 2.2), with
+// the expansion threshold thr_out (= W[0]) and the acceptance threshold
+// thr_in (= W[i]) of section 3.1.  All lanes of a warp must call it.
+// ---------------------------------------------------------------------------
+struct SliceCfg {
+  int d, n_steps, e_max, s_max, t_max;
+  float width;
+  uint32_t k0, k1, t;
+};
+
+template <int DMAX>
+__device__ __forceinline__ void new_direction(const SliceCfg& S, const float* __restrict__ chol,
+                                              Stream& st, float (&v)[DMAX], float& a, float& b) {
+  const int d = S.d;
+  float z[DMAX];
+#pragma unroll
+  for (int p = 0; p < (DMAX + 1) / 2; ++p)
+    if (2 * p < d) {
+      const float u1 = u24_open0(st.next());
+      const float u2 = u24(st.next());
+      const float rho = sqrtf(-2.f * logf(u1));
+      float sn, cs;
+      sincospif(2.f * u2, &sn, &cs);
+      z[2 * p] = rho * cs;
+      if (2 * p + 1 < DMAX) z[2 * p + 1] = rho * sn;
+    }
+  float nz = 0.f;
+#pragma unroll
+  for (int i = 0; i < DMAX; ++i)
+    if (i < d) nz = fmaf(z[i], z[i], nz);
+  float inv = 1.f;
+  if (nz > 0.f) {
+    inv = rsqrtf(nz);
+  } else {
+#pragma unroll
+    for (int i = 0; i < DMAX; ++i) z[i] = (i == 0) ? 1.f : 0.f;
+  }
+#pragma unroll
+  for (int i = 0; i < DMAX; ++i) z[i] *= inv;
+#pragma unroll
+  for (int i = 0; i < DMAX; ++i) {
+    float acc = 0.f;
+    if (i < d) {
+#pragma unroll
+      for (int k = 0; k <= i; ++k) acc = fmaf(chol[i * d + k], z[k], acc);
+    }
+    v[i] = acc;
+  }
+  const float r = u24(st.next());
+  a = -r * S.width;
+  b = (1.f - r) * S.width;
+}
+
+struct WalkerOut {
+  float* new_x;      // [d]
+  float* new_l;      // [1]
+  float* hist_l;     // [t_max]
+  float* hist_x;     // [t_max][d]
+  int* hist_len;     // [1]
+};
+
+template <int DMAX>
+inline __device__ void slice_walker(const LikParams& P, const SliceCfg& S, int walker, bool active,
+                             const float* __restrict__ x0, int x0_stride, float l0,
+                             const float* __restrict__ chol, float thr_out, float thr_in,
+                             const WalkerOut& O, long long& evals_out, int& flags_out) {
+  const int d = S.d;
+  float x[DMAX], v[DMAX];
+  float l = l0;
+#pragma unroll
+  for (int i = 0; i < DMAX; ++i) {
+    x[i] = (active && i < d) ? x0[(size_t)i * x0_stride] : 0.f;
+    v[i] = 0.f;
+  }
+  const bool was_active = active;
+  int step = 0, phase = 0, nexp = 0, nsh = 0, hlen = 0, flags = 0;
+  long long evals = 0;
+  float a = 0.f, b = 0.f;
+  Stream st;
+  st.init(S.k0, S.k1, S.t, (uint32_t)walker, 0u);
+  if (S.n_steps <= 0) active = false;
+  if (active) new_direction<DMAX>(S, chol, st, v, a, b);
+  while (__any_sync(kFull, active)) {
+    if (active) {
+      float tp;
+      if (phase == 2) {
+        const float u = u24(st.next());
+        tp = fmaf(u, b - a, a);
+      } else {
+        tp = (phase == 0) ? a : b;
+      }
+      bool in = true;
+#pragma unroll
+      for (int i = 0; i < DMAX; ++i)
+        if (i < d) {
+          const float ui = fmaf(tp, v[i], x[i]);
+          in = in && (ui >= 0.f) && (ui <= 1.f);
+        }
+      float lp = -CUDART_INF_F;
+      if (in) {
+        lp = loglike<DMAX>(P, x, v, tp, d);
+        ++evals;
+      }
+      if (phase < 2) {
+        const bool up = in && (lp > thr_out);
+        if (up && nexp < S.e_max) {
+          if (phase == 0) a -= S.width;
+          else b += S.width;
+          ++nexp;
+        } else {
+          if (up) flags |= 1;
+          ++phase;
+          nexp = 0;
+          nsh = 0;
+        }
+      } else {
+        const bool last = (step == S.n_steps - 1);
+        const bool ok = in && (lp > thr_in);
+        if (last) {
+          int slot = -1;
+          if (nsh < S.t_max - 1) {
+            slot = nsh;
+            hlen = nsh + 1;
+          } else if (ok) {
+            slot = S.t_max - 1;
+            hlen = S.t_max;
+          }
+          if (slot >= 0) {
+            O.hist_l[slot] = lp;
+#pragma unroll
+            for (int i = 0; i < DMAX; ++i)
+              if (i < d) O.hist_x[(size_t)slot * d + i] = fmaf(tp, v[i], x[i]);
+          }
+        }
+        bool advance = false;
+        if (ok) {
+#pragma unroll
+          for (int i = 0; i < DMAX; ++i) x[i] = fmaf(tp, v[i], x[i]);
+          l = lp;
+          advance = true;
+        } else {
+          if (tp < 0.f) a = tp;
+          else b = tp;
+          ++nsh;
+          if (nsh >= S.s_max) {
+            flags |= 2;
+            advance = true;
+          }
+        }
+        if (advance) {
+          ++step;
+          if (step < S.n_steps) {
+            st.init(S.k0, S.k1, S.t, (uint32_t)walker, (uint32_t)step);
+            new_direction<DMAX>(S, chol, st, v, a, b);
+            phase = 0;
+            nexp = 0;
+            nsh = 0;
+          } else {
+            active = false;
+          }
+        }
+      }
+    }
+  }
+  evals_out = evals;
+  flags_out = flags;
+  if (was_active) {
+#pragma unroll
+    for (int i = 0; i < DMAX; ++i)
+      if (i < d) O.new_x[i] = x[i];
+    O.new_l[0] = l;
+    O.hist_len[0] = hlen;
+  }
+}
+
+// ---------------------------------------------------------------------------
+// a8-a9: Algorithm 1 (batch sorting) and Algorithm 2 (history correction).
+// Candidates 0..m-1: removed points W; m..2m-1: walkers' new points.
+// ---------------------------------------------------------------------------
+struct Cand {
+  float* l;
+  float* P;
+  int* src;
+  int* H;
+  int* hp;
+};
+
+// sort `in` (2m entries) by (l, src) into `out` (rank by counting)
+__device__ __forceinline__ void cand_sort(const Cand& in, const Cand& out, int n) {
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const float le = in.l[e];
+    const int se = in.src[e];
+    int r = 0;
+    for (int q = 0; q < n; ++q) {
+      const float lq = in.l[q];
+      r += (lq < le) || (lq == le && in.src[q] < se);
+    }
+    out.l[r] = le;
+    out.P[r] = in.P[e];
+    out.src[r] = se;
+    out.H[r] = in.H[e];
+    out.hp[r] = in.hp[e];
+  }
+  __syncthreads();
+}
+
+// Ordered compaction of predicate over [0, n): out[rank] = index.
+template <class Pred>
+__device__ __forceinline__ int block_compact(int n, Pred pred, int* out, BlockScratch& S) {
+  const int B = blockDim.x, tid = threadIdx.x;
+  const int C = (n + B - 1) / B;
+  const int j0 = min(n, tid * C), j1 = min(n, j0 + C);
+  int cnt = 0;
+  for (int j = j0; j < j1; ++j) cnt += pred(j) ? 1 : 0;
+  int tot;
+  int base = block_exclusive_scan(cnt, S, &tot);
+  for (int j = j0; j < j1; ++j)
+    if (pred(j)) out[base++] = j;
+  __syncthreads();
+  return tot;
+}
+
+// A, Bf: two candidate buffers of 2m entries each (smem).  On return the
+// sorted candidates are in A: rejected A[0:m], accepted A[m:2m].
+// list_f, list_i: smem int [m]; vals: smem float [m].  Returns n_relaxed.
+inline __device__ int batch_correct(int m, int K, int correction, const float* __restrict__ W,
+                             const float* __restrict__ new_l, const float* __restrict__ hist_l,
+                             const int* __restrict__ hist_len, int t_max, const Cand& A,
+                             const Cand& Bf, int* list_f, float* vals, int* counter,
+                             BlockScratch& S) {
+  const int tid = threadIdx.x, B = blockDim.x;
+  for (int i = tid; i < m; i += B) {
+    A.l[i] = W[i];
+    A.P[i] = -1.f;
+    A.src[i] = i;
+    A.H[i] = -1;
+    A.hp[i] = -1;
+    A.l[m + i] = new_l[i];
+    A.P[m + i] = W[i];
+    A.src[m + i] = m + i;
+    A.H[m + i] = i;
+    A.hp[m + i] = -1;
+  }
+  if (tid == 0) *counter = 0;
+  __syncthreads();
+  if (correction == 0 || correction == 3) {
+    // the removed points die (already ascending), the new points go live
+    Cand a_in{A.l + m, A.P + m, A.src + m, A.H + m, A.hp + m};
+    Cand a_out{Bf.l, Bf.P, Bf.src, Bf.H, Bf.hp};
+    cand_sort(a_in, a_out, m);
+    for (int i = tid; i < m; i += B) {
+      A.l[m + i] = Bf.l[i];
+      A.P[m + i] = Bf.P[i];
+      A.src[m + i] = Bf.src[i];
+      A.H[m + i] = Bf.H[i];
+      A.hp[m + i] = Bf.hp[i];
+    }
+    __syncthreads();
+    return 0;
+  }
+  cand_sort(A, Bf, 2 * m);  // Alg1.sort: Bf sorted
+  const Cand* cur = &Bf;
+  const Cand* oth = &A;
+  if (correction == 2) {
+    for (int k = 1; k <= K; ++k) {
+      const Cand C = *cur;
+      const float amin = C.l[m];
+      const int nF = block_compact(
+          m, [&](int j) { return C.H[m + j] >= 0 && C.P[m + j] >= amin; }, list_f, S);
+      if (nF == 0) break;
+      // instant deaths: rejected new points, ascending
+      int* list_i = list_f + m;
+      const int nI = block_compact(m, [&](int j) { return C.H[j] >= 0; }, list_i, S);
+      const int np = min(nF, nI);
+      for (int i = tid; i < np; i += B) vals[i] = C.l[list_i[i]];
+      __syncthreads();
+      for (int i = tid; i < np; i += B) {
+        const int e = m + list_f[i];
+        const int w = C.H[e];
+        const float thr = vals[i];
+        const int hl = min(hist_len[w], t_max);
+        for (int h = 0; h < hl; ++h) {
+          const float hv = hist_l[(size_t)w * t_max + h];
+          if (hv > thr) {
+            C.l[e] = hv;
+            C.hp[e] = h;
+            C.P[e] = thr;
+            atomicAdd(counter, 1);
+            break;
+          }
+        }
+      }
+      __syncthreads();
+      cand_sort(*cur, *oth, 2 * m);
+      const Cand* tmp = cur;
+      cur = oth;
+      oth = tmp;
+    }
+  }
+  if (cur != &A) {
+    for (int i = tid; i < 2 * m; i += B) {
+      A.l[i] = cur->l[i];
+      A.P[i] = cur->P[i];
+      A.src[i] = cur->src[i];
+      A.H[i] = cur->H[i];
+      A.hp[i] = cur->hp[i];
+    }
+  }
+  __syncthreads();
+  const int rel = *counter;
+  __syncthreads();
+  return rel;
+}
+
+// ---------------------------------------------------------------------------
+// a11: FP64 evidence.  X_k = exp(-k/N); a dead point k has weight
+// L (X_{k-1} - X_k); the live tail shares X_K.  The batch of n points is
+// added at once with the invariant Z (H + log Z) = sum w L.
+// state: logz, info, k.  Returns per-point log weights in logw.
+// ---------------------------------------------------------------------------
+struct EvidState {
+  double logz, info;
+  long long k;
+};
+
+inline __device__ void evidence_add(EvidState& E, int N, int n, const float* __restrict__ l_in,
+                             double* logw_out, bool live, BlockScratch& S) {
+  const double Nd = (double)N;
+  const double cN = log(-expm1(-1.0 / Nd));
+  const int tid = threadIdx.x, B = blockDim.x;
+  const long long k0 = E.k;
+  double mx = E.logz;
+  for (int j = tid; j < n; j += B) {
+    const double l = (double)l_in[j];
+    const double lw = live ? l - (double)k0 / Nd - log(Nd) : l - (double)(k0 + j) / Nd + cN;
+    if (logw_out) logw_out[j] = lw;
+    mx = fmax(mx, lw);
+  }
+  mx = block_max_d(mx, S);
+  if (mx == -CUDART_INF) {
+    if (!live) E.k = k0 + n;
+    return;
+  }
+  double sw = 0.0, swl = 0.0;
+  for (int j = tid; j < n; j += B) {
+    const double l = (double)l_in[j];
+    const double lw = live ? l - (double)k0 / Nd - log(Nd) : l - (double)(k0 + j) / Nd + cN;
+    const double w = exp(lw - mx);
+    sw += w;
+    if (l > -CUDART_INF) swl += w * l;
+  }
+  sw = block_sum_d(sw, S);
+  swl = block_sum_d(swl, S);
+  if (tid == 0) {
+    double Bs = sw, As = swl;
+    if (E.logz > -CUDART_INF) {
+      const double w0 = exp(E.logz - mx);
+      Bs += w0;
+      As += w0 * (E.info + E.logz);
+    }
+    const double lz = mx + log(Bs);
+    S.dw[0] = lz;
+    S.dw[1] = As / Bs - lz;
+  }
+  __syncthreads();
+  E.logz = S.dw[0];
+  E.info = S.dw[1];
+  if (!live) E.k = k0 + n;
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// a3: clustering (section 2.1).  FP32 products accumulated per 64-point
+// tile, FP64 across tiles; FP64 regularised Cholesky.
+// ---------------------------------------------------------------------------
+constexpr int kTile = 64;
+
+// One warp: L = chol(A) for a d x d FP64 matrix (smem, row-major).  Returns
+// false (uniformly) if a pivot is not positive.
+inline __device__ bool warp_cholesky(int d, const double* A, double* L) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < d * d; i += 32) L[i] = 0.0;
+  __syncwarp();
+  for (int j = 0; j < d; ++j) {
+    double part = 0.0;
+    for (int k = lane; k < j; k += 32) part += L[j * d + k] * L[j * d + k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+    const double s = A[j * d + j] - part;
+    if (!(s > 0.0) || !isfinite(s)) return false;
+    const double ljj = sqrt(s);
+    if (lane > j && lane < d) {
+      double u = A[lane * d + j];
+      for (int k = 0; k < j; ++k) u -= L[lane * d + k] * L[j * d + k];
+      L[lane * d + j] = u / ljj;
+    }
+    if (lane == j) L[j * d + j] = ljj;
+    __syncwarp();
+  }
+  return true;
+}
+
+// Single-thread cyclic Jacobi (rare path: a covariance that is not
+// numerically positive definite).  A: d x d, destroyed; Q: eigenvectors in
+// columns; lam: eigenvalues.
+inline __device__ void jacobi_eigen_serial(int d, double* A, double* Q, double* lam) {
+  for (int i = 0; i < d * d; ++i) Q[i] = 0.0;
+  for (int i = 0; i < d; ++i) Q[i * d + i] = 1.0;
+  for (int sweep = 0; sweep < 100; ++sweep) {
+    double off = 0.0;
+    for (int p = 0; p < d; ++p)
+      for (int q = p + 1; q < d; ++q) off += A[p * d + q] * A[p * d + q];
+    if (off < 1e-300) break;
+    for (int p = 0; p < d; ++p)
+      for (int q = p + 1; q < d; ++q) {
+        const double apq = A[p * d + q];
+        if (apq == 0.0) continue;
+        const double th = (A[q * d + q] - A[p * d + p]) / (2.0 * apq);
+        const double tt = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
+        const double c = 1.0 / sqrt(tt * tt + 1.0), s = tt * c;
+        for (int k = 0; k < d; ++k) {
+          const double akp = A[k * d + p], akq = A[k * d + q];
+          A[k * d + p] = c * akp - s * akq;
+          A[k * d + q] = s * akp + c * akq;
+        }
+        for (int k = 0; k < d; ++k) {
+          const double apk = A[p * d + k], aqk = A[q * d + k];
+          A[p * d + k] = c * apk - s * aqk;
+          A[q * d + k] = s * apk + c * aqk;
+        }
+        for (int k = 0; k < d; ++k) {
+          const double qkp = Q[k * d + p], qkq = Q[k * d + q];
+          Q[k * d + p] = c * qkp - s * qkq;
+          Q[k * d + q] = s * qkp + c * qkq;
+        }
+      }
+  }
+  for (int i = 0; i < d; ++i) lam[i] = A[i * d + i];
+}
+
+// Regularised Cholesky of the covariance in C (smem FP64, d x d):
+// chol(C + delta I), delta = 1e-10 tr(C)/d; if that fails, eigenvalues are
+// clipped at 1e-10 lambda_max first (section 2.1).  Work: smem FP64 [3 d d + d].
+// Called by the whole block; the result lands in L (smem FP64).
+inline __device__ void reg_cholesky(int d, double* C, double* L, double* work, BlockScratch& S) {
+  const int tid = threadIdx.x;
+  double* A = work;
+  if (tid == 0) {
+    double tr = 0.0;
+    for (int i = 0; i < d; ++i) tr += C[i * d + i];
+    S.dw[0] = tr;
+  }
+  __syncthreads();
+  const double tr = S.dw[0];
+  __syncthreads();
+  if (!(tr > 0.0) || !isfinite(tr)) {
+    for (int i = tid; i < d * d; i += blockDim.x) L[i] = ((i / d) == (i % d)) ? 1e-6 : 0.0;
+    __syncthreads();
+    return;
+  }
+  const double delta = 1e-10 * tr / d;
+  for (int i = tid; i < d * d; i += blockDim.x) A[i] = C[i] + (((i / d) == (i % d)) ? delta : 0.0);
+  __syncthreads();
+  if (tid < 32) {
+    const bool ok = warp_cholesky(d, A, L);
+    if (tid == 0) S.iw[0] = ok ? 1 : 0;
+  }
+  __syncthreads();
+  const int ok = S.iw[0];
+  __syncthreads();
+  if (ok) return;
+  if (tid == 0) {
+    double* Q = work + d * d;
+    double* lam = work + 2 * d * d;
+    double* T = work + 2 * d * d + d;  // d*d
+    for (int i = 0; i < d * d; ++i) T[i] = C[i];
+    jacobi_eigen_serial(d, T, Q, lam);
+    double lmax = 0.0;
+    for (int i = 0; i < d; ++i) lmax = fmax(lmax, lam[i]);
+    for (int i = 0; i < d; ++i) lam[i] = fmax(lam[i], 1e-10 * lmax);
+    for (int i = 0; i < d; ++i)
+      for (int j = 0; j < d; ++j) {
+        double s = 0.0;
+        for (int k = 0; k < d; ++k) s += Q[i * d + k] * lam[k] * Q[j * d + k];
+        A[i * d + j] = s + (i == j ? delta : 0.0);
+      }
+  }
+  __syncthreads();
+  if (tid < 32) {
+    const bool ok2 = warp_cholesky(d, A, L);
+    if (tid == 0) S.iw[0] = ok2 ? 1 : 0;
+  }
+  __syncthreads();
+  if (!S.iw[0] && tid == 0) {
+    for (int i = 0; i < d * d; ++i) L[i] = 0.0;
+    for (int i = 0; i < d; ++i) L[i * d + i] = sqrt(A[i * d + i] > 0 ? A[i * d + i] : 1e-12);
+  }
+  __syncthreads();
+}
+
+// Mean and covariance (1/n) of the points j in [0, N) with member(j) true
+// (live_x [d][n_pad]).  tile: smem float [d][kTile]; acc: smem FP64
+// [d + d*d]; returns n.  Results: mean in acc[0:d], cov in acc[d:d+d*d].
+template <class Member>
+inline __device__ int node_moments(const float* __restrict__ live_x, int n_pad, int N, int d, Member member,
+                            float* tile, double* acc, BlockScratch& S) {
+  const int tid = threadIdx.x, B = blockDim.x;
+  const int ne = d * (d + 1) / 2;
+  for (int i = tid; i < d + d * d; i += B) acc[i] = 0.0;
+  __syncthreads();
+  int cnt = 0;
+  // pass 1: sums
+  for (int j0 = 0; j0 < N; j0 += kTile) {
+    for (int q = tid; q < d * kTile; q += B) {
+      const int i = q / kTile, jj = q % kTile, j = j0 + jj;
+      tile[q] = (j < N && member(j)) ? live_x[(size_t)i * n_pad + j] : 0.f;
+    }
+    if (tid < kTile) cnt += (j0 + tid < N && member(j0 + tid)) ? 1 : 0;
+    __syncthreads();
+    if (tid < d) {
+      float s = 0.f;
+      for (int jj = 0; jj < kTile; ++jj) s += tile[tid * kTile + jj];
+      acc[tid] += (double)s;
+    }
+    __syncthreads();
+  }
+  const int n = (int)block_sum_ll(cnt, S);
+  const double inv = n > 0 ? 1.0 / n : 0.0;
+  for (int i = tid; i < d; i += B) acc[i] *= inv;
+  __syncthreads();
+  // pass 2: centred products
+  for (int j0 = 0; j0 < N; j0 += kTile) {
+    for (int q = tid; q < d * kTile; q += B) {
+      const int i = q / kTile, jj = q % kTile, j = j0 + jj;
+      tile[q] = (j < N && member(j)) ? (float)((double)live_x[(size_t)i * n_pad + j] - acc[i]) : 0.f;
+    }
+    __syncthreads();
+    for (int e = tid; e < ne; e += B) {
+      int a = 0;
+      while ((a + 1) * (a + 2) / 2 <= e) ++a;
+      const int bcol = e - a * (a + 1) / 2;
+      float s = 0.f;
+      const float* ta = tile + a * kTile;
+      const float* tb = tile + bcol * kTile;
+      for (int jj = 0; jj < kTile; ++jj) s = fmaf(ta[jj], tb[jj], s);
+      acc[d + a * d + bcol] += (double)s;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < ne; e += B) {
+    int a = 0;
+    while ((a + 1) * (a + 2) / 2 <= e) ++a;
+    const int bcol = e - a * (a + 1) / 2;
+    const double v = acc[d + a * d + bcol] * inv;
+    acc[d + a * d + bcol] = v;
+    acc[d + bcol * d + a] = v;
+  }
+  __syncthreads();
+  return n;
+}
+
+}  // namespace nsd

@@ -1,0 +1,39 @@
+// ns_inst.cu -- instantiates the per-dimension kernels for one register
+// class (compiled once per class with -DNS_DMAX=4, 8, 16 or 32, so the four
+// classes build in parallel).
+#include "ns_run.cuh"
+
+#ifndef NS_DMAX
+#error "compile with -DNS_DMAX=<4|8|16|32>"
+#endif
+
+namespace nsd {
+
+#define NS_CAT2(a, b) a##b
+#define NS_CAT(a, b) NS_CAT2(a, b)
+
+cudaError_t NS_CAT(launch_run_, NS_DMAX)(const RunDesc* runs, const int* ids, int n, int block, size_t smem,
+                                         int chunk, cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_run<NS_DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_run<NS_DMAX><<<n, block, smem, s>>>(runs, ids, chunk);
+  return cudaGetLastError();
+}
+
+cudaError_t NS_CAT(launch_loglike_, NS_DMAX)(const LikParams& P, int n, const float* x, float* out,
+                                             cudaStream_t s) {
+  k_loglike<NS_DMAX><<<(n + 127) / 128, 128, 0, s>>>(P, n, x, out);
+  return cudaGetLastError();
+}
+
+cudaError_t NS_CAT(launch_slice_, NS_DMAX)(const LikParams& P, const SliceCfg& SC, int m, int n_pad,
+                                           int correction, const float* live_x, const float* live_l,
+                                           const int* seed_slot, const float* W, const float* chol, const int* cid,
+                                           float* new_x, float* new_l, float* hist_l, float* hist_x, int* hist_len,
+                                           long long* evals, int* flags, cudaStream_t s) {
+  k_slice<NS_DMAX><<<(m + 127) / 128, 128, 0, s>>>(P, SC, m, n_pad, correction, live_x, live_l, seed_slot, W, chol,
+                                                   cid, new_x, new_l, hist_l, hist_x, hist_len, evals, flags);
+  return cudaGetLastError();
+}
+
+}  // namespace nsd

@@ -1,0 +1,951 @@
+// ns_lib.cu -- kernels and C ABI of the GB300 batched nested sampler
+// (arXiv 2608.28514: slice-sampling replacement, section 2.2; batch sorting
+// and history correction, Algorithms 1-2 of section 3.1; clustering, section
+// 2.1; evidence, eq. 1.1).
+//
+// Execution model: one persistent thread block per run.  A launch advances
+// each of its runs by up to `chunk_iters` iterations (select -> slice
+// walkers -> Algorithms 1/2 -> live/dead update -> FP64 evidence -> stop
+// test) with no host involvement; the host reads one status word per run
+// between launches.  Walkers are threads of the run's block.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "../../include/ns_gb300.h"
+#include "ns_run.cuh"
+
+using namespace nsd;
+
+namespace {
+
+// ---------------------------------------------------------------------------
+// Step-level kernels (same device code, caller buffers)
+// ---------------------------------------------------------------------------
+__global__ void k_philox(const uint32_t* __restrict__ ctr, uint32_t k0, uint32_t k1, int n,
+                         uint32_t* __restrict__ out) {
+  const int i = blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const U4 r = philox(ctr[4 * i], ctr[4 * i + 1], ctr[4 * i + 2], ctr[4 * i + 3], k0, k1);
+  out[4 * i] = r.x;
+  out[4 * i + 1] = r.y;
+  out[4 * i + 2] = r.z;
+  out[4 * i + 3] = r.w;
+}
+
+struct SelectArgs {
+  uint32_t keys[2 * 128];
+};
+
+__global__ void k_select(int N, int m, const float* __restrict__ logl, const SelectArgs K, uint32_t t,
+                         int* worst, float* W, int* seed_slot) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ BlockScratch S;
+  __shared__ SelectScratch X;
+  int* sel_slot = reinterpret_cast<int*>(sm);
+  uint32_t* sel_key = reinterpret_cast<uint32_t*>(sm + al16(sizeof(int) * m));
+  const int r = blockIdx.x;
+  select_worst(logl + (size_t)r * N, N, m, K.keys[2 * r], K.keys[2 * r + 1], t, sel_slot, sel_key,
+               worst + (size_t)r * m, W + (size_t)r * m, seed_slot + (size_t)r * m, X, S);
+}
+
+__global__ void k_correct(int m, int K, int correction, const float* __restrict__ W,
+                          const float* __restrict__ new_l, const float* __restrict__ hist_l,
+                          const int* __restrict__ hist_len, int t_max, int* acc_src, int* acc_hpos,
+                          float* acc_l, float* acc_P, int* rej_src, int* rej_hpos, float* rej_l,
+                          float* rej_P, int* n_relaxed) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ BlockScratch S;
+  __shared__ int ctr;
+  const size_t cb = al16((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
+  const Cand A = cand_at(sm, m);
+  const Cand Bf = cand_at(sm + cb, m);
+  int* list = reinterpret_cast<int*>(sm + 2 * cb);
+  float* vals = reinterpret_cast<float*>(sm + 2 * cb + al16(sizeof(int) * 2 * m));
+  const int rel = batch_correct(m, K, correction, W, new_l, hist_l, hist_len, t_max, A, Bf, list, vals, &ctr, S);
+  for (int j = threadIdx.x; j < m; j += blockDim.x) {
+    rej_src[j] = A.src[j];
+    rej_hpos[j] = A.hp[j];
+    rej_l[j] = A.l[j];
+    rej_P[j] = A.P[j];
+    acc_src[j] = A.src[m + j];
+    acc_hpos[j] = A.hp[m + j];
+    acc_l[j] = A.l[m + j];
+    acc_P[j] = A.P[m + j];
+  }
+  if (threadIdx.x == 0) *n_relaxed = rel;
+}
+
+__global__ void k_evidence(int N, int n, const float* __restrict__ l, double* state, double* logw, int live) {
+  __shared__ BlockScratch S;
+  __shared__ EvidState E;
+  if (threadIdx.x == 0) {
+    E.logz = state[0];
+    E.info = state[1];
+    E.k = (long long)state[2];
+  }
+  __syncthreads();
+  evidence_add(E, N, n, l, logw, live != 0, S);
+  if (threadIdx.x == 0) {
+    state[0] = E.logz;
+    state[1] = E.info;
+    state[2] = (double)E.k;
+  }
+}
+
+__global__ void k_cluster(RunDesc R) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ BlockScratch S;
+  const Carve cv = make_carve(R.d, 1, R.n_nodes);
+  cluster_phase(R, sm, cv, S);
+}
+
+// ---------------------------------------------------------------------------
+// Host side
+// ---------------------------------------------------------------------------
+std::mutex g_err_mu;
+std::string g_err;
+
+void set_err(std::string* dst, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  g_err = buf;
+  if (dst) *dst = buf;
+}
+
+#define NS_CUDA(call, errdst)                                                                  \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess) {                                                                   \
+      set_err(errdst, "%s failed: %s (%s:%d)", #call, cudaGetErrorString(e_), __FILE__, __LINE__); \
+      return e_ == cudaErrorMemoryAllocation ? NS_ERR_OOM : NS_ERR_CUDA;                       \
+    }                                                                                          \
+  } while (0)
+
+int dmax_class(int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32; }
+
+int block_for_m(int m) {
+  int b = ((m + 31) / 32) * 32;
+  if (b < 128) b = 128;
+  if (b > 256) b = 256;
+  return b;
+}
+
+bool finite_pos(double v) { return std::isfinite(v) && v > 0; }
+
+ns_status check_lik(const ns_likelihood* L, int d, std::string* err) {
+  if (!L) {
+    set_err(err, "likelihood is NULL");
+    return NS_ERR_ARG;
+  }
+  switch (L->kind) {
+    case NS_LIK_GAUSS_ISO:
+      if (!L->mean || !finite_pos(L->sigma)) {
+        set_err(err, "GAUSS_ISO needs mean and sigma > 0");
+        return NS_ERR_ARG;
+      }
+      for (int i = 0; i < d; ++i)
+        if (!std::isfinite(L->mean[i])) {
+          set_err(err, "mean[%d] is not finite", i);
+          return NS_ERR_ARG;
+        }
+      return NS_OK;
+    case NS_LIK_GAUSS_CORR:
+      if (!L->mean || !L->prec_chol) {
+        set_err(err, "GAUSS_CORR needs mean and prec_chol");
+        return NS_ERR_ARG;
+      }
+      for (int i = 0; i < d; ++i) {
+        if (!std::isfinite(L->mean[i]) || !finite_pos(L->prec_chol[i * d + i])) {
+          set_err(err, "GAUSS_CORR: mean[%d] not finite or prec_chol diagonal not positive", i);
+          return NS_ERR_ARG;
+        }
+        for (int j = 0; j <= i; ++j)
+          if (!std::isfinite(L->prec_chol[i * d + j])) {
+            set_err(err, "prec_chol[%d][%d] is not finite", i, j);
+            return NS_ERR_ARG;
+          }
+      }
+      return NS_OK;
+    case NS_LIK_ROSENBROCK:
+      if (!std::isfinite(L->a) || !std::isfinite(L->b) || L->b < 0 || d < 2) {
+        set_err(err, "ROSENBROCK needs finite a, b >= 0 and d >= 2");
+        return NS_ERR_ARG;
+      }
+      return NS_OK;
+    case NS_LIK_MIXTURE:
+      if (!L->centres || L->n_modes < 1 || L->n_modes > NS_MAX_MODES || !finite_pos(L->sigma)) {
+        set_err(err, "MIXTURE needs 1..%d centres and sigma > 0", NS_MAX_MODES);
+        return NS_ERR_ARG;
+      }
+      for (int k = 0; k < L->n_modes * d; ++k)
+        if (!std::isfinite(L->centres[k])) {
+          set_err(err, "centres[%d] is not finite", k);
+          return NS_ERR_ARG;
+        }
+      return NS_OK;
+    case NS_LIK_MLP:
+      set_err(err, "MLP likelihood is not available in this build");
+      return NS_ERR_UNSUPPORTED;
+    default:
+      set_err(err, "unknown likelihood kind %d", L->kind);
+      return NS_ERR_ARG;
+  }
+}
+
+ns_status check_opts(const ns_options& o, std::string* err) {
+  if (o.depth < 0 || o.depth > NS_MAX_DEPTH) {
+    set_err(err, "depth must be in 0..%d", NS_MAX_DEPTH);
+    return NS_ERR_ARG;
+  }
+  if (o.depth > 0) {
+    set_err(err, "cluster trees deeper than 0 are not available in this build");
+    return NS_ERR_UNSUPPORTED;
+  }
+  if (o.recluster_every < 0 || o.kmeans_iters < 0 || o.history_iters < 0 || o.e_max < 0 || o.s_max < 1 ||
+      o.t_max < 1 || o.t_max > NS_MAX_HISTORY || !(o.width > 0) || !std::isfinite(o.width) ||
+      o.correction < 0 || o.correction > 3 || o.max_iter < 1 || o.dead_cap < 0 || o.chunk_iters < 0 ||
+      !(o.vol_frac >= 0 && o.vol_frac < 1)) {
+    set_err(err, "an option is out of range");
+    return NS_ERR_ARG;
+  }
+  return NS_OK;
+}
+
+ns_status check_problem(const ns_problem& p, std::string* err) {
+  if (p.d < 1 || p.d > NS_MAX_DIM) {
+    set_err(err, "d = %d outside 1..%d", p.d, NS_MAX_DIM);
+    return NS_ERR_ARG;
+  }
+  if (p.n_live < 2 || p.n_live > NS_MAX_LIVE) {
+    set_err(err, "n_live = %d outside 2..%d", p.n_live, NS_MAX_LIVE);
+    return NS_ERR_ARG;
+  }
+  if (p.m < 1 || 2 * p.m > p.n_live || p.m > NS_MAX_BATCH) {
+    set_err(err, "m = %d must satisfy 1 <= m <= n_live/2 and m <= %d", p.m, NS_MAX_BATCH);
+    return NS_ERR_ARG;
+  }
+  if (p.n_slice_steps < 1 || p.n_slice_steps > 0xFFFF) {
+    set_err(err, "n_slice_steps = %d outside 1..65535", p.n_slice_steps);
+    return NS_ERR_ARG;
+  }
+  if (!(p.stop_frac > 0 && p.stop_frac < 1)) {
+    set_err(err, "stop_frac must be in (0, 1)");
+    return NS_ERR_ARG;
+  }
+  if (!p.lo || !p.hi) {
+    set_err(err, "prior box is NULL");
+    return NS_ERR_ARG;
+  }
+  for (int i = 0; i < p.d; ++i)
+    if (!std::isfinite(p.lo[i]) || !std::isfinite(p.hi[i]) || !(p.lo[i] < p.hi[i])) {
+      set_err(err, "prior box dimension %d needs finite lo < hi", i);
+      return NS_ERR_ARG;
+    }
+  return check_lik(p.lik, p.d, err);
+}
+
+LikParams make_lik(const ns_likelihood& L, const double* lo, const double* hi, int d) {
+  LikParams P;
+  std::memset(&P, 0, sizeof(P));
+  P.kind = L.kind;
+  P.d = d;
+  for (int i = 0; i < d; ++i) {
+    P.lo[i] = (float)lo[i];
+    P.span[i] = (float)(hi[i] - lo[i]);
+  }
+  switch (L.kind) {
+    case NS_LIK_GAUSS_ISO:
+      P.inv2s2 = (float)(1.0 / (2.0 * L.sigma * L.sigma));
+      for (int i = 0; i < d; ++i) P.c[i] = (float)(lo[i] - L.mean[i]);
+      break;
+    case NS_LIK_GAUSS_CORR:
+      for (int i = 0; i < d; ++i) {
+        P.c[i] = (float)(lo[i] - L.mean[i]);
+        for (int j = 0; j <= i; ++j) P.Lp[i * d + j] = (float)L.prec_chol[i * d + j];
+      }
+      break;
+    case NS_LIK_ROSENBROCK:
+      P.a = (float)L.a;
+      P.b = (float)L.b;
+      break;
+    case NS_LIK_MIXTURE:
+      P.n_modes = L.n_modes;
+      P.inv2s2 = (float)(1.0 / (2.0 * L.sigma * L.sigma));
+      P.log_k = (float)std::log((double)L.n_modes);
+      for (int k = 0; k < L.n_modes; ++k)
+        for (int i = 0; i < d; ++i) P.cm[k * d + i] = (float)(lo[i] - L.centres[k * d + i]);
+      break;
+    default:
+      break;
+  }
+  return P;
+}
+
+struct HostRun {
+  int d, N, m;
+  long long dead_cap;
+  bool fetched = false;
+  std::vector<float> dead_x, dead_l;
+  std::vector<double> dead_logw;
+};
+
+struct ClassGroup {
+  int dmax = 0, block = 0, n = 0;
+  size_t smem = 0;
+  int* d_ids = nullptr;
+};
+
+cudaError_t launch_class(const ClassGroup& g, const RunDesc* d_runs, int chunk, cudaStream_t s) {
+  switch (g.dmax) {
+    case 4: return launch_run_4(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
+    case 8: return launch_run_8(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
+    case 16: return launch_run_16(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
+    default: return launch_run_32(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
+  }
+}
+
+}  // namespace
+
+struct ns_handle {
+  int n_runs = 0;
+  ns_options opt;
+  void* arena = nullptr;
+  size_t arena_bytes = 0;
+  RunDesc* d_runs = nullptr;
+  RunState* d_states = nullptr;
+  RunState* h_states = nullptr;  // pinned
+  std::vector<RunDesc> runs;
+  std::vector<HostRun> host;
+  std::vector<ClassGroup> groups;
+  bool ran = false;
+  double last_ms = 0;
+  double kernel_ms = 0;
+  long long launches = 0;
+  long long h2d_bytes = 0;
+  long long d2h_bytes = 0;
+  std::string err;
+};
+
+extern "C" {
+
+ns_status ns_default_options(ns_options* o) {
+  if (!o) return NS_ERR_ARG;
+  std::memset(o, 0, sizeof(*o));
+  o->depth = 0;
+  o->recluster_every = 0;
+  o->n_min = 0;
+  o->vol_frac = 0.5;
+  o->kmeans_iters = 10;
+  o->correction = 2;
+  o->history_iters = 1;
+  o->t_max = 64;
+  o->e_max = 64;
+  o->s_max = 128;
+  o->width = 1.0;
+  o->max_iter = 1000000;
+  o->dead_cap = 0;
+  o->chunk_iters = 1000;
+  o->precision = 0;
+  o->reeval_margin = 0.0;
+  return NS_OK;
+}
+
+ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* opt_in, ns_handle** out) {
+  if (!out) {
+    set_err(nullptr, "out is NULL");
+    return NS_ERR_ARG;
+  }
+  *out = nullptr;
+  if (n_runs < 1 || !runs) {
+    set_err(nullptr, "n_runs must be >= 1 and runs non-NULL");
+    return NS_ERR_ARG;
+  }
+  ns_options opt;
+  if (opt_in) opt = *opt_in;
+  else ns_default_options(&opt);
+  ns_status st = check_opts(opt, nullptr);
+  if (st != NS_OK) return st;
+  for (int r = 0; r < n_runs; ++r) {
+    st = check_problem(runs[r], nullptr);
+    if (st != NS_OK) {
+      std::string m;
+      {
+        std::lock_guard<std::mutex> lk(g_err_mu);
+        m = g_err;
+      }
+      set_err(nullptr, "run %d: %s", r, m.c_str());
+      return st;
+    }
+  }
+  ns_handle* h = new ns_handle();
+  h->n_runs = n_runs;
+  h->opt = opt;
+  const int n_nodes = (1 << (opt.depth + 1)) - 1;
+  // arena layout
+  std::vector<size_t> offs;
+  size_t total = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = total;
+    total += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  struct Off {
+    size_t lik, live_x, live_l, live_cid, new_x, new_l, hist_l, hist_x, hist_len, stage_x, dead_x, dead_l,
+        dead_logw, centres, chol, chol64, logvol, count, split, mask;
+  };
+  std::vector<Off> off(n_runs);
+  h->host.resize(n_runs);
+  h->runs.resize(n_runs);
+  for (int r = 0; r < n_runs; ++r) {
+    const ns_problem& p = runs[r];
+    const int d = p.d, N = p.n_live, m = p.m, n_pad = ((N + 31) / 32) * 32;
+    const long long cap = opt.dead_cap > 0 ? opt.dead_cap : 400LL * N + 4LL * m;
+    Off& o = off[r];
+    o.lik = take(sizeof(LikParams));
+    o.live_x = take(sizeof(float) * (size_t)d * n_pad);
+    o.live_l = take(sizeof(float) * N);
+    o.live_cid = take(sizeof(int) * N);
+    o.new_x = take(sizeof(float) * (size_t)m * d);
+    o.new_l = take(sizeof(float) * m);
+    o.hist_l = take(sizeof(float) * (size_t)m * opt.t_max);
+    o.hist_x = take(sizeof(float) * (size_t)m * opt.t_max * d);
+    o.hist_len = take(sizeof(int) * m);
+    o.stage_x = take(sizeof(float) * (size_t)m * d);
+    o.dead_x = take(sizeof(float) * (size_t)cap * d);
+    o.dead_l = take(sizeof(float) * (size_t)cap);
+    o.dead_logw = take(sizeof(double) * (size_t)cap);
+    o.centres = take(sizeof(float) * n_nodes * d);
+    o.chol = take(sizeof(float) * n_nodes * d * d);
+    o.chol64 = take(sizeof(double) * n_nodes * d * d);
+    o.logvol = take(sizeof(float) * n_nodes);
+    o.count = take(sizeof(int) * n_nodes);
+    o.split = take(sizeof(int) * n_nodes);
+    o.mask = take(sizeof(int) * n_nodes);
+    HostRun& hr = h->host[r];
+    hr.d = d;
+    hr.N = N;
+    hr.m = m;
+    hr.dead_cap = cap;
+  }
+  const size_t off_desc = take(sizeof(RunDesc) * n_runs);
+  const size_t off_state = take(sizeof(RunState) * n_runs);
+  // class groups
+  int counts[4] = {0, 0, 0, 0};
+  std::vector<std::vector<int>> members(4);
+  for (int r = 0; r < n_runs; ++r) {
+    const int c = dmax_class(runs[r].d);
+    const int ci = c == 4 ? 0 : c == 8 ? 1 : c == 16 ? 2 : 3;
+    members[ci].push_back(r);
+    counts[ci]++;
+  }
+  size_t off_ids[4];
+  for (int ci = 0; ci < 4; ++ci) off_ids[ci] = take(sizeof(int) * std::max(1, counts[ci]));
+  h->arena_bytes = total;
+  cudaError_t e = cudaMalloc(&h->arena, total);
+  if (e != cudaSuccess) {
+    set_err(&h->err, "cudaMalloc of %zu bytes failed: %s", total, cudaGetErrorString(e));
+    delete h;
+    return e == cudaErrorMemoryAllocation ? NS_ERR_OOM : NS_ERR_CUDA;
+  }
+  char* base = static_cast<char*>(h->arena);
+  e = cudaMallocHost(&h->h_states, sizeof(RunState) * n_runs);
+  if (e != cudaSuccess) {
+    set_err(&h->err, "cudaMallocHost failed: %s", cudaGetErrorString(e));
+    cudaFree(h->arena);
+    delete h;
+    return NS_ERR_CUDA;
+  }
+  std::vector<LikParams> liks(n_runs);
+  for (int r = 0; r < n_runs; ++r) {
+    const ns_problem& p = runs[r];
+    const Off& o = off[r];
+    RunDesc& R = h->runs[r];
+    std::memset(&R, 0, sizeof(R));
+    R.d = p.d;
+    R.N = p.n_live;
+    R.m = p.m;
+    R.n_pad = ((p.n_live + 31) / 32) * 32;
+    R.n_steps = p.n_slice_steps;
+    R.depth = opt.depth;
+    R.n_nodes = n_nodes;
+    R.recluster_every = opt.recluster_every > 0 ? opt.recluster_every : std::max(1, 100 / p.m);
+    R.n_min = opt.n_min > 0 ? opt.n_min : p.d + 1;
+    R.kmeans_iters = opt.kmeans_iters;
+    R.correction = opt.correction;
+    R.K = opt.history_iters;
+    R.t_max = opt.t_max;
+    R.e_max = opt.e_max;
+    R.s_max = opt.s_max;
+    R.k0 = (uint32_t)(p.seed & 0xFFFFFFFFull);
+    R.k1 = (uint32_t)(p.seed >> 32);
+    R.width = (float)opt.width;
+    R.vol_frac = (float)opt.vol_frac;
+    R.log_stop = std::log(p.stop_frac);
+    R.max_iter = opt.max_iter;
+    R.dead_cap = h->host[r].dead_cap;
+    R.lik = reinterpret_cast<const LikParams*>(base + o.lik);
+    R.live_x = reinterpret_cast<float*>(base + o.live_x);
+    R.live_l = reinterpret_cast<float*>(base + o.live_l);
+    R.live_cid = reinterpret_cast<int*>(base + o.live_cid);
+    R.new_x = reinterpret_cast<float*>(base + o.new_x);
+    R.new_l = reinterpret_cast<float*>(base + o.new_l);
+    R.hist_l = reinterpret_cast<float*>(base + o.hist_l);
+    R.hist_x = reinterpret_cast<float*>(base + o.hist_x);
+    R.hist_len = reinterpret_cast<int*>(base + o.hist_len);
+    R.stage_x = reinterpret_cast<float*>(base + o.stage_x);
+    R.dead_x = reinterpret_cast<float*>(base + o.dead_x);
+    R.dead_l = reinterpret_cast<float*>(base + o.dead_l);
+    R.dead_logw = reinterpret_cast<double*>(base + o.dead_logw);
+    R.centres = reinterpret_cast<float*>(base + o.centres);
+    R.chol = reinterpret_cast<float*>(base + o.chol);
+    R.chol64 = reinterpret_cast<double*>(base + o.chol64);
+    R.logvol = reinterpret_cast<float*>(base + o.logvol);
+    R.count = reinterpret_cast<int*>(base + o.count);
+    R.split = reinterpret_cast<int*>(base + o.split);
+    R.mask = reinterpret_cast<int*>(base + o.mask);
+    R.st = reinterpret_cast<RunState*>(base + off_state) + r;
+    liks[r] = make_lik(*p.lik, p.lo, p.hi, p.d);
+  }
+  h->d_runs = reinterpret_cast<RunDesc*>(base + off_desc);
+  h->d_states = reinterpret_cast<RunState*>(base + off_state);
+  auto fail = [&](ns_status s) {
+    cudaFreeHost(h->h_states);
+    cudaFree(h->arena);
+    delete h;
+    return s;
+  };
+  h->h2d_bytes = (long long)(sizeof(LikParams) + sizeof(RunDesc)) * n_runs;
+  for (int r = 0; r < n_runs; ++r) {
+    e = cudaMemcpy(base + off[r].lik, &liks[r], sizeof(LikParams), cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      set_err(nullptr, "cudaMemcpy failed: %s", cudaGetErrorString(e));
+      return fail(NS_ERR_CUDA);
+    }
+  }
+  e = cudaMemcpy(h->d_runs, h->runs.data(), sizeof(RunDesc) * n_runs, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemset(h->d_states, 0, sizeof(RunState) * n_runs);
+  if (e != cudaSuccess) {
+    set_err(nullptr, "device setup failed: %s", cudaGetErrorString(e));
+    return fail(NS_ERR_CUDA);
+  }
+  for (int ci = 0; ci < 4; ++ci) {
+    if (counts[ci] == 0) continue;
+    ClassGroup g;
+    g.dmax = ci == 0 ? 4 : ci == 1 ? 8 : ci == 2 ? 16 : 32;
+    g.n = counts[ci];
+    g.d_ids = reinterpret_cast<int*>(base + off_ids[ci]);
+    int maxm = 1;
+    size_t smem = 0;
+    for (int r : members[ci]) {
+      maxm = std::max(maxm, runs[r].m);
+      smem = std::max(smem, make_carve(runs[r].d, runs[r].m, n_nodes).total);
+    }
+    g.block = block_for_m(maxm);
+    g.smem = smem;
+    e = cudaMemcpy(g.d_ids, members[ci].data(), sizeof(int) * g.n, cudaMemcpyHostToDevice);
+    h->h2d_bytes += (long long)sizeof(int) * g.n;
+    if (e != cudaSuccess) {
+      set_err(nullptr, "cudaMemcpy failed: %s", cudaGetErrorString(e));
+      return fail(NS_ERR_CUDA);
+    }
+    h->groups.push_back(g);
+  }
+  *out = h;
+  return NS_OK;
+}
+
+ns_status ns_create(const ns_likelihood* lik, const double* lo, const double* hi, int d, int n_live, int m,
+                    int n_slice_steps, double stop_frac, uint64_t seed, const ns_options* opt, ns_handle** out) {
+  ns_problem p;
+  p.lik = lik;
+  p.lo = lo;
+  p.hi = hi;
+  p.d = d;
+  p.n_live = n_live;
+  p.m = m;
+  p.n_slice_steps = n_slice_steps;
+  p.stop_frac = stop_frac;
+  p.seed = seed;
+  return ns_create_batch(1, &p, opt, out);
+}
+
+int ns_n_runs(const ns_handle* h) { return h ? h->n_runs : -1; }
+
+ns_status ns_reset(ns_handle* h, void* stream) {
+  if (!h) return NS_ERR_ARG;
+  NS_CUDA(cudaMemsetAsync(h->d_states, 0, sizeof(RunState) * h->n_runs, (cudaStream_t)stream), &h->err);
+  for (auto& hr : h->host) {
+    hr.fetched = false;
+  }
+  h->ran = false;
+  return NS_OK;
+}
+
+ns_status ns_run(ns_handle* h, void* stream_v) {
+  if (!h) return NS_ERR_ARG;
+  cudaStream_t s = (cudaStream_t)stream_v;
+  cudaEvent_t e0, e1, k0, k1;
+  NS_CUDA(cudaEventCreate(&e0), &h->err);
+  NS_CUDA(cudaEventCreate(&e1), &h->err);
+  NS_CUDA(cudaEventCreate(&k0), &h->err);
+  NS_CUDA(cudaEventCreate(&k1), &h->err);
+  auto cleanup = [&]() {
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    cudaEventDestroy(k0);
+    cudaEventDestroy(k1);
+  };
+  NS_CUDA(cudaEventRecord(e0, s), &h->err);
+  const int chunk = h->opt.chunk_iters > 0 ? h->opt.chunk_iters : 1000;
+  long long rounds = 0;
+  const long long max_rounds = h->opt.max_iter / chunk + 2;
+  h->kernel_ms = 0;
+  h->launches = 0;
+  h->d2h_bytes = 0;
+  for (;;) {
+    NS_CUDA(cudaEventRecord(k0, s), &h->err);
+    for (const ClassGroup& g : h->groups) {
+      cudaError_t e = launch_class(g, h->d_runs, chunk, s);
+      if (e != cudaSuccess) {
+        set_err(&h->err, "run kernel launch failed: %s", cudaGetErrorString(e));
+        cleanup();
+        return NS_ERR_CUDA;
+      }
+      h->launches++;
+    }
+    NS_CUDA(cudaEventRecord(k1, s), &h->err);
+    NS_CUDA(cudaMemcpyAsync(h->h_states, h->d_states, sizeof(RunState) * h->n_runs, cudaMemcpyDeviceToHost, s),
+            &h->err);
+    NS_CUDA(cudaStreamSynchronize(s), &h->err);
+    h->d2h_bytes += (long long)sizeof(RunState) * h->n_runs;
+    float kms = 0.f;
+    cudaEventElapsedTime(&kms, k0, k1);
+    h->kernel_ms += kms;
+    ++rounds;
+    bool done = true;
+    for (int r = 0; r < h->n_runs; ++r)
+      if (!h->h_states[r].stopped && h->h_states[r].status == 0) done = false;
+    if (done || rounds > max_rounds) break;
+  }
+  NS_CUDA(cudaEventRecord(e1, s), &h->err);
+  NS_CUDA(cudaEventSynchronize(e1), &h->err);
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, e0, e1);
+  h->last_ms = ms;
+  cleanup();
+  h->ran = true;
+  for (auto& hr : h->host) hr.fetched = false;
+  ns_status worst = NS_OK;
+  for (int r = 0; r < h->n_runs; ++r)
+    if (h->h_states[r].status != 0) worst = (ns_status)h->h_states[r].status;
+  if (worst != NS_OK) set_err(&h->err, "a run ended with status %d", (int)worst);
+  return worst;
+}
+
+ns_status ns_get_stats(const ns_handle* h, ns_stats* out) {
+  if (!h || !out) return NS_ERR_ARG;
+  out->run_ms = h->last_ms;
+  out->kernel_ms = h->kernel_ms;
+  out->launches = h->launches;
+  out->h2d_bytes = h->h2d_bytes;
+  out->d2h_bytes = h->d2h_bytes;
+  return NS_OK;
+}
+
+ns_status ns_last_run_ms(const ns_handle* h, double* ms) {
+  if (!h || !ms) return NS_ERR_ARG;
+  if (!h->ran) return NS_ERR_STATE;
+  *ms = h->last_ms;
+  return NS_OK;
+}
+
+ns_status ns_result(ns_handle* h, int run, ns_result_t* out) {
+  if (!h || !out || run < 0 || run >= h->n_runs) return NS_ERR_ARG;
+  if (!h->ran) {
+    set_err(&h->err, "ns_result before ns_run");
+    return NS_ERR_STATE;
+  }
+  const RunState& S = h->h_states[run];
+  HostRun& hr = h->host[run];
+  const RunDesc& R = h->runs[run];
+  if (!hr.fetched) {
+    const long long n = S.n_dead;
+    hr.dead_x.resize((size_t)std::max(1LL, n) * hr.d);
+    hr.dead_l.resize((size_t)std::max(1LL, n));
+    hr.dead_logw.resize((size_t)std::max(1LL, n));
+    if (n > 0) {
+      NS_CUDA(cudaMemcpy(hr.dead_x.data(), R.dead_x, sizeof(float) * (size_t)n * hr.d, cudaMemcpyDeviceToHost),
+              &h->err);
+      NS_CUDA(cudaMemcpy(hr.dead_l.data(), R.dead_l, sizeof(float) * (size_t)n, cudaMemcpyDeviceToHost), &h->err);
+      NS_CUDA(cudaMemcpy(hr.dead_logw.data(), R.dead_logw, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost),
+              &h->err);
+      h->d2h_bytes += (long long)n * (long long)(sizeof(float) * hr.d + sizeof(float) + sizeof(double));
+    }
+    hr.fetched = true;
+  }
+  out->log_z = S.logz;
+  out->log_z_err = std::sqrt(S.info > 0 ? S.info / hr.N : 0.0);
+  out->info_h = S.info;
+  out->n_dead = S.n_dead;
+  out->n_evals = S.n_evals;
+  out->n_iter = S.n_iter;
+  out->n_relaxed = S.n_relaxed;
+  out->n_reeval = S.n_reeval;
+  out->n_capped = S.n_capped;
+  out->status = S.status;
+  out->d = hr.d;
+  out->dead_x = hr.dead_x.data();
+  out->dead_logl = hr.dead_l.data();
+  out->dead_logw = hr.dead_logw.data();
+  return NS_OK;
+}
+
+ns_status ns_summary(const ns_handle* h, int run, ns_result_t* out) {
+  if (!h || !out || run < 0 || run >= h->n_runs) return NS_ERR_ARG;
+  if (!h->ran) return NS_ERR_STATE;
+  const RunState& S = h->h_states[run];
+  const HostRun& hr = h->host[run];
+  std::memset(out, 0, sizeof(*out));
+  out->log_z = S.logz;
+  out->log_z_err = std::sqrt(S.info > 0 ? S.info / hr.N : 0.0);
+  out->info_h = S.info;
+  out->n_dead = S.n_dead;
+  out->n_evals = S.n_evals;
+  out->n_iter = S.n_iter;
+  out->n_relaxed = S.n_relaxed;
+  out->n_reeval = S.n_reeval;
+  out->n_capped = S.n_capped;
+  out->status = S.status;
+  out->d = hr.d;
+  return NS_OK;
+}
+
+ns_status ns_phase_cycles(const ns_handle* h, int run, long long* out) {
+  if (!h || !out || run < 0 || run >= h->n_runs) return NS_ERR_ARG;
+  if (!h->ran) return NS_ERR_STATE;
+  for (int i = 0; i < 8; ++i) out[i] = h->h_states[run].cycles[i];
+  return NS_OK;
+}
+
+const char* ns_last_error(const ns_handle* h) {
+  if (h) return h->err.c_str();
+  std::lock_guard<std::mutex> lk(g_err_mu);
+  static thread_local std::string copy;
+  copy = g_err;
+  return copy.c_str();
+}
+
+void ns_destroy(ns_handle* h) {
+  if (!h) return;
+  if (h->h_states) cudaFreeHost(h->h_states);
+  if (h->arena) cudaFree(h->arena);
+  delete h;
+}
+
+// ---- step-level entry points ----------------------------------------------
+ns_status ns_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, int n, uint32_t* out, void* stream) {
+  if (n < 0 || (n > 0 && (!ctr || !out))) {
+    set_err(nullptr, "ns_philox4x32_10: bad arguments");
+    return NS_ERR_ARG;
+  }
+  if (n == 0) return NS_OK;
+  k_philox<<<(n + 255) / 256, 256, 0, (cudaStream_t)stream>>>(ctr, key0, key1, n, out);
+  NS_CUDA(cudaGetLastError(), nullptr);
+  return NS_OK;
+}
+
+ns_status ns_loglike(const ns_likelihood* lik, const double* lo, const double* hi, int d, int n, const float* x,
+                     float* logl, void* stream) {
+  ns_problem p;
+  std::memset(&p, 0, sizeof(p));
+  p.lik = lik;
+  p.lo = lo;
+  p.hi = hi;
+  p.d = d;
+  p.n_live = 2;
+  p.m = 1;
+  p.n_slice_steps = 1;
+  p.stop_frac = 0.5;
+  ns_status st = check_problem(p, nullptr);
+  if (st != NS_OK) return st;
+  if (n < 0 || (n > 0 && (!x || !logl))) {
+    set_err(nullptr, "ns_loglike: bad arguments");
+    return NS_ERR_ARG;
+  }
+  if (n == 0) return NS_OK;
+  const LikParams P = make_lik(*lik, lo, hi, d);
+  cudaStream_t s = (cudaStream_t)stream;
+  cudaError_t e;
+  switch (dmax_class(d)) {
+    case 4: e = launch_loglike_4(P, n, x, logl, s); break;
+    case 8: e = launch_loglike_8(P, n, x, logl, s); break;
+    case 16: e = launch_loglike_16(P, n, x, logl, s); break;
+    default: e = launch_loglike_32(P, n, x, logl, s); break;
+  }
+  NS_CUDA(e, nullptr);
+  return NS_OK;
+}
+
+ns_status ns_select_worst(int n_runs, int N, int m, const float* logl, const uint64_t* seeds, uint32_t t,
+                          int* worst, float* W, int* seed_slot, void* stream) {
+  if (n_runs < 0 || N < 2 || N > NS_MAX_LIVE || m < 1 || 2 * m > N || m > NS_MAX_BATCH ||
+      (n_runs > 0 && (!logl || !seeds || !worst || !W || !seed_slot))) {
+    set_err(nullptr, "ns_select_worst: bad arguments (need 1 <= m <= N/2, m <= %d)", NS_MAX_BATCH);
+    return NS_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t smem = al16(sizeof(int) * m) + al16(sizeof(uint32_t) * m);
+  for (int r0 = 0; r0 < n_runs; r0 += 128) {
+    const int nr = std::min(128, n_runs - r0);
+    SelectArgs K;
+    for (int r = 0; r < nr; ++r) {
+      K.keys[2 * r] = (uint32_t)(seeds[r0 + r] & 0xFFFFFFFFull);
+      K.keys[2 * r + 1] = (uint32_t)(seeds[r0 + r] >> 32);
+    }
+    k_select<<<nr, 256, smem, s>>>(N, m, logl + (size_t)r0 * N, K, t, worst + (size_t)r0 * m, W + (size_t)r0 * m,
+                                  seed_slot + (size_t)r0 * m);
+    NS_CUDA(cudaGetLastError(), nullptr);
+  }
+  return NS_OK;
+}
+
+ns_status ns_slice_replace(const ns_likelihood* lik, const double* lo, const double* hi, int d, int N, int n_pad,
+                           int m, int n_steps, const ns_options* opt_in, uint64_t seed, uint32_t t,
+                           const float* live_x, const float* live_l, const int* seed_slot, const float* W,
+                           const float* chol, const int* cid, float* new_x, float* new_l, float* hist_l,
+                           float* hist_x, int* hist_len, long long* evals, int* flags, void* stream) {
+  ns_options opt;
+  if (opt_in) opt = *opt_in;
+  else ns_default_options(&opt);
+  ns_status st = check_opts(opt, nullptr);
+  if (st != NS_OK) return st;
+  ns_problem p;
+  p.lik = lik;
+  p.lo = lo;
+  p.hi = hi;
+  p.d = d;
+  p.n_live = N;
+  p.m = m;
+  p.n_slice_steps = n_steps;
+  p.stop_frac = 0.5;
+  p.seed = seed;
+  st = check_problem(p, nullptr);
+  if (st != NS_OK) return st;
+  if (n_pad < N || !live_x || !live_l || !seed_slot || !W || !chol || !cid || !new_x || !new_l || !hist_l ||
+      !hist_x || !hist_len || !evals || !flags) {
+    set_err(nullptr, "ns_slice_replace: NULL buffer or n_pad < N");
+    return NS_ERR_ARG;
+  }
+  const LikParams P = make_lik(*lik, lo, hi, d);
+  SliceCfg SC;
+  SC.d = d;
+  SC.n_steps = n_steps;
+  SC.e_max = opt.e_max;
+  SC.s_max = opt.s_max;
+  SC.t_max = opt.t_max;
+  SC.width = (float)opt.width;
+  SC.k0 = (uint32_t)(seed & 0xFFFFFFFFull);
+  SC.k1 = (uint32_t)(seed >> 32);
+  SC.t = t;
+  cudaStream_t s = (cudaStream_t)stream;
+#define NS_SLICE_ARGS P, SC, m, n_pad, opt.correction, live_x, live_l, seed_slot, W, chol, cid, new_x, new_l, hist_l, \
+                      hist_x, hist_len, evals, flags, s
+  cudaError_t e;
+  switch (dmax_class(d)) {
+    case 4: e = launch_slice_4(NS_SLICE_ARGS); break;
+    case 8: e = launch_slice_8(NS_SLICE_ARGS); break;
+    case 16: e = launch_slice_16(NS_SLICE_ARGS); break;
+    default: e = launch_slice_32(NS_SLICE_ARGS); break;
+  }
+#undef NS_SLICE_ARGS
+  NS_CUDA(e, nullptr);
+  return NS_OK;
+}
+
+ns_status ns_batch_correct(int m, int K, int correction, const float* W, const float* new_l, const float* hist_l,
+                           const int* hist_len, int t_max, int* acc_src, int* acc_hpos, float* acc_l, float* acc_P,
+                           int* rej_src, int* rej_hpos, float* rej_l, float* rej_P, int* n_relaxed, void* stream) {
+  if (m < 1 || m > NS_MAX_BATCH || K < 0 || correction < 0 || correction > 3 || t_max < 1 ||
+      t_max > NS_MAX_HISTORY || !W || !new_l || !hist_l || !hist_len || !acc_src || !acc_hpos || !acc_l ||
+      !acc_P || !rej_src || !rej_hpos || !rej_l || !rej_P || !n_relaxed) {
+    set_err(nullptr, "ns_batch_correct: bad arguments");
+    return NS_ERR_ARG;
+  }
+  const size_t cb = al16((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
+  const size_t smem = 2 * cb + al16(sizeof(int) * 2 * m) + al16(sizeof(float) * m);
+  k_correct<<<1, 256, smem, (cudaStream_t)stream>>>(m, K, correction, W, new_l, hist_l, hist_len, t_max, acc_src,
+                                                    acc_hpos, acc_l, acc_P, rej_src, rej_hpos, rej_l, rej_P,
+                                                    n_relaxed);
+  NS_CUDA(cudaGetLastError(), nullptr);
+  return NS_OK;
+}
+
+ns_status ns_evidence_update(int N, int n, const float* dead_l, double* state, double* logw, int live,
+                             void* stream) {
+  if (N < 1 || n < 0 || (n > 0 && (!dead_l || !logw)) || !state) {
+    set_err(nullptr, "ns_evidence_update: bad arguments");
+    return NS_ERR_ARG;
+  }
+  if (n == 0) return NS_OK;
+  k_evidence<<<1, 256, 0, (cudaStream_t)stream>>>(N, n, dead_l, state, logw, live);
+  NS_CUDA(cudaGetLastError(), nullptr);
+  return NS_OK;
+}
+
+ns_status ns_cluster(int N, int n_pad, int d, const float* live_x, const ns_options* opt_in, uint64_t seed,
+                     uint32_t t, float* centres, float* chol, double* chol64, float* logvol, int* count, int* split,
+                     int* mask, int* cid, void* stream) {
+  ns_options opt;
+  if (opt_in) opt = *opt_in;
+  else ns_default_options(&opt);
+  ns_status st = check_opts(opt, nullptr);
+  if (st != NS_OK) return st;
+  if (N < 2 || n_pad < N || d < 1 || d > NS_MAX_DIM || !live_x || !centres || !chol || !chol64 || !logvol ||
+      !count || !split || !mask || !cid) {
+    set_err(nullptr, "ns_cluster: bad arguments");
+    return NS_ERR_ARG;
+  }
+  RunDesc R;
+  std::memset(&R, 0, sizeof(R));
+  R.d = d;
+  R.N = N;
+  R.m = 1;
+  R.n_pad = n_pad;
+  R.depth = opt.depth;
+  R.n_nodes = (1 << (opt.depth + 1)) - 1;
+  R.n_min = opt.n_min > 0 ? opt.n_min : d + 1;
+  R.kmeans_iters = opt.kmeans_iters;
+  R.vol_frac = (float)opt.vol_frac;
+  R.k0 = (uint32_t)(seed & 0xFFFFFFFFull);
+  R.k1 = (uint32_t)(seed >> 32);
+  R.live_x = const_cast<float*>(live_x);
+  R.live_cid = cid;
+  R.centres = centres;
+  R.chol = chol;
+  R.chol64 = chol64;
+  R.logvol = logvol;
+  R.count = count;
+  R.split = split;
+  R.mask = mask;
+  (void)t;
+  const size_t smem = make_carve(d, 1, R.n_nodes).total;
+  NS_CUDA(cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), nullptr);
+  k_cluster<<<1, 256, smem, (cudaStream_t)stream>>>(R);
+  NS_CUDA(cudaGetLastError(), nullptr);
+  return NS_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,453 @@
+// ns_run.cuh -- per-run descriptor, shared-memory layout and the
+// persistent run kernel of the batched nested sampler (one thread block per
+// run; walkers are the block's threads).  Included by the per-dimension
+// instantiation units and by the host library.
+#pragma once
+
+#include "../../include/ns_gb300.h"
+#include "ns_device.cuh"
+
+namespace nsd {
+
+// ---------------------------------------------------------------------------
+// Per-run device state and descriptor
+// ---------------------------------------------------------------------------
+// Phases timed by the run kernel (SM cycles, thread 0, between barriers).
+enum Phase { kPhCluster = 0, kPhSelect, kPhSlice, kPhCorrect, kPhUpdate, kPhEvidence, kNumPhases };
+
+struct RunState {
+  double logz, info;
+  long long k, n_dead, n_evals, n_iter, n_relaxed, n_reeval, n_capped;
+  long long cycles[8];
+  int t, stopped, status, initialized;
+};
+
+struct RunDesc {
+  int d, N, m, n_pad, n_steps, depth, n_nodes, recluster_every, n_min, kmeans_iters, correction, K,
+      t_max, e_max, s_max;
+  uint32_t k0, k1;
+  float width, vol_frac;
+  double log_stop;
+  long long max_iter, dead_cap;
+  const LikParams* lik;
+  float* live_x;
+  float* live_l;
+  int* live_cid;
+  float* new_x;
+  float* new_l;
+  float* hist_l;
+  float* hist_x;
+  int* hist_len;
+  float* stage_x;
+  float* dead_x;
+  float* dead_l;
+  double* dead_logw;
+  float* centres;
+  float* chol;
+  double* chol64;
+  float* logvol;
+  int* count;
+  int* split;
+  int* mask;
+  RunState* st;
+};
+
+// Shared-memory carve of the run kernel, computed identically on host and
+// device from the run's sizes.
+struct Carve {
+  size_t lik, scr, sel, chol, cent, mask, worst, W, seed, sel_slot, sel_key, candA, candB, list, vals,
+      ctr, stage_cid, tile, acc, c64, l64, work, total;
+};
+
+__host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
+
+__host__ __device__ inline Carve make_carve(int d, int m, int n_nodes) {
+  Carve c;
+  size_t o = 0;
+  auto take = [&](size_t bytes) {
+    size_t r = o;
+    o = al16(o + bytes);
+    return r;
+  };
+  c.lik = take(sizeof(LikParams));
+  c.scr = take(sizeof(BlockScratch));
+  c.sel = take(sizeof(SelectScratch));
+  c.chol = take(sizeof(float) * n_nodes * d * d);
+  c.cent = take(sizeof(float) * n_nodes * d);
+  c.mask = take(sizeof(int) * n_nodes);
+  c.worst = take(sizeof(int) * m);
+  c.W = take(sizeof(float) * m);
+  c.seed = take(sizeof(int) * m);
+  c.sel_slot = take(sizeof(int) * m);
+  c.sel_key = take(sizeof(uint32_t) * m);
+  c.candA = take((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
+  c.candB = take((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
+  c.list = take(sizeof(int) * 2 * m);
+  c.vals = take(sizeof(float) * m);
+  c.ctr = take(sizeof(int) * 4);
+  c.stage_cid = take(sizeof(int) * m);
+  c.tile = take(sizeof(float) * d * kTile);
+  c.acc = take(sizeof(double) * (d + d * d));
+  c.c64 = take(sizeof(double) * d * d);
+  c.l64 = take(sizeof(double) * d * d);
+  c.work = take(sizeof(double) * (3 * d * d + d));
+  c.total = o;
+  return c;
+}
+
+__device__ inline Cand cand_at(char* base, int m) {
+  Cand c;
+  c.l = reinterpret_cast<float*>(base);
+  c.P = c.l + 2 * m;
+  c.src = reinterpret_cast<int*>(c.P + 2 * m);
+  c.H = c.src + 2 * m;
+  c.hp = c.H + 2 * m;
+  return c;
+}
+
+// ---------------------------------------------------------------------------
+// Phases of one iteration on one run (whole block)
+// ---------------------------------------------------------------------------
+template <int DMAX>
+inline __device__ void init_live(const RunDesc& R, const LikParams& P) {
+  const int d = R.d;
+  for (int j = threadIdx.x; j < R.N; j += blockDim.x) {
+    float x[DMAX], v[DMAX];
+#pragma unroll
+    for (int i = 0; i < DMAX; ++i) {
+      v[i] = 0.f;
+      x[i] = (i < d) ? u24(draw_at(R.k0, R.k1, kTInit, (uint32_t)j, 0u, (uint32_t)i)) : 0.f;
+      if (i < d) R.live_x[(size_t)i * R.n_pad + j] = x[i];
+    }
+    R.live_l[j] = loglike<DMAX>(P, x, v, 0.f, d);
+    R.live_cid[j] = 0;
+  }
+}
+
+// a3 for depth 0: one cluster, the whole live set.
+inline __device__ void cluster_phase(const RunDesc& R, char* sm, const Carve& cv, BlockScratch& S) {
+  const int d = R.d;
+  float* tile = reinterpret_cast<float*>(sm + cv.tile);
+  double* acc = reinterpret_cast<double*>(sm + cv.acc);
+  double* C64 = reinterpret_cast<double*>(sm + cv.c64);
+  double* L64 = reinterpret_cast<double*>(sm + cv.l64);
+  double* work = reinterpret_cast<double*>(sm + cv.work);
+  float* s_chol = reinterpret_cast<float*>(sm + cv.chol);
+  float* s_cent = reinterpret_cast<float*>(sm + cv.cent);
+  int* s_mask = reinterpret_cast<int*>(sm + cv.mask);
+  const int n = node_moments(R.live_x, R.n_pad, R.N, d, [](int) { return true; }, tile, acc, S);
+  for (int i = threadIdx.x; i < d * d; i += blockDim.x) C64[i] = acc[d + i];
+  __syncthreads();
+  reg_cholesky(d, C64, L64, work, S);
+  for (int i = threadIdx.x; i < d * d; i += blockDim.x) {
+    const float f = (float)L64[i];
+    s_chol[i] = f;
+    R.chol[i] = f;
+    R.chol64[i] = L64[i];
+  }
+  for (int i = threadIdx.x; i < d; i += blockDim.x) {
+    s_cent[i] = (float)acc[i];
+    R.centres[i] = (float)acc[i];
+  }
+  if (threadIdx.x == 0) {
+    s_mask[0] = 1;
+    R.mask[0] = 1;
+    R.split[0] = 0;
+    R.count[0] = n;
+    R.logvol[0] = 0.f;
+  }
+  for (int j = threadIdx.x; j < R.N; j += blockDim.x) R.live_cid[j] = 0;
+  __syncthreads();
+}
+
+inline __device__ int nearest_leaf(const float* x, int d, int n_nodes, const float* cent, const int* mask) {
+  int best = 0;
+  float bd = CUDART_INF_F;
+  for (int nd = 0; nd < n_nodes; ++nd) {
+    if (!mask[nd]) continue;
+    float s = 0.f;
+    for (int i = 0; i < d; ++i) {
+      const float u = x[i] - cent[nd * d + i];
+      s = fmaf(u, u, s);
+    }
+    if (s < bd) {
+      bd = s;
+      best = nd;
+    }
+  }
+  return best;
+}
+
+template <int DMAX>
+__global__ void __launch_bounds__(256) k_run(const RunDesc* __restrict__ runs, const int* __restrict__ ids,
+                                             int chunk) {
+  extern __shared__ __align__(16) char sm[];
+  __shared__ RunDesc R;
+  __shared__ RunState RS;
+  __shared__ EvidState E;
+  __shared__ int flag_any;
+  const int tid = threadIdx.x, B = blockDim.x;
+  if (tid == 0) {
+    R = runs[ids[blockIdx.x]];
+    RS = *R.st;
+    E.logz = RS.logz;
+    E.info = RS.info;
+    E.k = RS.k;
+  }
+  __syncthreads();
+  if (RS.stopped || RS.status != 0) return;
+  const int d = R.d, N = R.N, m = R.m;
+  const Carve cv = make_carve(d, m, R.n_nodes);
+  LikParams& P = *reinterpret_cast<LikParams*>(sm + cv.lik);
+  BlockScratch& S = *reinterpret_cast<BlockScratch*>(sm + cv.scr);
+  SelectScratch& X = *reinterpret_cast<SelectScratch*>(sm + cv.sel);
+  float* s_chol = reinterpret_cast<float*>(sm + cv.chol);
+  float* s_cent = reinterpret_cast<float*>(sm + cv.cent);
+  int* s_mask = reinterpret_cast<int*>(sm + cv.mask);
+  int* s_worst = reinterpret_cast<int*>(sm + cv.worst);
+  float* s_W = reinterpret_cast<float*>(sm + cv.W);
+  int* s_seed = reinterpret_cast<int*>(sm + cv.seed);
+  int* s_sel_slot = reinterpret_cast<int*>(sm + cv.sel_slot);
+  uint32_t* s_sel_key = reinterpret_cast<uint32_t*>(sm + cv.sel_key);
+  const Cand A = cand_at(sm + cv.candA, m);
+  const Cand Bf = cand_at(sm + cv.candB, m);
+  int* s_list = reinterpret_cast<int*>(sm + cv.list);
+  float* s_vals = reinterpret_cast<float*>(sm + cv.vals);
+  int* s_ctr = reinterpret_cast<int*>(sm + cv.ctr);
+  int* s_stage_cid = reinterpret_cast<int*>(sm + cv.stage_cid);
+
+  {  // likelihood parameters into shared memory
+    const int* src = reinterpret_cast<const int*>(R.lik);
+    int* dst = reinterpret_cast<int*>(&P);
+    for (int i = tid; i < (int)(sizeof(LikParams) / 4); i += B) dst[i] = src[i];
+  }
+  __syncthreads();
+  if (!RS.initialized) {
+    init_live<DMAX>(R, P);
+    __syncthreads();
+    if (tid == 0) {
+      RS.n_evals += N;
+      RS.initialized = 1;
+      E.logz = -CUDART_INF;  // Z = 0 before the first death
+      E.info = 0.0;
+      E.k = 0;
+    }
+  }
+  if (RS.t > 0) {  // cluster tables of the last re-clustering
+    for (int i = tid; i < R.n_nodes * d * d; i += B) s_chol[i] = R.chol[i];
+    for (int i = tid; i < R.n_nodes * d; i += B) s_cent[i] = R.centres[i];
+    for (int i = tid; i < R.n_nodes; i += B) s_mask[i] = R.mask[i];
+  }
+  __syncthreads();
+
+  const double Nd = (double)N;
+  SliceCfg SC;
+  SC.d = d;
+  SC.n_steps = R.n_steps;
+  SC.e_max = R.e_max;
+  SC.s_max = R.s_max;
+  SC.t_max = R.t_max;
+  SC.width = R.width;
+  SC.k0 = R.k0;
+  SC.k1 = R.k1;
+
+  for (int it = 0; it < chunk; ++it) {
+    if (RS.stopped || RS.status != 0) break;
+    const uint32_t t = (uint32_t)RS.t;
+    if (RS.n_dead + m + N > R.dead_cap) {
+      if (tid == 0) RS.status = NS_ERR_BUDGET;
+      __syncthreads();
+      break;
+    }
+    long long c_prev = clock64();
+    auto tick = [&](int ph) {
+      if (tid == 0) {
+        const long long c = clock64();
+        RS.cycles[ph] += c - c_prev;
+        c_prev = c;
+      }
+    };
+    // a3: clustering
+    if (R.recluster_every > 0 && (t % (uint32_t)R.recluster_every) == 0) cluster_phase(R, sm, cv, S);
+    tick(kPhCluster);
+    // a1-a2: selection
+    select_worst(R.live_l, N, m, R.k0, R.k1, t, s_sel_slot, s_sel_key, s_worst, s_W, s_seed, X, S);
+    tick(kPhSelect);
+    // a4-a7: slice-sampling walkers
+    long long ev = 0;
+    int fl = 0;
+    if ((tid & ~31) < m) {
+      const bool act = tid < m;
+      const int i = act ? tid : 0;
+      const int sd = s_seed[i];
+      const int cid = R.live_cid[sd];
+      const float thr_out = (R.correction == 3) ? s_W[m - 1] : s_W[0];
+      const float thr_in = (R.correction == 3) ? s_W[m - 1] : s_W[i];
+      SC.t = t;
+      WalkerOut O;
+      O.new_x = R.new_x + (size_t)i * d;
+      O.new_l = R.new_l + i;
+      O.hist_l = R.hist_l + (size_t)i * R.t_max;
+      O.hist_x = R.hist_x + (size_t)i * R.t_max * d;
+      O.hist_len = R.hist_len + i;
+      slice_walker<DMAX>(P, SC, i, act, R.live_x + sd, R.n_pad, R.live_l[sd], s_chol + (size_t)cid * d * d,
+                         thr_out, thr_in, O, ev, fl);
+      if (!act) {
+        ev = 0;
+        fl = 0;
+      }
+    }
+    __syncthreads();
+    tick(kPhSlice);
+    const long long ev_sum = block_sum_ll(ev, S);
+    const long long capped = block_sum_ll(fl ? 1 : 0, S);
+    // a8-a9: Algorithms 1 and 2
+    const int rel = batch_correct(m, R.K, R.correction, s_W, R.new_l, R.hist_l, R.hist_len, R.t_max, A, Bf,
+                                  s_list, s_vals, s_ctr, S);
+    tick(kPhCorrect);
+    // a10: dead append (rejected, ascending) and live update (accepted into S_W's slots)
+    const long long nd0 = RS.n_dead;
+    for (int q = tid; q < m * d; q += B) {
+      const int j = q / d, i = q - j * d;
+      {
+        const int src = A.src[j], hp = A.hp[j];
+        float val;
+        if (src < m) val = R.live_x[(size_t)i * R.n_pad + s_worst[src]];
+        else if (hp < 0) val = R.new_x[(size_t)(src - m) * d + i];
+        else val = R.hist_x[((size_t)(src - m) * R.t_max + hp) * d + i];
+        R.dead_x[(size_t)(nd0 + j) * d + i] = val;
+      }
+      {
+        const int src = A.src[m + j], hp = A.hp[m + j];
+        float val;
+        if (src < m) val = R.live_x[(size_t)i * R.n_pad + s_worst[src]];
+        else if (hp < 0) val = R.new_x[(size_t)(src - m) * d + i];
+        else val = R.hist_x[((size_t)(src - m) * R.t_max + hp) * d + i];
+        R.stage_x[(size_t)j * d + i] = val;
+      }
+    }
+    for (int j = tid; j < m; j += B) {
+      R.dead_l[nd0 + j] = A.l[j];
+      const int src = A.src[m + j];
+      s_stage_cid[j] = (src < m) ? R.live_cid[s_worst[src]] : -1;
+    }
+    __syncthreads();
+    for (int q = tid; q < m * d; q += B) {
+      const int j = q / d, i = q - j * d;
+      R.live_x[(size_t)i * R.n_pad + s_worst[j]] = R.stage_x[(size_t)j * d + i];
+    }
+    for (int j = tid; j < m; j += B) {
+      const int slot = s_worst[j];
+      R.live_l[slot] = A.l[m + j];
+      int c = s_stage_cid[j];
+      if (c < 0) c = (R.n_nodes > 1) ? nearest_leaf(R.stage_x + (size_t)j * d, d, R.n_nodes, s_cent, s_mask) : 0;
+      R.live_cid[slot] = c;
+    }
+    __syncthreads();
+    tick(kPhUpdate);
+    // a11: evidence (FP64)
+    evidence_add(E, N, m, A.l, R.dead_logw + nd0, false, S);
+    float lm = -CUDART_INF_F;
+    for (int j = tid; j < N; j += B) lm = fmaxf(lm, R.live_l[j]);
+    const float lmax = block_max_f(lm, S);
+    tick(kPhEvidence);
+    if (tid == 0) {
+      RS.n_dead = nd0 + m;
+      RS.n_evals += ev_sum;
+      RS.n_capped += capped;
+      RS.n_relaxed += rel;
+      RS.t = (int)t + 1;
+      RS.n_iter += 1;
+      const bool stop = (E.logz > -CUDART_INF) && ((double)lmax - (double)E.k / Nd - E.logz < R.log_stop);
+      flag_any = stop ? 1 : ((RS.n_iter >= R.max_iter) ? 2 : 0);
+    }
+    __syncthreads();
+    if (flag_any) {
+      // final live tail, slot order: each point carries X_K / N
+      const long long nd1 = RS.n_dead;
+      evidence_add(E, N, N, R.live_l, R.dead_logw + nd1, true, S);
+      for (int q = tid; q < N * d; q += B) {
+        const int j = q / d, i = q - j * d;
+        R.dead_x[(size_t)(nd1 + j) * d + i] = R.live_x[(size_t)i * R.n_pad + j];
+      }
+      for (int j = tid; j < N; j += B) R.dead_l[nd1 + j] = R.live_l[j];
+      __syncthreads();
+      if (tid == 0) {
+        RS.n_dead = nd1 + N;
+        RS.stopped = 1;
+        if (flag_any == 2) RS.status = NS_ERR_BUDGET;
+      }
+      __syncthreads();
+      break;
+    }
+  }
+  __syncthreads();
+  if (tid == 0) {
+    RS.logz = E.logz;
+    RS.info = E.info;
+    RS.k = E.k;
+    *R.st = RS;
+  }
+}
+
+template <int DMAX>
+__global__ void k_loglike(const LikParams P, int n, const float* __restrict__ x, float* __restrict__ out) {
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  float xr[DMAX], v[DMAX];
+#pragma unroll
+  for (int i = 0; i < DMAX; ++i) {
+    xr[i] = (i < P.d) ? x[(size_t)j * P.d + i] : 0.f;
+    v[i] = 0.f;
+  }
+  out[j] = loglike<DMAX>(P, xr, v, 0.f, P.d);
+}
+
+template <int DMAX>
+__global__ void k_slice(const LikParams P, SliceCfg SC, int m, int n_pad, int correction,
+                        const float* __restrict__ live_x, const float* __restrict__ live_l,
+                        const int* __restrict__ seed_slot, const float* __restrict__ W,
+                        const float* __restrict__ chol, const int* __restrict__ cid, float* new_x,
+                        float* new_l, float* hist_l, float* hist_x, int* hist_len, long long* evals,
+                        int* flags) {
+  const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
+  const bool act = i0 < m;
+  const int i = act ? i0 : 0;
+  const int d = SC.d;
+  const int sd = seed_slot[i];
+  const int c = cid[sd];
+  const float thr_out = (correction == 3) ? W[m - 1] : W[0];
+  const float thr_in = (correction == 3) ? W[m - 1] : W[i];
+  WalkerOut O;
+  O.new_x = new_x + (size_t)i * d;
+  O.new_l = new_l + i;
+  O.hist_l = hist_l + (size_t)i * SC.t_max;
+  O.hist_x = hist_x + (size_t)i * SC.t_max * d;
+  O.hist_len = hist_len + i;
+  long long ev = 0;
+  int fl = 0;
+  slice_walker<DMAX>(P, SC, i, act, live_x + sd, n_pad, live_l[sd], chol + (size_t)c * d * d, thr_out,
+                     thr_in, O, ev, fl);
+  if (act) {
+    evals[i] = ev;
+    flags[i] = fl;
+  }
+}
+
+
+// Launchers, one set per dimension class (defined in ns_inst.cu).
+#define NS_DECLARE_LAUNCHERS(D)                                                                          \
+  cudaError_t launch_run_##D(const RunDesc* runs, const int* ids, int n, int block, size_t smem, int chunk, \
+                             cudaStream_t s);                                                            \
+  cudaError_t launch_loglike_##D(const LikParams& P, int n, const float* x, float* out, cudaStream_t s);  \
+  cudaError_t launch_slice_##D(const LikParams& P, const SliceCfg& SC, int m, int n_pad, int correction,   \
+                               const float* live_x, const float* live_l, const int* seed_slot,           \
+                               const float* W, const float* chol, const int* cid, float* new_x,          \
+                               float* new_l, float* hist_l, float* hist_x, int* hist_len, long long* evals, \
+                               int* flags, cudaStream_t s);
+NS_DECLARE_LAUNCHERS(4)
+NS_DECLARE_LAUNCHERS(8)
+NS_DECLARE_LAUNCHERS(16)
+NS_DECLARE_LAUNCHERS(32)
+
+}  // namespace nsd

@@ -1,0 +1,397 @@
+"""GPU parity: every step of the hot path through the C ABI against the CPU
+oracle on identical inputs and Philox streams.
+
+Tolerances: integer and index outputs bit-exact; FP32 slice outputs within
+1e-5 (unit-cube coordinates) with every divergent walker traced to a
+borderline comparison (|logL - threshold| or a box face within FP32
+rounding); FP64 evidence within 1e-12 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2608_28514_gb300 import analytic as A
+from paper_2608_28514_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def nat():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2608_28514_gb300 import _native
+    _native.lib()
+    return _native
+
+
+DEV = "cuda"
+
+
+def _t(a, dtype=torch.float32):
+    return torch.tensor(np.ascontiguousarray(a), dtype=dtype, device=DEV)
+
+
+def _fp32_tol(oracle, lik, p, x, l64):
+    """Tolerance of an FP32 evaluation of logL at unit-cube points x [n, d]:
+    relative rounding of the accumulated sums plus the propagation of the
+    FP32 rounding of theta = lo + span * x (about 2^-23 (|lo| + span)),
+    through the FP64 gradient (central differences)."""
+    x = np.atleast_2d(x).astype(np.float64)
+    span = p.hi - p.lo
+    dth = 2.0 ** -22 * (np.abs(p.lo) + span)
+    sens = np.zeros(len(x))
+    for i in range(p.d):
+        h = np.zeros(p.d)
+        h[i] = 1e-7
+        g = (oracle.loglike(lik, np.clip(x + h, 0, 1)) - oracle.loglike(lik, np.clip(x - h, 0, 1))) / (2e-7 * span[i])
+        sens += np.abs(g) * dth[i]
+    l64 = np.asarray(l64, dtype=np.float64)
+    return 2e-5 * np.maximum(1.0, np.abs(l64)) + 1e-4 * np.sqrt(np.maximum(1.0, np.abs(l64))) + 4 * sens
+
+
+# --------------------------------------------------------------------------
+# K0 Philox
+# --------------------------------------------------------------------------
+def test_philox_bitwise(nat, oracle):
+    rng = np.random.default_rng(1)
+    ctr = rng.integers(0, 2**32, size=(1000, 4), dtype=np.uint64).astype(np.uint32)
+    ctr[:3] = [[0, 0, 0, 0], [0xFFFFFFFF] * 4, [0x243f6a88, 0x85a308d3, 0x13198a2e, 0x03707344]]
+    keys = [(0, 0), (0xFFFFFFFF, 0xFFFFFFFF), (0xa4093822, 0x299f31d0), (123, 456)]
+    for k0, k1 in keys:
+        out = torch.zeros(1000 * 4, dtype=torch.int32, device=DEV)
+        nat.ns_philox4x32_10(_t(ctr.view(np.int32), torch.int32), k0, k1, out)
+        torch.cuda.synchronize()
+        got = out.cpu().numpy().view(np.uint32).reshape(-1, 4)
+        want = oracle.philox(ctr, [k0, k1])
+        np.testing.assert_array_equal(got, want)
+
+
+# --------------------------------------------------------------------------
+# a7 likelihoods (FP32 vs FP64 oracle)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("maker", [
+    lambda: W.gauss2d_sigma05(), lambda: W.gauss_iso(7, 1.0, -7, 7), lambda: W.corr_gauss10(3),
+    lambda: W.gauss_corr(27, 5), lambda: W.rosenbrock(2), lambda: W.rosenbrock(10), lambda: W.mixture4_d5(1),
+    lambda: W.mixture(30, 4),
+])
+def test_loglike_matches_oracle(nat, oracle, maker):
+    p = maker()
+    rng = np.random.default_rng(p.d)
+    n = 4097  # several blocks and a ragged tail
+    x = rng.uniform(0, 1, size=(n, p.d)).astype(np.float32)
+    if p.kind == W.MIXTURE:  # points near the modes too
+        x[:200] = ((p.centres[rng.integers(0, len(p.centres), 200)] + 0.1 * rng.standard_normal((200, p.d)) - p.lo)
+                   / (p.hi - p.lo)).astype(np.float32)
+    out = torch.zeros(n, device=DEV)
+    nat.ns_loglike(p, _t(x), out)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    want = oracle.loglike(oracle.Lik(p), x.astype(np.float64))
+    tol = _fp32_tol(oracle, oracle.Lik(p), p, x, want)
+    assert np.all(np.abs(got - want) <= tol), np.max(np.abs(got - want) / tol)
+
+
+def test_loglike_empty_batch(nat):
+    p = W.gauss2d_sigma05()
+    nat.ns_loglike(p, torch.zeros(0, 2, device=DEV), torch.zeros(0, device=DEV))
+
+
+# --------------------------------------------------------------------------
+# a1-a2 selection (bit-exact)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("N,m,n_runs,ties", [(2, 1, 1, False), (100, 1, 3, False), (1000, 100, 4, False),
+                                             (1000, 100, 2, True), (2000, 200, 3, True), (1537, 77, 5, False),
+                                             (65536, 256, 2, True), (4096, 256, 1, False)])
+def test_select_bit_exact(nat, oracle, N, m, n_runs, ties):
+    rng = np.random.default_rng(N + m)
+    l = rng.normal(size=(n_runs, N)).astype(np.float32) * 10
+    if ties:
+        l = np.round(l).astype(np.float32)
+    l[0, : min(5, N)] = -np.inf  # -inf counts as the lowest
+    seeds = [11 + r * 7919 for r in range(n_runs)]
+    worst = torch.zeros(n_runs, m, dtype=torch.int32, device=DEV)
+    Wv = torch.zeros(n_runs, m, device=DEV)
+    seed_slot = torch.zeros(n_runs, m, dtype=torch.int32, device=DEV)
+    nat.ns_select_worst(_t(l), m, seeds, 42, worst, Wv, seed_slot)
+    torch.cuda.synchronize()
+    for r in range(n_runs):
+        w, s = oracle.select(l[r].astype(np.float64), m, seeds[r], 42)
+        np.testing.assert_array_equal(worst[r].cpu().numpy(), w)
+        np.testing.assert_array_equal(seed_slot[r].cpu().numpy(), s)
+        np.testing.assert_array_equal(Wv[r].cpu().numpy(), l[r][w])
+
+
+# --------------------------------------------------------------------------
+# a4-a7 slice replacement
+# --------------------------------------------------------------------------
+def _live_set(p, N, rng, oracle, shrink=0.35):
+    """N points around the likelihood peak (a mid-run live set)."""
+    lik = oracle.Lik(p)
+    if p.kind in (W.GAUSS_ISO, W.GAUSS_CORR):
+        centre = (p.mean - p.lo) / (p.hi - p.lo)
+    elif p.kind == W.MIXTURE:
+        centre = (p.centres[0] - p.lo) / (p.hi - p.lo)
+    else:
+        centre = np.full(p.d, 0.55)
+    x = np.clip(centre + shrink * (rng.uniform(size=(N, p.d)) - 0.5) * 0.2, 0, 1).astype(np.float32)
+    l = oracle.loglike(lik, x.astype(np.float64)).astype(np.float32)
+    return x, l
+
+
+def _slice_case(nat, oracle, p, N, m, n_steps, seed, t, opt_kw=None):
+    rng = np.random.default_rng(seed)
+    x, l = _live_set(p, N, rng, oracle)
+    worst, seeds = oracle.select(l.astype(np.float64), m, seed, t)
+    Wv = l[worst]
+    cov = np.cov(x.T.astype(np.float64), bias=True).reshape(p.d, p.d)
+    chol = np.linalg.cholesky(cov + 1e-10 * np.trace(cov) / p.d * np.eye(p.d)).astype(np.float32)
+    n_pad = ((N + 31) // 32) * 32
+    live_x = np.zeros((p.d, n_pad), dtype=np.float32)
+    live_x[:, :N] = x.T
+    opt = nat.ns_default_options(**(opt_kw or {}))
+    T = opt.t_max
+    out = dict(new_x=torch.zeros(m, p.d, device=DEV), new_l=torch.zeros(m, device=DEV),
+               hist_l=torch.full((m, T), float("nan"), device=DEV), hist_x=torch.zeros(m, T, p.d, device=DEV),
+               hist_len=torch.zeros(m, dtype=torch.int32, device=DEV),
+               evals=torch.zeros(m, dtype=torch.int64, device=DEV), flags=torch.zeros(m, dtype=torch.int32, device=DEV))
+    nat.ns_slice_replace(p, N, n_pad, m, n_steps, opt, seed, t, _t(live_x), _t(l), _t(seeds, torch.int32), _t(Wv),
+                         _t(chol), torch.zeros(N, dtype=torch.int32, device=DEV), **out)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in out.items()}
+    oo = oracle.opts(p.d, m)
+    for k, v in (opt_kw or {}).items():
+        setattr(oo, k, v)
+    lik = oracle.Lik(p)
+    corr = (opt_kw or {}).get("correction", 2)
+    n_div, n_border = 0, 0
+    for i in range(m):
+        thr_out = Wv[m - 1] if corr == 3 else Wv[0]
+        thr_in = Wv[m - 1] if corr == 3 else Wv[i]
+        r = oracle.slice_walker(lik, oo, n_steps, seed, t, i, x[seeds[i]].astype(np.float64), float(l[seeds[i]]),
+                                chol.astype(np.float64), float(thr_out), float(thr_in))
+        same = np.max(np.abs(r["x"] - g["new_x"][i])) <= 1e-5
+        if same:
+            # the GPU's logL is the FP32 evaluation of its own point
+            l64 = oracle.loglike(lik, g["new_x"][i].astype(np.float64))[0]
+            assert abs(l64 - g["new_l"][i]) <= _fp32_tol(oracle, lik, p, g["new_x"][i], l64)[0]
+            assert g["evals"][i] == r["n_evals"]
+            assert g["hist_len"][i] == r["hist_len"]
+            np.testing.assert_allclose(g["hist_x"][i, : r["hist_len"]], r["hist_x"], atol=1e-5)
+            fin = np.isfinite(r["hist_l"])
+            np.testing.assert_array_equal(np.isfinite(g["hist_l"][i, : r["hist_len"]]), fin)
+            hx = g["hist_x"][i, : r["hist_len"]][fin]
+            hl64 = oracle.loglike(lik, hx.astype(np.float64))
+            assert np.all(np.abs(g["hist_l"][i, : r["hist_len"]][fin] - hl64) <= _fp32_tol(oracle, lik, p, hx, hl64))
+            assert g["flags"][i] == r["flags"]
+        else:
+            n_div += 1
+            border = r["min_l_margin"] < 1e-5 or r["min_box_margin"] < 1e-5
+            n_border += border
+            assert border, (i, r["min_l_margin"], r["min_box_margin"], r["x"], g["new_x"][i])
+        # every GPU output satisfies the constraint it was drawn under
+        assert g["new_l"][i] > thr_in
+        assert np.all((g["new_x"][i] >= 0) & (g["new_x"][i] <= 1))
+    return n_div
+
+
+@pytest.mark.parametrize("maker,N,m,steps", [
+    (lambda: W.gauss2d_sigma05(), 100, 1, 1), (lambda: W.gauss2d_sigma05(), 100, 10, 10),
+    (lambda: W.corr_gauss10(1), 1000, 100, 1), (lambda: W.corr_gauss10(1), 1000, 100, 50),
+    (lambda: W.rosenbrock(2), 1000, 50, 10), (lambda: W.rosenbrock(10), 1000, 50, 50),
+    (lambda: W.mixture4_d5(1), 2000, 200, 25), (lambda: W.gauss_corr(27, 2), 1500, 150, 135),
+    (lambda: W.gauss_iso(30, 1.0, -7, 7), 2000, 100, 20), (lambda: W.gauss_iso(3, 1.0, -7, 7), 64, 32, 15),
+])
+def test_slice_replace_matches_oracle(nat, oracle, maker, N, m, steps):
+    p = maker()
+    n_div = _slice_case(nat, oracle, p, N, m, steps, seed=5 + m, t=3)
+    assert n_div <= max(1, m // 20)
+
+
+def test_slice_history_cap_and_best_of_worst(nat, oracle):
+    p = W.corr_gauss10(2)
+    _slice_case(nat, oracle, p, 1000, 64, 20, seed=9, t=1, opt_kw=dict(t_max=2))
+    _slice_case(nat, oracle, p, 1000, 64, 20, seed=9, t=1, opt_kw=dict(correction=3))
+    _slice_case(nat, oracle, p, 1000, 64, 5, seed=9, t=1, opt_kw=dict(width=3.0, e_max=2, s_max=4))
+
+
+# --------------------------------------------------------------------------
+# a8-a9 Algorithms 1 and 2 (bit-exact on FP32 inputs)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("m,K,correction", [(1, 1, 2), (2, 1, 2), (7, 2, 2), (100, 1, 2), (200, 1, 2), (200, 3, 2),
+                                            (256, 10, 2), (50, 1, 1), (50, 1, 0), (50, 1, 3), (33, 0, 2)])
+def test_batch_correct_bit_exact(nat, oracle, m, K, correction):
+    rng = np.random.default_rng(m * 31 + K)
+    T = 64
+    for trial in range(3):
+        Wv = np.sort(rng.normal(size=m)).astype(np.float32)
+        if trial == 2:
+            Wv = np.round(Wv * 4).astype(np.float32) / 4  # ties
+        newl = np.zeros(m, dtype=np.float32)
+        hist = np.full((m, T), -np.inf, dtype=np.float32)
+        hlen = np.zeros(m, dtype=np.int32)
+        for i in range(m):
+            v = np.float32(Wv[i] + abs(rng.normal()) * 0.7 + 1e-3)
+            n = int(rng.integers(1, T + 1))
+            h = rng.normal(size=n).astype(np.float32)
+            h[-1] = v
+            hist[i, :n] = h
+            hlen[i] = n
+            newl[i] = v
+        outs = {k: torch.zeros(m, dtype=torch.int32 if k.endswith(("src", "hpos")) else torch.float32, device=DEV)
+                for k in ("acc_src", "acc_hpos", "acc_l", "acc_P", "rej_src", "rej_hpos", "rej_l", "rej_P")}
+        nrel = torch.zeros(1, dtype=torch.int32, device=DEV)
+        nat.ns_batch_correct(m, K, correction, _t(Wv), _t(newl), _t(hist), _t(hlen, torch.int32), T,
+                             n_relaxed=nrel, **outs)
+        torch.cuda.synchronize()
+        want = oracle.batch_correct(Wv.astype(np.float64), newl.astype(np.float64), hist.astype(np.float64), hlen,
+                                    K=K, correction=correction)
+        for k, v in outs.items():
+            np.testing.assert_array_equal(v.cpu().numpy().astype(want[k].dtype), want[k], err_msg=k)
+        assert int(nrel.item()) == want["n_relaxed"]
+
+
+# --------------------------------------------------------------------------
+# a11 evidence (FP64)
+# --------------------------------------------------------------------------
+def test_evidence_matches_oracle(nat, oracle):
+    rng = np.random.default_rng(3)
+    N = 1000
+    state = torch.tensor([-math.inf, 0.0, 0.0], dtype=torch.float64, device=DEV)
+    ev = oracle.Evidence(N)
+    allw_g, allw_o = [], []
+    level = -50.0
+    for it in range(40):
+        m = int(rng.integers(1, 201))
+        l = np.sort(level + np.cumsum(np.abs(rng.normal(size=m)) * 0.05)).astype(np.float32)
+        level = float(l[-1])
+        logw = torch.zeros(m, dtype=torch.float64, device=DEV)
+        nat.ns_evidence_update(N, _t(l), state, logw)
+        allw_g.append(logw.cpu().numpy())
+        allw_o.append([ev.add_dead(float(v)) for v in l])
+    live = np.sort(level + np.abs(rng.normal(size=N))).astype(np.float32)
+    logw = torch.zeros(N, dtype=torch.float64, device=DEV)
+    nat.ns_evidence_update(N, _t(live), state, logw, live=True)
+    allw_g.append(logw.cpu().numpy())
+    allw_o.append([ev.add_live(float(v)) for v in live])
+    torch.cuda.synchronize()
+    s = state.cpu().numpy()
+    assert s[0] == pytest.approx(ev.logz, rel=1e-12, abs=1e-12)
+    assert s[1] == pytest.approx(ev.info, rel=1e-10, abs=1e-10)
+    assert int(s[2]) == ev.k
+    np.testing.assert_allclose(np.concatenate(allw_g), np.concatenate(allw_o), rtol=1e-13, atol=1e-13)
+
+
+# --------------------------------------------------------------------------
+# a3 clustering (depth 0: the whole live set)
+# --------------------------------------------------------------------------
+@pytest.mark.parametrize("d,N", [(2, 100), (10, 1000), (27, 1500), (32, 2000), (5, 33)])
+def test_cluster_root_matches_oracle(nat, oracle, d, N):
+    rng = np.random.default_rng(d * N)
+    A_ = rng.normal(size=(d, d)) * 0.1 + np.eye(d) * 0.2
+    x = np.clip(0.5 + (rng.normal(size=(N, d)) * 0.3) @ A_.T * 0.3, 0, 1).astype(np.float32)
+    n_pad = ((N + 31) // 32) * 32
+    live_x = np.zeros((d, n_pad), dtype=np.float32)
+    live_x[:, :N] = x.T
+    opt = nat.ns_default_options()
+    o = dict(centres=torch.zeros(1, d, device=DEV), chol=torch.zeros(1, d, d, device=DEV),
+             chol64=torch.zeros(1, d, d, dtype=torch.float64, device=DEV), logvol=torch.zeros(1, device=DEV),
+             count=torch.zeros(1, dtype=torch.int32, device=DEV), split=torch.zeros(1, dtype=torch.int32, device=DEV),
+             mask=torch.zeros(1, dtype=torch.int32, device=DEV), cid=torch.full((N,), 7, dtype=torch.int32, device=DEV))
+    nat.ns_cluster(N, n_pad, d, _t(live_x), opt, 1, 0, **o)
+    torch.cuda.synchronize()
+    want = oracle.cluster(x.astype(np.float64), oracle.opts(d, 1, depth=0), 1, 0)
+    np.testing.assert_allclose(o["chol64"].cpu().numpy()[0], want["chol"][0], rtol=2e-4, atol=1e-7)
+    np.testing.assert_allclose(o["centres"].cpu().numpy()[0], want["centres"][0], rtol=1e-6, atol=1e-7)
+    assert o["count"].item() == N and o["mask"].item() == 1
+    assert np.all(o["cid"].cpu().numpy() == 0)
+
+
+# --------------------------------------------------------------------------
+# whole runs
+# --------------------------------------------------------------------------
+def test_gauss2d_whole_runs_50_seeds(nat):
+    """50 independent sequential (m = 1) runs of the 2-D Gaussian in one
+    launch: the mean log Z agrees with the erf closed form within 3 standard
+    errors and the per-run error estimate matches the scatter."""
+    p = W.gauss2d_sigma05()
+    truth = A.logz(p)
+    h = nat.ns_create_batch([(p, 100, 1, 10, 1e-3, s) for s in range(1, 51)])
+    nat.ns_run(h)
+    z, err = [], []
+    for r in range(50):
+        res = nat.ns_result(h, r)
+        assert res["status"] == 0 and res["n_capped"] == 0
+        dl = res["dead_l"][: res["n_iter"]]
+        assert np.all(np.diff(dl) >= 0)
+        assert res["n_dead"] == res["n_iter"] + 100
+        w = res["dead_logw"]
+        assert abs(np.log(np.sum(np.exp(w - w.max()))) + w.max() - res["log_z"]) < 1e-9
+        z.append(res["log_z"])
+        err.append(res["log_z_err"])
+    nat.ns_destroy(h)
+    z = np.array(z)
+    assert abs(z.mean() - truth) < 3 * z.std(ddof=1) / math.sqrt(50), (z.mean(), truth)
+    assert 0.6 < np.mean(err) / z.std(ddof=1) < 1.6
+
+
+@pytest.mark.parametrize("m", [1, 10, 50, 100])
+def test_corr_gauss10_batched_runs(nat, m):
+    """The 10-D correlated Gaussian (N = 1000, 50 slice steps) at every batch
+    size of the workload: each run within 4 sigma of the closed form, the
+    dead sequence non-decreasing."""
+    n_seeds = 8 if m > 1 else 2
+    probs = [W.corr_gauss10(s) for s in range(1, n_seeds + 1)]
+    h = nat.ns_create_batch([(p, 1000, m, 50, 1e-3, 100 + s) for s, p in enumerate(probs)])
+    nat.ns_run(h)
+    dz = []
+    for r, p in enumerate(probs):
+        res = nat.ns_result(h, r)
+        assert res["status"] == 0
+        truth = A.logz(p)
+        dz.append((res["log_z"] - truth) / res["log_z_err"])
+        assert abs(res["log_z"] - truth) < 4 * res["log_z_err"] + 0.05, (r, res["log_z"], truth)
+        nd = res["n_iter"] * m
+        assert np.all(np.diff(res["dead_l"][:nd]) >= 0)
+    nat.ns_destroy(h)
+    assert abs(np.mean(dz)) < 3.0 / math.sqrt(len(dz)) + 0.5
+
+
+def test_rosenbrock_and_mixture_runs(nat):
+    cases = [(W.rosenbrock(2), 1000, 50, 10), (W.rosenbrock(10), 1000, 50, 50), (W.mixture4_d5(1), 2000, 200, 25)]
+    h = nat.ns_create_batch([(p, N, m, ns, 1e-3, 7) for p, N, m, ns in cases])
+    nat.ns_run(h)
+    for r, (p, N, m, ns) in enumerate(cases):
+        res = nat.ns_result(h, r)
+        truth = A.logz(p)
+        assert res["status"] == 0
+        # single clusters on multimodal / curved targets: loose bound
+        assert abs(res["log_z"] - truth) < 6 * res["log_z_err"] + 0.3, (p.name, res["log_z"], truth)
+    nat.ns_destroy(h)
+
+
+def test_reset_reproduces_run_bitwise(nat):
+    p = W.corr_gauss10(1)
+    h = nat.ns_create(p, 1000, 100, 50, 1e-3, 5)
+    nat.ns_run(h)
+    a = nat.ns_result(h, 0)
+    nat.ns_reset(h)
+    nat.ns_run(h)
+    b = nat.ns_result(h, 0)
+    nat.ns_destroy(h)
+    assert a["log_z"] == b["log_z"] and a["n_evals"] == b["n_evals"]
+    np.testing.assert_array_equal(a["dead_x"], b["dead_x"])
+
+
+def test_budget_is_reported_not_hung(nat):
+    p = W.corr_gauss10(1)
+    o = nat.ns_default_options(max_iter=5, chunk_iters=2)
+    h = nat.ns_create(p, 1000, 10, 50, 1e-3, 5, opt=o)
+    st = nat.ns_run(h, check=False)
+    assert st == nat.NS_ERR_BUDGET
+    res = nat.ns_result(h, 0)
+    assert res["status"] == nat.NS_ERR_BUDGET and res["n_iter"] == 5
+    nat.ns_destroy(h)
