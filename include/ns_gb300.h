@@ -211,6 +211,40 @@ const char* ns_last_error(const ns_handle* h);
 /* Frees every device and host resource of the handle.  NULL is ignored. */
 void ns_destroy(ns_handle* h);
 
+/* ---- a whole run without any device allocation -------------------------
+ * The paper has no counterpart to this call; it exists for callers that
+ * cannot use cudaMalloc: a library loaded into a host program whose device
+ * memory is already reserved by another allocator (so a fresh cudaMalloc
+ * fails or fragments that pool), or code on a latency-critical path where
+ * cudaMalloc's implicit device-wide synchronisation would stall other work.
+ *
+ * ns_run_noalloc does what ns_create + ns_run + ns_summary do for one run,
+ * but all of its working memory (live set, walker staging, history, cluster
+ * tables, run state) lives in one file-scope device array of
+ * NS_NOALLOC_SCRATCH_BYTES that every GPU loading the library holds until
+ * the process exits.  It calls no cudaMalloc, cudaFree or other allocating
+ * routine.  The caller provides the outputs: dead_x [dead_cap*d],
+ * dead_logl [dead_cap] and dead_logw [dead_cap] in device memory, filled as
+ * in ns_result (dead points in death order, then the final live points), and
+ * `out` on the host, whose three sample pointers are set to NULL (the
+ * samples are in the caller's device arrays).  `problem` and `opt` are host
+ * structs as for ns_create_batch (opt NULL = defaults; opt->dead_cap is
+ * ignored, dead_cap sizes the caller's arrays).
+ *
+ * Limits and errors: a run whose working set does not fit the array
+ * (roughly d <= 32, N <= 4096, m <= 256 with the default history) is
+ * rejected with NS_ERR_ARG and a message giving the bytes it needs; so is
+ * dead_cap < N + m.  Every call shares the one array: it is re-initialised
+ * at the start of each call, and calls whose GPU work overlaps (two host
+ * threads, or two streams) race on it and give wrong results -- serialise
+ * them.  The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture begins.  The call waits for the run to finish
+ * on `stream`. */
+#define NS_NOALLOC_SCRATCH_BYTES (8u << 20)
+ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt, float* dead_x, float* dead_logl,
+                         double* dead_logw, long long dead_cap, ns_result_t* out, void* stream);
+
 /* ---- step-level calls (device buffers, asynchronous, no allocation) ----
  * These run the same device code as ns_run, one step at a time, on caller
  * buffers.  Layouts: live_x is structure-of-arrays [d][n_pad] (n_pad >= N);

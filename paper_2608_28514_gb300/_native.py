@@ -94,6 +94,8 @@ def lib():
     L.ns_result.argtypes = [_vp, C.c_int, C.POINTER(NsResult)]
     L.ns_summary.argtypes = [_vp, C.c_int, C.POINTER(NsResult)]
     L.ns_phase_cycles.argtypes = [_vp, C.c_int, C.POINTER(C.c_longlong)]
+    L.ns_run_noalloc.argtypes = [C.POINTER(NsProblem), C.POINTER(NsOptions), _vp, _vp, _vp, C.c_longlong,
+                                 C.POINTER(NsResult), _vp]
     L.ns_n_runs.argtypes = [_vp]
     L.ns_n_runs.restype = C.c_int
     L.ns_last_run_ms.argtypes = [_vp, C.POINTER(C.c_double)]
@@ -115,7 +117,7 @@ def lib():
     L.ns_cluster.argtypes = [C.c_int, C.c_int, C.c_int, _vp, C.POINTER(NsOptions), C.c_uint64, C.c_uint32,
                              _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
     for name in ("ns_default_options", "ns_create", "ns_create_batch", "ns_run", "ns_reset", "ns_result", "ns_summary",
-                 "ns_phase_cycles",
+                 "ns_phase_cycles", "ns_run_noalloc",
                  "ns_last_run_ms", "ns_get_stats", "ns_philox4x32_10", "ns_loglike", "ns_select_worst", "ns_slice_replace",
                  "ns_batch_correct", "ns_evidence_update", "ns_cluster"):
         getattr(L, name).restype = C.c_int
@@ -314,6 +316,37 @@ def ns_destroy(h):
     if h is not None and h.ptr is not None and h.ptr.value:
         lib().ns_destroy(h.ptr)
         h.ptr = _vp()
+
+
+def ns_run_noalloc(problem, n_live, m, n_slice_steps, stop_frac, seed, dead_x, dead_logl, dead_logw,
+                   opt=None, stream=None, check=True):
+    """One whole run that allocates no device memory: the library works in
+    its fixed static device array and writes the samples into the caller's
+    device tensors dead_x [cap, d], dead_logl [cap], dead_logw [cap]
+    (float32, float32, float64).  For callers that cannot allocate device
+    memory themselves (see ns_run_noalloc in include/ns_gb300.h).  Returns
+    the scalar results; samples stay in the caller's tensors."""
+    keep = _Keep()
+    lik = likelihood_struct(problem, keep)
+    pr = NsProblem()
+    pr.lik = C.pointer(lik)
+    pr.lo = keep.dptr(problem.lo)
+    pr.hi = keep.dptr(problem.hi)
+    pr.d = int(problem.d)
+    pr.n_live = int(n_live)
+    pr.m = int(m)
+    pr.n_slice_steps = int(n_slice_steps)
+    pr.stop_frac = float(stop_frac)
+    pr.seed = int(seed) & (2**64 - 1)
+    r = NsResult()
+    cap = int(dead_logl.numel())
+    st = lib().ns_run_noalloc(C.byref(pr), C.byref(opt) if opt is not None else None, _ptr(dead_x),
+                              _ptr(dead_logl), _ptr(dead_logw), cap, C.byref(r), _stream_ptr(stream))
+    if check:
+        _check(st)
+    return dict(log_z=r.log_z, log_z_err=r.log_z_err, info=r.info_h, n_dead=r.n_dead, n_evals=r.n_evals,
+                n_iter=r.n_iter, n_relaxed=r.n_relaxed, n_reeval=r.n_reeval, n_capped=r.n_capped,
+                status=r.status, d=r.d, ret=st)
 
 
 # --------------------------------------------------------------------------

@@ -755,6 +755,177 @@ void ns_destroy(ns_handle* h) {
   delete h;
 }
 
+// ---- a whole run in a static device array (no allocation) -------------------
+}  // extern "C"
+
+namespace {
+
+// One fixed array per GPU that loads the library; its host-side name is a
+// stand-in, so the device address is looked up once per device.
+static __device__ __align__(256) unsigned char g_noalloc_scratch[NS_NOALLOC_SCRATCH_BYTES];
+std::mutex g_noalloc_mu;
+void* g_noalloc_addr[256] = {};
+
+}  // namespace
+
+extern "C" {
+
+ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt_in, float* dead_x, float* dead_logl,
+                         double* dead_logw, long long dead_cap, ns_result_t* out, void* stream) {
+  if (!problem || !out || !dead_x || !dead_logl || !dead_logw) {
+    set_err(nullptr, "ns_run_noalloc: NULL argument");
+    return NS_ERR_ARG;
+  }
+  ns_options opt;
+  if (opt_in) opt = *opt_in;
+  else ns_default_options(&opt);
+  ns_status st = check_opts(opt, nullptr);
+  if (st != NS_OK) return st;
+  st = check_problem(*problem, nullptr);
+  if (st != NS_OK) return st;
+  const ns_problem& p = *problem;
+  const int d = p.d, N = p.n_live, m = p.m, n_pad = ((N + 31) / 32) * 32;
+  if (dead_cap < (long long)N + m) {
+    set_err(nullptr, "ns_run_noalloc: dead_cap = %lld is below N + m = %d", dead_cap, N + m);
+    return NS_ERR_ARG;
+  }
+  const int n_nodes = (1 << (opt.depth + 1)) - 1;
+  // layout of the static array for this run
+  size_t total = 0;
+  auto take = [&](size_t bytes) {
+    size_t o = total;
+    total += (bytes + 255) & ~(size_t)255;
+    return o;
+  };
+  const size_t o_lik = take(sizeof(LikParams)), o_desc = take(sizeof(RunDesc)), o_state = take(sizeof(RunState)),
+               o_ids = take(sizeof(int)), o_live_x = take(sizeof(float) * (size_t)d * n_pad),
+               o_live_l = take(sizeof(float) * N), o_live_cid = take(sizeof(int) * N),
+               o_new_x = take(sizeof(float) * (size_t)m * d), o_new_l = take(sizeof(float) * m),
+               o_hist_l = take(sizeof(float) * (size_t)m * opt.t_max),
+               o_hist_x = take(sizeof(float) * (size_t)m * opt.t_max * d), o_hist_len = take(sizeof(int) * m),
+               o_stage_x = take(sizeof(float) * (size_t)m * d), o_centres = take(sizeof(float) * n_nodes * d),
+               o_chol = take(sizeof(float) * n_nodes * d * d), o_chol64 = take(sizeof(double) * n_nodes * d * d),
+               o_logvol = take(sizeof(float) * n_nodes), o_count = take(sizeof(int) * n_nodes),
+               o_split = take(sizeof(int) * n_nodes), o_mask = take(sizeof(int) * n_nodes);
+  if (total > (size_t)NS_NOALLOC_SCRATCH_BYTES) {
+    set_err(nullptr, "ns_run_noalloc: this run needs %zu bytes of working memory; the static array holds %u",
+            total, (unsigned)NS_NOALLOC_SCRATCH_BYTES);
+    return NS_ERR_ARG;
+  }
+  int dev = 0;
+  NS_CUDA(cudaGetDevice(&dev), nullptr);
+  if (dev < 0 || dev >= 256) {
+    set_err(nullptr, "ns_run_noalloc: device ordinal %d out of range", dev);
+    return NS_ERR_ARG;
+  }
+  char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lk(g_noalloc_mu);
+    if (!g_noalloc_addr[dev]) {
+      void* ptr = nullptr;
+      cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr) {
+        set_err(nullptr, "ns_run_noalloc: cudaGetSymbolAddress failed: %s", cudaGetErrorString(e));
+        return NS_ERR_CUDA;
+      }
+      g_noalloc_addr[dev] = ptr;
+    }
+    base = static_cast<char*>(g_noalloc_addr[dev]);
+  }
+  RunDesc R;
+  std::memset(&R, 0, sizeof(R));
+  R.d = d;
+  R.N = N;
+  R.m = m;
+  R.n_pad = n_pad;
+  R.n_steps = p.n_slice_steps;
+  R.depth = opt.depth;
+  R.n_nodes = n_nodes;
+  R.recluster_every = opt.recluster_every > 0 ? opt.recluster_every : std::max(1, 100 / m);
+  R.n_min = opt.n_min > 0 ? opt.n_min : d + 1;
+  R.kmeans_iters = opt.kmeans_iters;
+  R.correction = opt.correction;
+  R.K = opt.history_iters;
+  R.t_max = opt.t_max;
+  R.e_max = opt.e_max;
+  R.s_max = opt.s_max;
+  R.k0 = (uint32_t)(p.seed & 0xFFFFFFFFull);
+  R.k1 = (uint32_t)(p.seed >> 32);
+  R.width = (float)opt.width;
+  R.vol_frac = (float)opt.vol_frac;
+  R.log_stop = std::log(p.stop_frac);
+  R.max_iter = opt.max_iter;
+  R.dead_cap = dead_cap;
+  R.lik = reinterpret_cast<const LikParams*>(base + o_lik);
+  R.live_x = reinterpret_cast<float*>(base + o_live_x);
+  R.live_l = reinterpret_cast<float*>(base + o_live_l);
+  R.live_cid = reinterpret_cast<int*>(base + o_live_cid);
+  R.new_x = reinterpret_cast<float*>(base + o_new_x);
+  R.new_l = reinterpret_cast<float*>(base + o_new_l);
+  R.hist_l = reinterpret_cast<float*>(base + o_hist_l);
+  R.hist_x = reinterpret_cast<float*>(base + o_hist_x);
+  R.hist_len = reinterpret_cast<int*>(base + o_hist_len);
+  R.stage_x = reinterpret_cast<float*>(base + o_stage_x);
+  R.dead_x = dead_x;
+  R.dead_l = dead_logl;
+  R.dead_logw = dead_logw;
+  R.centres = reinterpret_cast<float*>(base + o_centres);
+  R.chol = reinterpret_cast<float*>(base + o_chol);
+  R.chol64 = reinterpret_cast<double*>(base + o_chol64);
+  R.logvol = reinterpret_cast<float*>(base + o_logvol);
+  R.count = reinterpret_cast<int*>(base + o_count);
+  R.split = reinterpret_cast<int*>(base + o_split);
+  R.mask = reinterpret_cast<int*>(base + o_mask);
+  R.st = reinterpret_cast<RunState*>(base + o_state);
+  const LikParams P = make_lik(*p.lik, p.lo, p.hi, d);
+  const int id0 = 0;
+  cudaStream_t s = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: upload this run's
+  // descriptor and start its state from zero
+  NS_CUDA(cudaMemcpyAsync(base + o_lik, &P, sizeof(P), cudaMemcpyHostToDevice, s), nullptr);
+  NS_CUDA(cudaMemcpyAsync(base + o_desc, &R, sizeof(R), cudaMemcpyHostToDevice, s), nullptr);
+  NS_CUDA(cudaMemcpyAsync(base + o_ids, &id0, sizeof(int), cudaMemcpyHostToDevice, s), nullptr);
+  NS_CUDA(cudaMemsetAsync(base + o_state, 0, sizeof(RunState), s), nullptr);
+  const RunDesc* d_desc = reinterpret_cast<const RunDesc*>(base + o_desc);
+  const int* d_ids = reinterpret_cast<const int*>(base + o_ids);
+  const int block = block_for_m(m);
+  const size_t smem = make_carve(d, m, n_nodes).total;
+  const int chunk = opt.chunk_iters > 0 ? opt.chunk_iters : 1000;
+  const long long max_rounds = opt.max_iter / chunk + 2;
+  RunState hs;
+  std::memset(&hs, 0, sizeof(hs));
+  for (long long round = 0;; ++round) {
+    cudaError_t e;
+    switch (dmax_class(d)) {
+      case 4: e = launch_run_4(d_desc, d_ids, 1, block, smem, chunk, s); break;
+      case 8: e = launch_run_8(d_desc, d_ids, 1, block, smem, chunk, s); break;
+      case 16: e = launch_run_16(d_desc, d_ids, 1, block, smem, chunk, s); break;
+      default: e = launch_run_32(d_desc, d_ids, 1, block, smem, chunk, s); break;
+    }
+    NS_CUDA(e, nullptr);
+    NS_CUDA(cudaMemcpyAsync(&hs, base + o_state, sizeof(RunState), cudaMemcpyDeviceToHost, s), nullptr);
+    NS_CUDA(cudaStreamSynchronize(s), nullptr);
+    if (hs.stopped || hs.status != 0 || round + 1 > max_rounds) break;
+  }
+  std::memset(out, 0, sizeof(*out));
+  out->log_z = hs.logz;
+  out->log_z_err = std::sqrt(hs.info > 0 ? hs.info / N : 0.0);
+  out->info_h = hs.info;
+  out->n_dead = hs.n_dead;
+  out->n_evals = hs.n_evals;
+  out->n_iter = hs.n_iter;
+  out->n_relaxed = hs.n_relaxed;
+  out->n_reeval = hs.n_reeval;
+  out->n_capped = hs.n_capped;
+  out->status = hs.status;
+  out->d = d;
+  if (hs.status != 0) {
+    set_err(nullptr, "ns_run_noalloc: the run ended with status %d", hs.status);
+    return (ns_status)hs.status;
+  }
+  return NS_OK;
+}
+
 // ---- step-level entry points ----------------------------------------------
 ns_status ns_philox4x32_10(const uint32_t* ctr, uint32_t key0, uint32_t key1, int n, uint32_t* out, void* stream) {
   if (n < 0 || (n > 0 && (!ctr || !out))) {
