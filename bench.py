@@ -52,17 +52,23 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--runs", type=int, default=304, help="independent runs per GPU")
+    ap.add_argument("--runs", type=int, default=0,
+                    help="independent runs per GPU (0: as many as the GPU holds resident, one wave)")
     ap.add_argument("--m", type=int, default=M)
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--chunk", type=int, default=1000)
+    ap.add_argument("--profile", action="store_true",
+                    help="profiling case: short launches (--chunk), dead buffers of --dead-cap, run "
+                         "status ignored; prints no bench line")
+    ap.add_argument("--dead-cap", type=int, default=0)
     return ap.parse_args()
 
 
 def workload_config(args, runs):
     return {"workload": f"10-D correlated Gaussian, prior [-10,10]^10, N_live={N_LIVE}, m={args.m}, "
-                        f"{N_STEPS} slice steps, stop 1e-3; {runs} independent seeded runs per GPU",
+                        f"{N_STEPS} slice steps, stop 1e-3; {runs} independent seeded runs per GPU "
+                        f"(as many as are resident at once)",
             "d": D, "n_live": N_LIVE, "m": args.m, "slice_steps": N_STEPS, "stop_frac": STOP,
             "runs_per_gpu": runs, "correction": "sorting + history (K=1)",
             "l2": "flushed between timed steps (256 MiB write)"}
@@ -220,12 +226,25 @@ def main():
     if world > 1:
         dist.init_process_group("nccl")
     R = args.runs
+    if R <= 0:
+        per_sm = nat.ns_resident_runs_per_sm(D, args.m, 0)
+        R = max(1, per_sm) * torch.cuda.get_device_properties(local).multi_processor_count
     seeds = [1 + rank * R + r for r in range(R)]
     probs = [W.corr_gauss10(s) for s in seeds]
     truths = np.array([analytic.logz(p) for p in probs])
     runs = [(p, N_LIVE, args.m, N_STEPS, STOP, s) for p, s in zip(probs, seeds)]
-    opt = nat.ns_default_options(chunk_iters=args.chunk)
+    opt = nat.ns_default_options(chunk_iters=args.chunk, dead_cap=args.dead_cap)
+    if args.profile:
+        opt.max_iter = 3 * args.chunk
     h = nat.ns_create_batch(runs, opt)
+    if args.profile:
+        for _ in range(3):
+            nat.ns_reset(h)
+            nat.ns_run(h, check=False)
+        torch.cuda.synchronize()
+        print("profile case done", nat.ns_get_stats(h))
+        nat.ns_destroy(h)
+        return
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
@@ -302,7 +321,7 @@ def main():
         except (ValueError, KeyError):
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                "traffic": traffic, "kernel": "k_run<16>",
+                "traffic": traffic, "kernel": "nsd::k_run<10>",
                 "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (recipe unit counts, max clock)",
                 "flop_per_eval": FLOP_PER_EVAL}
 

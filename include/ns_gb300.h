@@ -184,6 +184,12 @@ ns_status ns_summary(const ns_handle* h, int run, ns_result_t* out);
  * stop test; out[6..7] = 0.  Valid after ns_run. */
 ns_status ns_phase_cycles(const ns_handle* h, int run, long long* out);
 
+/* How many runs of dimension d, batch m and tree depth one SM of the
+ * current device holds at once (one thread block each); -1 on error.
+ * ns_create_batch with (this) x (SM count) runs of that shape fills the
+ * GPU in a single wave. */
+int ns_resident_runs_per_sm(int d, int m, int depth);
+
 /* Number of runs in the handle, or -1 for NULL. */
 int ns_n_runs(const ns_handle* h);
 
@@ -274,13 +280,18 @@ ns_status ns_select_worst(int n_runs, int N, int m, const float* logl, const uin
  * W[0] and shrinkage against W[i] (W[m-1] for both under correction 3).
  * Outputs (device): new_x [m][d], new_l [m], the last step's shrink history
  * hist_l [m][t_max], hist_x [m][t_max][d], hist_len [m], evals [m] and
- * flags [m] (bit0 step-out cap, bit1 shrink cap). */
+ * flags [m] (bit0 step-out cap, bit1 shrink cap).  dir_scratch: device
+ * working memory of ns_slice_scratch_bytes(d, m, n_steps) bytes, 16-byte
+ * aligned, owned by the caller (it receives the drawn directions). */
 ns_status ns_slice_replace(const ns_likelihood* lik, const double* lo, const double* hi, int d,
                            int N, int n_pad, int m, int n_steps, const ns_options* opt,
                            uint64_t seed, uint32_t t, const float* live_x, const float* live_l,
                            const int* seed_slot, const float* W, const float* chol, const int* cid,
                            float* new_x, float* new_l, float* hist_l, float* hist_x, int* hist_len,
-                           long long* evals, int* flags, void* stream);
+                           long long* evals, int* flags, float* dir_scratch, void* stream);
+
+/* Bytes of dir_scratch that ns_slice_replace needs (0 for bad sizes). */
+size_t ns_slice_scratch_bytes(int d, int m, int n_steps);
 
 /* a8-a9 (Algorithms 1 and 2): 2m candidates -- the removed points W [m]
  * (candidates 0..m-1) and the new points new_l [m] of walkers 0..m-1

@@ -96,6 +96,8 @@ def lib():
     L.ns_phase_cycles.argtypes = [_vp, C.c_int, C.POINTER(C.c_longlong)]
     L.ns_run_noalloc.argtypes = [C.POINTER(NsProblem), C.POINTER(NsOptions), _vp, _vp, _vp, C.c_longlong,
                                  C.POINTER(NsResult), _vp]
+    L.ns_resident_runs_per_sm.argtypes = [C.c_int, C.c_int, C.c_int]
+    L.ns_resident_runs_per_sm.restype = C.c_int
     L.ns_n_runs.argtypes = [_vp]
     L.ns_n_runs.restype = C.c_int
     L.ns_last_run_ms.argtypes = [_vp, C.POINTER(C.c_double)]
@@ -111,7 +113,9 @@ def lib():
                                   _vp, _vp]
     L.ns_slice_replace.argtypes = [C.POINTER(NsLikelihood), C.POINTER(C.c_double), C.POINTER(C.c_double),
                                    C.c_int, C.c_int, C.c_int, C.c_int, C.c_int, C.POINTER(NsOptions), C.c_uint64,
-                                   C.c_uint32] + [_vp] * 14
+                                   C.c_uint32] + [_vp] * 15
+    L.ns_slice_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
+    L.ns_slice_scratch_bytes.restype = C.c_size_t
     L.ns_batch_correct.argtypes = [C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, C.c_int] + [_vp] * 10
     L.ns_evidence_update.argtypes = [C.c_int, C.c_int, _vp, _vp, _vp, C.c_int, _vp]
     L.ns_cluster.argtypes = [C.c_int, C.c_int, C.c_int, _vp, C.POINTER(NsOptions), C.c_uint64, C.c_uint32,
@@ -266,6 +270,10 @@ def ns_reset(h, stream=None):
     _check(lib().ns_reset(h.ptr, _stream_ptr(stream)), h.ptr)
 
 
+def ns_resident_runs_per_sm(d, m, depth=0):
+    return int(lib().ns_resident_runs_per_sm(int(d), int(m), int(depth)))
+
+
 def ns_last_run_ms(h):
     ms = C.c_double()
     _check(lib().ns_last_run_ms(h.ptr, C.byref(ms)), h.ptr)
@@ -373,8 +381,18 @@ def ns_select_worst(logl, m, seeds, t, worst, W, seed_slot, stream=None):
                                  _ptr(seed_slot), _stream_ptr(stream)))
 
 
+def ns_slice_scratch_bytes(d, m, n_steps):
+    return int(lib().ns_slice_scratch_bytes(int(d), int(m), int(n_steps)))
+
+
 def ns_slice_replace(problem, N, n_pad, m, n_steps, opt, seed, t, live_x, live_l, seed_slot, W, chol, cid,
-                     new_x, new_l, hist_l, hist_x, hist_len, evals, flags, stream=None):
+                     new_x, new_l, hist_l, hist_x, hist_len, evals, flags, dir_scratch=None, stream=None):
+    """dir_scratch: a device tensor of ns_slice_scratch_bytes(d, m, n_steps)
+    bytes; allocated here with torch when not given."""
+    if dir_scratch is None:
+        import torch
+        nb = ns_slice_scratch_bytes(problem.d, m, n_steps)
+        dir_scratch = torch.empty((nb + 3) // 4, dtype=torch.float32, device=new_x.device)
     keep = _Keep()
     lik = likelihood_struct(problem, keep)
     _check(lib().ns_slice_replace(C.byref(lik), keep.dptr(problem.lo), keep.dptr(problem.hi), int(problem.d),
@@ -382,7 +400,7 @@ def ns_slice_replace(problem, N, n_pad, m, n_steps, opt, seed, t, live_x, live_l
                                   int(seed) & (2**64 - 1), int(t) & 0xFFFFFFFF, _ptr(live_x), _ptr(live_l),
                                   _ptr(seed_slot), _ptr(W), _ptr(chol), _ptr(cid), _ptr(new_x), _ptr(new_l),
                                   _ptr(hist_l), _ptr(hist_x), _ptr(hist_len), _ptr(evals), _ptr(flags),
-                                  _stream_ptr(stream)))
+                                  _ptr(dir_scratch), _stream_ptr(stream)))
 
 
 def ns_batch_correct(m, K, correction, W, new_l, hist_l, hist_len, t_max, acc_src, acc_hpos, acc_l, acc_P,

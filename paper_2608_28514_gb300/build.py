@@ -1,6 +1,6 @@
 """Build the sm_103a shared library ``libns_gb300.so`` in-tree.
 
-Five translation units compile in parallel (the host library and one
+The translation units compile in parallel (the host library and one
 instantiation of the per-dimension kernels for each register class), then
 nvcc links them with the static CUDA runtime.  Objects go to ``_build/``.
 """
@@ -15,7 +15,7 @@ BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(HERE, "libns_gb300.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "-Xcompiler", "-fPIC", "--expt-relaxed-constexpr"]
-CLASSES = (4, 8, 16, 32)
+CLASSES = (2, 4, 6, 8, 10, 12, 16, 20, 24, 28, 32)
 
 
 def _sources():
@@ -34,6 +34,8 @@ def _deps():
 
 def _compile(src, obj, extra, nvcc, verbose):
     cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
+    if os.environ.get("NS_RUN_MINB"):
+        cmd.insert(1, "-DNS_RUN_MINB=" + str(int(os.environ["NS_RUN_MINB"])))
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)
@@ -49,7 +51,8 @@ def build(force=False, verbose=False):
     os.makedirs(BUILD, exist_ok=True)
     nvcc = os.environ.get("NVCC", "nvcc")
     logs = []
-    with cf.ThreadPoolExecutor(max_workers=len(CLASSES) + 1) as ex:
+    workers = max(2, min(len(CLASSES) + 1, os.cpu_count() or 4))
+    with cf.ThreadPoolExecutor(max_workers=workers) as ex:
         futs = [ex.submit(_compile, s, o, e, nvcc, verbose) for s, o, e in _sources()]
         for f in futs:
             logs.append(f.result())

@@ -95,9 +95,12 @@ __device__ __forceinline__ float u24_open0(uint32_t w) {
 __device__ __forceinline__ int u_index(uint32_t w, int n) { return (int)__umulhi(w, (uint32_t)n); }
 
 // ---------------------------------------------------------------------------
-// Likelihoods (FP32).  theta_i = lo_i + span_i * u_i; constants folded so
-// that each coordinate costs one FMA: c_i = lo_i - mean_i (Gaussians),
-// cm_ki = lo_i - centre_ki (mixture).
+// Likelihoods (FP32).  theta_i = lo_i + span_i * u_i with u the unit-cube
+// point; constants are folded so that each coordinate costs one FMA:
+// c_i = lo_i - mean_i (Gaussians), cm_ki = lo_i - centre_ki (mixture).
+// Every array is zero beyond d and every matrix has the fixed stride
+// kMaxDim, so a register class DMAX >= d needs no bounds tests: padded
+// coordinates are 0 and contribute 0.
 // ---------------------------------------------------------------------------
 struct LikParams {
   int kind, d, n_modes, pad0;
@@ -107,80 +110,103 @@ struct LikParams {
   float lo[kMaxDim];
   float span[kMaxDim];
   float c[kMaxDim];
-  float Lp[kMaxDim * kMaxDim];     // [i*d + j], lower, inverse covariance = L L^T
-  float cm[kMaxModes * kMaxDim];   // [k*d + i]
+  float rw[kMaxDim];               // Rosenbrock: 1 for the d-1 chain links, else 0
+  float2 LpP[(kMaxDim / 2) * kMaxDim];  // [jp*kMaxDim + i] = (L[i][2jp], L[i][2jp+1]), L L^T = inverse covariance
+  float cm[kMaxModes * kMaxDim];   // [k*kMaxDim + i]
 };
 
-// logL at u = x + tp * v (u computed per coordinate with one FMA).
+__device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
+__device__ __forceinline__ float2 ld2(const float* p) { return *reinterpret_cast<const float2*>(p); }
+
+// u = x + tp v (two coordinates per packed FMA) and whether u is in the unit
+// cube.
 template <int DMAX>
-__device__ __forceinline__ float loglike(const LikParams& P, const float (&x)[DMAX],
-                                         const float (&v)[DMAX], float tp, int d) {
+__device__ __forceinline__ bool candidate(const float (&x)[DMAX], const float (&v)[DMAX], float tp,
+                                          float (&u)[DMAX]) {
+  const float2 t2 = f2(tp, tp);
+#pragma unroll
+  for (int i = 0; i < DMAX; i += 2) {
+    const float2 r = __ffma2_rn(t2, f2(v[i], v[i + 1]), f2(x[i], x[i + 1]));
+    u[i] = r.x;
+    u[i + 1] = r.y;
+  }
+  float mn = u[0], mx = u[0];
+#pragma unroll
+  for (int i = 1; i < DMAX; ++i) {
+    mn = fminf(mn, u[i]);
+    mx = fmaxf(mx, u[i]);
+  }
+  return (mn >= 0.f) && (mx <= 1.f);
+}
+
+// logL at the unit-cube point u (zero beyond d).  Pairs of coordinates (and
+// pairs of rows of L^T) go through one packed FMA each.
+template <int DMAX>
+__device__ __forceinline__ float loglike_u(const LikParams& P, const float (&u)[DMAX]) {
   float ll;
   switch (P.kind) {
     case kIso: {
-      float s = 0.f;
+      float2 acc = f2(0.f, 0.f);
 #pragma unroll
-      for (int i = 0; i < DMAX; ++i)
-        if (i < d) {
-          const float y = fmaf(P.span[i], fmaf(tp, v[i], x[i]), P.c[i]);
-          s = fmaf(y, y, s);
-        }
-      ll = -s * P.inv2s2;
+      for (int i = 0; i < DMAX; i += 2) {
+        const float2 y = __ffma2_rn(ld2(P.span + i), f2(u[i], u[i + 1]), ld2(P.c + i));
+        acc = __ffma2_rn(y, y, acc);
+      }
+      ll = -(acc.x + acc.y) * P.inv2s2;
       break;
     }
     case kCorr: {
       float y[DMAX];
 #pragma unroll
-      for (int i = 0; i < DMAX; ++i) y[i] = (i < d) ? fmaf(P.span[i], fmaf(tp, v[i], x[i]), P.c[i]) : 0.f;
-      float s = 0.f;
+      for (int i = 0; i < DMAX; i += 2) {
+        const float2 q = __ffma2_rn(ld2(P.span + i), f2(u[i], u[i + 1]), ld2(P.c + i));
+        y[i] = q.x;
+        y[i + 1] = q.y;
+      }
+      float2 acc = f2(0.f, 0.f);
 #pragma unroll
-      for (int j = 0; j < DMAX; ++j)
-        if (j < d) {
-          float z = 0.f;
+      for (int jp = 0; jp < DMAX / 2; ++jp) {
+        // (z_{2jp}, z_{2jp+1}) = sum_{i >= 2jp} (L[i][2jp], L[i][2jp+1]) y_i
+        float2 z = f2(0.f, 0.f);
 #pragma unroll
-          for (int i = j; i < DMAX; ++i)
-            if (i < d) z = fmaf(P.Lp[i * d + j], y[i], z);
-          s = fmaf(z, z, s);
-        }
-      ll = -0.5f * s;
+        for (int i = 2 * jp; i < DMAX; ++i) z = __ffma2_rn(P.LpP[jp * kMaxDim + i], f2(y[i], y[i]), z);
+        acc = __ffma2_rn(z, z, acc);
+      }
+      ll = -0.5f * (acc.x + acc.y);
       break;
     }
     case kRosen: {
-      float s = 0.f;
-      float th_prev = 0.f;
+      float th[DMAX];
 #pragma unroll
-      for (int i = 0; i < DMAX; ++i)
-        if (i < d) {
-          const float th = fmaf(P.span[i], fmaf(tp, v[i], x[i]), P.lo[i]);
-          if (i > 0) {
-            const float p = P.a - th_prev;
-            const float q = fmaf(-th_prev, th_prev, th);
-            s = fmaf(p, p, s);
-            s = fmaf(P.b * q, q, s);
-          }
-          th_prev = th;
-        }
+      for (int i = 0; i < DMAX; i += 2) {
+        const float2 q = __ffma2_rn(ld2(P.span + i), f2(u[i], u[i + 1]), ld2(P.lo + i));
+        th[i] = q.x;
+        th[i + 1] = q.y;
+      }
+      float s = 0.f;
+#pragma unroll
+      for (int i = 0; i + 1 < DMAX; ++i) {
+        const float p = P.a - th[i];
+        const float q = fmaf(-th[i], th[i], th[i + 1]);
+        s = fmaf(P.rw[i], fmaf(p, p, P.b * q * q), s);
+      }
       ll = -s;
       break;
     }
     case kMix: {
-      float u[DMAX];
-#pragma unroll
-      for (int i = 0; i < DMAX; ++i) u[i] = (i < d) ? fmaf(tp, v[i], x[i]) : 0.f;
       float e[kMaxModes];
       float emax = -CUDART_INF_F;
 #pragma unroll
       for (int k = 0; k < kMaxModes; ++k) {
         e[k] = -CUDART_INF_F;
         if (k < P.n_modes) {
-          float s = 0.f;
+          float2 acc = f2(0.f, 0.f);
 #pragma unroll
-          for (int i = 0; i < DMAX; ++i)
-            if (i < d) {
-              const float y = fmaf(P.span[i], u[i], P.cm[k * d + i]);
-              s = fmaf(y, y, s);
-            }
-          e[k] = -s * P.inv2s2;
+          for (int i = 0; i < DMAX; i += 2) {
+            const float2 y = __ffma2_rn(ld2(P.span + i), f2(u[i], u[i + 1]), ld2(P.cm + k * kMaxDim + i));
+            acc = __ffma2_rn(y, y, acc);
+          }
+          e[k] = -(acc.x + acc.y) * P.inv2s2;
           emax = fmaxf(emax, e[k]);
         }
       }
@@ -430,11 +456,16 @@ inline __device__ void select_worst(const float* __restrict__ logl, int N, int m
 }
 
 // ---------------------------------------------------------------------------
-// a4-a7: one walker per thread.  A round evaluates one candidate per active
-// walker; the walker's state machine moves through expansion to the left,
-// expansion to the right, and shrinkage, n_steps times (section 2.2), with
-// the expansion threshold thr_out (= W[0]) and the acceptance threshold
-// thr_in (= W[i]) of section 3.1.  All lanes of a warp must call it.
+// a4-a7: slice sampling, one walker per thread (section 2.2), with the
+// expansion threshold thr_out (= W[0]) and the acceptance threshold thr_in
+// (= W[i]) of section 3.1.
+//
+// Each iteration first draws, for every walker and every slice step, the
+// direction v = L_c z/|z| (z: Box-Muller normals from the step's stream) and
+// the bracket offset r, all lanes in step (draw_directions).  The walk then
+// runs as a state machine in which a round evaluates one candidate per
+// active walker: expansion to the left, expansion to the right, shrinkage;
+// after the direction draws a step's stream continues with the shrink draws.
 // ---------------------------------------------------------------------------
 struct SliceCfg {
   int d, n_steps, e_max, s_max, t_max;
@@ -442,47 +473,71 @@ struct SliceCfg {
   uint32_t k0, k1, t;
 };
 
+// First stream draw of a step after the direction and r (2 ceil(d/2) + 1).
+__host__ __device__ __forceinline__ uint32_t shrink_draw0(int d) { return 2u * (uint32_t)((d + 1) / 2) + 1u; }
+
+// Shrink draws of a step that are drawn ahead with its direction.
+constexpr int kPreShrink = 3;
+
+// Row of the per-step table: v[0..DMAX), r, kPreShrink shrink uniforms,
+// padded to a multiple of 4 floats (16-byte rows).
+__host__ __device__ constexpr int dir_row(int dmax) { return ((dmax + 1 + kPreShrink) + 3) & ~3; }
+
+// dirs: this walker's [n_steps][dir_row(DMAX)] table (zero beyond d).
+// chol: the walker's cluster factor, [d][d] row-major lower.
 template <int DMAX>
-__device__ __forceinline__ void new_direction(const SliceCfg& S, const float* __restrict__ chol,
-                                              Stream& st, float (&v)[DMAX], float& a, float& b) {
+__device__ __forceinline__ void draw_directions(const SliceCfg& S, int walker, const float* __restrict__ chol,
+                                                float* __restrict__ dirs) {
+  constexpr int RW = dir_row(DMAX);
   const int d = S.d;
-  float z[DMAX];
+  for (int s = 0; s < S.n_steps; ++s) {
+    Stream st;
+    st.init(S.k0, S.k1, S.t, (uint32_t)walker, (uint32_t)s);
+    float z[DMAX];
 #pragma unroll
-  for (int p = 0; p < (DMAX + 1) / 2; ++p)
-    if (2 * p < d) {
-      const float u1 = u24_open0(st.next());
-      const float u2 = u24(st.next());
-      const float rho = sqrtf(-2.f * logf(u1));
-      float sn, cs;
-      sincospif(2.f * u2, &sn, &cs);
-      z[2 * p] = rho * cs;
-      if (2 * p + 1 < DMAX) z[2 * p + 1] = rho * sn;
+    for (int i = 0; i < DMAX; ++i) z[i] = 0.f;
+#pragma unroll
+    for (int p = 0; p < (DMAX + 1) / 2; ++p)
+      if (2 * p < d) {
+        const float u1 = u24_open0(st.next());
+        const float u2 = u24(st.next());
+        const float rho = sqrtf(-2.f * logf(u1));
+        float sn, cs;
+        sincospif(2.f * u2, &sn, &cs);
+        z[2 * p] = rho * cs;
+        if (2 * p + 1 < DMAX && 2 * p + 1 < d) z[2 * p + 1] = rho * sn;
+      }
+    float nz = 0.f;
+#pragma unroll
+    for (int i = 0; i < DMAX; ++i) nz = fmaf(z[i], z[i], nz);
+    if (nz > 0.f) {
+      const float inv = rsqrtf(nz);
+#pragma unroll
+      for (int i = 0; i < DMAX; ++i) z[i] *= inv;
+    } else {
+#pragma unroll
+      for (int i = 0; i < DMAX; ++i) z[i] = (i == 0) ? 1.f : 0.f;
     }
-  float nz = 0.f;
+    float row[RW];
 #pragma unroll
-  for (int i = 0; i < DMAX; ++i)
-    if (i < d) nz = fmaf(z[i], z[i], nz);
-  float inv = 1.f;
-  if (nz > 0.f) {
-    inv = rsqrtf(nz);
-  } else {
+    for (int i = 0; i < RW; ++i) row[i] = 0.f;
 #pragma unroll
-    for (int i = 0; i < DMAX; ++i) z[i] = (i == 0) ? 1.f : 0.f;
-  }
+    for (int i = 0; i < DMAX; ++i) {
+      float acc = 0.f;
+      if (i < d) {
 #pragma unroll
-  for (int i = 0; i < DMAX; ++i) z[i] *= inv;
-#pragma unroll
-  for (int i = 0; i < DMAX; ++i) {
-    float acc = 0.f;
-    if (i < d) {
-#pragma unroll
-      for (int k = 0; k <= i; ++k) acc = fmaf(chol[i * d + k], z[k], acc);
+        for (int k = 0; k <= i; ++k) acc = fmaf(chol[i * d + k], z[k], acc);
+      }
+      row[i] = acc;
     }
-    v[i] = acc;
+    row[DMAX] = u24(st.next());
+#pragma unroll
+    for (int j = 0; j < kPreShrink; ++j) row[DMAX + 1 + j] = u24(st.next());
+    float* out = dirs + (size_t)s * RW;
+#pragma unroll
+    for (int i = 0; i < RW; i += 4)
+      *reinterpret_cast<float4*>(out + i) = make_float4(row[i], row[i + 1], row[i + 2], row[i + 3]);
   }
-  const float r = u24(st.next());
-  a = -r * S.width;
-  b = (1.f - r) * S.width;
 }
 
 struct WalkerOut {
@@ -493,90 +548,141 @@ struct WalkerOut {
   int* hist_len;     // [1]
 };
 
+// Asynchronous global -> shared copies (cp.async, 16 bytes each); a thread
+// waits only for the copies it issued.
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gmem_src) {
+  const unsigned s = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem_src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// Starts copying one step's row (dir_row(DMAX) floats, 16-byte aligned) into
+// this walker's shared-memory slot.
+template <int DMAX>
+__device__ __forceinline__ void prefetch_row(float* slot, const float* __restrict__ src) {
+  constexpr int RW = dir_row(DMAX);
+#pragma unroll
+  for (int i = 0; i < RW; i += 4) cp_async16(slot + i, src + i);
+  cp_async_commit();
+}
+
+// Waits for the walker's prefetched row and unpacks it.
+template <int DMAX>
+__device__ __forceinline__ void take_row(const float* slot, float (&v)[DMAX], float& r, float (&pre)[kPreShrink]) {
+  cp_async_wait_all();
+#pragma unroll
+  for (int i = 0; i < DMAX; i += 2) {
+    const float2 q = *reinterpret_cast<const float2*>(slot + i);
+    v[i] = q.x;
+    v[i + 1] = q.y;
+  }
+  r = slot[DMAX];
+#pragma unroll
+  for (int j = 0; j < kPreShrink; ++j) pre[j] = slot[DMAX + 1 + j];
+}
+
+// All lanes of a warp must call it.  dirs: this walker's table from
+// draw_directions; slot: dir_row(DMAX) floats of shared memory (16-byte
+// aligned) private to this walker, used to prefetch the next step's row.
 template <int DMAX>
 inline __device__ void slice_walker(const LikParams& P, const SliceCfg& S, int walker, bool active,
-                             const float* __restrict__ x0, int x0_stride, float l0,
-                             const float* __restrict__ chol, float thr_out, float thr_in,
-                             const WalkerOut& O, long long& evals_out, int& flags_out) {
+                                    const float* __restrict__ x0, int x0_stride, float l0,
+                                    const float* __restrict__ dirs, float* slot, float thr_out, float thr_in,
+                                    const WalkerOut& O, long long& evals_out, int& flags_out) {
+  constexpr int RW = dir_row(DMAX);
   const int d = S.d;
+  const uint32_t n0 = shrink_draw0(d);
   float x[DMAX], v[DMAX];
+  float pre[kPreShrink];
   float l = l0;
 #pragma unroll
   for (int i = 0; i < DMAX; ++i) {
     x[i] = (active && i < d) ? x0[(size_t)i * x0_stride] : 0.f;
     v[i] = 0.f;
   }
+#pragma unroll
+  for (int j = 0; j < kPreShrink; ++j) pre[j] = 0.f;
   const bool was_active = active;
   int step = 0, phase = 0, nexp = 0, nsh = 0, hlen = 0, flags = 0;
   long long evals = 0;
   float a = 0.f, b = 0.f;
   Stream st;
   st.init(S.k0, S.k1, S.t, (uint32_t)walker, 0u);
+  st.n = n0 + kPreShrink;
   if (S.n_steps <= 0) active = false;
-  if (active) new_direction<DMAX>(S, chol, st, v, a, b);
+  if (active) {
+    prefetch_row<DMAX>(slot, dirs);
+    float r;
+    take_row<DMAX>(slot, v, r, pre);
+    a = -r * S.width;
+    b = (1.f - r) * S.width;
+    if (S.n_steps > 1) prefetch_row<DMAX>(slot, dirs + RW);
+  }
   while (__any_sync(kFull, active)) {
     if (active) {
-      float tp;
+      float tp = (phase == 0) ? a : b;
       if (phase == 2) {
-        const float u = u24(st.next());
-        tp = fmaf(u, b - a, a);
-      } else {
-        tp = (phase == 0) ? a : b;
-      }
-      bool in = true;
+        float uu;
+        if (nsh < kPreShrink) {
+          uu = pre[0];
 #pragma unroll
-      for (int i = 0; i < DMAX; ++i)
-        if (i < d) {
-          const float ui = fmaf(tp, v[i], x[i]);
-          in = in && (ui >= 0.f) && (ui <= 1.f);
-        }
-      float lp = -CUDART_INF_F;
-      if (in) {
-        lp = loglike<DMAX>(P, x, v, tp, d);
-        ++evals;
-      }
-      if (phase < 2) {
-        const bool up = in && (lp > thr_out);
-        if (up && nexp < S.e_max) {
-          if (phase == 0) a -= S.width;
-          else b += S.width;
-          ++nexp;
+          for (int j = 1; j < kPreShrink; ++j)
+            if (nsh == j) uu = pre[j];
         } else {
-          if (up) flags |= 1;
-          ++phase;
-          nexp = 0;
-          nsh = 0;
+          uu = u24(st.next());
         }
+        tp = fmaf(uu, b - a, a);
+      }
+      float lp = -CUDART_INF_F;
+      bool in;
+      {
+        float u[DMAX];
+        in = candidate<DMAX>(x, v, tp, u);
+        if (in) {
+          lp = loglike_u<DMAX>(P, u);
+          ++evals;
+        }
+      }
+      const bool ok = in && (lp > ((phase == 2) ? thr_in : thr_out));
+      if (phase < 2) {
+        // expansion: predicated updates, no branches
+        const bool expand = ok && (nexp < S.e_max);
+        a = (expand && phase == 0) ? a - S.width : a;
+        b = (expand && phase == 1) ? b + S.width : b;
+        flags |= (ok && !expand) ? 1 : 0;
+        nexp = expand ? nexp + 1 : 0;
+        phase = expand ? phase : phase + 1;
       } else {
-        const bool last = (step == S.n_steps - 1);
-        const bool ok = in && (lp > thr_in);
-        if (last) {
-          int slot = -1;
+        if (step == S.n_steps - 1) {
+          int hs = -1;
           if (nsh < S.t_max - 1) {
-            slot = nsh;
+            hs = nsh;
             hlen = nsh + 1;
           } else if (ok) {
-            slot = S.t_max - 1;
+            hs = S.t_max - 1;
             hlen = S.t_max;
           }
-          if (slot >= 0) {
-            O.hist_l[slot] = lp;
+          if (hs >= 0) {
+            float u[DMAX];
+            candidate<DMAX>(x, v, tp, u);
+            O.hist_l[hs] = lp;
 #pragma unroll
             for (int i = 0; i < DMAX; ++i)
-              if (i < d) O.hist_x[(size_t)slot * d + i] = fmaf(tp, v[i], x[i]);
+              if (i < d) O.hist_x[(size_t)hs * d + i] = u[i];
           }
         }
-        bool advance = false;
+        bool advance = ok;
         if (ok) {
+          float u[DMAX];
+          candidate<DMAX>(x, v, tp, u);  // the accepted point, bit for bit
 #pragma unroll
-          for (int i = 0; i < DMAX; ++i) x[i] = fmaf(tp, v[i], x[i]);
+          for (int i = 0; i < DMAX; ++i) x[i] = u[i];
           l = lp;
-          advance = true;
         } else {
           if (tp < 0.f) a = tp;
           else b = tp;
-          ++nsh;
-          if (nsh >= S.s_max) {
+          if (++nsh >= S.s_max) {
             flags |= 2;
             advance = true;
           }
@@ -584,11 +690,16 @@ inline __device__ void slice_walker(const LikParams& P, const SliceCfg& S, int w
         if (advance) {
           ++step;
           if (step < S.n_steps) {
+            float r;
+            take_row<DMAX>(slot, v, r, pre);
+            a = -r * S.width;
+            b = (1.f - r) * S.width;
+            if (step + 1 < S.n_steps) prefetch_row<DMAX>(slot, dirs + (size_t)(step + 1) * RW);
             st.init(S.k0, S.k1, S.t, (uint32_t)walker, (uint32_t)step);
-            new_direction<DMAX>(S, chol, st, v, a, b);
+            st.n = n0 + kPreShrink;
             phase = 0;
-            nexp = 0;
             nsh = 0;
+            nexp = 0;
           } else {
             active = false;
           }
@@ -619,21 +730,49 @@ struct Cand {
   int* hp;
 };
 
-// sort `in` (2m entries) by (l, src) into `out` (rank by counting)
-__device__ __forceinline__ void cand_sort(const Cand& in, const Cand& out, int n) {
+__device__ __forceinline__ bool cand_less(float la, int sa, float lb, int sb) {
+  return (la < lb) || (la == lb && sa < sb);
+}
+
+__device__ __forceinline__ void cand_copy(const Cand& from, int i, const Cand& to, int j) {
+  to.l[j] = from.l[i];
+  to.P[j] = from.P[i];
+  to.src[j] = from.src[i];
+  to.H[j] = from.H[i];
+  to.hp[j] = from.hp[i];
+}
+
+// Sort the 2m entries of `in` by (l, src) into `out`: each half is ranked
+// by counting within itself (skipped for a half already in order), then
+// the halves are merged by binary search.  `tmp` holds the sorted halves.
+__device__ __forceinline__ void cand_sort(const Cand& in, const Cand& tmp, const Cand& out, int m,
+                                          bool first_half_sorted) {
+  const int n = 2 * m;
   for (int e = threadIdx.x; e < n; e += blockDim.x) {
-    const float le = in.l[e];
-    const int se = in.src[e];
-    int r = 0;
-    for (int q = 0; q < n; ++q) {
-      const float lq = in.l[q];
-      r += (lq < le) || (lq == le && in.src[q] < se);
+    const int h0 = (e < m) ? 0 : m;
+    int r;
+    if (h0 == 0 && first_half_sorted) {
+      r = e;
+    } else {
+      const float le = in.l[e];
+      const int se = in.src[e];
+      r = 0;
+      for (int q = h0; q < h0 + m; ++q) r += cand_less(in.l[q], in.src[q], le, se) ? 1 : 0;
     }
-    out.l[r] = le;
-    out.P[r] = in.P[e];
-    out.src[r] = se;
-    out.H[r] = in.H[e];
-    out.hp[r] = in.hp[e];
+    cand_copy(in, e, tmp, h0 + r);
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < n; e += blockDim.x) {
+    const int h0 = (e < m) ? 0 : m, o0 = m - h0;
+    const float le = tmp.l[e];
+    const int se = tmp.src[e];
+    int lo = 0, hi = m;  // entries of the other half below e
+    while (lo < hi) {
+      const int mid = (lo + hi) >> 1;
+      if (cand_less(tmp.l[o0 + mid], tmp.src[o0 + mid], le, se)) lo = mid + 1;
+      else hi = mid;
+    }
+    cand_copy(tmp, e, out, (e - h0) + lo);
   }
   __syncthreads();
 }
@@ -654,50 +793,47 @@ __device__ __forceinline__ int block_compact(int n, Pred pred, int* out, BlockSc
   return tot;
 }
 
-// A, Bf: two candidate buffers of 2m entries each (smem).  On return the
-// sorted candidates are in A: rejected A[0:m], accepted A[m:2m].
-// list_f, list_i: smem int [m]; vals: smem float [m].  Returns n_relaxed.
+// A, Bf, Tm: three candidate buffers of 2m entries each (smem).  On return
+// the sorted candidates are in A: rejected A[0:m], accepted A[m:2m].
+// list_f: smem int [2m]; vals: smem float [m].  Returns n_relaxed.
 inline __device__ int batch_correct(int m, int K, int correction, const float* __restrict__ W,
-                             const float* __restrict__ new_l, const float* __restrict__ hist_l,
-                             const int* __restrict__ hist_len, int t_max, const Cand& A,
-                             const Cand& Bf, int* list_f, float* vals, int* counter,
-                             BlockScratch& S) {
+                                    const float* __restrict__ new_l, const float* __restrict__ hist_l,
+                                    const int* __restrict__ hist_len, int t_max, const Cand& A, const Cand& Bf,
+                                    const Cand& Tm, int* list_f, float* vals, int* counter, BlockScratch& S) {
   const int tid = threadIdx.x, B = blockDim.x;
+  // Bf holds the unsorted candidates: W (ascending, candidates 0..m-1), then
+  // the walkers' new points (candidates m..2m-1)
   for (int i = tid; i < m; i += B) {
-    A.l[i] = W[i];
-    A.P[i] = -1.f;
-    A.src[i] = i;
-    A.H[i] = -1;
-    A.hp[i] = -1;
-    A.l[m + i] = new_l[i];
-    A.P[m + i] = W[i];
-    A.src[m + i] = m + i;
-    A.H[m + i] = i;
-    A.hp[m + i] = -1;
+    Bf.l[i] = W[i];
+    Bf.P[i] = -1.f;
+    Bf.src[i] = i;
+    Bf.H[i] = -1;
+    Bf.hp[i] = -1;
+    Bf.l[m + i] = new_l[i];
+    Bf.P[m + i] = W[i];
+    Bf.src[m + i] = m + i;
+    Bf.H[m + i] = i;
+    Bf.hp[m + i] = -1;
   }
   if (tid == 0) *counter = 0;
   __syncthreads();
   if (correction == 0 || correction == 3) {
     // the removed points die (already ascending), the new points go live
-    Cand a_in{A.l + m, A.P + m, A.src + m, A.H + m, A.hp + m};
-    Cand a_out{Bf.l, Bf.P, Bf.src, Bf.H, Bf.hp};
-    cand_sort(a_in, a_out, m);
-    for (int i = tid; i < m; i += B) {
-      A.l[m + i] = Bf.l[i];
-      A.P[m + i] = Bf.P[i];
-      A.src[m + i] = Bf.src[i];
-      A.H[m + i] = Bf.H[i];
-      A.hp[m + i] = Bf.hp[i];
+    for (int e = tid; e < m; e += B) {
+      const float le = Bf.l[m + e];
+      const int se = Bf.src[m + e];
+      int r = 0;
+      for (int q = m; q < 2 * m; ++q) r += cand_less(Bf.l[q], Bf.src[q], le, se) ? 1 : 0;
+      cand_copy(Bf, e, A, e);
+      cand_copy(Bf, m + e, A, m + r);
     }
     __syncthreads();
     return 0;
   }
-  cand_sort(A, Bf, 2 * m);  // Alg1.sort: Bf sorted
-  const Cand* cur = &Bf;
-  const Cand* oth = &A;
+  cand_sort(Bf, Tm, A, m, true);  // Alg1.sort
   if (correction == 2) {
     for (int k = 1; k <= K; ++k) {
-      const Cand C = *cur;
+      const Cand C = A;
       const float amin = C.l[m];
       const int nF = block_compact(
           m, [&](int j) { return C.H[m + j] >= 0 && C.P[m + j] >= amin; }, list_f, S);
@@ -725,22 +861,12 @@ inline __device__ int batch_correct(int m, int K, int correction, const float* _
         }
       }
       __syncthreads();
-      cand_sort(*cur, *oth, 2 * m);
-      const Cand* tmp = cur;
-      cur = oth;
-      oth = tmp;
+      // re-sort r and a: r is still in order, a may not be
+      for (int e = tid; e < 2 * m; e += B) cand_copy(A, e, Bf, e);
+      __syncthreads();
+      cand_sort(Bf, Tm, A, m, true);
     }
   }
-  if (cur != &A) {
-    for (int i = tid; i < 2 * m; i += B) {
-      A.l[i] = cur->l[i];
-      A.P[i] = cur->P[i];
-      A.src[i] = cur->src[i];
-      A.H[i] = cur->H[i];
-      A.hp[i] = cur->hp[i];
-    }
-  }
-  __syncthreads();
   const int rel = *counter;
   __syncthreads();
   return rel;
@@ -760,13 +886,15 @@ struct EvidState {
 inline __device__ void evidence_add(EvidState& E, int N, int n, const float* __restrict__ l_in,
                              double* logw_out, bool live, BlockScratch& S) {
   const double Nd = (double)N;
-  const double cN = log(-expm1(-1.0 / Nd));
+  const double invN = 1.0 / Nd;
+  const double cN = log(-expm1(-invN));
+  const double live_off = -(double)E.k * invN - log(Nd);
   const int tid = threadIdx.x, B = blockDim.x;
   const long long k0 = E.k;
   double mx = E.logz;
   for (int j = tid; j < n; j += B) {
     const double l = (double)l_in[j];
-    const double lw = live ? l - (double)k0 / Nd - log(Nd) : l - (double)(k0 + j) / Nd + cN;
+    const double lw = live ? l + live_off : l - (double)(k0 + j) * invN + cN;
     if (logw_out) logw_out[j] = lw;
     mx = fmax(mx, lw);
   }
@@ -778,7 +906,7 @@ inline __device__ void evidence_add(EvidState& E, int N, int n, const float* __r
   double sw = 0.0, swl = 0.0;
   for (int j = tid; j < n; j += B) {
     const double l = (double)l_in[j];
-    const double lw = live ? l - (double)k0 / Nd - log(Nd) : l - (double)(k0 + j) / Nd + cN;
+    const double lw = live ? l + live_off : l - (double)(k0 + j) * invN + cN;
     const double w = exp(lw - mx);
     sw += w;
     if (l > -CUDART_INF) swl += w * l;
@@ -807,7 +935,7 @@ inline __device__ void evidence_add(EvidState& E, int N, int n, const float* __r
 // a3: clustering (section 2.1).  FP32 products accumulated per 64-point
 // tile, FP64 across tiles; FP64 regularised Cholesky.
 // ---------------------------------------------------------------------------
-constexpr int kTile = 64;
+constexpr int kTile = 128;
 
 // One warp: L = chol(A) for a d x d FP64 matrix (smem, row-major).  Returns
 // false (uniformly) if a pivot is not positive.
@@ -933,62 +1061,69 @@ inline __device__ void reg_cholesky(int d, double* C, double* L, double* work, B
 }
 
 // Mean and covariance (1/n) of the points j in [0, N) with member(j) true
-// (live_x [d][n_pad]).  tile: smem float [d][kTile]; acc: smem FP64
-// [d + d*d]; returns n.  Results: mean in acc[0:d], cov in acc[d:d+d*d].
+// (live_x [d][n_pad]), in one pass: coordinates are shifted by the first
+// member x_ref (so that E[(x - x_ref)(x - x_ref)^T] - (mu - x_ref)(mu -
+// x_ref)^T suffers no cancellation), products accumulate in FP32 within a
+// tile of kTile points and in FP64 across tiles.  tile: smem float
+// [d][kTile] + d; acc: smem FP64 [d + d*d]; returns n.  Results: mean in
+// acc[0:d], covariance in acc[d:d+d*d].
 template <class Member>
 inline __device__ int node_moments(const float* __restrict__ live_x, int n_pad, int N, int d, Member member,
-                            float* tile, double* acc, BlockScratch& S) {
+                                   float* tile, double* acc, BlockScratch& S) {
   const int tid = threadIdx.x, B = blockDim.x;
   const int ne = d * (d + 1) / 2;
+  float* ref = tile + d * kTile;
   for (int i = tid; i < d + d * d; i += B) acc[i] = 0.0;
+  if (tid == 0) {
+    int j0 = 0;
+    while (j0 < N && !member(j0)) ++j0;
+    S.iw[0] = j0;
+  }
+  __syncthreads();
+  const int jr = S.iw[0];
+  for (int i = tid; i < d; i += B) ref[i] = (jr < N) ? live_x[(size_t)i * n_pad + jr] : 0.f;
   __syncthreads();
   int cnt = 0;
-  // pass 1: sums
   for (int j0 = 0; j0 < N; j0 += kTile) {
     for (int q = tid; q < d * kTile; q += B) {
       const int i = q / kTile, jj = q % kTile, j = j0 + jj;
-      tile[q] = (j < N && member(j)) ? live_x[(size_t)i * n_pad + j] : 0.f;
+      tile[q] = (j < N && member(j)) ? live_x[(size_t)i * n_pad + j] - ref[i] : 0.f;
     }
     if (tid < kTile) cnt += (j0 + tid < N && member(j0 + tid)) ? 1 : 0;
     __syncthreads();
-    if (tid < d) {
-      float s = 0.f;
-      for (int jj = 0; jj < kTile; ++jj) s += tile[tid * kTile + jj];
-      acc[tid] += (double)s;
+    for (int e = tid; e < ne + d; e += B) {
+      if (e < ne) {
+        int a = 0;
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        const int bcol = e - a * (a + 1) / 2;
+        const float* ta = tile + a * kTile;
+        const float* tb = tile + bcol * kTile;
+        float2 s2 = f2(0.f, 0.f);
+#pragma unroll 8
+        for (int jj = 0; jj < kTile; jj += 2) s2 = __ffma2_rn(ld2(ta + jj), ld2(tb + jj), s2);
+        acc[d + a * d + bcol] += (double)(s2.x + s2.y);
+      } else {
+        const float* ta = tile + (e - ne) * kTile;
+        float2 s2 = f2(0.f, 0.f);
+#pragma unroll 8
+        for (int jj = 0; jj < kTile; jj += 2) s2 = __fadd2_rn(ld2(ta + jj), s2);
+        acc[e - ne] += (double)(s2.x + s2.y);
+      }
     }
     __syncthreads();
   }
   const int n = (int)block_sum_ll(cnt, S);
   const double inv = n > 0 ? 1.0 / n : 0.0;
-  for (int i = tid; i < d; i += B) acc[i] *= inv;
-  __syncthreads();
-  // pass 2: centred products
-  for (int j0 = 0; j0 < N; j0 += kTile) {
-    for (int q = tid; q < d * kTile; q += B) {
-      const int i = q / kTile, jj = q % kTile, j = j0 + jj;
-      tile[q] = (j < N && member(j)) ? (float)((double)live_x[(size_t)i * n_pad + j] - acc[i]) : 0.f;
-    }
-    __syncthreads();
-    for (int e = tid; e < ne; e += B) {
-      int a = 0;
-      while ((a + 1) * (a + 2) / 2 <= e) ++a;
-      const int bcol = e - a * (a + 1) / 2;
-      float s = 0.f;
-      const float* ta = tile + a * kTile;
-      const float* tb = tile + bcol * kTile;
-      for (int jj = 0; jj < kTile; ++jj) s = fmaf(ta[jj], tb[jj], s);
-      acc[d + a * d + bcol] += (double)s;
-    }
-    __syncthreads();
-  }
   for (int e = tid; e < ne; e += B) {
     int a = 0;
     while ((a + 1) * (a + 2) / 2 <= e) ++a;
     const int bcol = e - a * (a + 1) / 2;
-    const double v = acc[d + a * d + bcol] * inv;
+    const double v = acc[d + a * d + bcol] * inv - (acc[a] * inv) * (acc[bcol] * inv);
     acc[d + a * d + bcol] = v;
     acc[d + bcol * d + a] = v;
   }
+  __syncthreads();
+  for (int i = tid; i < d; i += B) acc[i] = acc[i] * inv + (double)ref[i];
   __syncthreads();
   return n;
 }

@@ -1,10 +1,10 @@
 // ns_inst.cu -- instantiates the per-dimension kernels for one register
-// class (compiled once per class with -DNS_DMAX=4, 8, 16 or 32, so the four
-// classes build in parallel).
+// class (compiled once per class with -DNS_DMAX=<class>, so the classes
+// build in parallel).
 #include "ns_run.cuh"
 
 #ifndef NS_DMAX
-#error "compile with -DNS_DMAX=<4|8|16|32>"
+#error "compile with -DNS_DMAX=<register class>"
 #endif
 
 namespace nsd {
@@ -20,6 +20,12 @@ cudaError_t NS_CAT(launch_run_, NS_DMAX)(const RunDesc* runs, const int* ids, in
   return cudaGetLastError();
 }
 
+cudaError_t NS_CAT(occupancy_run_, NS_DMAX)(int block, size_t smem, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(k_run<NS_DMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_run<NS_DMAX>, block, smem);
+}
+
 cudaError_t NS_CAT(launch_loglike_, NS_DMAX)(const LikParams& P, int n, const float* x, float* out,
                                              cudaStream_t s) {
   k_loglike<NS_DMAX><<<(n + 127) / 128, 128, 0, s>>>(P, n, x, out);
@@ -30,9 +36,10 @@ cudaError_t NS_CAT(launch_slice_, NS_DMAX)(const LikParams& P, const SliceCfg& S
                                            int correction, const float* live_x, const float* live_l,
                                            const int* seed_slot, const float* W, const float* chol, const int* cid,
                                            float* new_x, float* new_l, float* hist_l, float* hist_x, int* hist_len,
-                                           long long* evals, int* flags, cudaStream_t s) {
-  k_slice<NS_DMAX><<<(m + 127) / 128, 128, 0, s>>>(P, SC, m, n_pad, correction, live_x, live_l, seed_slot, W, chol,
-                                                   cid, new_x, new_l, hist_l, hist_x, hist_len, evals, flags);
+                                           long long* evals, int* flags, float* dir_scratch, cudaStream_t s) {
+  k_slice<NS_DMAX><<<(m + 127) / 128, 128, sizeof(float) * 128 * dir_row(NS_DMAX), s>>>(P, SC, m, n_pad, correction, live_x, live_l, seed_slot, W, chol,
+                                                   cid, new_x, new_l, hist_l, hist_x, hist_len, evals, flags,
+                                                   dir_scratch);
   return cudaGetLastError();
 }
 

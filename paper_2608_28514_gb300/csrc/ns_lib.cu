@@ -68,9 +68,10 @@ __global__ void k_correct(int m, int K, int correction, const float* __restrict_
   const size_t cb = al16((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
   const Cand A = cand_at(sm, m);
   const Cand Bf = cand_at(sm + cb, m);
-  int* list = reinterpret_cast<int*>(sm + 2 * cb);
-  float* vals = reinterpret_cast<float*>(sm + 2 * cb + al16(sizeof(int) * 2 * m));
-  const int rel = batch_correct(m, K, correction, W, new_l, hist_l, hist_len, t_max, A, Bf, list, vals, &ctr, S);
+  const Cand Tm = cand_at(sm + 2 * cb, m);
+  int* list = reinterpret_cast<int*>(sm + 3 * cb);
+  float* vals = reinterpret_cast<float*>(sm + 3 * cb + al16(sizeof(int) * 2 * m));
+  const int rel = batch_correct(m, K, correction, W, new_l, hist_l, hist_len, t_max, A, Bf, Tm, list, vals, &ctr, S);
   for (int j = threadIdx.x; j < m; j += blockDim.x) {
     rej_src[j] = A.src[j];
     rej_hpos[j] = A.hp[j];
@@ -104,7 +105,7 @@ __global__ void k_evidence(int N, int n, const float* __restrict__ l, double* st
 __global__ void k_cluster(RunDesc R) {
   extern __shared__ __align__(16) char sm[];
   __shared__ BlockScratch S;
-  const Carve cv = make_carve(R.d, 1, R.n_nodes);
+  const Carve cv = make_carve(R.d, 1, R.n_nodes, kMaxDim);
   cluster_phase(R, sm, cv, S);
 }
 
@@ -134,7 +135,25 @@ void set_err(std::string* dst, const char* fmt, ...) {
     }                                                                                          \
   } while (0)
 
-int dmax_class(int d) { return d <= 4 ? 4 : d <= 8 ? 8 : d <= 16 ? 16 : 32; }
+struct ClassFns {
+  int dmax;
+  cudaError_t (*run)(const RunDesc*, const int*, int, int, size_t, int, cudaStream_t);
+  cudaError_t (*ll)(const LikParams&, int, const float*, float*, cudaStream_t);
+  cudaError_t (*sl)(const LikParams&, const SliceCfg&, int, int, int, const float*, const float*, const int*,
+                    const float*, const float*, const int*, float*, float*, float*, float*, int*, long long*, int*,
+                    float*, cudaStream_t);
+  cudaError_t (*occ)(int, size_t, int*);
+};
+#define NS_CLASS_ENTRY(D) {D, launch_run_##D, launch_loglike_##D, launch_slice_##D, occupancy_run_##D},
+const ClassFns kClasses[] = {NS_FOR_EACH_CLASS(NS_CLASS_ENTRY)};
+constexpr int kNumClasses = sizeof(kClasses) / sizeof(kClasses[0]);
+
+int class_index(int d) {
+  for (int c = 0; c < kNumClasses; ++c)
+    if (d <= kClasses[c].dmax) return c;
+  return kNumClasses - 1;
+}
+int dmax_class(int d) { return kClasses[class_index(d)].dmax; }
 
 int block_for_m(int m) {
   int b = ((m + 31) / 32) * 32;
@@ -274,19 +293,24 @@ LikParams make_lik(const ns_likelihood& L, const double* lo, const double* hi, i
     case NS_LIK_GAUSS_CORR:
       for (int i = 0; i < d; ++i) {
         P.c[i] = (float)(lo[i] - L.mean[i]);
-        for (int j = 0; j <= i; ++j) P.Lp[i * d + j] = (float)L.prec_chol[i * d + j];
+        for (int j = 0; j <= i; ++j) {
+          float2& cell = P.LpP[(j / 2) * kMaxDim + i];
+          if (j % 2 == 0) cell.x = (float)L.prec_chol[i * d + j];
+          else cell.y = (float)L.prec_chol[i * d + j];
+        }
       }
       break;
     case NS_LIK_ROSENBROCK:
       P.a = (float)L.a;
       P.b = (float)L.b;
+      for (int i = 0; i + 1 < d; ++i) P.rw[i] = 1.f;
       break;
     case NS_LIK_MIXTURE:
       P.n_modes = L.n_modes;
       P.inv2s2 = (float)(1.0 / (2.0 * L.sigma * L.sigma));
       P.log_k = (float)std::log((double)L.n_modes);
       for (int k = 0; k < L.n_modes; ++k)
-        for (int i = 0; i < d; ++i) P.cm[k * d + i] = (float)(lo[i] - L.centres[k * d + i]);
+        for (int i = 0; i < d; ++i) P.cm[k * kMaxDim + i] = (float)(lo[i] - L.centres[k * d + i]);
       break;
     default:
       break;
@@ -309,12 +333,7 @@ struct ClassGroup {
 };
 
 cudaError_t launch_class(const ClassGroup& g, const RunDesc* d_runs, int chunk, cudaStream_t s) {
-  switch (g.dmax) {
-    case 4: return launch_run_4(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
-    case 8: return launch_run_8(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
-    case 16: return launch_run_16(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
-    default: return launch_run_32(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
-  }
+  return kClasses[class_index(g.dmax)].run(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
 }
 
 }  // namespace
@@ -403,8 +422,8 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     return o;
   };
   struct Off {
-    size_t lik, live_x, live_l, live_cid, new_x, new_l, hist_l, hist_x, hist_len, stage_x, dead_x, dead_l,
-        dead_logw, centres, chol, chol64, logvol, count, split, mask;
+    size_t lik, live_x, live_l, live_cid, new_x, new_l, hist_l, hist_x, hist_len, stage_x, dirs, dead_x,
+        dead_l, dead_logw, centres, chol, chol64, logvol, count, split, mask;
   };
   std::vector<Off> off(n_runs);
   h->host.resize(n_runs);
@@ -424,6 +443,7 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     o.hist_x = take(sizeof(float) * (size_t)m * opt.t_max * d);
     o.hist_len = take(sizeof(int) * m);
     o.stage_x = take(sizeof(float) * (size_t)m * d);
+    o.dirs = take(sizeof(float) * (size_t)m * p.n_slice_steps * dir_row(dmax_class(d)));
     o.dead_x = take(sizeof(float) * (size_t)cap * d);
     o.dead_l = take(sizeof(float) * (size_t)cap);
     o.dead_logw = take(sizeof(double) * (size_t)cap);
@@ -443,16 +463,15 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
   const size_t off_desc = take(sizeof(RunDesc) * n_runs);
   const size_t off_state = take(sizeof(RunState) * n_runs);
   // class groups
-  int counts[4] = {0, 0, 0, 0};
-  std::vector<std::vector<int>> members(4);
+  std::vector<int> counts(kNumClasses, 0);
+  std::vector<std::vector<int>> members(kNumClasses);
   for (int r = 0; r < n_runs; ++r) {
-    const int c = dmax_class(runs[r].d);
-    const int ci = c == 4 ? 0 : c == 8 ? 1 : c == 16 ? 2 : 3;
+    const int ci = class_index(runs[r].d);
     members[ci].push_back(r);
     counts[ci]++;
   }
-  size_t off_ids[4];
-  for (int ci = 0; ci < 4; ++ci) off_ids[ci] = take(sizeof(int) * std::max(1, counts[ci]));
+  std::vector<size_t> off_ids(kNumClasses);
+  for (int ci = 0; ci < kNumClasses; ++ci) off_ids[ci] = take(sizeof(int) * std::max(1, counts[ci]));
   h->arena_bytes = total;
   cudaError_t e = cudaMalloc(&h->arena, total);
   if (e != cudaSuccess) {
@@ -506,6 +525,7 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     R.hist_x = reinterpret_cast<float*>(base + o.hist_x);
     R.hist_len = reinterpret_cast<int*>(base + o.hist_len);
     R.stage_x = reinterpret_cast<float*>(base + o.stage_x);
+    R.dirs = reinterpret_cast<float*>(base + o.dirs);
     R.dead_x = reinterpret_cast<float*>(base + o.dead_x);
     R.dead_l = reinterpret_cast<float*>(base + o.dead_l);
     R.dead_logw = reinterpret_cast<double*>(base + o.dead_logw);
@@ -541,17 +561,17 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     set_err(nullptr, "device setup failed: %s", cudaGetErrorString(e));
     return fail(NS_ERR_CUDA);
   }
-  for (int ci = 0; ci < 4; ++ci) {
+  for (int ci = 0; ci < kNumClasses; ++ci) {
     if (counts[ci] == 0) continue;
     ClassGroup g;
-    g.dmax = ci == 0 ? 4 : ci == 1 ? 8 : ci == 2 ? 16 : 32;
+    g.dmax = kClasses[ci].dmax;
     g.n = counts[ci];
     g.d_ids = reinterpret_cast<int*>(base + off_ids[ci]);
     int maxm = 1;
     size_t smem = 0;
     for (int r : members[ci]) {
       maxm = std::max(maxm, runs[r].m);
-      smem = std::max(smem, make_carve(runs[r].d, runs[r].m, n_nodes).total);
+      smem = std::max(smem, make_carve(runs[r].d, runs[r].m, n_nodes, kClasses[ci].dmax).total);
     }
     g.block = block_for_m(maxm);
     g.smem = smem;
@@ -583,6 +603,20 @@ ns_status ns_create(const ns_likelihood* lik, const double* lo, const double* hi
 }
 
 int ns_n_runs(const ns_handle* h) { return h ? h->n_runs : -1; }
+
+int ns_resident_runs_per_sm(int d, int m, int depth) {
+  if (d < 1 || d > NS_MAX_DIM || m < 1 || m > NS_MAX_BATCH || depth < 0 || depth > NS_MAX_DEPTH) return -1;
+  const int n_nodes = (1 << (depth + 1)) - 1;
+  const int ci = class_index(d);
+  int blocks = 0;
+  const cudaError_t e =
+      kClasses[ci].occ(block_for_m(m), make_carve(d, m, n_nodes, kClasses[ci].dmax).total, &blocks);
+  if (e != cudaSuccess) {
+    set_err(nullptr, "occupancy query failed: %s", cudaGetErrorString(e));
+    return -1;
+  }
+  return blocks;
+}
 
 ns_status ns_reset(ns_handle* h, void* stream) {
   if (!h) return NS_ERR_ARG;
@@ -803,7 +837,9 @@ ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt_in, fl
                o_new_x = take(sizeof(float) * (size_t)m * d), o_new_l = take(sizeof(float) * m),
                o_hist_l = take(sizeof(float) * (size_t)m * opt.t_max),
                o_hist_x = take(sizeof(float) * (size_t)m * opt.t_max * d), o_hist_len = take(sizeof(int) * m),
-               o_stage_x = take(sizeof(float) * (size_t)m * d), o_centres = take(sizeof(float) * n_nodes * d),
+               o_stage_x = take(sizeof(float) * (size_t)m * d),
+               o_dirs = take(sizeof(float) * (size_t)m * p.n_slice_steps * dir_row(dmax_class(d))),
+               o_centres = take(sizeof(float) * n_nodes * d),
                o_chol = take(sizeof(float) * n_nodes * d * d), o_chol64 = take(sizeof(double) * n_nodes * d * d),
                o_logvol = take(sizeof(float) * n_nodes), o_count = take(sizeof(int) * n_nodes),
                o_split = take(sizeof(int) * n_nodes), o_mask = take(sizeof(int) * n_nodes);
@@ -866,6 +902,7 @@ ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt_in, fl
   R.hist_x = reinterpret_cast<float*>(base + o_hist_x);
   R.hist_len = reinterpret_cast<int*>(base + o_hist_len);
   R.stage_x = reinterpret_cast<float*>(base + o_stage_x);
+  R.dirs = reinterpret_cast<float*>(base + o_dirs);
   R.dead_x = dead_x;
   R.dead_l = dead_logl;
   R.dead_logw = dead_logw;
@@ -889,19 +926,13 @@ ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt_in, fl
   const RunDesc* d_desc = reinterpret_cast<const RunDesc*>(base + o_desc);
   const int* d_ids = reinterpret_cast<const int*>(base + o_ids);
   const int block = block_for_m(m);
-  const size_t smem = make_carve(d, m, n_nodes).total;
+  const size_t smem = make_carve(d, m, n_nodes, dmax_class(d)).total;
   const int chunk = opt.chunk_iters > 0 ? opt.chunk_iters : 1000;
   const long long max_rounds = opt.max_iter / chunk + 2;
   RunState hs;
   std::memset(&hs, 0, sizeof(hs));
   for (long long round = 0;; ++round) {
-    cudaError_t e;
-    switch (dmax_class(d)) {
-      case 4: e = launch_run_4(d_desc, d_ids, 1, block, smem, chunk, s); break;
-      case 8: e = launch_run_8(d_desc, d_ids, 1, block, smem, chunk, s); break;
-      case 16: e = launch_run_16(d_desc, d_ids, 1, block, smem, chunk, s); break;
-      default: e = launch_run_32(d_desc, d_ids, 1, block, smem, chunk, s); break;
-    }
+    const cudaError_t e = kClasses[class_index(d)].run(d_desc, d_ids, 1, block, smem, chunk, s);
     NS_CUDA(e, nullptr);
     NS_CUDA(cudaMemcpyAsync(&hs, base + o_state, sizeof(RunState), cudaMemcpyDeviceToHost, s), nullptr);
     NS_CUDA(cudaStreamSynchronize(s), nullptr);
@@ -959,13 +990,7 @@ ns_status ns_loglike(const ns_likelihood* lik, const double* lo, const double* h
   if (n == 0) return NS_OK;
   const LikParams P = make_lik(*lik, lo, hi, d);
   cudaStream_t s = (cudaStream_t)stream;
-  cudaError_t e;
-  switch (dmax_class(d)) {
-    case 4: e = launch_loglike_4(P, n, x, logl, s); break;
-    case 8: e = launch_loglike_8(P, n, x, logl, s); break;
-    case 16: e = launch_loglike_16(P, n, x, logl, s); break;
-    default: e = launch_loglike_32(P, n, x, logl, s); break;
-  }
+  const cudaError_t e = kClasses[class_index(d)].ll(P, n, x, logl, s);
   NS_CUDA(e, nullptr);
   return NS_OK;
 }
@@ -997,7 +1022,8 @@ ns_status ns_slice_replace(const ns_likelihood* lik, const double* lo, const dou
                            int m, int n_steps, const ns_options* opt_in, uint64_t seed, uint32_t t,
                            const float* live_x, const float* live_l, const int* seed_slot, const float* W,
                            const float* chol, const int* cid, float* new_x, float* new_l, float* hist_l,
-                           float* hist_x, int* hist_len, long long* evals, int* flags, void* stream) {
+                           float* hist_x, int* hist_len, long long* evals, int* flags, float* dir_scratch,
+                           void* stream) {
   ns_options opt;
   if (opt_in) opt = *opt_in;
   else ns_default_options(&opt);
@@ -1016,7 +1042,7 @@ ns_status ns_slice_replace(const ns_likelihood* lik, const double* lo, const dou
   st = check_problem(p, nullptr);
   if (st != NS_OK) return st;
   if (n_pad < N || !live_x || !live_l || !seed_slot || !W || !chol || !cid || !new_x || !new_l || !hist_l ||
-      !hist_x || !hist_len || !evals || !flags) {
+      !hist_x || !hist_len || !evals || !flags || !dir_scratch) {
     set_err(nullptr, "ns_slice_replace: NULL buffer or n_pad < N");
     return NS_ERR_ARG;
   }
@@ -1032,18 +1058,16 @@ ns_status ns_slice_replace(const ns_likelihood* lik, const double* lo, const dou
   SC.k1 = (uint32_t)(seed >> 32);
   SC.t = t;
   cudaStream_t s = (cudaStream_t)stream;
-#define NS_SLICE_ARGS P, SC, m, n_pad, opt.correction, live_x, live_l, seed_slot, W, chol, cid, new_x, new_l, hist_l, \
-                      hist_x, hist_len, evals, flags, s
-  cudaError_t e;
-  switch (dmax_class(d)) {
-    case 4: e = launch_slice_4(NS_SLICE_ARGS); break;
-    case 8: e = launch_slice_8(NS_SLICE_ARGS); break;
-    case 16: e = launch_slice_16(NS_SLICE_ARGS); break;
-    default: e = launch_slice_32(NS_SLICE_ARGS); break;
-  }
-#undef NS_SLICE_ARGS
+  const cudaError_t e = kClasses[class_index(d)].sl(P, SC, m, n_pad, opt.correction, live_x, live_l, seed_slot, W,
+                                                     chol, cid, new_x, new_l, hist_l, hist_x, hist_len, evals, flags,
+                                                     dir_scratch, s);
   NS_CUDA(e, nullptr);
   return NS_OK;
+}
+
+size_t ns_slice_scratch_bytes(int d, int m, int n_steps) {
+  if (d < 1 || d > NS_MAX_DIM || m < 1 || n_steps < 1) return 0;
+  return sizeof(float) * (size_t)m * n_steps * dir_row(dmax_class(d));
 }
 
 ns_status ns_batch_correct(int m, int K, int correction, const float* W, const float* new_l, const float* hist_l,
@@ -1056,7 +1080,7 @@ ns_status ns_batch_correct(int m, int K, int correction, const float* W, const f
     return NS_ERR_ARG;
   }
   const size_t cb = al16((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
-  const size_t smem = 2 * cb + al16(sizeof(int) * 2 * m) + al16(sizeof(float) * m);
+  const size_t smem = 3 * cb + al16(sizeof(int) * 2 * m) + al16(sizeof(float) * m);
   k_correct<<<1, 256, smem, (cudaStream_t)stream>>>(m, K, correction, W, new_l, hist_l, hist_len, t_max, acc_src,
                                                     acc_hpos, acc_l, acc_P, rej_src, rej_hpos, rej_l, rej_P,
                                                     n_relaxed);
@@ -1112,7 +1136,7 @@ ns_status ns_cluster(int N, int n_pad, int d, const float* live_x, const ns_opti
   R.split = split;
   R.mask = mask;
   (void)t;
-  const size_t smem = make_carve(d, 1, R.n_nodes).total;
+  const size_t smem = make_carve(d, 1, R.n_nodes, kMaxDim).total;
   NS_CUDA(cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), nullptr);
   k_cluster<<<1, 256, smem, (cudaStream_t)stream>>>(R);
   NS_CUDA(cudaGetLastError(), nullptr);

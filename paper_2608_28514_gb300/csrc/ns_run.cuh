@@ -39,6 +39,7 @@ struct RunDesc {
   float* hist_x;
   int* hist_len;
   float* stage_x;
+  float* dirs;     // [m][n_steps][dir_row(DMAX of the run's class)] per-step directions and draws
   float* dead_x;
   float* dead_l;
   double* dead_logw;
@@ -55,13 +56,13 @@ struct RunDesc {
 // Shared-memory carve of the run kernel, computed identically on host and
 // device from the run's sizes.
 struct Carve {
-  size_t lik, scr, sel, chol, cent, mask, worst, W, seed, sel_slot, sel_key, candA, candB, list, vals,
+  size_t lik, scr, sel, chol, cent, mask, worst, W, seed, sel_slot, sel_key, candA, candB, candT, list, vals, slots,
       ctr, stage_cid, tile, acc, c64, l64, work, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline Carve make_carve(int d, int m, int n_nodes) {
+__host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax) {
   Carve c;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -82,11 +83,13 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes) {
   c.sel_key = take(sizeof(uint32_t) * m);
   c.candA = take((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
   c.candB = take((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
+  c.candT = take((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
   c.list = take(sizeof(int) * 2 * m);
   c.vals = take(sizeof(float) * m);
+  c.slots = take(sizeof(float) * (size_t)dir_row(dmax) * (m + 31) / 32 * 32);
   c.ctr = take(sizeof(int) * 4);
   c.stage_cid = take(sizeof(int) * m);
-  c.tile = take(sizeof(float) * d * kTile);
+  c.tile = take(sizeof(float) * (d * kTile + d));
   c.acc = take(sizeof(double) * (d + d * d));
   c.c64 = take(sizeof(double) * d * d);
   c.l64 = take(sizeof(double) * d * d);
@@ -112,14 +115,13 @@ template <int DMAX>
 inline __device__ void init_live(const RunDesc& R, const LikParams& P) {
   const int d = R.d;
   for (int j = threadIdx.x; j < R.N; j += blockDim.x) {
-    float x[DMAX], v[DMAX];
+    float x[DMAX];
 #pragma unroll
     for (int i = 0; i < DMAX; ++i) {
-      v[i] = 0.f;
       x[i] = (i < d) ? u24(draw_at(R.k0, R.k1, kTInit, (uint32_t)j, 0u, (uint32_t)i)) : 0.f;
       if (i < d) R.live_x[(size_t)i * R.n_pad + j] = x[i];
     }
-    R.live_l[j] = loglike<DMAX>(P, x, v, 0.f, d);
+    R.live_l[j] = loglike_u<DMAX>(P, x);
     R.live_cid[j] = 0;
   }
 }
@@ -178,8 +180,47 @@ inline __device__ int nearest_leaf(const float* x, int d, int n_nodes, const flo
   return best;
 }
 
+// a4-a7 for the calling thread's walker (threads of warps that hold a walker
+// call it; lanes past m take part in the warp votes only).  Kept out of line
+// so that its registers are allocated apart from the rest of the run kernel.
 template <int DMAX>
-__global__ void __launch_bounds__(256) k_run(const RunDesc* __restrict__ runs, const int* __restrict__ ids,
+__device__ __noinline__ void walker_phase(const RunDesc& R, const LikParams& P, const SliceCfg& SC,
+                                          const float* s_W, const int* s_seed, const float* s_chol, float* s_slots,
+                                          long long& ev, int& fl) {
+  const int tid = threadIdx.x, m = R.m, d = R.d;
+  const bool act = tid < m;
+  const int i = act ? tid : 0;
+  const int sd = s_seed[i];
+  const int cid = R.live_cid[sd];
+  const float thr_out = (R.correction == 3) ? s_W[m - 1] : s_W[0];
+  const float thr_in = (R.correction == 3) ? s_W[m - 1] : s_W[i];
+  WalkerOut O;
+  O.new_x = R.new_x + (size_t)i * d;
+  O.new_l = R.new_l + i;
+  O.hist_l = R.hist_l + (size_t)i * R.t_max;
+  O.hist_x = R.hist_x + (size_t)i * R.t_max * d;
+  O.hist_len = R.hist_len + i;
+  float* my_dirs = R.dirs + (size_t)i * R.n_steps * dir_row(DMAX);
+  if (act) draw_directions<DMAX>(SC, i, s_chol + (size_t)cid * d * d, my_dirs);
+  long long e = 0;
+  int f = 0;
+  slice_walker<DMAX>(P, SC, i, act, R.live_x + sd, R.n_pad, R.live_l[sd], my_dirs, s_slots + (size_t)tid * dir_row(DMAX),
+                     thr_out, thr_in, O, e, f);
+  ev = act ? e : 0;
+  fl = act ? f : 0;
+}
+
+// Blocks of up to 256 threads.  For the small register classes two such
+// blocks per SM cap the registers at 128 per thread (more runs resident per
+// SM hide the walkers' latency); the wide classes keep the full register
+// file.  NS_RUN_MINB overrides the choice at build time.
+#ifdef NS_RUN_MINB
+#define NS_MINB(D) NS_RUN_MINB
+#else
+#define NS_MINB(D) ((D) <= 12 ? 2 : 1)
+#endif
+template <int DMAX>
+__global__ void __launch_bounds__(256, NS_MINB(DMAX)) k_run(const RunDesc* __restrict__ runs, const int* __restrict__ ids,
                                              int chunk) {
   extern __shared__ __align__(16) char sm[];
   __shared__ RunDesc R;
@@ -197,7 +238,8 @@ __global__ void __launch_bounds__(256) k_run(const RunDesc* __restrict__ runs, c
   __syncthreads();
   if (RS.stopped || RS.status != 0) return;
   const int d = R.d, N = R.N, m = R.m;
-  const Carve cv = make_carve(d, m, R.n_nodes);
+  const Carve cv = make_carve(d, m, R.n_nodes, DMAX);
+  float* s_slots = reinterpret_cast<float*>(sm + cv.slots);
   LikParams& P = *reinterpret_cast<LikParams*>(sm + cv.lik);
   BlockScratch& S = *reinterpret_cast<BlockScratch*>(sm + cv.scr);
   SelectScratch& X = *reinterpret_cast<SelectScratch*>(sm + cv.sel);
@@ -211,6 +253,7 @@ __global__ void __launch_bounds__(256) k_run(const RunDesc* __restrict__ runs, c
   uint32_t* s_sel_key = reinterpret_cast<uint32_t*>(sm + cv.sel_key);
   const Cand A = cand_at(sm + cv.candA, m);
   const Cand Bf = cand_at(sm + cv.candB, m);
+  const Cand Tm = cand_at(sm + cv.candT, m);
   int* s_list = reinterpret_cast<int*>(sm + cv.list);
   float* s_vals = reinterpret_cast<float*>(sm + cv.vals);
   int* s_ctr = reinterpret_cast<int*>(sm + cv.ctr);
@@ -277,32 +320,15 @@ __global__ void __launch_bounds__(256) k_run(const RunDesc* __restrict__ runs, c
     long long ev = 0;
     int fl = 0;
     if ((tid & ~31) < m) {
-      const bool act = tid < m;
-      const int i = act ? tid : 0;
-      const int sd = s_seed[i];
-      const int cid = R.live_cid[sd];
-      const float thr_out = (R.correction == 3) ? s_W[m - 1] : s_W[0];
-      const float thr_in = (R.correction == 3) ? s_W[m - 1] : s_W[i];
       SC.t = t;
-      WalkerOut O;
-      O.new_x = R.new_x + (size_t)i * d;
-      O.new_l = R.new_l + i;
-      O.hist_l = R.hist_l + (size_t)i * R.t_max;
-      O.hist_x = R.hist_x + (size_t)i * R.t_max * d;
-      O.hist_len = R.hist_len + i;
-      slice_walker<DMAX>(P, SC, i, act, R.live_x + sd, R.n_pad, R.live_l[sd], s_chol + (size_t)cid * d * d,
-                         thr_out, thr_in, O, ev, fl);
-      if (!act) {
-        ev = 0;
-        fl = 0;
-      }
+      walker_phase<DMAX>(R, P, SC, s_W, s_seed, s_chol, s_slots, ev, fl);
     }
     __syncthreads();
     tick(kPhSlice);
     const long long ev_sum = block_sum_ll(ev, S);
     const long long capped = block_sum_ll(fl ? 1 : 0, S);
     // a8-a9: Algorithms 1 and 2
-    const int rel = batch_correct(m, R.K, R.correction, s_W, R.new_l, R.hist_l, R.hist_len, R.t_max, A, Bf,
+    const int rel = batch_correct(m, R.K, R.correction, s_W, R.new_l, R.hist_l, R.hist_len, R.t_max, A, Bf, Tm,
                                   s_list, s_vals, s_ctr, S);
     tick(kPhCorrect);
     // a10: dead append (rejected, ascending) and live update (accepted into S_W's slots)
@@ -394,22 +420,22 @@ template <int DMAX>
 __global__ void k_loglike(const LikParams P, int n, const float* __restrict__ x, float* __restrict__ out) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
   if (j >= n) return;
-  float xr[DMAX], v[DMAX];
+  float xr[DMAX];
 #pragma unroll
-  for (int i = 0; i < DMAX; ++i) {
-    xr[i] = (i < P.d) ? x[(size_t)j * P.d + i] : 0.f;
-    v[i] = 0.f;
-  }
-  out[j] = loglike<DMAX>(P, xr, v, 0.f, P.d);
+  for (int i = 0; i < DMAX; ++i) xr[i] = (i < P.d) ? x[(size_t)j * P.d + i] : 0.f;
+  out[j] = loglike_u<DMAX>(P, xr);
 }
 
+// Step-level slice kernel: dir_scratch holds the walkers' per-step tables,
+// [m][n_steps][dir_row(DMAX)].
 template <int DMAX>
 __global__ void k_slice(const LikParams P, SliceCfg SC, int m, int n_pad, int correction,
                         const float* __restrict__ live_x, const float* __restrict__ live_l,
                         const int* __restrict__ seed_slot, const float* __restrict__ W,
                         const float* __restrict__ chol, const int* __restrict__ cid, float* new_x,
                         float* new_l, float* hist_l, float* hist_x, int* hist_len, long long* evals,
-                        int* flags) {
+                        int* flags, float* dir_scratch) {
+  extern __shared__ __align__(16) char sm[];
   const int i0 = blockIdx.x * blockDim.x + threadIdx.x;
   const bool act = i0 < m;
   const int i = act ? i0 : 0;
@@ -424,18 +450,22 @@ __global__ void k_slice(const LikParams P, SliceCfg SC, int m, int n_pad, int co
   O.hist_l = hist_l + (size_t)i * SC.t_max;
   O.hist_x = hist_x + (size_t)i * SC.t_max * d;
   O.hist_len = hist_len + i;
+  float* my_dirs = dir_scratch + (size_t)i * SC.n_steps * dir_row(DMAX);
+  if (act) draw_directions<DMAX>(SC, i, chol + (size_t)c * d * d, my_dirs);
   long long ev = 0;
   int fl = 0;
-  slice_walker<DMAX>(P, SC, i, act, live_x + sd, n_pad, live_l[sd], chol + (size_t)c * d * d, thr_out,
-                     thr_in, O, ev, fl);
+  float* slot = reinterpret_cast<float*>(sm) + (size_t)threadIdx.x * dir_row(DMAX);
+  slice_walker<DMAX>(P, SC, i, act, live_x + sd, n_pad, live_l[sd], my_dirs, slot, thr_out, thr_in, O, ev, fl);
   if (act) {
     evals[i] = ev;
     flags[i] = fl;
   }
 }
 
+// Register classes: a run of dimension d uses the smallest class >= d.
+#define NS_FOR_EACH_CLASS(X) X(2) X(4) X(6) X(8) X(10) X(12) X(16) X(20) X(24) X(28) X(32)
 
-// Launchers, one set per dimension class (defined in ns_inst.cu).
+// Launchers, one set per class (defined in ns_inst.cu).
 #define NS_DECLARE_LAUNCHERS(D)                                                                          \
   cudaError_t launch_run_##D(const RunDesc* runs, const int* ids, int n, int block, size_t smem, int chunk, \
                              cudaStream_t s);                                                            \
@@ -444,10 +474,8 @@ __global__ void k_slice(const LikParams P, SliceCfg SC, int m, int n_pad, int co
                                const float* live_x, const float* live_l, const int* seed_slot,           \
                                const float* W, const float* chol, const int* cid, float* new_x,          \
                                float* new_l, float* hist_l, float* hist_x, int* hist_len, long long* evals, \
-                               int* flags, cudaStream_t s);
-NS_DECLARE_LAUNCHERS(4)
-NS_DECLARE_LAUNCHERS(8)
-NS_DECLARE_LAUNCHERS(16)
-NS_DECLARE_LAUNCHERS(32)
+                               int* flags, float* dir_scratch, cudaStream_t s);                            \
+  cudaError_t occupancy_run_##D(int block, size_t smem, int* blocks_per_sm);
+NS_FOR_EACH_CLASS(NS_DECLARE_LAUNCHERS)
 
 }  // namespace nsd
