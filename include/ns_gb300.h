@@ -315,13 +315,26 @@ ns_status ns_evidence_update(int N, int n, const float* dead_l, double* state, d
                              int live, void* stream);
 
 /* a3 (section 2.1): cluster tree of one live set live_x [d][n_pad] (device)
- * at iteration t: node centres [n_nodes][d], Cholesky factors chol
- * [n_nodes][d][d] (FP32) and chol64 (FP64), log volumes [n_nodes],
- * counts [n_nodes], split flags [n_nodes], accepted-leaf mask [n_nodes]
- * and each point's leaf cid [N] (all device).  n_nodes = 2^(depth+1) - 1. */
+ * at iteration t: the root is the whole set; for depth >= 1 every node is
+ * split by 2-means (points whitened by the root's Cholesky factor; first
+ * centre the Philox-chosen member of stream (t, node, NS_PURPOSE_KMEANS),
+ * second the member farthest from it; Lloyd iterations to a fixed point or
+ * kmeans_iters), then the tree is pruned bottom-up (children replace their
+ * parent only if both hold more than n_min points and their bounding-
+ * ellipsoid volumes add up to less than (1 - vol_frac) of the parent's).
+ * Outputs (device): node centres [n_nodes][d], Cholesky factors chol
+ * [n_nodes][d][d] (FP32) and chol64 (FP64), log volumes [n_nodes] (unit-ball
+ * constant dropped), counts [n_nodes], split flags [n_nodes], accepted-leaf
+ * mask [n_nodes] and each point's leaf cid [N].  n_nodes = 2^(depth+1) - 1.
+ * scratch: ns_cluster_scratch_bytes(N, n_pad, d) bytes of device memory
+ * (unused, may be NULL, at depth 0). */
 ns_status ns_cluster(int N, int n_pad, int d, const float* live_x, const ns_options* opt,
                      uint64_t seed, uint32_t t, float* centres, float* chol, double* chol64,
-                     float* logvol, int* count, int* split, int* mask, int* cid, void* stream);
+                     float* logvol, int* count, int* split, int* mask, int* cid, void* scratch,
+                     void* stream);
+
+/* Bytes of scratch that ns_cluster needs (0 for bad sizes). */
+size_t ns_cluster_scratch_bytes(int N, int n_pad, int d);
 
 #ifdef __cplusplus
 }

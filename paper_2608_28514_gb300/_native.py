@@ -119,7 +119,9 @@ def lib():
     L.ns_batch_correct.argtypes = [C.c_int, C.c_int, C.c_int, _vp, _vp, _vp, _vp, C.c_int] + [_vp] * 10
     L.ns_evidence_update.argtypes = [C.c_int, C.c_int, _vp, _vp, _vp, C.c_int, _vp]
     L.ns_cluster.argtypes = [C.c_int, C.c_int, C.c_int, _vp, C.POINTER(NsOptions), C.c_uint64, C.c_uint32,
-                             _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+                             _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.ns_cluster_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
+    L.ns_cluster_scratch_bytes.restype = C.c_size_t
     for name in ("ns_default_options", "ns_create", "ns_create_batch", "ns_run", "ns_reset", "ns_result", "ns_summary",
                  "ns_phase_cycles", "ns_run_noalloc",
                  "ns_last_run_ms", "ns_get_stats", "ns_philox4x32_10", "ns_loglike", "ns_select_worst", "ns_slice_replace",
@@ -416,9 +418,19 @@ def ns_evidence_update(N, dead_l, state, logw, live=False, stream=None):
                                     1 if live else 0, _stream_ptr(stream)))
 
 
+def ns_cluster_scratch_bytes(N, n_pad, d):
+    return int(lib().ns_cluster_scratch_bytes(int(N), int(n_pad), int(d)))
+
+
 def ns_cluster(N, n_pad, d, live_x, opt, seed, t, centres, chol, chol64, logvol, count, split, mask, cid,
-               stream=None):
+               scratch=None, stream=None):
+    """scratch: a device tensor of ns_cluster_scratch_bytes(N, n_pad, d)
+    bytes (allocated here with torch when not given)."""
+    if scratch is None:
+        import torch
+        nb = ns_cluster_scratch_bytes(N, n_pad, d)
+        scratch = torch.empty(max(1, nb), dtype=torch.uint8, device=live_x.device)
     _check(lib().ns_cluster(int(N), int(n_pad), int(d), _ptr(live_x), C.byref(opt) if opt is not None else None,
                             int(seed) & (2**64 - 1), int(t) & 0xFFFFFFFF, _ptr(centres), _ptr(chol),
                             _ptr(chol64), _ptr(logvol), _ptr(count), _ptr(split), _ptr(mask), _ptr(cid),
-                            _stream_ptr(stream)))
+                            _ptr(scratch), _stream_ptr(stream)))

@@ -102,11 +102,11 @@ __global__ void k_evidence(int N, int n, const float* __restrict__ l, double* st
   }
 }
 
-__global__ void k_cluster(RunDesc R) {
+__global__ void k_cluster(RunDesc R, uint32_t t) {
   extern __shared__ __align__(16) char sm[];
   __shared__ BlockScratch S;
   const Carve cv = make_carve(R.d, 1, R.n_nodes, kMaxDim);
-  cluster_phase(R, sm, cv, S);
+  cluster_phase(R, t, sm, cv, S);
 }
 
 // ---------------------------------------------------------------------------
@@ -228,10 +228,6 @@ ns_status check_opts(const ns_options& o, std::string* err) {
   if (o.depth < 0 || o.depth > NS_MAX_DEPTH) {
     set_err(err, "depth must be in 0..%d", NS_MAX_DEPTH);
     return NS_ERR_ARG;
-  }
-  if (o.depth > 0) {
-    set_err(err, "cluster trees deeper than 0 are not available in this build");
-    return NS_ERR_UNSUPPORTED;
   }
   if (o.recluster_every < 0 || o.kmeans_iters < 0 || o.history_iters < 0 || o.e_max < 0 || o.s_max < 1 ||
       o.t_max < 1 || o.t_max > NS_MAX_HISTORY || !(o.width > 0) || !std::isfinite(o.width) ||
@@ -422,7 +418,7 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     return o;
   };
   struct Off {
-    size_t lik, live_x, live_l, live_cid, new_x, new_l, hist_l, hist_x, hist_len, stage_x, dirs, dead_x,
+    size_t lik, live_x, live_l, live_cid, new_x, new_l, hist_l, hist_x, hist_len, stage_x, dirs, wsp, side, dead_x,
         dead_l, dead_logw, centres, chol, chol64, logvol, count, split, mask;
   };
   std::vector<Off> off(n_runs);
@@ -444,6 +440,8 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     o.hist_len = take(sizeof(int) * m);
     o.stage_x = take(sizeof(float) * (size_t)m * d);
     o.dirs = take(sizeof(float) * (size_t)m * p.n_slice_steps * dir_row(dmax_class(d)));
+    o.wsp = take(opt.depth > 0 ? sizeof(float) * (size_t)d * n_pad : 16);
+    o.side = take(opt.depth > 0 ? sizeof(int) * (size_t)N : 16);
     o.dead_x = take(sizeof(float) * (size_t)cap * d);
     o.dead_l = take(sizeof(float) * (size_t)cap);
     o.dead_logw = take(sizeof(double) * (size_t)cap);
@@ -526,6 +524,8 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     R.hist_len = reinterpret_cast<int*>(base + o.hist_len);
     R.stage_x = reinterpret_cast<float*>(base + o.stage_x);
     R.dirs = reinterpret_cast<float*>(base + o.dirs);
+    R.wsp = reinterpret_cast<float*>(base + o.wsp);
+    R.side = reinterpret_cast<int*>(base + o.side);
     R.dead_x = reinterpret_cast<float*>(base + o.dead_x);
     R.dead_l = reinterpret_cast<float*>(base + o.dead_l);
     R.dead_logw = reinterpret_cast<double*>(base + o.dead_logw);
@@ -575,6 +575,11 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     }
     g.block = block_for_m(maxm);
     g.smem = smem;
+    if (smem > 227 * 1024) {
+      set_err(nullptr, "runs of dimension class %d need %zu bytes of shared memory (limit 227 KB): "
+              "lower the tree depth or m", g.dmax, smem);
+      return fail(NS_ERR_ARG);
+    }
     e = cudaMemcpy(g.d_ids, members[ci].data(), sizeof(int) * g.n, cudaMemcpyHostToDevice);
     h->h2d_bytes += (long long)sizeof(int) * g.n;
     if (e != cudaSuccess) {
@@ -839,6 +844,8 @@ ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt_in, fl
                o_hist_x = take(sizeof(float) * (size_t)m * opt.t_max * d), o_hist_len = take(sizeof(int) * m),
                o_stage_x = take(sizeof(float) * (size_t)m * d),
                o_dirs = take(sizeof(float) * (size_t)m * p.n_slice_steps * dir_row(dmax_class(d))),
+               o_wsp = take(opt.depth > 0 ? sizeof(float) * (size_t)d * n_pad : 16),
+               o_side = take(opt.depth > 0 ? sizeof(int) * (size_t)N : 16),
                o_centres = take(sizeof(float) * n_nodes * d),
                o_chol = take(sizeof(float) * n_nodes * d * d), o_chol64 = take(sizeof(double) * n_nodes * d * d),
                o_logvol = take(sizeof(float) * n_nodes), o_count = take(sizeof(int) * n_nodes),
@@ -903,6 +910,8 @@ ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt_in, fl
   R.hist_len = reinterpret_cast<int*>(base + o_hist_len);
   R.stage_x = reinterpret_cast<float*>(base + o_stage_x);
   R.dirs = reinterpret_cast<float*>(base + o_dirs);
+  R.wsp = reinterpret_cast<float*>(base + o_wsp);
+  R.side = reinterpret_cast<int*>(base + o_side);
   R.dead_x = dead_x;
   R.dead_l = dead_logl;
   R.dead_logw = dead_logw;
@@ -1100,16 +1109,21 @@ ns_status ns_evidence_update(int N, int n, const float* dead_l, double* state, d
   return NS_OK;
 }
 
+size_t ns_cluster_scratch_bytes(int N, int n_pad, int d) {
+  if (N < 2 || n_pad < N || d < 1 || d > NS_MAX_DIM) return 0;
+  return sizeof(float) * (size_t)d * n_pad + sizeof(int) * (size_t)N;
+}
+
 ns_status ns_cluster(int N, int n_pad, int d, const float* live_x, const ns_options* opt_in, uint64_t seed,
                      uint32_t t, float* centres, float* chol, double* chol64, float* logvol, int* count, int* split,
-                     int* mask, int* cid, void* stream) {
+                     int* mask, int* cid, void* scratch, void* stream) {
   ns_options opt;
   if (opt_in) opt = *opt_in;
   else ns_default_options(&opt);
   ns_status st = check_opts(opt, nullptr);
   if (st != NS_OK) return st;
   if (N < 2 || n_pad < N || d < 1 || d > NS_MAX_DIM || !live_x || !centres || !chol || !chol64 || !logvol ||
-      !count || !split || !mask || !cid) {
+      !count || !split || !mask || !cid || (opt.depth > 0 && !scratch)) {
     set_err(nullptr, "ns_cluster: bad arguments");
     return NS_ERR_ARG;
   }
@@ -1135,10 +1149,17 @@ ns_status ns_cluster(int N, int n_pad, int d, const float* live_x, const ns_opti
   R.count = count;
   R.split = split;
   R.mask = mask;
-  (void)t;
+  if (opt.depth > 0) {
+    R.wsp = static_cast<float*>(scratch);
+    R.side = reinterpret_cast<int*>(static_cast<char*>(scratch) + sizeof(float) * (size_t)d * n_pad);
+  }
   const size_t smem = make_carve(d, 1, R.n_nodes, kMaxDim).total;
+  if (smem > 227 * 1024) {
+    set_err(nullptr, "ns_cluster: %zu bytes of shared memory needed (limit 227 KB)", smem);
+    return NS_ERR_ARG;
+  }
   NS_CUDA(cudaFuncSetAttribute(k_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem), nullptr);
-  k_cluster<<<1, 256, smem, (cudaStream_t)stream>>>(R);
+  k_cluster<<<1, 256, smem, (cudaStream_t)stream>>>(R, t);
   NS_CUDA(cudaGetLastError(), nullptr);
   return NS_OK;
 }

@@ -5,6 +5,7 @@
 #pragma once
 
 #include "../../include/ns_gb300.h"
+#include "ns_cluster.cuh"
 #include "ns_device.cuh"
 
 namespace nsd {
@@ -40,6 +41,8 @@ struct RunDesc {
   int* hist_len;
   float* stage_x;
   float* dirs;     // [m][n_steps][dir_row(DMAX of the run's class)] per-step directions and draws
+  float* wsp;      // [d][n_pad] whitened live points (cluster tree, depth >= 1)
+  int* side;       // [N] child choices of each live point (cluster tree)
   float* dead_x;
   float* dead_l;
   double* dead_logw;
@@ -57,7 +60,7 @@ struct RunDesc {
 // device from the run's sizes.
 struct Carve {
   size_t lik, scr, sel, chol, cent, mask, worst, W, seed, sel_slot, sel_key, candA, candB, candT, list, vals, slots,
-      ctr, stage_cid, tile, acc, c64, l64, work, total;
+      ctr, stage_cid, tile, acc, c64, l64, work, tree, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
@@ -94,6 +97,7 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax)
   c.c64 = take(sizeof(double) * d * d);
   c.l64 = take(sizeof(double) * d * d);
   c.work = take(sizeof(double) * (3 * d * d + d));
+  c.tree = take(tree_bytes(d, n_nodes, 8, tree_chol_warps(d, 8)));
   c.total = o;
   return c;
 }
@@ -126,8 +130,10 @@ inline __device__ void init_live(const RunDesc& R, const LikParams& P) {
   }
 }
 
-// a3 for depth 0: one cluster, the whole live set.
-inline __device__ void cluster_phase(const RunDesc& R, char* sm, const Carve& cv, BlockScratch& S) {
+// a3 (section 2.1): the root node is the whole live set (mean, covariance,
+// regularised FP64 Cholesky); for depth >= 1 the tree of cluster_tree
+// follows.
+inline __device__ void cluster_phase(const RunDesc& R, uint32_t t, char* sm, const Carve& cv, BlockScratch& S) {
   const int d = R.d;
   float* tile = reinterpret_cast<float*>(sm + cv.tile);
   double* acc = reinterpret_cast<double*>(sm + cv.acc);
@@ -151,15 +157,49 @@ inline __device__ void cluster_phase(const RunDesc& R, char* sm, const Carve& cv
     s_cent[i] = (float)acc[i];
     R.centres[i] = (float)acc[i];
   }
-  if (threadIdx.x == 0) {
-    s_mask[0] = 1;
-    R.mask[0] = 1;
-    R.split[0] = 0;
-    R.count[0] = n;
-    R.logvol[0] = 0.f;
+  if (R.n_nodes == 1) {
+    if (threadIdx.x == 0) {
+      s_mask[0] = 1;
+      R.mask[0] = 1;
+      R.split[0] = 0;
+      R.count[0] = n;
+      R.logvol[0] = 0.f;
+    }
+    for (int j = threadIdx.x; j < R.N; j += blockDim.x) R.live_cid[j] = 0;
+    __syncthreads();
+    return;
   }
-  for (int j = threadIdx.x; j < R.N; j += blockDim.x) R.live_cid[j] = 0;
+  const int nw = blockDim.x >> 5;
+  const int nw_chol = tree_chol_warps(d, 8) < nw ? tree_chol_warps(d, 8) : nw;
+  const TreeScratch T = tree_carve(sm + cv.tree, d, nw, tree_chol_warps(d, 8));
+  if (threadIdx.x == 0) T.node_n[0] = n;
   __syncthreads();
+  TreeIO io;
+  io.x = R.live_x;
+  io.y = R.wsp;
+  io.side = R.side;
+  io.N = R.N;
+  io.n_pad = R.n_pad;
+  io.d = d;
+  io.depth = R.depth;
+  io.n_min = R.n_min;
+  io.kmeans_iters = R.kmeans_iters;
+  io.vol_frac = R.vol_frac;
+  io.k0 = R.k0;
+  io.k1 = R.k1;
+  io.t = t;
+  io.centres = R.centres;
+  io.chol = R.chol;
+  io.chol64 = R.chol64;
+  io.logvol = R.logvol;
+  io.count = R.count;
+  io.split = R.split;
+  io.mask = R.mask;
+  io.cid = R.live_cid;
+  io.s_chol = s_chol;
+  io.s_cent = s_cent;
+  io.s_mask = s_mask;
+  cluster_tree(io, T, S, nw_chol);
 }
 
 inline __device__ int nearest_leaf(const float* x, int d, int n_nodes, const float* cent, const int* mask) {
@@ -311,7 +351,7 @@ __global__ void __launch_bounds__(256, NS_MINB(DMAX)) k_run(const RunDesc* __res
       }
     };
     // a3: clustering
-    if (R.recluster_every > 0 && (t % (uint32_t)R.recluster_every) == 0) cluster_phase(R, sm, cv, S);
+    if (R.recluster_every > 0 && (t % (uint32_t)R.recluster_every) == 0) cluster_phase(R, t, sm, cv, S);
     tick(kPhCluster);
     // a1-a2: selection
     select_worst(R.live_l, N, m, R.k0, R.k1, t, s_sel_slot, s_sel_key, s_worst, s_W, s_seed, X, S);

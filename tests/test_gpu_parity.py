@@ -395,3 +395,84 @@ def test_budget_is_reported_not_hung(nat):
     res = nat.ns_result(h, 0)
     assert res["status"] == nat.NS_ERR_BUDGET and res["n_iter"] == 5
     nat.ns_destroy(h)
+
+
+# --------------------------------------------------------------------------
+# a3 cluster tree (depth >= 1)
+# --------------------------------------------------------------------------
+def _tree_case(nat, oracle, x, depth, seed=3, t=0):
+    N, d = x.shape
+    n_pad = ((N + 31) // 32) * 32
+    live_x = np.zeros((d, n_pad), dtype=np.float32)
+    live_x[:, :N] = x.T
+    nn = (1 << (depth + 1)) - 1
+    opt = nat.ns_default_options(depth=depth)
+    o = dict(centres=torch.zeros(nn, d, device=DEV), chol=torch.zeros(nn, d, d, device=DEV),
+             chol64=torch.zeros(nn, d, d, dtype=torch.float64, device=DEV), logvol=torch.zeros(nn, device=DEV),
+             count=torch.zeros(nn, dtype=torch.int32, device=DEV), split=torch.zeros(nn, dtype=torch.int32, device=DEV),
+             mask=torch.zeros(nn, dtype=torch.int32, device=DEV), cid=torch.full((N,), -1, dtype=torch.int32, device=DEV))
+    nat.ns_cluster(N, n_pad, d, _t(live_x), opt, seed, t, **o)
+    torch.cuda.synchronize()
+    g = {k: v.cpu().numpy() for k, v in o.items()}
+    want = oracle.cluster(x.astype(np.float64), oracle.opts(d, 1, depth=depth), seed, t)
+    return g, want
+
+
+def _blobs(rng, centres, sd, n):
+    return np.vstack([rng.normal(c, sd, size=(n, len(c))) for c in centres]).astype(np.float32)
+
+
+@pytest.mark.parametrize("case", ["two_blobs_d1", "four_modes_d3", "ball_d2", "eight_blobs_d3"])
+def test_cluster_tree_matches_oracle(nat, oracle, case):
+    rng = np.random.default_rng(hash(case) % 2**32)
+    if case == "two_blobs_d1":
+        x, depth = _blobs(rng, [[0.25, 0.3, 0.3], [0.75, 0.7, 0.6]], 0.03, 150), 1
+    elif case == "four_modes_d3":
+        p = W.mixture4_d5(1)
+        th = np.vstack([c + p.sigma * rng.standard_normal((250, 5)) for c in p.centres])
+        x, depth = ((th - p.lo) / (p.hi - p.lo)).astype(np.float32), 3
+    elif case == "ball_d2":
+        gv = rng.normal(size=(1200, 3))
+        x = (0.5 + 0.2 * gv / np.linalg.norm(gv, axis=1, keepdims=True) * rng.uniform(0, 1, (1200, 1)) ** (1 / 3))
+        x, depth = x.astype(np.float32), 2
+    else:
+        cs = [[0.2 + 0.6 * (k & 1), 0.2 + 0.6 * ((k >> 1) & 1), 0.2 + 0.6 * ((k >> 2) & 1), 0.5] for k in range(8)]
+        x, depth = _blobs(rng, cs, 0.02, 120), 3
+    x = rng.permutation(x)
+    g, want = _tree_case(nat, oracle, x, depth)
+    np.testing.assert_array_equal(g["split"], want["split"])
+    np.testing.assert_array_equal(g["mask"], want["mask"])
+    np.testing.assert_array_equal(g["count"], want["count"])
+    np.testing.assert_array_equal(g["cid"], want["assign"])
+    used = want["count"] > 1
+    np.testing.assert_allclose(g["centres"][used], want["centres"][used], atol=2e-6)
+    np.testing.assert_allclose(g["chol64"][used], want["chol"][used], rtol=2e-3, atol=2e-6)
+    fin = np.isfinite(want["logvol"]) & used
+    np.testing.assert_allclose(g["logvol"][fin], want["logvol"][fin], rtol=1e-4, atol=1e-3)
+
+
+def test_cluster_tree_invariants_on_uniform_points(nat, oracle):
+    rng = np.random.default_rng(77)
+    x = rng.uniform(size=(1500, 4)).astype(np.float32)
+    g, want = _tree_case(nat, oracle, x, 2)
+    assert np.all(g["mask"][g["cid"]] == 1)
+    assert g["count"][0] == 1500
+    leaves = np.flatnonzero(g["mask"])
+    assert sum(int(np.sum(g["cid"] == lf)) for lf in leaves) == 1500
+    # a uniform cube is not split by the volume rule
+    assert g["split"][0] == want["split"][0] == 0
+
+
+def test_mixture_run_with_cluster_tree(nat):
+    """4-mode mixture, N = 2000, m = 200, depth-3 tree: log Z against the
+    closed form (erf products)."""
+    p = W.mixture4_d5(1)
+    truth = A.logz(p)
+    o = nat.ns_default_options(depth=3)
+    h = nat.ns_create_batch([(p, 2000, 200, 25, 1e-3, s) for s in (1, 2, 3)], o)
+    nat.ns_run(h)
+    for r in range(3):
+        res = nat.ns_result(h, r)
+        assert res["status"] == 0
+        assert abs(res["log_z"] - truth) < 4 * res["log_z_err"] + 0.05, (r, res["log_z"], truth)
+    nat.ns_destroy(h)
