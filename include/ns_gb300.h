@@ -336,6 +336,27 @@ ns_status ns_cluster(int N, int n_pad, int d, const float* live_x, const ns_opti
 /* Bytes of scratch that ns_cluster needs (0 for bad sizes). */
 size_t ns_cluster_scratch_bytes(int N, int n_pad, int d);
 
+/* a7, MLP likelihood (the emulator of section 5, replaced by a SiLU MLP and
+ * a chi^2 against a data vector).  The weights live on the device as one
+ * packed image: BF16 copies in the tensor cores' 128-byte-swizzled tile
+ * layout (128 output features x 64 inputs per 16 KB tile), then FP32 biases,
+ * data, 1/sigma and the FP32 weights.  Hidden layers up to 512 wide; the
+ * output layer any width.
+ * ns_mlp_image_bytes: size of that image for `lik` (0 if it does not fit).
+ * ns_mlp_pack: builds the image on the host and copies it to `image`
+ *   (device, 1024-byte aligned, caller-owned); synchronous on `stream`. */
+size_t ns_mlp_image_bytes(const ns_likelihood* lik, int d);
+ns_status ns_mlp_pack(const ns_likelihood* lik, int d, void* image, void* stream);
+
+/* log L of n points x [n][d] (device, unit cube) -> logl [n] (device):
+ * precision 1 = BF16 inputs, weights and activations on the tensor cores
+ * (tcgen05, FP32 accumulation in tensor memory), 64 points per block;
+ * precision 0 = FP32 on the CUDA cores.  A block whose tensor-core pipeline
+ * stalls past its wait budget writes NaN for its points. */
+ns_status ns_mlp_loglike(const ns_likelihood* lik, const double* lo, const double* hi, int d,
+                         const void* image, int n, const float* x, float* logl, int precision,
+                         void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -120,6 +120,13 @@ def lib():
     L.ns_evidence_update.argtypes = [C.c_int, C.c_int, _vp, _vp, _vp, C.c_int, _vp]
     L.ns_cluster.argtypes = [C.c_int, C.c_int, C.c_int, _vp, C.POINTER(NsOptions), C.c_uint64, C.c_uint32,
                              _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp, _vp]
+    L.ns_mlp_image_bytes.argtypes = [C.POINTER(NsLikelihood), C.c_int]
+    L.ns_mlp_image_bytes.restype = C.c_size_t
+    L.ns_mlp_pack.argtypes = [C.POINTER(NsLikelihood), C.c_int, _vp, _vp]
+    L.ns_mlp_pack.restype = C.c_int
+    L.ns_mlp_loglike.argtypes = [C.POINTER(NsLikelihood), C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
+                                 _vp, C.c_int, _vp, _vp, C.c_int, _vp]
+    L.ns_mlp_loglike.restype = C.c_int
     L.ns_cluster_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
     L.ns_cluster_scratch_bytes.restype = C.c_size_t
     for name in ("ns_default_options", "ns_create", "ns_create_batch", "ns_run", "ns_reset", "ns_result", "ns_summary",
@@ -416,6 +423,28 @@ def ns_batch_correct(m, K, correction, W, new_l, hist_l, hist_len, t_max, acc_sr
 def ns_evidence_update(N, dead_l, state, logw, live=False, stream=None):
     _check(lib().ns_evidence_update(int(N), int(dead_l.numel()), _ptr(dead_l), _ptr(state), _ptr(logw),
                                     1 if live else 0, _stream_ptr(stream)))
+
+
+def ns_mlp_image_bytes(problem):
+    keep = _Keep()
+    lik = likelihood_struct(problem, keep)
+    return int(lib().ns_mlp_image_bytes(C.byref(lik), int(problem.d)))
+
+
+def ns_mlp_pack(problem, image, stream=None):
+    """image: a device uint8 tensor of ns_mlp_image_bytes(problem) bytes,
+    1024-byte aligned."""
+    keep = _Keep()
+    lik = likelihood_struct(problem, keep)
+    _check(lib().ns_mlp_pack(C.byref(lik), int(problem.d), _ptr(image), _stream_ptr(stream)))
+
+
+def ns_mlp_loglike(problem, image, x, logl, precision=1, stream=None):
+    keep = _Keep()
+    lik = likelihood_struct(problem, keep)
+    _check(lib().ns_mlp_loglike(C.byref(lik), keep.dptr(problem.lo), keep.dptr(problem.hi), int(problem.d),
+                                _ptr(image), int(x.shape[0]), _ptr(x), _ptr(logl), int(precision),
+                                _stream_ptr(stream)))
 
 
 def ns_cluster_scratch_bytes(N, n_pad, d):

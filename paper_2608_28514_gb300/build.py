@@ -19,7 +19,8 @@ CLASSES = (2, 4, 6, 8, 10, 12, 16, 20, 24, 28, 32)
 
 
 def _sources():
-    out = [(os.path.join(CSRC, "ns_lib.cu"), os.path.join(BUILD, "ns_lib.o"), [])]
+    out = [(os.path.join(CSRC, "ns_lib.cu"), os.path.join(BUILD, "ns_lib.o"), []),
+           (os.path.join(CSRC, "ns_mlp.cu"), os.path.join(BUILD, "ns_mlp.o"), [])]
     for d in CLASSES:
         out.append((os.path.join(CSRC, "ns_inst.cu"), os.path.join(BUILD, f"ns_inst_{d}.o"),
                     [f"-DNS_DMAX={d}"]))

@@ -1,0 +1,211 @@
+// ns_mlp.cu -- batched evaluation of the MLP (emulator-style) likelihood:
+// the packed weight image, the BF16 tensor-core evaluator (tcgen05, TMA bulk
+// copies, tensor memory) and the FP32 CUDA-core evaluator, behind the C ABI.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/ns_gb300.h"
+#include "ns_mlp.cuh"
+
+using namespace nsd;
+
+namespace {
+
+__global__ void __launch_bounds__(128, 1)
+    k_mlp_bf16(const MlpDesc M, const uint8_t* __restrict__ tiles, const float* __restrict__ f32,
+               const float* __restrict__ x, int n, float* __restrict__ out) {
+  extern __shared__ __align__(1024) char sm_raw[];
+  const unsigned base = smem_u32(sm_raw);
+  char* sm = sm_raw + ((1024u - (base & 1023u)) & 1023u);
+  const int b0 = blockIdx.x * kMlpNb;
+  const int nb = min(kMlpNb, n - b0);
+  const bool ok = mlp_eval_bf16(M, tiles, f32, x + (size_t)b0 * M.d, M.d, nb, out + b0, sm);
+  if (!ok)
+    for (int r = threadIdx.x; r < nb; r += blockDim.x) out[b0 + r] = __int_as_float(0x7fffffff);
+}
+
+__global__ void __launch_bounds__(256)
+    k_mlp_f32(const MlpDesc M, const float* __restrict__ f32, const float* __restrict__ x, int n,
+              float* __restrict__ out) {
+  __shared__ float act[2 * kMlpF32Nb * kMlpMaxK];
+  const int b0 = blockIdx.x * kMlpF32Nb;
+  const int nb = min(kMlpF32Nb, n - b0);
+  mlp_eval_f32(M, f32, x + (size_t)b0 * M.d, M.d, nb, out + b0, act);
+}
+
+int round_up(int v, int q) { return (v + q - 1) / q * q; }
+
+// Host description of the image; false (with a message) if the network does
+// not fit the evaluators.
+bool make_desc(const ns_likelihood& L, const double* lo, const double* hi, int d, MlpDesc* M, std::string* msg) {
+  std::memset(M, 0, sizeof(*M));
+  if (L.kind != NS_LIK_MLP || L.n_layers < 1 || L.n_layers > kMlpMaxLayers || !L.widths || !L.weights ||
+      !L.biases || !L.data || !L.sigma_out) {
+    *msg = "MLP likelihood needs 1..8 layers with widths, weights, biases, data and sigma_out";
+    return false;
+  }
+  if (L.widths[0] != d || d > kMaxDim) {
+    *msg = "MLP widths[0] must equal d (<= 32)";
+    return false;
+  }
+  M->n_layers = L.n_layers;
+  M->d = d;
+  for (int i = 0; i < d; ++i) {
+    M->lo[i] = (float)lo[i];
+    M->span[i] = (float)(hi[i] - lo[i]);
+  }
+  int tiles = 0;
+  long long f = 0;
+  for (int l = 0; l < L.n_layers; ++l) {
+    const int in = L.widths[l], out = L.widths[l + 1];
+    if (in < 1 || out < 1 || out > 65536) {
+      *msg = "MLP widths must be positive (and <= 65536)";
+      return false;
+    }
+    M->in[l] = in;
+    M->out[l] = out;
+    M->kpad[l] = round_up(in, 64);
+    M->mpad[l] = round_up(out, 128);
+    if (M->kpad[l] > kMlpMaxK || (l + 1 < L.n_layers && M->mpad[l] > kMlpMaxK)) {
+      *msg = "MLP layers wider than 512 are supported only as the output layer";
+      return false;
+    }
+    M->tile0[l] = tiles;
+    tiles += (M->mpad[l] / 128) * (M->kpad[l] / 64);
+    M->bias0[l] = f;
+    f += M->mpad[l];
+  }
+  const int last = L.n_layers - 1;
+  M->data0 = f;
+  f += M->mpad[last];
+  M->isig0 = f;
+  f += M->mpad[last];
+  for (int l = 0; l < L.n_layers; ++l) {
+    M->w32_0[l] = f;
+    f += (long long)M->in[l] * M->out[l];
+  }
+  M->n_tiles = tiles;
+  M->tile_bytes = (long long)tiles * kMlpTileBytes;
+  M->f32_floats = f;
+  for (int k = 0; k < L.widths[last + 1]; ++k)
+    if (!(L.sigma_out[k] > 0.f) || !std::isfinite(L.sigma_out[k]) || !std::isfinite(L.data[k])) {
+      *msg = "MLP sigma_out must be positive and data finite";
+      return false;
+    }
+  return true;
+}
+
+uint16_t bf16_bits(float v) {
+  uint32_t u;
+  std::memcpy(&u, &v, 4);
+  const uint32_t rounding = ((u >> 16) & 1u) + 0x7FFFu;
+  return (uint16_t)((u + rounding) >> 16);
+}
+
+std::string g_mlp_err;
+
+}  // namespace
+
+// Shared with ns_lib.cu (validation of MLP runs).
+bool ns_mlp_make_desc(const ns_likelihood& L, const double* lo, const double* hi, int d, MlpDesc* M,
+                      std::string* msg) {
+  return make_desc(L, lo, hi, d, M, msg);
+}
+
+void ns_mlp_pack_host(const ns_likelihood& L, const MlpDesc& M, std::vector<uint8_t>& img) {
+  img.assign((size_t)M.tile_bytes + sizeof(float) * (size_t)M.f32_floats, 0);
+  const float* W = L.weights;
+  const float* Bv = L.biases;
+  for (int l = 0; l < M.n_layers; ++l) {
+    const int in = M.in[l], out = M.out[l], MT = M.mpad[l] / 128, KB = M.kpad[l] / 64;
+    for (int t = 0; t < MT; ++t)
+      for (int kb = 0; kb < KB; ++kb) {
+        uint8_t* tile = img.data() + (size_t)(M.tile0[l] + t * KB + kb) * kMlpTileBytes;
+        for (int r = 0; r < 128; ++r)
+          for (int k = 0; k < 64; ++k) {
+            const int f = t * 128 + r, i = kb * 64 + k;
+            const float v = (f < out && i < in) ? W[(size_t)f * in + i] : 0.f;
+            const uint16_t b = bf16_bits(v);
+            std::memcpy(tile + sw128_offset(r, k), &b, 2);
+          }
+      }
+    float* f32 = reinterpret_cast<float*>(img.data() + M.tile_bytes);
+    for (int o = 0; o < out; ++o) f32[M.bias0[l] + o] = Bv[o];
+    std::memcpy(f32 + M.w32_0[l], W, sizeof(float) * (size_t)in * out);
+    W += (size_t)in * out;
+    Bv += out;
+  }
+  float* f32 = reinterpret_cast<float*>(img.data() + M.tile_bytes);
+  const int last = M.n_layers - 1;
+  for (int k = 0; k < M.out[last]; ++k) {
+    f32[M.data0 + k] = L.data[k];
+    f32[M.isig0 + k] = 1.f / L.sigma_out[k];
+  }
+}
+
+cudaError_t ns_mlp_launch(const MlpDesc& M, const void* image, int n, const float* x, float* logl, int precision,
+                          cudaStream_t s) {
+  const uint8_t* tiles = static_cast<const uint8_t*>(image);
+  const float* f32 = reinterpret_cast<const float*>(tiles + M.tile_bytes);
+  if (precision == 1) {
+    const int smem = MlpSmem::kBytes + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_mlp_bf16<<<(n + kMlpNb - 1) / kMlpNb, 128, smem, s>>>(M, tiles, f32, x, n, logl);
+  } else {
+    k_mlp_f32<<<(n + kMlpF32Nb - 1) / kMlpF32Nb, 256, 0, s>>>(M, f32, x, n, logl);
+  }
+  return cudaGetLastError();
+}
+
+extern "C" {
+
+size_t ns_mlp_image_bytes(const ns_likelihood* lik, int d) {
+  if (!lik) return 0;
+  MlpDesc M;
+  std::string msg;
+  std::vector<double> lo(d > 0 ? d : 1, 0.0), hi(d > 0 ? d : 1, 1.0);
+  if (!make_desc(*lik, lo.data(), hi.data(), d, &M, &msg)) return 0;
+  return (size_t)M.tile_bytes + sizeof(float) * (size_t)M.f32_floats;
+}
+
+ns_status ns_mlp_pack(const ns_likelihood* lik, int d, void* image, void* stream) {
+  if (!lik || !image) return NS_ERR_ARG;
+  MlpDesc M;
+  std::string msg;
+  std::vector<double> lo(d > 0 ? d : 1, 0.0), hi(d > 0 ? d : 1, 1.0);
+  if (!make_desc(*lik, lo.data(), hi.data(), d, &M, &msg)) {
+    g_mlp_err = msg;
+    return NS_ERR_ARG;
+  }
+  if (reinterpret_cast<uintptr_t>(image) % 1024 != 0) {
+    g_mlp_err = "ns_mlp_pack: image must be 1024-byte aligned";
+    return NS_ERR_ARG;
+  }
+  std::vector<uint8_t> img;
+  ns_mlp_pack_host(*lik, M, img);
+  cudaError_t e = cudaMemcpyAsync(image, img.data(), img.size(), cudaMemcpyHostToDevice, (cudaStream_t)stream);
+  if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  return e == cudaSuccess ? NS_OK : NS_ERR_CUDA;
+}
+
+ns_status ns_mlp_loglike(const ns_likelihood* lik, const double* lo, const double* hi, int d, const void* image, int n,
+                         const float* x, float* logl, int precision, void* stream) {
+  if (!lik || !lo || !hi || !image || n < 0 || (n > 0 && (!x || !logl)) || precision < 0 || precision > 1)
+    return NS_ERR_ARG;
+  MlpDesc M;
+  std::string msg;
+  if (!make_desc(*lik, lo, hi, d, &M, &msg)) {
+    g_mlp_err = msg;
+    return NS_ERR_ARG;
+  }
+  if (n == 0) return NS_OK;
+  return ns_mlp_launch(M, image, n, x, logl, precision, (cudaStream_t)stream) == cudaSuccess ? NS_OK
+                                                                                           : NS_ERR_CUDA;
+}
+
+}  // extern "C"

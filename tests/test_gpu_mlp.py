@@ -1,0 +1,97 @@
+"""The MLP likelihood's batch evaluators through the C ABI.
+
+FP32 CUDA-core path: against the FP64 oracle at FP32 tolerance.  BF16
+tensor-core path (tcgen05): against a numpy emulation of the same BF16
+pipeline (inputs, weights and activations rounded to bf16, accumulation in
+high precision) at a tolerance that allows an activation to round the other
+way, and against the FP64 oracle at BF16 accuracy.
+"""
+import numpy as np
+import pytest
+
+from paper_2608_28514_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def nat():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2608_28514_gb300 import _native
+    _native.lib()
+    return _native
+
+
+def _bf16(a):
+    f = np.asarray(a, dtype=np.float32)
+    u = f.view(np.uint32).astype(np.uint64)
+    u = ((u + (((u >> 16) & 1) + 0x7FFF)) >> 16) << 16
+    return u.astype(np.uint32).view(np.float32).astype(np.float64)
+
+
+def _emulate_bf16(p, x):
+    th = _bf16(p.lo + (p.hi - p.lo) * x.astype(np.float32))
+    h = th
+    L = len(p.mlp.weights)
+    for i, (Wt, Bt) in enumerate(zip(p.mlp.weights, p.mlp.biases)):
+        z = h @ Wt.astype(np.float64).T + Bt.astype(np.float64)
+        if i + 1 < L:
+            h = _bf16(z / (1.0 + np.exp(-z)))
+        else:
+            h = z
+    r = (h - p.mlp.data.astype(np.float32).astype(np.float64)) / p.mlp.sigma_out.astype(np.float32)
+    return -0.5 * (r * r).sum(1)
+
+
+def _problem(widths, seed, unit_sigma):
+    p = W.mlp_emulator(seed, widths=widths)
+    if unit_sigma:
+        p.mlp.sigma_out = np.ones_like(p.mlp.sigma_out)
+        p.mlp.data = np.zeros_like(p.mlp.data)
+    return p
+
+
+def _image(nat, p):
+    nb = nat.ns_mlp_image_bytes(p)
+    assert nb > 0
+    img = torch.empty(nb + 1024, dtype=torch.uint8, device="cuda")
+    off = (-img.data_ptr()) % 1024
+    img = img[off:off + nb]
+    nat.ns_mlp_pack(p, img)
+    return img
+
+
+@pytest.mark.parametrize("widths,n", [((27, 512, 512, 512, 512, 2000), 150), ((5, 128, 200, 300), 64),
+                                      ((3, 64, 100), 1), ((27, 512, 512, 512, 512, 2000), 257)])
+def test_mlp_fp32_matches_oracle(nat, oracle, widths, n):
+    p = _problem(widths, 3, unit_sigma=False)
+    img = _image(nat, p)
+    rng = np.random.default_rng(n)
+    x = rng.uniform(0, 1, size=(n, p.d)).astype(np.float32)
+    x[0] = p.mlp.theta_star
+    out = torch.zeros(n, device="cuda")
+    nat.ns_mlp_loglike(p, img, torch.tensor(x, device="cuda"), out, precision=0)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    want = oracle.loglike(oracle.Lik(p), x.astype(np.float64))
+    np.testing.assert_allclose(got, want, rtol=2e-5, atol=1e-3)
+
+
+@pytest.mark.parametrize("widths,n", [((5, 128, 200, 300), 64), ((27, 512, 512, 512, 512, 2000), 150),
+                                      ((3, 64, 100), 1), ((27, 512, 512, 512, 512, 2000), 257)])
+def test_mlp_bf16_tensor_cores(nat, oracle, widths, n):
+    p = _problem(widths, 5, unit_sigma=True)
+    img = _image(nat, p)
+    rng = np.random.default_rng(n + 7)
+    x = rng.uniform(0, 1, size=(n, p.d)).astype(np.float32)
+    out = torch.zeros(n, device="cuda")
+    nat.ns_mlp_loglike(p, img, torch.tensor(x, device="cuda"), out, precision=1)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(got)), "a tensor-core block timed out"
+    emu = _emulate_bf16(p, x)
+    np.testing.assert_allclose(got, emu, rtol=3e-3, atol=1e-3)
+    exact = oracle.loglike(oracle.Lik(p), x.astype(np.float64))
+    np.testing.assert_allclose(got, exact, rtol=5e-2, atol=1e-2)
