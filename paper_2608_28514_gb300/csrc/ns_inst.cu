@@ -43,4 +43,15 @@ cudaError_t NS_CAT(launch_slice_, NS_DMAX)(const LikParams& P, const SliceCfg& S
   return cudaGetLastError();
 }
 
+#if NS_DMAX == 32
+// MLP runs (any d <= 32) use the widest class with the lock-step walkers.
+cudaError_t launch_run_mlp(const RunDesc* runs, const int* ids, int n, int block, size_t smem, int chunk,
+                           cudaStream_t s) {
+  cudaError_t e = cudaFuncSetAttribute(k_run<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  k_run<32, true><<<n, block, smem, s>>>(runs, ids, chunk);
+  return cudaGetLastError();
+}
+#endif
+
 }  // namespace nsd

@@ -25,6 +25,11 @@
 
 using namespace nsd;
 
+// From ns_mlp.cu.
+bool ns_mlp_make_desc(const ns_likelihood& L, const double* lo, const double* hi, int d, MlpDesc* M,
+                      std::string* msg);
+void ns_mlp_pack_host(const ns_likelihood& L, const MlpDesc& M, std::vector<uint8_t>& img);
+
 namespace {
 
 // ---------------------------------------------------------------------------
@@ -215,9 +220,16 @@ ns_status check_lik(const ns_likelihood* L, int d, std::string* err) {
           return NS_ERR_ARG;
         }
       return NS_OK;
-    case NS_LIK_MLP:
-      set_err(err, "MLP likelihood is not available in this build");
-      return NS_ERR_UNSUPPORTED;
+    case NS_LIK_MLP: {
+      MlpDesc M;
+      std::string msg;
+      std::vector<double> lo(d, 0.0), hi(d, 1.0);
+      if (!ns_mlp_make_desc(*L, lo.data(), hi.data(), d, &M, &msg)) {
+        set_err(err, "%s", msg.c_str());
+        return NS_ERR_ARG;
+      }
+      return NS_OK;
+    }
     default:
       set_err(err, "unknown likelihood kind %d", L->kind);
       return NS_ERR_ARG;
@@ -232,7 +244,8 @@ ns_status check_opts(const ns_options& o, std::string* err) {
   if (o.recluster_every < 0 || o.kmeans_iters < 0 || o.history_iters < 0 || o.e_max < 0 || o.s_max < 1 ||
       o.t_max < 1 || o.t_max > NS_MAX_HISTORY || !(o.width > 0) || !std::isfinite(o.width) ||
       o.correction < 0 || o.correction > 3 || o.max_iter < 1 || o.dead_cap < 0 || o.chunk_iters < 0 ||
-      !(o.vol_frac >= 0 && o.vol_frac < 1)) {
+      !(o.vol_frac >= 0 && o.vol_frac < 1) || o.precision < 0 || o.precision > 1 || !(o.reeval_margin >= 0) ||
+      !std::isfinite(o.reeval_margin)) {
     set_err(err, "an option is out of range");
     return NS_ERR_ARG;
   }
@@ -324,11 +337,13 @@ struct HostRun {
 
 struct ClassGroup {
   int dmax = 0, block = 0, n = 0;
+  bool mlp = false;
   size_t smem = 0;
   int* d_ids = nullptr;
 };
 
 cudaError_t launch_class(const ClassGroup& g, const RunDesc* d_runs, int chunk, cudaStream_t s) {
+  if (g.mlp) return launch_run_mlp(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
   return kClasses[class_index(g.dmax)].run(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
 }
 
@@ -418,7 +433,7 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     return o;
   };
   struct Off {
-    size_t lik, live_x, live_l, live_cid, new_x, new_l, hist_l, hist_x, hist_len, stage_x, dirs, wsp, side, dead_x,
+    size_t lik, mlp_img, mlp_desc, live_x, live_l, live_cid, new_x, new_l, hist_l, hist_x, hist_len, stage_x, dirs, wsp, side, dead_x,
         dead_l, dead_logw, centres, chol, chol64, logvol, count, split, mask;
   };
   std::vector<Off> off(n_runs);
@@ -430,6 +445,13 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     const long long cap = opt.dead_cap > 0 ? opt.dead_cap : 400LL * N + 4LL * m;
     Off& o = off[r];
     o.lik = take(sizeof(LikParams));
+    o.mlp_img = 0;
+    o.mlp_desc = 0;
+    if (p.lik->kind == NS_LIK_MLP) {
+      total = (total + 1023) & ~(size_t)1023;
+      o.mlp_img = take(ns_mlp_image_bytes(p.lik, d));
+      o.mlp_desc = take(sizeof(MlpDesc));
+    }
     o.live_x = take(sizeof(float) * (size_t)d * n_pad);
     o.live_l = take(sizeof(float) * N);
     o.live_cid = take(sizeof(int) * N);
@@ -439,7 +461,8 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     o.hist_x = take(sizeof(float) * (size_t)m * opt.t_max * d);
     o.hist_len = take(sizeof(int) * m);
     o.stage_x = take(sizeof(float) * (size_t)m * d);
-    o.dirs = take(sizeof(float) * (size_t)m * p.n_slice_steps * dir_row(dmax_class(d)));
+    o.dirs = take(sizeof(float) * (size_t)m * p.n_slice_steps *
+                  dir_row(p.lik->kind == NS_LIK_MLP ? kMaxDim : dmax_class(d)));
     o.wsp = take(opt.depth > 0 ? sizeof(float) * (size_t)d * n_pad : 16);
     o.side = take(opt.depth > 0 ? sizeof(int) * (size_t)N : 16);
     o.dead_x = take(sizeof(float) * (size_t)cap * d);
@@ -461,23 +484,24 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
   const size_t off_desc = take(sizeof(RunDesc) * n_runs);
   const size_t off_state = take(sizeof(RunState) * n_runs);
   // class groups
-  std::vector<int> counts(kNumClasses, 0);
-  std::vector<std::vector<int>> members(kNumClasses);
+  // one launch group per register class, plus one for MLP runs (index kNumClasses)
+  std::vector<int> counts(kNumClasses + 1, 0);
+  std::vector<std::vector<int>> members(kNumClasses + 1);
   for (int r = 0; r < n_runs; ++r) {
-    const int ci = class_index(runs[r].d);
+    const int ci = runs[r].lik->kind == NS_LIK_MLP ? kNumClasses : class_index(runs[r].d);
     members[ci].push_back(r);
     counts[ci]++;
   }
-  std::vector<size_t> off_ids(kNumClasses);
-  for (int ci = 0; ci < kNumClasses; ++ci) off_ids[ci] = take(sizeof(int) * std::max(1, counts[ci]));
-  h->arena_bytes = total;
-  cudaError_t e = cudaMalloc(&h->arena, total);
+  std::vector<size_t> off_ids(kNumClasses + 1);
+  for (int ci = 0; ci <= kNumClasses; ++ci) off_ids[ci] = take(sizeof(int) * std::max(1, counts[ci]));
+  h->arena_bytes = total + 1024;
+  cudaError_t e = cudaMalloc(&h->arena, total + 1024);
   if (e != cudaSuccess) {
     set_err(&h->err, "cudaMalloc of %zu bytes failed: %s", total, cudaGetErrorString(e));
     delete h;
     return e == cudaErrorMemoryAllocation ? NS_ERR_OOM : NS_ERR_CUDA;
   }
-  char* base = static_cast<char*>(h->arena);
+  char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->arena) + 1023) & ~(uintptr_t)1023);
   e = cudaMallocHost(&h->h_states, sizeof(RunState) * n_runs);
   if (e != cudaSuccess) {
     set_err(&h->err, "cudaMallocHost failed: %s", cudaGetErrorString(e));
@@ -537,6 +561,16 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     R.split = reinterpret_cast<int*>(base + o.split);
     R.mask = reinterpret_cast<int*>(base + o.mask);
     R.st = reinterpret_cast<RunState*>(base + off_state) + r;
+    R.precision = opt.precision;
+    R.reeval_margin = (float)opt.reeval_margin;
+    if (p.lik->kind == NS_LIK_MLP) {
+      R.mlp_tiles = reinterpret_cast<const uint8_t*>(base + o.mlp_img);
+      R.mlp_desc = reinterpret_cast<const MlpDesc*>(base + o.mlp_desc);
+      MlpDesc M;
+      std::string msg;
+      ns_mlp_make_desc(*p.lik, p.lo, p.hi, p.d, &M, &msg);
+      R.mlp_f32 = reinterpret_cast<const float*>(base + o.mlp_img + M.tile_bytes);
+    }
     liks[r] = make_lik(*p.lik, p.lo, p.hi, p.d);
   }
   h->d_runs = reinterpret_cast<RunDesc*>(base + off_desc);
@@ -549,6 +583,20 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
   };
   h->h2d_bytes = (long long)(sizeof(LikParams) + sizeof(RunDesc)) * n_runs;
   for (int r = 0; r < n_runs; ++r) {
+    if (runs[r].lik->kind == NS_LIK_MLP) {
+      MlpDesc M;
+      std::string msg;
+      ns_mlp_make_desc(*runs[r].lik, runs[r].lo, runs[r].hi, runs[r].d, &M, &msg);
+      std::vector<uint8_t> img;
+      ns_mlp_pack_host(*runs[r].lik, M, img);
+      e = cudaMemcpy(base + off[r].mlp_img, img.data(), img.size(), cudaMemcpyHostToDevice);
+      if (e == cudaSuccess) e = cudaMemcpy(base + off[r].mlp_desc, &M, sizeof(M), cudaMemcpyHostToDevice);
+      if (e != cudaSuccess) {
+        set_err(nullptr, "cudaMemcpy failed: %s", cudaGetErrorString(e));
+        return fail(NS_ERR_CUDA);
+      }
+      h->h2d_bytes += (long long)img.size() + (long long)sizeof(M);
+    }
     e = cudaMemcpy(base + off[r].lik, &liks[r], sizeof(LikParams), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       set_err(nullptr, "cudaMemcpy failed: %s", cudaGetErrorString(e));
@@ -561,17 +609,18 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     set_err(nullptr, "device setup failed: %s", cudaGetErrorString(e));
     return fail(NS_ERR_CUDA);
   }
-  for (int ci = 0; ci < kNumClasses; ++ci) {
+  for (int ci = 0; ci <= kNumClasses; ++ci) {
     if (counts[ci] == 0) continue;
     ClassGroup g;
-    g.dmax = kClasses[ci].dmax;
+    g.mlp = (ci == kNumClasses);
+    g.dmax = g.mlp ? kMaxDim : kClasses[ci].dmax;
     g.n = counts[ci];
     g.d_ids = reinterpret_cast<int*>(base + off_ids[ci]);
     int maxm = 1;
     size_t smem = 0;
     for (int r : members[ci]) {
       maxm = std::max(maxm, runs[r].m);
-      smem = std::max(smem, make_carve(runs[r].d, runs[r].m, n_nodes, kClasses[ci].dmax).total);
+      smem = std::max(smem, make_carve(runs[r].d, runs[r].m, n_nodes, g.dmax, g.mlp).total);
     }
     g.block = block_for_m(maxm);
     g.smem = smem;
@@ -822,6 +871,10 @@ ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt_in, fl
   if (st != NS_OK) return st;
   st = check_problem(*problem, nullptr);
   if (st != NS_OK) return st;
+  if (problem->lik->kind == NS_LIK_MLP) {
+    set_err(nullptr, "ns_run_noalloc: the MLP likelihood needs its weight image; use ns_create");
+    return NS_ERR_UNSUPPORTED;
+  }
   const ns_problem& p = *problem;
   const int d = p.d, N = p.n_live, m = p.m, n_pad = ((N + 31) / 32) * 32;
   if (dead_cap < (long long)N + m) {
@@ -992,6 +1045,10 @@ ns_status ns_loglike(const ns_likelihood* lik, const double* lo, const double* h
   p.stop_frac = 0.5;
   ns_status st = check_problem(p, nullptr);
   if (st != NS_OK) return st;
+  if (lik->kind == NS_LIK_MLP) {
+    set_err(nullptr, "ns_loglike: use ns_mlp_loglike for the MLP likelihood");
+    return NS_ERR_ARG;
+  }
   if (n < 0 || (n > 0 && (!x || !logl))) {
     set_err(nullptr, "ns_loglike: bad arguments");
     return NS_ERR_ARG;
@@ -1050,6 +1107,10 @@ ns_status ns_slice_replace(const ns_likelihood* lik, const double* lo, const dou
   p.seed = seed;
   st = check_problem(p, nullptr);
   if (st != NS_OK) return st;
+  if (lik->kind == NS_LIK_MLP) {
+    set_err(nullptr, "ns_slice_replace: the MLP likelihood is sampled by whole runs only");
+    return NS_ERR_ARG;
+  }
   if (n_pad < N || !live_x || !live_l || !seed_slot || !W || !chol || !cid || !new_x || !new_l || !hist_l ||
       !hist_x || !hist_len || !evals || !flags || !dir_scratch) {
     set_err(nullptr, "ns_slice_replace: NULL buffer or n_pad < N");

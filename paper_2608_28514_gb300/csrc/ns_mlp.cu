@@ -19,11 +19,13 @@ __global__ void __launch_bounds__(128, 1)
     k_mlp_bf16(const MlpDesc M, const uint8_t* __restrict__ tiles, const float* __restrict__ f32,
                const float* __restrict__ x, int n, float* __restrict__ out) {
   extern __shared__ __align__(1024) char sm_raw[];
-  const unsigned base = smem_u32(sm_raw);
-  char* sm = sm_raw + ((1024u - (base & 1023u)) & 1023u);
+  __shared__ unsigned tmem_slot;
+  char* sm = align1024_shared(sm_raw);
   const int b0 = blockIdx.x * kMlpNb;
   const int nb = min(kMlpNb, n - b0);
-  const bool ok = mlp_eval_bf16(M, tiles, f32, x + (size_t)b0 * M.d, M.d, nb, out + b0, sm);
+  const unsigned tmem = mlp_tmem_alloc(&tmem_slot);
+  const bool ok = mlp_eval_bf16(M, tiles, f32, x + (size_t)b0 * M.d, M.d, nb, out + b0, sm, tmem);
+  mlp_tmem_free(tmem);
   if (!ok)
     for (int r = threadIdx.x; r < nb; r += blockDim.x) out[b0 + r] = __int_as_float(0x7fffffff);
 }

@@ -29,7 +29,7 @@ namespace nsd {
 
 constexpr int kMlpMaxLayers = 8;
 constexpr int kMlpNb = 64;        // candidates per block (the MMA's N)
-constexpr int kMlpStages = 8;     // weight tiles in flight
+constexpr int kMlpStages = 6;     // weight tiles in flight
 constexpr int kMlpTileBytes = 128 * 128;  // 128 rows x 64 BF16 (128 bytes)
 constexpr int kMlpMaxK = 512;     // widest padded layer input
 constexpr unsigned kMlpWaitCap = 1u << 22;
@@ -173,13 +173,38 @@ struct MlpSmem {
   static constexpr int kBytes = kMiscOff + 64;
 };
 
+// Tensor memory of the BF16 evaluator: 512 columns, allocated once per block
+// (allocating again after the permit is relinquished is not allowed) and
+// freed once before the block exits.  Called by every thread; returns the
+// base address.
+inline __device__ unsigned mlp_tmem_alloc(unsigned* slot) {
+  if ((threadIdx.x >> 5) == 0) tmem_alloc(slot, 512);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  return *slot;
+}
+inline __device__ void mlp_tmem_free(unsigned tmem) {
+  tc_fence_before();
+  __syncthreads();
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, 512);
+  __syncthreads();
+}
+
+// 1024-byte aligned start (in the shared window) of a region beginning at p.
+__device__ __forceinline__ char* align1024_shared(char* p) {
+  const unsigned a = smem_u32(p);
+  return p + ((1024u - (a & 1023u)) & 1023u);
+}
+
 // Evaluates the batch x [n][d] (unit cube, n <= kMlpNb) with the BF16
-// tensor-core path into out[n] (log L).  Must be called by exactly 128
-// threads (four warps) of the block.  `sm` is 1024-byte aligned and holds
+// tensor-core path into out[n] (log L), using the block's tensor memory
+// `tmem` (mlp_tmem_alloc).  Must be called by every thread of the block (at
+// least 128 threads: warps 0-3 read the accumulators back).  `sm` is 1024-byte aligned and holds
 // MlpSmem::kBytes.  Returns false (for every thread) on a wait timeout.
 inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict__ tiles,
                                      const float* __restrict__ f32, const float* x, int x_stride, int n,
-                                     float* out, char* sm) {
+                                     float* out, char* sm, unsigned tmem) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   char* stages = sm + MlpSmem::kStageOff;
   char* act = sm + MlpSmem::kActOff;
@@ -187,7 +212,7 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
   uint64_t* full = reinterpret_cast<uint64_t*>(sm + MlpSmem::kBarOff);
   uint64_t* empty = full + kMlpStages;
   uint64_t* done = empty + kMlpStages;
-  unsigned* misc = reinterpret_cast<unsigned*>(sm + MlpSmem::kMiscOff);  // [0] tmem base, [1] error
+  unsigned* misc = reinterpret_cast<unsigned*>(sm + MlpSmem::kMiscOff);  // [1] error flag
   const unsigned NB = kMlpNb;
   const unsigned idesc = idesc_bf16(128, kMlpNb);
 
@@ -210,12 +235,10 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
     *reinterpret_cast<__nv_bfloat16*>(act + kb * kMlpNb * 128 + sw128_offset(r, k)) = __float2bfloat16_rn(v);
   }
   for (int q = tid; q < 4 * kMlpNb; q += blockDim.x) chi[q] = 0.f;
-  if (warp == 0) tmem_alloc(&misc[0], 512);
   fence_proxy_async();
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  const unsigned tmem = misc[0];
 
   unsigned item = 0;      // weight tiles consumed so far (stage ring position)
   unsigned done_phase = 0;
@@ -301,7 +324,7 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
       }
       tc_fence_after();
       // epilogue: warp w reads lanes 32w..32w+31 (output features) of each M-tile
-      for (int t = g0; t < g1; ++t) {
+      for (int t = g0; t < g1 && warp < 4; ++t) {
         const int f = t * 128 + warp * 32 + lane;
         for (int c0 = 0; c0 < kMlpNb; c0 += 16) {
           float v[16];
@@ -354,8 +377,6 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
       out[r] = -0.5f * (chi[r] + chi[kMlpNb + r] + chi[2 * kMlpNb + r] + chi[3 * kMlpNb + r]);
   }
   tc_fence_before();
-  __syncthreads();
-  if (warp == 0) tmem_dealloc(tmem, 512);
   __syncthreads();
   return ok;
 }

@@ -7,6 +7,7 @@
 #include "../../include/ns_gb300.h"
 #include "ns_cluster.cuh"
 #include "ns_device.cuh"
+#include "ns_mlp.cuh"
 
 namespace nsd {
 
@@ -54,18 +55,24 @@ struct RunDesc {
   int* split;
   int* mask;
   RunState* st;
+  // MLP likelihood (kind 4): the packed weight image and its description
+  const uint8_t* mlp_tiles;
+  const float* mlp_f32;
+  const MlpDesc* mlp_desc;
+  int precision;          // 0 FP32 CUDA cores, 1 BF16 tensor cores + FP32 re-evaluation
+  float reeval_margin;    // re-evaluate in FP32 when |logL_bf16 - threshold| < margin
 };
 
 // Shared-memory carve of the run kernel, computed identically on host and
 // device from the run's sizes.
 struct Carve {
   size_t lik, scr, sel, chol, cent, mask, worst, W, seed, sel_slot, sel_key, candA, candB, candT, list, vals, slots,
-      ctr, stage_cid, tile, acc, c64, l64, work, tree, total;
+      ctr, stage_cid, xbuf, lbuf, rlist, tile, acc, c64, l64, work, tree, mlp, total;
 };
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax) {
+__host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax, bool mlp = false) {
   Carve c;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -89,15 +96,28 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax)
   c.candT = take((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
   c.list = take(sizeof(int) * 2 * m);
   c.vals = take(sizeof(float) * m);
-  c.slots = take(sizeof(float) * (size_t)dir_row(dmax) * (m + 31) / 32 * 32);
+  c.slots = take(mlp ? 0 : sizeof(float) * (size_t)dir_row(dmax) * (m + 31) / 32 * 32);
   c.ctr = take(sizeof(int) * 4);
   c.stage_cid = take(sizeof(int) * m);
+  // MLP runs: candidate points, their log L, the re-evaluation list
+  c.xbuf = take(mlp ? sizeof(float) * (size_t)(m + kMlpF32Nb) * kMaxDim : 0);
+  c.lbuf = take(mlp ? sizeof(float) * (size_t)(m + kMlpF32Nb) : 0);
+  c.rlist = take(mlp ? sizeof(int) * (size_t)(m + kMlpF32Nb) : 0);
+  // from here on: the clustering scratch, which the MLP evaluators reuse
+  // (they run in the slice phase, never at the same time)
   c.tile = take(sizeof(float) * (d * kTile + d));
   c.acc = take(sizeof(double) * (d + d * d));
   c.c64 = take(sizeof(double) * d * d);
   c.l64 = take(sizeof(double) * d * d);
   c.work = take(sizeof(double) * (3 * d * d + d));
   c.tree = take(tree_bytes(d, n_nodes, 8, tree_chol_warps(d, 8)));
+  c.mlp = c.tile;
+  if (mlp) {
+    const size_t need = c.mlp + MlpSmem::kBytes + 1024;  // + alignment of the tensor-core region
+    const size_t f32 = c.mlp + sizeof(float) * 2 * kMlpF32Nb * kMlpMaxK;
+    if (need > o) o = need;
+    if (f32 > o) o = f32;
+  }
   c.total = o;
   return c;
 }
@@ -250,6 +270,265 @@ __device__ __noinline__ void walker_phase(const RunDesc& R, const LikParams& P, 
   fl = act ? f : 0;
 }
 
+// a4-a7 for MLP runs: the walkers advance in lock step, one round at a time;
+// each round the block evaluates every walker's candidate as one batch (on
+// the tensor cores in BF16, or on the CUDA cores in FP32).  In BF16 mode a
+// candidate whose log L falls within reeval_margin of the threshold it is
+// compared with is re-evaluated in FP32 before the decision; each walker's
+// final point and its history samples are re-evaluated in FP32 afterwards,
+// so every log L that is stored (dead points, Algorithm 2) is an FP32 value.
+// Called by every thread of the block.
+inline __device__ bool mlp_batch_f32(const RunDesc& R, const float* xs, int n, float* ls, float* act) {
+  for (int b0 = 0; b0 < n; b0 += kMlpF32Nb)
+    mlp_eval_f32(*R.mlp_desc, R.mlp_f32, xs + (size_t)b0 * kMaxDim, kMaxDim, min(kMlpF32Nb, n - b0), ls + b0, act);
+  return true;
+}
+
+inline __device__ bool mlp_batch_bf16(const RunDesc& R, const float* xs, int n, float* ls, char* tsm,
+                                      unsigned tmem) {
+  bool ok = true;
+  for (int b0 = 0; b0 < n && ok; b0 += kMlpNb)
+    ok = mlp_eval_bf16(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, xs + (size_t)b0 * kMaxDim, kMaxDim, min(kMlpNb, n - b0),
+                       ls + b0, tsm, tmem);
+  return ok;
+}
+
+// FP32 re-evaluation of the listed rows of xbuf (indices in list[0..n)),
+// written back into lbuf; xg/lg: kMlpF32Nb staging rows.
+inline __device__ void mlp_reeval(const RunDesc& R, float* xbuf, float* lbuf, const int* list, int n, float* xg,
+                                  float* lg, float* act) {
+  for (int g0 = 0; g0 < n; g0 += kMlpF32Nb) {
+    const int ng = min(kMlpF32Nb, n - g0);
+    for (int q = threadIdx.x; q < ng * kMaxDim; q += blockDim.x)
+      xg[q] = xbuf[(size_t)list[g0 + q / kMaxDim] * kMaxDim + q % kMaxDim];
+    __syncthreads();
+    mlp_eval_f32(*R.mlp_desc, R.mlp_f32, xg, kMaxDim, ng, lg, act);
+    for (int q = threadIdx.x; q < ng; q += blockDim.x) lbuf[list[g0 + q]] = lg[q];
+    __syncthreads();
+  }
+}
+
+template <int DMAX>
+__device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& S, const float* s_W, const int* s_seed,
+                                              const float* s_chol, float* xbuf, float* lbuf, int* rlist, char* msm,
+                                              unsigned tmem, BlockScratch& BS, long long& ev_out, int& fl_out,
+                                              long long& re_out, int& err_out) {
+  constexpr int RW = dir_row(DMAX);
+  const int tid = threadIdx.x, m = R.m, d = S.d;
+  const bool bf16 = (R.precision == 1);
+  char* tsm = align1024_shared(msm);
+  float* act = reinterpret_cast<float*>(msm);
+  float* xg = xbuf + (size_t)m * kMaxDim;  // kMlpF32Nb staging rows after the m walker rows
+  float* lg = lbuf + m;
+  const bool mine = tid < m;
+  const int i = mine ? tid : 0;
+  const int sd = s_seed[i];
+  const int cid = R.live_cid[sd];
+  const float thr_out = (R.correction == 3) ? s_W[m - 1] : s_W[0];
+  const float thr_in = (R.correction == 3) ? s_W[m - 1] : s_W[i];
+  const float* dirs = R.dirs + (size_t)i * S.n_steps * RW;
+  if (mine) draw_directions<DMAX>(S, i, s_chol + (size_t)cid * d * d, const_cast<float*>(dirs));
+  const uint32_t n0 = shrink_draw0(d);
+  float x[DMAX], v[DMAX], pre[kPreShrink];
+  float l = mine ? R.live_l[sd] : 0.f;
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k) x[k] = (mine && k < d) ? R.live_x[(size_t)k * R.n_pad + sd] : 0.f;
+  int step = 0, phase = 0, nexp = 0, nsh = 0, hlen = 0, flags = 0;
+  long long evals = 0, reevals = 0;
+  float a = 0.f, b = 0.f;
+  Stream st;
+  st.init(S.k0, S.k1, S.t, (uint32_t)i, 0u);
+  st.n = n0 + kPreShrink;
+  auto load_step = [&](int s_) {
+    const float* row = dirs + (size_t)s_ * RW;
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k) v[k] = row[k];
+    const float r = row[DMAX];
+#pragma unroll
+    for (int j = 0; j < kPreShrink; ++j) pre[j] = row[DMAX + 1 + j];
+    a = -r * S.width;
+    b = (1.f - r) * S.width;
+  };
+  bool active = mine && S.n_steps > 0;
+  if (active) load_step(0);
+  int err = 0;
+  for (;;) {
+    if (!__syncthreads_or(active ? 1 : 0)) break;
+    float tp = 0.f;
+    bool in = false;
+    if (active) {
+      tp = (phase == 0) ? a : b;
+      if (phase == 2) {
+        float uu = pre[0];
+        if (nsh < kPreShrink) {
+#pragma unroll
+          for (int j = 1; j < kPreShrink; ++j)
+            if (nsh == j) uu = pre[j];
+        } else {
+          uu = u24(st.next());
+        }
+        tp = fmaf(uu, b - a, a);
+      }
+      float u[DMAX];
+      in = candidate<DMAX>(x, v, tp, u);
+      for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = in ? u[k] : 0.5f;
+    } else if (mine) {
+      for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = 0.5f;
+    }
+    __syncthreads();
+    if (bf16) {
+      if (!mlp_batch_bf16(R, xbuf, m, lbuf, tsm, tmem)) err = 1;
+      // re-evaluate in FP32 the candidates close to their threshold
+      const float thr = (phase == 2) ? thr_in : thr_out;
+      const bool need = active && in && R.reeval_margin > 0.f && fabsf(lbuf[tid] - thr) < R.reeval_margin;
+      int cnt;
+      const int pos = block_exclusive_scan(need ? 1 : 0, BS, &cnt);
+      if (need) rlist[pos] = tid;
+      __syncthreads();
+      if (cnt > 0) {
+        mlp_reeval(R, xbuf, lbuf, rlist, cnt, xg, lg, act);
+        reevals += (tid == 0) ? cnt : 0;
+      }
+    } else {
+      mlp_batch_f32(R, xbuf, m, lbuf, act);
+    }
+    __syncthreads();
+    if (active) {
+      const float lp = in ? lbuf[tid] : -CUDART_INF_F;
+      if (in) ++evals;
+      const bool ok = in && (lp > ((phase == 2) ? thr_in : thr_out));
+      if (phase < 2) {
+        const bool expand = ok && (nexp < S.e_max);
+        a = (expand && phase == 0) ? a - S.width : a;
+        b = (expand && phase == 1) ? b + S.width : b;
+        flags |= (ok && !expand) ? 1 : 0;
+        nexp = expand ? nexp + 1 : 0;
+        phase = expand ? phase : phase + 1;
+      } else {
+        if (step == S.n_steps - 1) {
+          int hs = -1;
+          if (nsh < S.t_max - 1) {
+            hs = nsh;
+            hlen = nsh + 1;
+          } else if (ok) {
+            hs = S.t_max - 1;
+            hlen = S.t_max;
+          }
+          if (hs >= 0) {
+            float u[DMAX];
+            candidate<DMAX>(x, v, tp, u);
+            R.hist_l[(size_t)i * S.t_max + hs] = lp;
+            for (int k = 0; k < d; ++k) R.hist_x[((size_t)i * S.t_max + hs) * d + k] = u[k];
+          }
+        }
+        bool advance = ok;
+        if (ok) {
+          float u[DMAX];
+          candidate<DMAX>(x, v, tp, u);
+#pragma unroll
+          for (int k = 0; k < DMAX; ++k) x[k] = u[k];
+          l = lp;
+        } else {
+          if (tp < 0.f) a = tp;
+          else b = tp;
+          if (++nsh >= S.s_max) {
+            flags |= 2;
+            advance = true;
+          }
+        }
+        if (advance) {
+          ++step;
+          if (step < S.n_steps) {
+            load_step(step);
+            st.init(S.k0, S.k1, S.t, (uint32_t)i, (uint32_t)step);
+            st.n = n0 + kPreShrink;
+            phase = 0;
+            nsh = 0;
+            nexp = 0;
+          } else {
+            active = false;
+          }
+        }
+      }
+    }
+    if (__syncthreads_or(err)) {
+      err = 1;
+      break;
+    }
+  }
+  __syncthreads();
+  // stored values in FP32: each walker's final point, then its history samples
+  if (bf16 && !err) {
+    if (mine)
+      for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = x[k];
+    if (tid < m) rlist[tid] = tid;
+    __syncthreads();
+    mlp_reeval(R, xbuf, lbuf, rlist, m, xg, lg, act);
+    if (mine) l = lbuf[tid];
+    reevals += (tid == 0) ? m : 0;
+    // history: rows (walker, slot) with an in-box sample
+    int nh = mine ? hlen : 0;
+    int tot;
+    const int base = block_exclusive_scan(nh, BS, &tot);
+    for (int h0 = 0; h0 < tot; h0 += m) {
+      // stage up to m history samples per pass in xbuf
+      const int nb = min(m, tot - h0);
+      for (int h = 0; h < nh; ++h) {
+        const int gidx = base + h - h0;
+        if (gidx >= 0 && gidx < nb) {
+          const float* hx = R.hist_x + ((size_t)i * S.t_max + h) * d;
+          for (int k = 0; k < d; ++k) xbuf[(size_t)gidx * kMaxDim + k] = hx[k];
+        }
+      }
+      for (int q = tid; q < nb; q += blockDim.x) rlist[q] = q;
+      __syncthreads();
+      mlp_reeval(R, xbuf, lbuf, rlist, nb, xg, lg, act);
+      for (int h = 0; h < nh; ++h) {
+        const int gidx = base + h - h0;
+        if (gidx >= 0 && gidx < nb) {
+          float* hl = R.hist_l + (size_t)i * S.t_max + h;
+          if (*hl > -CUDART_INF_F) *hl = lbuf[gidx];
+        }
+      }
+      __syncthreads();
+      reevals += (tid == 0) ? nb : 0;
+    }
+  }
+  if (mine) {
+    for (int k = 0; k < d; ++k) R.new_x[(size_t)i * d + k] = x[k];
+    R.new_l[i] = l;
+    R.hist_len[i] = hlen;
+  }
+  ev_out = mine ? evals : 0;
+  fl_out = mine ? flags : 0;
+  re_out = reevals;
+  err_out = err;
+}
+
+// Initial live points of an MLP run, evaluated in FP32.
+template <int DMAX>
+inline __device__ void init_live_mlp(const RunDesc& R, float* xbuf, float* lbuf, int* rlist, char* msm) {
+  const int d = R.d;
+  float* act = reinterpret_cast<float*>(msm);
+  for (int j0 = 0; j0 < R.N; j0 += R.m) {
+    const int nb = min(R.m, R.N - j0);
+    for (int q = threadIdx.x; q < nb * d; q += blockDim.x) {
+      const int j = j0 + q / d, k = q % d;
+      const float xv = u24(draw_at(R.k0, R.k1, kTInit, (uint32_t)j, 0u, (uint32_t)k));
+      R.live_x[(size_t)k * R.n_pad + j] = xv;
+      xbuf[(size_t)(q / d) * kMaxDim + k] = xv;
+    }
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) rlist[q] = q;
+    __syncthreads();
+    mlp_reeval(R, xbuf, lbuf, rlist, nb, xbuf + (size_t)R.m * kMaxDim, lbuf + R.m, act);
+    for (int q = threadIdx.x; q < nb; q += blockDim.x) {
+      R.live_l[j0 + q] = lbuf[q];
+      R.live_cid[j0 + q] = 0;
+    }
+    __syncthreads();
+  }
+}
+
 // Blocks of up to 256 threads.  For the small register classes two such
 // blocks per SM cap the registers at 128 per thread (more runs resident per
 // SM hide the walkers' latency); the wide classes keep the full register
@@ -259,9 +538,9 @@ __device__ __noinline__ void walker_phase(const RunDesc& R, const LikParams& P, 
 #else
 #define NS_MINB(D) ((D) <= 12 ? 2 : 1)
 #endif
-template <int DMAX>
-__global__ void __launch_bounds__(256, NS_MINB(DMAX)) k_run(const RunDesc* __restrict__ runs, const int* __restrict__ ids,
-                                             int chunk) {
+template <int DMAX, bool MLP = false>
+__global__ void __launch_bounds__(256, (MLP ? 1 : NS_MINB(DMAX))) k_run(const RunDesc* __restrict__ runs,
+                                                                        const int* __restrict__ ids, int chunk) {
   extern __shared__ __align__(16) char sm[];
   __shared__ RunDesc R;
   __shared__ RunState RS;
@@ -277,9 +556,18 @@ __global__ void __launch_bounds__(256, NS_MINB(DMAX)) k_run(const RunDesc* __res
   }
   __syncthreads();
   if (RS.stopped || RS.status != 0) return;
+  __shared__ unsigned tmem_slot;
+  unsigned tmem = 0;
+  if constexpr (MLP) {
+    if (R.precision == 1) tmem = mlp_tmem_alloc(&tmem_slot);
+  }
   const int d = R.d, N = R.N, m = R.m;
-  const Carve cv = make_carve(d, m, R.n_nodes, DMAX);
+  const Carve cv = make_carve(d, m, R.n_nodes, DMAX, MLP);
   float* s_slots = reinterpret_cast<float*>(sm + cv.slots);
+  float* s_xbuf = reinterpret_cast<float*>(sm + cv.xbuf);
+  float* s_lbuf = reinterpret_cast<float*>(sm + cv.lbuf);
+  int* s_rlist = reinterpret_cast<int*>(sm + cv.rlist);
+  char* s_mlp = sm + cv.mlp;
   LikParams& P = *reinterpret_cast<LikParams*>(sm + cv.lik);
   BlockScratch& S = *reinterpret_cast<BlockScratch*>(sm + cv.scr);
   SelectScratch& X = *reinterpret_cast<SelectScratch*>(sm + cv.sel);
@@ -306,7 +594,8 @@ __global__ void __launch_bounds__(256, NS_MINB(DMAX)) k_run(const RunDesc* __res
   }
   __syncthreads();
   if (!RS.initialized) {
-    init_live<DMAX>(R, P);
+    if constexpr (MLP) init_live_mlp<DMAX>(R, s_xbuf, s_lbuf, s_rlist, s_mlp);
+    else init_live<DMAX>(R, P);
     __syncthreads();
     if (tid == 0) {
       RS.n_evals += N;
@@ -357,14 +646,25 @@ __global__ void __launch_bounds__(256, NS_MINB(DMAX)) k_run(const RunDesc* __res
     select_worst(R.live_l, N, m, R.k0, R.k1, t, s_sel_slot, s_sel_key, s_worst, s_W, s_seed, X, S);
     tick(kPhSelect);
     // a4-a7: slice-sampling walkers
-    long long ev = 0;
-    int fl = 0;
-    if ((tid & ~31) < m) {
-      SC.t = t;
-      walker_phase<DMAX>(R, P, SC, s_W, s_seed, s_chol, s_slots, ev, fl);
+    long long ev = 0, re = 0;
+    int fl = 0, werr = 0;
+    SC.t = t;
+    if constexpr (MLP) {
+      walker_phase_mlp<DMAX>(R, SC, s_W, s_seed, s_chol, s_xbuf, s_lbuf, s_rlist, s_mlp, tmem, S, ev, fl, re, werr);
+    } else {
+      if ((tid & ~31) < m) walker_phase<DMAX>(R, P, SC, s_W, s_seed, s_chol, s_slots, ev, fl);
     }
     __syncthreads();
     tick(kPhSlice);
+    if constexpr (MLP) {
+      const long long re_sum = block_sum_ll(re, S);
+      if (tid == 0) RS.n_reeval += re_sum;
+      if (__syncthreads_or(werr)) {
+        if (tid == 0) RS.status = NS_ERR_BUDGET;
+        __syncthreads();
+        break;
+      }
+    }
     const long long ev_sum = block_sum_ll(ev, S);
     const long long capped = block_sum_ll(fl ? 1 : 0, S);
     // a8-a9: Algorithms 1 and 2
@@ -448,6 +748,9 @@ __global__ void __launch_bounds__(256, NS_MINB(DMAX)) k_run(const RunDesc* __res
     }
   }
   __syncthreads();
+  if constexpr (MLP) {
+    if (R.precision == 1) mlp_tmem_free(tmem);
+  }
   if (tid == 0) {
     RS.logz = E.logz;
     RS.info = E.info;
@@ -517,5 +820,7 @@ __global__ void k_slice(const LikParams P, SliceCfg SC, int m, int n_pad, int co
                                int* flags, float* dir_scratch, cudaStream_t s);                            \
   cudaError_t occupancy_run_##D(int block, size_t smem, int* blocks_per_sm);
 NS_FOR_EACH_CLASS(NS_DECLARE_LAUNCHERS)
+cudaError_t launch_run_mlp(const RunDesc* runs, const int* ids, int n, int block, size_t smem, int chunk,
+                           cudaStream_t s);
 
 }  // namespace nsd

@@ -95,3 +95,56 @@ def test_mlp_bf16_tensor_cores(nat, oracle, widths, n):
     np.testing.assert_allclose(got, emu, rtol=3e-3, atol=1e-3)
     exact = oracle.loglike(oracle.Lik(p), x.astype(np.float64))
     np.testing.assert_allclose(got, exact, rtol=5e-2, atol=1e-2)
+
+
+# --------------------------------------------------------------------------
+# whole runs with the MLP likelihood
+# --------------------------------------------------------------------------
+def _small_emulator(seed=2):
+    p = W.mlp_emulator(seed, widths=(4, 64, 64, 60), sig_lo=1e-2, sig_hi=1e-1)
+    return p
+
+
+def test_mlp_runs_fp32_vs_oracle_and_bf16(nat, oracle):
+    """A 4-D emulator (4 -> 64 -> 64 -> 60): the GPU FP32 path agrees with
+    the FP64 oracle in distribution, and the BF16 tensor-core path with FP32
+    re-evaluation near the threshold stays within 0.1 of the FP32 path."""
+    p = _small_emulator()
+    N, m, ns, sf = 200, 20, 20, 1e-2
+    seeds = list(range(1, 9))
+    orc = np.array([oracle.run(p, N, m, ns, sf, s)["logz"] for s in seeds])
+    res = {}
+    for prec in (0, 1):
+        o = nat.ns_default_options(precision=prec, reeval_margin=5.0)
+        h = nat.ns_create_batch([(p, N, m, ns, sf, s) for s in seeds], o)
+        nat.ns_run(h)
+        out = [nat.ns_result(h, r, samples=False) for r in range(len(seeds))]
+        nat.ns_destroy(h)
+        assert all(r["status"] == 0 for r in out)
+        res[prec] = out
+    z32 = np.array([r["log_z"] for r in res[0]])
+    z16 = np.array([r["log_z"] for r in res[1]])
+    err = np.mean([r["log_z_err"] for r in res[0]])
+    se = np.sqrt(z32.var(ddof=1) / len(seeds) + orc.var(ddof=1) / len(seeds))
+    assert abs(z32.mean() - orc.mean()) < 3.5 * se + 0.02, (z32.mean(), orc.mean(), se)
+    assert abs(z16.mean() - z32.mean()) < 0.1 + 2 * err / np.sqrt(len(seeds)), (z16.mean(), z32.mean())
+    assert sum(r["n_reeval"] for r in res[1]) > 0
+    assert all(r["n_reeval"] == 0 for r in res[0])
+
+
+def test_full_emulator_runs_a_few_iterations(nat):
+    """The 27 -> 512 x 4 -> 2000 emulator workload (N = 1500, m = 150, 135
+    slice steps), BF16 with FP32 re-evaluation: a few iterations complete on
+    the tensor-core path and every stored value is finite."""
+    p = W.mlp_emulator(1)
+    o = nat.ns_default_options(precision=1, reeval_margin=20.0, max_iter=2, chunk_iters=2)
+    h = nat.ns_create(p, 1500, 150, 135, 1e-3, 3, opt=o)
+    st = nat.ns_run(h, check=False)
+    r = nat.ns_result(h, 0)
+    nat.ns_destroy(h)
+    assert st == nat.NS_ERR_BUDGET and r["status"] == nat.NS_ERR_BUDGET and r["n_iter"] == 2
+    assert r["n_evals"] > 1500 + 2 * 150 * 135
+    assert np.all(np.isfinite(r["dead_l"]))
+    # dead points of the two iterations, in ascending order
+    nd = 2 * 150
+    assert np.all(np.diff(r["dead_l"][:nd]) >= 0)
