@@ -251,8 +251,11 @@ def ns_create_batch(runs, opt=None):
     keep = _Keep()
     runs = list(runs)
     arr = (NsProblem * len(runs))()
+    liks = {}  # one struct per problem object: runs of one network share its arrays
     for i, (p, N, m, ns, sf, seed) in enumerate(runs):
-        lik = likelihood_struct(p, keep)
+        if id(p) not in liks:
+            liks[id(p)] = likelihood_struct(p, keep)
+        lik = liks[id(p)]
         arr[i].lik = C.pointer(lik)
         arr[i].lo = keep.dptr(p.lo)
         arr[i].hi = keep.dptr(p.hi)

@@ -160,6 +160,26 @@ int class_index(int d) {
 }
 int dmax_class(int d) { return kClasses[class_index(d)].dmax; }
 
+// True when two MLP likelihoods describe the same network and data (equal
+// widths, weights, biases, data and sigma_out; pointer-equal arrays are
+// taken as equal without a comparison).
+bool same_network(const ns_likelihood& a, const ns_likelihood& b) {
+  if (a.n_layers != b.n_layers) return false;
+  for (int l = 0; l <= a.n_layers; ++l)
+    if (a.widths[l] != b.widths[l]) return false;
+  size_t nw = 0, nb = 0;
+  for (int l = 0; l < a.n_layers; ++l) {
+    nw += (size_t)a.widths[l] * a.widths[l + 1];
+    nb += (size_t)a.widths[l + 1];
+  }
+  const size_t no = (size_t)a.widths[a.n_layers];
+  auto eq = [](const float* x, const float* y, size_t n) {
+    return x == y || std::memcmp(x, y, sizeof(float) * n) == 0;
+  };
+  return eq(a.weights, b.weights, nw) && eq(a.biases, b.biases, nb) && eq(a.data, b.data, no) &&
+         eq(a.sigma_out, b.sigma_out, no);
+}
+
 int block_for_m(int m) {
   int b = ((m + 31) / 32) * 32;
   if (b < 128) b = 128;
@@ -433,6 +453,7 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     return o;
   };
   struct Off {
+    int mlp_owner;  // the run whose MLP image this run reads (itself if it owns one)
     size_t lik, mlp_img, mlp_desc, live_x, live_l, live_cid, new_x, new_l, hist_l, hist_x, hist_len, stage_x, dirs, wsp, side, dead_x,
         dead_l, dead_logw, centres, chol, chol64, logvol, count, split, mask;
   };
@@ -447,9 +468,19 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     o.lik = take(sizeof(LikParams));
     o.mlp_img = 0;
     o.mlp_desc = 0;
+    o.mlp_owner = -1;
     if (p.lik->kind == NS_LIK_MLP) {
-      total = (total + 1023) & ~(size_t)1023;
-      o.mlp_img = take(ns_mlp_image_bytes(p.lik, d));
+      // runs of the same network share one image (one L2-resident copy)
+      for (int q = 0; q < r && o.mlp_owner < 0; ++q)
+        if (runs[q].lik->kind == NS_LIK_MLP && off[q].mlp_owner == q && same_network(*runs[q].lik, *p.lik))
+          o.mlp_owner = q;
+      if (o.mlp_owner >= 0) {
+        o.mlp_img = off[o.mlp_owner].mlp_img;
+      } else {
+        o.mlp_owner = r;
+        total = (total + 1023) & ~(size_t)1023;
+        o.mlp_img = take(ns_mlp_image_bytes(p.lik, d));
+      }
       o.mlp_desc = take(sizeof(MlpDesc));
     }
     o.live_x = take(sizeof(float) * (size_t)d * n_pad);
@@ -587,15 +618,19 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
       MlpDesc M;
       std::string msg;
       ns_mlp_make_desc(*runs[r].lik, runs[r].lo, runs[r].hi, runs[r].d, &M, &msg);
-      std::vector<uint8_t> img;
-      ns_mlp_pack_host(*runs[r].lik, M, img);
-      e = cudaMemcpy(base + off[r].mlp_img, img.data(), img.size(), cudaMemcpyHostToDevice);
+      e = cudaSuccess;
+      if (off[r].mlp_owner == r) {
+        std::vector<uint8_t> img;
+        ns_mlp_pack_host(*runs[r].lik, M, img);
+        e = cudaMemcpy(base + off[r].mlp_img, img.data(), img.size(), cudaMemcpyHostToDevice);
+        h->h2d_bytes += (long long)img.size();
+      }
       if (e == cudaSuccess) e = cudaMemcpy(base + off[r].mlp_desc, &M, sizeof(M), cudaMemcpyHostToDevice);
       if (e != cudaSuccess) {
         set_err(nullptr, "cudaMemcpy failed: %s", cudaGetErrorString(e));
         return fail(NS_ERR_CUDA);
       }
-      h->h2d_bytes += (long long)img.size() + (long long)sizeof(M);
+      h->h2d_bytes += (long long)sizeof(M);
     }
     e = cudaMemcpy(base + off[r].lik, &liks[r], sizeof(LikParams), cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
@@ -623,6 +658,7 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
       smem = std::max(smem, make_carve(runs[r].d, runs[r].m, n_nodes, g.dmax, g.mlp).total);
     }
     g.block = block_for_m(maxm);
+    if (g.mlp) g.block = std::max(g.block, kMlpThreads);  // the BF16 evaluator's warp roles
     g.smem = smem;
     if (smem > 227 * 1024) {
       set_err(nullptr, "runs of dimension class %d need %zu bytes of shared memory (limit 227 KB): "

@@ -3,6 +3,7 @@
 // copies, tensor memory) and the FP32 CUDA-core evaluator, behind the C ABI.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <string>
@@ -15,28 +16,32 @@ using namespace nsd;
 
 namespace {
 
-__global__ void __launch_bounds__(128, 1)
+// Persistent: each block sets up its tensor memory and barriers once and
+// evaluates batches of kMlpNb candidates, grid-strided.
+__global__ void __launch_bounds__(kMlpThreads, 1)
     k_mlp_bf16(const MlpDesc M, const uint8_t* __restrict__ tiles, const float* __restrict__ f32,
                const float* __restrict__ x, int n, float* __restrict__ out) {
   extern __shared__ __align__(1024) char sm_raw[];
-  __shared__ unsigned tmem_slot;
+  __shared__ MlpCtx ctx;
   char* sm = align1024_shared(sm_raw);
-  const int b0 = blockIdx.x * kMlpNb;
-  const int nb = min(kMlpNb, n - b0);
-  const unsigned tmem = mlp_tmem_alloc(&tmem_slot);
-  const bool ok = mlp_eval_bf16(M, tiles, f32, x + (size_t)b0 * M.d, M.d, nb, out + b0, sm, tmem);
-  mlp_tmem_free(tmem);
-  if (!ok)
-    for (int r = threadIdx.x; r < nb; r += blockDim.x) out[b0 + r] = __int_as_float(0x7fffffff);
+  mlp_ctx_init(&ctx);
+  const int n_batches = (n + kMlpNb - 1) / kMlpNb;
+  for (int b = blockIdx.x; b < n_batches; b += gridDim.x) {
+    const int b0 = b * kMlpNb;
+    const int nb = min(kMlpNb, n - b0);
+    if (!mlp_eval_bf16(M, tiles, f32, x + (size_t)b0 * M.d, M.d, nb, out + b0, sm, &ctx))
+      for (int r = threadIdx.x; r < nb; r += blockDim.x) out[b0 + r] = __int_as_float(0x7fffffff);
+  }
+  mlp_ctx_free(&ctx);
 }
 
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 1)
     k_mlp_f32(const MlpDesc M, const float* __restrict__ f32, const float* __restrict__ x, int n,
               float* __restrict__ out) {
-  __shared__ float act[2 * kMlpF32Nb * kMlpMaxK];
-  const int b0 = blockIdx.x * kMlpF32Nb;
-  const int nb = min(kMlpF32Nb, n - b0);
-  mlp_eval_f32(M, f32, x + (size_t)b0 * M.d, M.d, nb, out + b0, act);
+  extern __shared__ __align__(16) float act[];
+  const int b0 = blockIdx.x * kMlpF32NbWide;
+  const int nb = min(kMlpF32NbWide, n - b0);
+  mlp_eval_f32<kMlpF32NbWide>(M, f32, x + (size_t)b0 * M.d, M.d, nb, out + b0, act);
 }
 
 int round_up(int v, int q) { return (v + q - 1) / q * q; }
@@ -137,7 +142,8 @@ void ns_mlp_pack_host(const ns_likelihood& L, const MlpDesc& M, std::vector<uint
       }
     float* f32 = reinterpret_cast<float*>(img.data() + M.tile_bytes);
     for (int o = 0; o < out; ++o) f32[M.bias0[l] + o] = Bv[o];
-    std::memcpy(f32 + M.w32_0[l], W, sizeof(float) * (size_t)in * out);
+    for (int o = 0; o < out; ++o)  // transposed: [in][out]
+      for (int i = 0; i < in; ++i) f32[M.w32_0[l] + (size_t)i * out + o] = W[(size_t)o * in + i];
     W += (size_t)in * out;
     Bv += out;
   }
@@ -156,10 +162,17 @@ cudaError_t ns_mlp_launch(const MlpDesc& M, const void* image, int n, const floa
   if (precision == 1) {
     const int smem = MlpSmem::kBytes + 1024;
     cudaError_t e = cudaFuncSetAttribute(k_mlp_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, n_sm = 1;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    k_mlp_bf16<<<(n + kMlpNb - 1) / kMlpNb, 128, smem, s>>>(M, tiles, f32, x, n, logl);
+    const int n_batches = (n + kMlpNb - 1) / kMlpNb;
+    k_mlp_bf16<<<std::min(n_batches, n_sm), kMlpThreads, smem, s>>>(M, tiles, f32, x, n, logl);
   } else {
-    k_mlp_f32<<<(n + kMlpF32Nb - 1) / kMlpF32Nb, 256, 0, s>>>(M, f32, x, n, logl);
+    const int smem = (int)mlp_f32_act_bytes(kMlpF32NbWide);
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_f32, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    k_mlp_f32<<<(n + kMlpF32NbWide - 1) / kMlpF32NbWide, 256, smem, s>>>(M, f32, x, n, logl);
   }
   return cudaGetLastError();
 }

@@ -38,7 +38,7 @@ constexpr unsigned kMlpWaitCap = 1u << 22;
 //   tiles  : BF16 swizzled weight tiles, layer by layer, M-tile by M-tile,
 //            K-block by K-block (16 KB each);
 //   f32    : per layer bias (padded out), then data and 1/sigma of the last
-//            layer (padded out), then FP32 weights [out][in] row-major.
+//            layer (padded out), then the FP32 weights transposed, [in][out].
 struct MlpDesc {
   int n_layers, d;
   int in[kMlpMaxLayers], out[kMlpMaxLayers];        // true widths
@@ -162,32 +162,82 @@ __host__ __device__ __forceinline__ unsigned sw128_offset(int r, int k) {
 
 __device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
 
+// SiLU of the BF16 path's epilogues: exp and divide on the special-function
+// unit (relative error near FP32 rounding, far below the BF16 rounding of
+// the stored activation).
+__device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.f + __expf(-z)); }
+
 // Shared memory of the BF16 evaluator (offsets from a 1024-aligned base).
 struct MlpSmem {
   static constexpr int kStageOff = 0;
   static constexpr int kActOff = kStageOff + kMlpStages * kMlpTileBytes;      // [kpad/64][kMlpNb][128 B]
   static constexpr int kActBytes = (kMlpMaxK / 64) * kMlpNb * 128;
   static constexpr int kChiOff = kActOff + kActBytes;                         // [4][kMlpNb] floats
-  static constexpr int kBarOff = kChiOff + 4 * kMlpNb * 4;                    // mbarriers
-  static constexpr int kMiscOff = kBarOff + 8 * (2 * kMlpStages + 2);
-  static constexpr int kBytes = kMiscOff + 64;
+  static constexpr int kBytes = kChiOff + 4 * kMlpNb * 4;
 };
 
-// Tensor memory of the BF16 evaluator: 512 columns, allocated once per block
-// (allocating again after the permit is relinquished is not allowed) and
-// freed once before the block exits.  Called by every thread; returns the
-// base address.
-inline __device__ unsigned mlp_tmem_alloc(unsigned* slot) {
-  if ((threadIdx.x >> 5) == 0) tmem_alloc(slot, 512);
+// Warp roles of the BF16 evaluator: warps 0-3 read the accumulators back
+// (warp w owns tensor-memory lanes 32w..32w+31), warp 4 streams the weight
+// tiles, warp 5 issues the MMAs.  The block needs at least kMlpThreads.
+constexpr int kMlpEpiWarps = 4;
+constexpr int kMlpProducerWarp = 4;
+constexpr int kMlpMmaWarp = 5;
+constexpr int kMlpThreads = 192;
+// tensor memory: two halves of 256 columns; an output-layer group of M-tiles
+// fills one half while the epilogue drains the other
+constexpr int kMlpHalfCols = 256;
+constexpr int kMlpOutGroup = kMlpHalfCols / kMlpNb;
+
+// Per-block state of the BF16 evaluator that outlives one call: the tensor
+// memory, the mbarriers of the weight-tile ring and of the two accumulator
+// halves, and the running counters their phases follow.  Static shared
+// memory, set up once per block (mlp_ctx_init) and released before the
+// block exits (mlp_ctx_free).  An error (a wait that gave up) is sticky.
+struct MlpCtx {
+  uint64_t full[kMlpStages], empty[kMlpStages];
+  uint64_t acc_full[2], acc_free[2], drain;
+  unsigned tmem;
+  unsigned item;      // weight tiles consumed so far
+  unsigned uses[2];   // groups that have used each accumulator half
+  unsigned err;
+};
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(smem_u32(bar)) : "memory");
+}
+__device__ __forceinline__ void epi_bar_sync() {
+  asm volatile("bar.sync 1, %0;\n" ::"n"(kMlpEpiWarps * 32) : "memory");
+}
+__device__ __forceinline__ unsigned ctx_err(const MlpCtx* c) { return *reinterpret_cast<const volatile unsigned*>(&c->err); }
+__device__ __forceinline__ void ctx_set_err(MlpCtx* c) { *reinterpret_cast<volatile unsigned*>(&c->err) = 1u; }
+
+// Called by every thread of the block.
+inline __device__ void mlp_ctx_init(MlpCtx* c) {
+  const int tid = threadIdx.x;
+  if ((tid >> 5) == 0) tmem_alloc(&c->tmem, 512);
+  if (tid == 0) {
+    for (int s = 0; s < kMlpStages; ++s) {
+      mbar_init(&c->full[s], 1);
+      mbar_init(&c->empty[s], 1);
+    }
+    for (int h = 0; h < 2; ++h) {
+      mbar_init(&c->acc_full[h], 1);
+      mbar_init(&c->acc_free[h], kMlpEpiWarps * 32);
+    }
+    mbar_init(&c->drain, 1);
+    mbar_fence_init();
+    c->item = 0u;
+    c->uses[0] = c->uses[1] = 0u;
+    c->err = 0u;
+  }
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
-  return *slot;
 }
-inline __device__ void mlp_tmem_free(unsigned tmem) {
+inline __device__ void mlp_ctx_free(MlpCtx* c) {
   tc_fence_before();
   __syncthreads();
-  if ((threadIdx.x >> 5) == 0) tmem_dealloc(tmem, 512);
+  if ((threadIdx.x >> 5) == 0) tmem_dealloc(c->tmem, 512);
   __syncthreads();
 }
 
@@ -197,231 +247,357 @@ __device__ __forceinline__ char* align1024_shared(char* p) {
   return p + ((1024u - (a & 1023u)) & 1023u);
 }
 
+// Sum over the warp of 16 values per lane: lane L returns the total of
+// column (L >> 1) & 15 (butterfly reduce-scatter, 16 shuffles).
+__device__ __forceinline__ float warp_sum16(const float (&s)[16], int lane) {
+  float a[8], b[4], c[2];
+  const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+#pragma unroll
+  for (int j = 0; j < 8; ++j) a[j] = (b4 ? s[j + 8] : s[j]) + __shfl_xor_sync(kFull, b4 ? s[j] : s[j + 8], 16);
+#pragma unroll
+  for (int j = 0; j < 4; ++j) b[j] = (b3 ? a[j + 4] : a[j]) + __shfl_xor_sync(kFull, b3 ? a[j] : a[j + 4], 8);
+#pragma unroll
+  for (int j = 0; j < 2; ++j) c[j] = (b2 ? b[j + 2] : b[j]) + __shfl_xor_sync(kFull, b2 ? b[j] : b[j + 2], 4);
+  float d = (b1 ? c[1] : c[0]) + __shfl_xor_sync(kFull, b1 ? c[0] : c[1], 2);
+  return d + __shfl_xor_sync(kFull, d, 1);
+}
+
+// The order in which a network's M-tiles are grouped on the accumulator
+// halves.  Hidden layers: one group of all M-tiles from column 0 (the next
+// layer's input is written in place, so the layer's MMAs must all be done
+// first).  Output layer: groups of kMlpOutGroup M-tiles, alternating halves.
+struct MlpGroup {
+  int g0, g1, h0, nh;
+};
+__device__ __forceinline__ MlpGroup mlp_group(int MT, bool last, int gi) {
+  MlpGroup G;
+  if (!last) {
+    G.g0 = 0;
+    G.g1 = MT;
+    G.h0 = 0;
+    G.nh = (MT * kMlpNb > kMlpHalfCols) ? 2 : 1;
+  } else {
+    G.g0 = gi * kMlpOutGroup;
+    G.g1 = min(MT, G.g0 + kMlpOutGroup);
+    G.h0 = gi & 1;
+    G.nh = 1;
+  }
+  return G;
+}
+__device__ __forceinline__ int mlp_n_groups(int MT, bool last) {
+  return last ? (MT + kMlpOutGroup - 1) / kMlpOutGroup : 1;
+}
+
 // Evaluates the batch x [n][d] (unit cube, n <= kMlpNb) with the BF16
-// tensor-core path into out[n] (log L), using the block's tensor memory
-// `tmem` (mlp_tmem_alloc).  Must be called by every thread of the block (at
-// least 128 threads: warps 0-3 read the accumulators back).  `sm` is 1024-byte aligned and holds
-// MlpSmem::kBytes.  Returns false (for every thread) on a wait timeout.
+// tensor-core path into out[n] (log L).  Called by every thread of a block
+// of at least kMlpThreads threads, with the block's context `ctx`
+// (mlp_ctx_init).  `sm` is 1024-byte aligned and holds MlpSmem::kBytes.
+// Returns false (for every thread) if a wait gave up, now or before.
 inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict__ tiles,
                                      const float* __restrict__ f32, const float* x, int x_stride, int n,
-                                     float* out, char* sm, unsigned tmem) {
+                                     float* out, char* sm, MlpCtx* ctx) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   char* stages = sm + MlpSmem::kStageOff;
   char* act = sm + MlpSmem::kActOff;
   float* chi = reinterpret_cast<float*>(sm + MlpSmem::kChiOff);
-  uint64_t* full = reinterpret_cast<uint64_t*>(sm + MlpSmem::kBarOff);
-  uint64_t* empty = full + kMlpStages;
-  uint64_t* done = empty + kMlpStages;
-  unsigned* misc = reinterpret_cast<unsigned*>(sm + MlpSmem::kMiscOff);  // [1] error flag
-  const unsigned NB = kMlpNb;
-  const unsigned idesc = idesc_bf16(128, kMlpNb);
+  constexpr int NB = kMlpNb;
+  constexpr unsigned S = kMlpStages;
+  if (ctx_err(ctx)) return false;  // uniform: nothing writes it between calls
+  const unsigned item0 = ctx->item, use0 = ctx->uses[0], use1 = ctx->uses[1];
+  const unsigned tmem = ctx->tmem;
+  const int last = M.n_layers - 1;
 
-  if (tid == 0) {
-    for (int s = 0; s < kMlpStages; ++s) {
-      mbar_init(&full[s], 1);
-      mbar_init(&empty[s], 1);
-    }
-    mbar_init(done, 1);
-    mbar_fence_init();
-    misc[1] = 0u;
-  }
   // layer-0 input: theta = lo + span x in BF16, rows = candidates, K = d (pad 0)
   const int kb0 = M.kpad[0] / 64;
-  for (int q = tid; q < kb0 * kMlpNb * 64; q += blockDim.x) {
-    const int kb = q / (kMlpNb * 64), rem = q % (kMlpNb * 64), r = rem / 64, k = rem % 64;
+  for (int q = tid; q < kb0 * NB * 64; q += blockDim.x) {
+    const int kb = q / (NB * 64), rem = q % (NB * 64), r = rem / 64, k = rem % 64;
     const int i = kb * 64 + k;
     float v = 0.f;
     if (r < n && i < M.d) v = fmaf(M.span[i], x[(size_t)r * x_stride + i], M.lo[i]);
-    *reinterpret_cast<__nv_bfloat16*>(act + kb * kMlpNb * 128 + sw128_offset(r, k)) = __float2bfloat16_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(act + kb * NB * 128 + sw128_offset(r, k)) = __float2bfloat16_rn(v);
   }
-  for (int q = tid; q < 4 * kMlpNb; q += blockDim.x) chi[q] = 0.f;
+  for (int q = tid; q < 4 * NB; q += blockDim.x) chi[q] = 0.f;
   fence_proxy_async();
-  tc_fence_before();
   __syncthreads();
-  tc_fence_after();
 
-  unsigned item = 0;      // weight tiles consumed so far (stage ring position)
-  unsigned done_phase = 0;
-  bool ok = true;
-  for (int l = 0; l < M.n_layers && ok; ++l) {
-    const int KB = M.kpad[l] / 64, MT = M.mpad[l] / 128;
-    const bool last = (l == M.n_layers - 1);
-    const int group = 512 / kMlpNb;  // M-tiles whose accumulators fit in tensor memory at once
-    for (int g0 = 0; g0 < MT && ok; g0 += group) {
-      const int g1 = min(MT, g0 + group);
-      const int n_items = (g1 - g0) * KB;
-      if (tid == 0) {
-        // one thread streams the weight tiles (TMA bulk copies, kMlpStages in
-        // flight) and issues the MMAs; a stage is refilled once the MMAs of
-        // the tile before the current one have completed, so the tensor pipe
-        // always has queued work
-        const uint8_t* src0 = tiles + (size_t)(M.tile0[l] + g0 * KB) * kMlpTileBytes;
-        int issued = 0, consumed = 0;
-        bool err = false;
-        for (; issued < n_items && issued < kMlpStages; ++issued) {
-          const unsigned it = item + issued, s = it % kMlpStages;
-          if (it >= kMlpStages && !mbar_wait(&empty[s], ((it / kMlpStages) - 1) & 1)) {
-            err = true;
-            break;
-          }
-          mbar_expect_tx(&full[s], kMlpTileBytes);
-          bulk_g2s(stages + s * kMlpTileBytes, src0 + (size_t)issued * kMlpTileBytes, kMlpTileBytes, &full[s]);
+  if (warp == kMlpProducerWarp) {
+    // weight tiles in consumption order = image order
+    if (lane == 0) {
+      const unsigned end = item0 + (unsigned)M.n_tiles;
+      unsigned it = item0;
+      bool err = false;
+      for (; it < end; ++it) {
+        const unsigned s = it % S;
+        if (ctx_err(ctx) || (it >= S && !mbar_wait(&ctx->empty[s], ((it / S) - 1) & 1))) {
+          err = true;
+          break;
         }
-        for (int i = 0; i < n_items && !err; ++i) {
-          const unsigned it = item + i, s = it % kMlpStages;
-          if (!mbar_wait(&full[s], (it / kMlpStages) & 1)) {
-            err = true;
-            break;
-          }
-          consumed = i + 1;
-          tc_fence_after();
-          const int t = g0 + i / KB, kb = i % KB;
-          const unsigned d_tmem = tmem + (unsigned)((t - g0) * kMlpNb);
-          const unsigned a0 = smem_u32(stages + s * kMlpTileBytes);
-          const unsigned b0 = smem_u32(act + kb * kMlpNb * 128);
-#pragma unroll
-          for (int k = 0; k < 4; ++k)
-            umma_bf16(d_tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc,
-                      (kb > 0 || k > 0) ? 1u : 0u);
-          umma_commit(&empty[s]);
-          const int j = i - 1 + kMlpStages;  // next tile, into the stage of tile i-1
-          if (i >= 1 && j < n_items && j >= issued) {
-            const unsigned itj = item + j, sj = itj % kMlpStages;
-            if (!mbar_wait(&empty[sj], ((itj / kMlpStages) - 1) & 1)) {
-              err = true;
-              break;
-            }
-            mbar_expect_tx(&full[sj], kMlpTileBytes);
-            bulk_g2s(stages + sj * kMlpTileBytes, src0 + (size_t)j * kMlpTileBytes, kMlpTileBytes, &full[sj]);
-            issued = j + 1;
-          }
-        }
-        umma_commit(done);
-        if (err) {
-          // drain: every copy this thread issued lands before the block moves on
-          for (int i = consumed; i < issued; ++i) {
-            const unsigned it = item + i;
-            mbar_wait(&full[it % kMlpStages], (it / kMlpStages) & 1);
-          }
-          misc[1] = 1u;
-        }
+        mbar_expect_tx(&ctx->full[s], kMlpTileBytes);
+        bulk_g2s(stages + s * kMlpTileBytes, tiles + (size_t)(it - item0) * kMlpTileBytes, kMlpTileBytes,
+                 &ctx->full[s]);
       }
-      item += n_items;
-      __syncthreads();
-      if (misc[1] != 0u) {
-        ok = false;
-        break;
+      if (err) {
+        ctx_set_err(ctx);
+        // every copy issued lands before the block moves on (only the last S can be outstanding)
+        for (unsigned j = (it - item0 > S) ? it - S : item0; j < it; ++j) mbar_wait(&ctx->full[j % S], (j / S) & 1);
       }
-      // all threads wait for the group's MMAs
-      if (!mbar_wait(done, done_phase)) {
-        misc[1] = 1u;
-      }
-      done_phase ^= 1u;
-      __syncthreads();
-      if (misc[1] != 0u) {
-        ok = false;
-        break;
-      }
-      tc_fence_after();
-      // epilogue: warp w reads lanes 32w..32w+31 (output features) of each M-tile
-      for (int t = g0; t < g1 && warp < 4; ++t) {
-        const int f = t * 128 + warp * 32 + lane;
-        for (int c0 = 0; c0 < kMlpNb; c0 += 16) {
-          float v[16];
-          tmem_ld16(tmem + ((unsigned)(warp * 32) << 16) + (unsigned)((t - g0) * kMlpNb + c0), v);
-          if (!last) {
-            const float bias = f32[M.bias0[l] + f];
-            const int kb = f / 64, k = f % 64;
-            char* dst = act + kb * kMlpNb * 128;
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const float h = silu(v[c] + bias);
-              *reinterpret_cast<__nv_bfloat16*>(dst + sw128_offset(c0 + c, k)) = __float2bfloat16_rn(h);
-            }
-          } else {
-            const float bias = f32[M.bias0[l] + f];
-            const float dk = f32[M.data0 + f], is = f32[M.isig0 + f];
-            float r2[16];
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              const float r = (v[c] + bias - dk) * is;
-              r2[c] = r * r;
-            }
-            // sum over the warp's 32 features for each of the 16 columns
-#pragma unroll
-            for (int c = 0; c < 16; ++c) {
-              float s = r2[c];
-#pragma unroll
-              for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(kFull, s, o);
-              r2[c] = s;
-            }
-            if (lane < 16) {
-              float s = r2[0];
-#pragma unroll
-              for (int c = 1; c < 16; ++c)
-                if (lane == c) s = r2[c];
-              chi[warp * kMlpNb + c0 + lane] += s;
-            }
-          }
-        }
-      }
-      // the next layer's MMAs read the new activations: make them visible
-      fence_proxy_async();
-      tc_fence_before();
-      __syncthreads();
-      tc_fence_after();
     }
+    __syncwarp();
+  } else if (warp == kMlpMmaWarp) {
+    if (lane == 0) {
+      const unsigned idesc = idesc_bf16(128, NB);
+      unsigned it = item0, uses[2] = {use0, use1};
+      bool err = false;
+      for (int l = 0; l <= last && !err; ++l) {
+        const int KB = M.kpad[l] / 64, MT = M.mpad[l] / 128;
+        const int ng = mlp_n_groups(MT, l == last);
+        for (int gi = 0; gi < ng && !err; ++gi) {
+          const MlpGroup G = mlp_group(MT, l == last, gi);
+          // the previous user of each half has been drained; at a layer's
+          // first group, of both halves (that epilogue also wrote this layer's input)
+          for (int h = 0; h < 2 && !err; ++h) {
+            const bool need = (gi == 0) || (h >= G.h0 && h < G.h0 + G.nh);
+            if (need && uses[h] > 0 && !mbar_wait(&ctx->acc_free[h], (uses[h] - 1) & 1)) err = true;
+          }
+          if (err || ctx_err(ctx)) {
+            err = true;
+            break;
+          }
+          tc_fence_after();
+          const unsigned col0 = (unsigned)G.h0 * kMlpHalfCols;
+          for (int t = G.g0; t < G.g1 && !err; ++t) {
+            for (int kb = 0; kb < KB; ++kb, ++it) {
+              const unsigned s = it % S;
+              if (!mbar_wait(&ctx->full[s], (it / S) & 1)) {
+                err = true;
+                break;
+              }
+              tc_fence_after();
+              const unsigned d_tmem = tmem + col0 + (unsigned)((t - G.g0) * NB);
+              const unsigned a0 = smem_u32(stages + s * kMlpTileBytes);
+              const unsigned b0 = smem_u32(act + kb * NB * 128);
+#pragma unroll
+              for (int k = 0; k < 4; ++k)
+                umma_bf16(d_tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc,
+                          (kb > 0 || k > 0) ? 1u : 0u);
+              umma_commit(&ctx->empty[s]);
+            }
+          }
+          if (err) break;
+          for (int h = G.h0; h < G.h0 + G.nh; ++h) {
+            umma_commit(&ctx->acc_full[h]);
+            ++uses[h];
+          }
+        }
+      }
+      if (err) {
+        ctx_set_err(ctx);
+        umma_commit(&ctx->drain);  // the MMAs already issued finish before the block moves on
+        mbar_wait(&ctx->drain, 0);
+      } else {
+        ctx->item = it;
+        ctx->uses[0] = uses[0];
+        ctx->uses[1] = uses[1];
+      }
+    }
+    __syncwarp();
+  } else if (warp < kMlpEpiWarps) {
+    const int q = warp;  // tensor-memory lane quadrant
+    const unsigned lane_base = (unsigned)(q * 32) << 16;
+    unsigned uses[2] = {use0, use1};
+    bool err = false;
+    for (int l = 0; l <= last && !err; ++l) {
+      const int MT = M.mpad[l] / 128;
+      const bool is_last = (l == last);
+      const int ng = mlp_n_groups(MT, is_last);
+      for (int gi = 0; gi < ng && !err; ++gi) {
+        const MlpGroup G = mlp_group(MT, is_last, gi);
+        for (int h = G.h0; h < G.h0 + G.nh; ++h) {
+          bool ok = true;
+          if (lane == 0) ok = mbar_wait(&ctx->acc_full[h], uses[h] & 1);
+          if (!__shfl_sync(kFull, ok ? 1 : 0, 0)) err = true;
+        }
+        if (err) break;
+        tc_fence_after();
+        const unsigned col0 = (unsigned)G.h0 * kMlpHalfCols;
+        if (!is_last) {
+          // bias + SiLU, BF16 straight into the next layer's swizzled B operand
+          for (int t = G.g0; t < G.g1; ++t) {
+            const int f = t * 128 + q * 32 + lane;
+            const float bias = f32[M.bias0[l] + f];
+            const int kb = f >> 6, k = f & 63;
+            char* dst = act + kb * NB * 128;
+            for (int c0 = 0; c0 < NB; c0 += 16) {
+              float v[16];
+              tmem_ld16(tmem + lane_base + col0 + (unsigned)((t - G.g0) * NB + c0), v);
+#pragma unroll
+              for (int c = 0; c < 16; ++c)
+                *reinterpret_cast<__nv_bfloat16*>(dst + sw128_offset(c0 + c, k)) =
+                    __float2bfloat16_rn(silu_fast(v[c] + bias));
+            }
+          }
+          fence_proxy_async();
+        } else {
+          // chi^2: per candidate column, summed over the group's features
+          float is_t[kMlpOutGroup], cb_t[kMlpOutGroup];
+#pragma unroll
+          for (int j = 0; j < kMlpOutGroup; ++j) {
+            const int f = (G.g0 + j) * 128 + q * 32 + lane;
+            const bool in = G.g0 + j < G.g1;
+            const float is = in ? f32[M.isig0 + f] : 0.f;
+            is_t[j] = is;
+            cb_t[j] = in ? (f32[M.bias0[l] + f] - f32[M.data0 + f]) * is : 0.f;
+          }
+          for (int c0 = 0; c0 < NB; c0 += 16) {
+            float sacc[16];
+#pragma unroll
+            for (int c = 0; c < 16; ++c) sacc[c] = 0.f;
+#pragma unroll
+            for (int j = 0; j < kMlpOutGroup; ++j) {
+              if (G.g0 + j < G.g1) {
+                float v[16];
+                tmem_ld16(tmem + lane_base + col0 + (unsigned)(j * NB + c0), v);
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                  const float r = fmaf(v[c], is_t[j], cb_t[j]);
+                  sacc[c] = fmaf(r, r, sacc[c]);
+                }
+              }
+            }
+            const float tot = warp_sum16(sacc, lane);
+            if ((lane & 1) == 0) chi[q * NB + c0 + ((lane >> 1) & 15)] += tot;
+          }
+        }
+        tc_fence_before();
+        for (int h = G.h0; h < G.h0 + G.nh; ++h) {
+          mbar_arrive(&ctx->acc_free[h]);
+          ++uses[h];
+        }
+      }
+    }
+    if (err) ctx_set_err(ctx);
+    epi_bar_sync();
+    for (int r = tid; r < n; r += kMlpEpiWarps * 32)
+      out[r] = -0.5f * (chi[r] + chi[NB + r] + chi[2 * NB + r] + chi[3 * NB + r]);
   }
-  if (ok) {
-    for (int r = tid; r < n; r += blockDim.x)
-      out[r] = -0.5f * (chi[r] + chi[kMlpNb + r] + chi[2 * kMlpNb + r] + chi[3 * kMlpNb + r]);
-  }
-  tc_fence_before();
   __syncthreads();
-  return ok;
+  return ctx_err(ctx) == 0u;
 }
 
 // FP32 CUDA-core evaluator: the same function in FP32 (weights = the FP32
-// masters).  Each block evaluates up to kMlpF32Nb candidates; act: shared
-// FP32 [2][kMlpF32Nb][kMlpMaxK].
-constexpr int kMlpF32Nb = 8;
-inline __device__ void mlp_eval_f32(const MlpDesc& M, const float* __restrict__ f32, const float* x, int x_stride,
-                                    int n, float* out, float* act) {
+// masters, stored transposed [in][out] so that a warp's weight loads are
+// coalesced).  One pass evaluates up to NB candidates: thread t owns the
+// output features t and t + blockDim.x of each chunk of 2 blockDim.x
+// features and keeps their NB accumulators in registers; the activations
+// sit transposed in shared memory ([feature][candidate], row stride NB + 4)
+// so that one 16-byte broadcast load feeds 4 candidates.  Weights are
+// fetched one block of kMlpF32Ku inputs ahead.  act: mlp_f32_act_bytes(NB).
+constexpr int kMlpF32Nb = 8;        // candidates per pass of the re-evaluation
+constexpr int kMlpF32NbWide = 32;   // candidates per pass of the FP32 path
+constexpr int kMlpF32Ku = 4;
+__host__ __device__ constexpr int mlp_f32_stride(int nb) { return nb + 4; }
+__host__ __device__ constexpr size_t mlp_f32_act_bytes(int nb) {
+  return sizeof(float) * 2 * (size_t)kMlpMaxK * (size_t)mlp_f32_stride(nb);
+}
+
+template <int NB>
+__device__ __noinline__ void mlp_eval_f32(const MlpDesc& M, const float* __restrict__ f32, const float* x,
+                                          int x_stride, int n, float* out, float* act) {
+  static_assert(NB % 4 == 0, "NB must be a multiple of 4");
+  constexpr int S = mlp_f32_stride(NB);
+  constexpr int KU = kMlpF32Ku;
   const int tid = threadIdx.x, B = blockDim.x;
   float* a0 = act;
-  float* a1 = act + kMlpF32Nb * kMlpMaxK;
-  for (int q = tid; q < kMlpF32Nb * kMlpMaxK; q += B) {
-    const int r = q / kMlpMaxK, i = q % kMlpMaxK;
-    a0[q] = (r < n && i < M.d) ? fmaf(M.span[i], x[(size_t)r * x_stride + i], M.lo[i]) : 0.f;
+  float* a1 = act + kMlpMaxK * S;
+  for (int q = tid; q < M.d * NB; q += B) {
+    const int i = q / NB, r = q - i * NB;
+    a0[i * S + r] = (r < n) ? fmaf(M.span[i], x[(size_t)r * x_stride + i], M.lo[i]) : 0.f;
   }
   __syncthreads();
-  float part[kMlpF32Nb];
+  float part[NB];
 #pragma unroll
-  for (int r = 0; r < kMlpF32Nb; ++r) part[r] = 0.f;
+  for (int r = 0; r < NB; ++r) part[r] = 0.f;
   for (int l = 0; l < M.n_layers; ++l) {
     const int nin = M.in[l], nout = M.out[l];
     const bool last = (l == M.n_layers - 1);
-    const float* W = f32 + M.w32_0[l];
+    const float* WT = f32 + M.w32_0[l];
     const float* bias = f32 + M.bias0[l];
-    for (int o = tid; o < nout; o += B) {
-      float acc[kMlpF32Nb];
+    for (int o0 = 0; o0 < nout; o0 += 2 * B) {
+      const int oa = o0 + tid, ob = oa + B;
+      const bool va = oa < nout, vb = ob < nout;
+      const int ca = va ? oa : 0, cb = vb ? ob : 0;  // clamped: every load stays in the layer
+      float acc_a[NB], acc_b[NB];
+      {
+        const float ba = bias[ca], bb = bias[cb];
 #pragma unroll
-      for (int r = 0; r < kMlpF32Nb; ++r) acc[r] = bias[o];
-      const float* wr = W + (size_t)o * nin;
-      for (int i = 0; i < nin; ++i) {
-        const float w = wr[i];
+        for (int r = 0; r < NB; ++r) {
+          acc_a[r] = ba;
+          acc_b[r] = bb;
+        }
+      }
+      float wa[KU], wb[KU];
 #pragma unroll
-        for (int r = 0; r < kMlpF32Nb; ++r) acc[r] = fmaf(w, a0[r * kMlpMaxK + i], acc[r]);
+      for (int u = 0; u < KU; ++u) {
+        wa[u] = (u < nin) ? WT[(size_t)u * nout + ca] : 0.f;
+        wb[u] = (u < nin) ? WT[(size_t)u * nout + cb] : 0.f;
+      }
+      for (int i0 = 0; i0 < nin; i0 += KU) {
+        float na[KU], nb[KU];
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+          const int i = i0 + KU + u;
+          na[u] = (i < nin) ? WT[(size_t)i * nout + ca] : 0.f;
+          nb[u] = (i < nin) ? WT[(size_t)i * nout + cb] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+          if (i0 + u < nin) {
+            const float4* ar = reinterpret_cast<const float4*>(a0 + (i0 + u) * S);
+#pragma unroll
+            for (int q = 0; q < NB / 4; ++q) {
+              const float4 v = ar[q];
+              acc_a[4 * q + 0] = fmaf(wa[u], v.x, acc_a[4 * q + 0]);
+              acc_a[4 * q + 1] = fmaf(wa[u], v.y, acc_a[4 * q + 1]);
+              acc_a[4 * q + 2] = fmaf(wa[u], v.z, acc_a[4 * q + 2]);
+              acc_a[4 * q + 3] = fmaf(wa[u], v.w, acc_a[4 * q + 3]);
+              acc_b[4 * q + 0] = fmaf(wb[u], v.x, acc_b[4 * q + 0]);
+              acc_b[4 * q + 1] = fmaf(wb[u], v.y, acc_b[4 * q + 1]);
+              acc_b[4 * q + 2] = fmaf(wb[u], v.z, acc_b[4 * q + 2]);
+              acc_b[4 * q + 3] = fmaf(wb[u], v.w, acc_b[4 * q + 3]);
+            }
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < KU; ++u) {
+          wa[u] = na[u];
+          wb[u] = nb[u];
+        }
       }
       if (!last) {
+        if (va) {
 #pragma unroll
-        for (int r = 0; r < kMlpF32Nb; ++r) a1[r * kMlpMaxK + o] = silu(acc[r]);
+          for (int r = 0; r < NB; ++r) a1[oa * S + r] = silu(acc_a[r]);
+        }
+        if (vb) {
+#pragma unroll
+          for (int r = 0; r < NB; ++r) a1[ob * S + r] = silu(acc_b[r]);
+        }
       } else {
-        const float dk = f32[M.data0 + o], is = f32[M.isig0 + o];
+        if (va) {
+          const float dk = f32[M.data0 + oa], is = f32[M.isig0 + oa];
 #pragma unroll
-        for (int r = 0; r < kMlpF32Nb; ++r) {
-          const float rr = (acc[r] - dk) * is;
-          part[r] = fmaf(rr, rr, part[r]);
+          for (int r = 0; r < NB; ++r) {
+            const float rr = (acc_a[r] - dk) * is;
+            part[r] = fmaf(rr, rr, part[r]);
+          }
+        }
+        if (vb) {
+          const float dk = f32[M.data0 + ob], is = f32[M.isig0 + ob];
+#pragma unroll
+          for (int r = 0; r < NB; ++r) {
+            const float rr = (acc_b[r] - dk) * is;
+            part[r] = fmaf(rr, rr, part[r]);
+          }
         }
       }
     }
@@ -432,21 +608,22 @@ inline __device__ void mlp_eval_f32(const MlpDesc& M, const float* __restrict__ 
       a1 = tmp;
     }
   }
-  // chi^2: block sum of part[r] per candidate, fixed order
-  __shared__ float red[kMlpF32Nb][32];
+  // chi^2: block sum of part[r] per candidate in a fixed order (warp
+  // partials staged in the free activation buffer)
+  float* red = a1;  // [NB][32]
   const int lane = tid & 31, wid = tid >> 5, nw = B >> 5;
 #pragma unroll
-  for (int r = 0; r < kMlpF32Nb; ++r) {
+  for (int r = 0; r < NB; ++r) {
     float s = part[r];
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(kFull, s, o);
-    if (lane == 0) red[r][wid] = s;
+    if (lane == 0) red[r * 32 + wid] = s;
   }
   __syncthreads();
-  if (tid < n) {
+  for (int r = tid; r < n; r += B) {
     float s = 0.f;
-    for (int w = 0; w < nw; ++w) s += red[tid][w];
-    out[tid] = -0.5f * s;
+    for (int w = 0; w < nw; ++w) s += red[r * 32 + w];
+    out[r] = -0.5f * s;
   }
   __syncthreads();
 }

@@ -114,7 +114,7 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax,
   c.mlp = c.tile;
   if (mlp) {
     const size_t need = c.mlp + MlpSmem::kBytes + 1024;  // + alignment of the tensor-core region
-    const size_t f32 = c.mlp + sizeof(float) * 2 * kMlpF32Nb * kMlpMaxK;
+    const size_t f32 = c.mlp + mlp_f32_act_bytes(kMlpF32NbWide);
     if (need > o) o = need;
     if (f32 > o) o = f32;
   }
@@ -279,17 +279,18 @@ __device__ __noinline__ void walker_phase(const RunDesc& R, const LikParams& P, 
 // so every log L that is stored (dead points, Algorithm 2) is an FP32 value.
 // Called by every thread of the block.
 inline __device__ bool mlp_batch_f32(const RunDesc& R, const float* xs, int n, float* ls, float* act) {
-  for (int b0 = 0; b0 < n; b0 += kMlpF32Nb)
-    mlp_eval_f32(*R.mlp_desc, R.mlp_f32, xs + (size_t)b0 * kMaxDim, kMaxDim, min(kMlpF32Nb, n - b0), ls + b0, act);
+  for (int b0 = 0; b0 < n; b0 += kMlpF32NbWide)
+    mlp_eval_f32<kMlpF32NbWide>(*R.mlp_desc, R.mlp_f32, xs + (size_t)b0 * kMaxDim, kMaxDim,
+                                min(kMlpF32NbWide, n - b0), ls + b0, act);
   return true;
 }
 
 inline __device__ bool mlp_batch_bf16(const RunDesc& R, const float* xs, int n, float* ls, char* tsm,
-                                      unsigned tmem) {
+                                      MlpCtx* ctx) {
   bool ok = true;
   for (int b0 = 0; b0 < n && ok; b0 += kMlpNb)
     ok = mlp_eval_bf16(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, xs + (size_t)b0 * kMaxDim, kMaxDim, min(kMlpNb, n - b0),
-                       ls + b0, tsm, tmem);
+                       ls + b0, tsm, ctx);
   return ok;
 }
 
@@ -302,7 +303,7 @@ inline __device__ void mlp_reeval(const RunDesc& R, float* xbuf, float* lbuf, co
     for (int q = threadIdx.x; q < ng * kMaxDim; q += blockDim.x)
       xg[q] = xbuf[(size_t)list[g0 + q / kMaxDim] * kMaxDim + q % kMaxDim];
     __syncthreads();
-    mlp_eval_f32(*R.mlp_desc, R.mlp_f32, xg, kMaxDim, ng, lg, act);
+    mlp_eval_f32<kMlpF32Nb>(*R.mlp_desc, R.mlp_f32, xg, kMaxDim, ng, lg, act);
     for (int q = threadIdx.x; q < ng; q += blockDim.x) lbuf[list[g0 + q]] = lg[q];
     __syncthreads();
   }
@@ -311,7 +312,7 @@ inline __device__ void mlp_reeval(const RunDesc& R, float* xbuf, float* lbuf, co
 template <int DMAX>
 __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& S, const float* s_W, const int* s_seed,
                                               const float* s_chol, float* xbuf, float* lbuf, int* rlist, char* msm,
-                                              unsigned tmem, BlockScratch& BS, long long& ev_out, int& fl_out,
+                                              MlpCtx* ctx, BlockScratch& BS, long long& ev_out, int& fl_out,
                                               long long& re_out, int& err_out) {
   constexpr int RW = dir_row(DMAX);
   const int tid = threadIdx.x, m = R.m, d = S.d;
@@ -377,7 +378,7 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
     }
     __syncthreads();
     if (bf16) {
-      if (!mlp_batch_bf16(R, xbuf, m, lbuf, tsm, tmem)) err = 1;
+      if (!mlp_batch_bf16(R, xbuf, m, lbuf, tsm, ctx)) err = 1;
       // re-evaluate in FP32 the candidates close to their threshold
       const float thr = (phase == 2) ? thr_in : thr_out;
       const bool need = active && in && R.reeval_margin > 0.f && fabsf(lbuf[tid] - thr) < R.reeval_margin;
@@ -556,10 +557,9 @@ __global__ void __launch_bounds__(256, (MLP ? 1 : NS_MINB(DMAX))) k_run(const Ru
   }
   __syncthreads();
   if (RS.stopped || RS.status != 0) return;
-  __shared__ unsigned tmem_slot;
-  unsigned tmem = 0;
+  __shared__ MlpCtx mlp_ctx;
   if constexpr (MLP) {
-    if (R.precision == 1) tmem = mlp_tmem_alloc(&tmem_slot);
+    if (R.precision == 1) mlp_ctx_init(&mlp_ctx);
   }
   const int d = R.d, N = R.N, m = R.m;
   const Carve cv = make_carve(d, m, R.n_nodes, DMAX, MLP);
@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(256, (MLP ? 1 : NS_MINB(DMAX))) k_run(const Ru
     int fl = 0, werr = 0;
     SC.t = t;
     if constexpr (MLP) {
-      walker_phase_mlp<DMAX>(R, SC, s_W, s_seed, s_chol, s_xbuf, s_lbuf, s_rlist, s_mlp, tmem, S, ev, fl, re, werr);
+      walker_phase_mlp<DMAX>(R, SC, s_W, s_seed, s_chol, s_xbuf, s_lbuf, s_rlist, s_mlp, &mlp_ctx, S, ev, fl, re, werr);
     } else {
       if ((tid & ~31) < m) walker_phase<DMAX>(R, P, SC, s_W, s_seed, s_chol, s_slots, ev, fl);
     }
@@ -749,7 +749,7 @@ __global__ void __launch_bounds__(256, (MLP ? 1 : NS_MINB(DMAX))) k_run(const Ru
   }
   __syncthreads();
   if constexpr (MLP) {
-    if (R.precision == 1) mlp_tmem_free(tmem);
+    if (R.precision == 1) mlp_ctx_free(&mlp_ctx);
   }
   if (tid == 0) {
     RS.logz = E.logz;
