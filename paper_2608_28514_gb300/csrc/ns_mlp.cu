@@ -17,7 +17,10 @@ using namespace nsd;
 namespace {
 
 // Persistent: each block sets up its tensor memory and barriers once and
-// evaluates batches of kMlpNb candidates, grid-strided.
+// evaluates batches of kMlpNbMax candidates, grid-strided.
+constexpr int kMlpStandaloneStages = 4;
+using MlpSmemStandalone = MlpSmem<kMlpNbMax, kMlpStandaloneStages>;
+
 __global__ void __launch_bounds__(kMlpThreads, 1)
     k_mlp_bf16(const MlpDesc M, const uint8_t* __restrict__ tiles, const float* __restrict__ f32,
                const float* __restrict__ x, int n, float* __restrict__ out) {
@@ -25,11 +28,12 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
   __shared__ MlpCtx ctx;
   char* sm = align1024_shared(sm_raw);
   mlp_ctx_init(&ctx);
-  const int n_batches = (n + kMlpNb - 1) / kMlpNb;
+  const int n_batches = (n + kMlpNbMax - 1) / kMlpNbMax;
   for (int b = blockIdx.x; b < n_batches; b += gridDim.x) {
-    const int b0 = b * kMlpNb;
-    const int nb = min(kMlpNb, n - b0);
-    if (!mlp_eval_bf16(M, tiles, f32, x + (size_t)b0 * M.d, M.d, nb, out + b0, sm, &ctx))
+    const int b0 = b * kMlpNbMax;
+    const int nb = min(kMlpNbMax, n - b0);
+    if (!mlp_eval_bf16<kMlpNbMax, kMlpStandaloneStages>(M, tiles, f32, x + (size_t)b0 * M.d, M.d, nb, out + b0,
+                                                         sm, &ctx))
       for (int r = threadIdx.x; r < nb; r += blockDim.x) out[b0 + r] = __int_as_float(0x7fffffff);
   }
   mlp_ctx_free(&ctx);
@@ -160,13 +164,13 @@ cudaError_t ns_mlp_launch(const MlpDesc& M, const void* image, int n, const floa
   const uint8_t* tiles = static_cast<const uint8_t*>(image);
   const float* f32 = reinterpret_cast<const float*>(tiles + M.tile_bytes);
   if (precision == 1) {
-    const int smem = MlpSmem::kBytes + 1024;
+    const int smem = MlpSmemStandalone::kBytes + 1024;
     cudaError_t e = cudaFuncSetAttribute(k_mlp_bf16, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int dev = 0, n_sm = 1;
     if (e == cudaSuccess) e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return e;
-    const int n_batches = (n + kMlpNb - 1) / kMlpNb;
+    const int n_batches = (n + kMlpNbMax - 1) / kMlpNbMax;
     k_mlp_bf16<<<std::min(n_batches, n_sm), kMlpThreads, smem, s>>>(M, tiles, f32, x, n, logl);
   } else {
     const int smem = (int)mlp_f32_act_bytes(kMlpF32NbWide);

@@ -5,7 +5,7 @@
 // Two evaluators of a batch of candidate points:
 //  * BF16 on the 5th-generation tensor cores (tcgen05): per layer, the
 //    weights W [out][in] are the A operand (M = 128 output features per
-//    tile, K-major), the batch of candidates the B operand (N = kMlpNb
+//    tile, K-major), the batch of candidates the B operand (N <= kMlpNbMax
 //    points, K-major), the FP32 accumulators live in tensor memory.  Weight
 //    tiles are packed once, on the host, into the exact 128-byte-swizzled
 //    shared-memory image of one 128 x 64 BF16 tile (16 KB) and streamed by
@@ -28,8 +28,8 @@
 namespace nsd {
 
 constexpr int kMlpMaxLayers = 8;
-constexpr int kMlpNb = 64;        // candidates per block (the MMA's N)
-constexpr int kMlpStages = 6;     // weight tiles in flight
+constexpr int kMlpNbMax = 128;    // candidates per call, at most (the MMA's N)
+constexpr int kMlpStagesMax = 4;  // weight tiles in flight, at most
 constexpr int kMlpTileBytes = 128 * 128;  // 128 rows x 64 BF16 (128 bytes)
 constexpr int kMlpMaxK = 512;     // widest padded layer input
 constexpr unsigned kMlpWaitCap = 1u << 22;
@@ -167,26 +167,31 @@ __device__ __forceinline__ float silu(float z) { return z / (1.f + expf(-z)); }
 // the stored activation).
 __device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.f + __expf(-z)); }
 
-// Shared memory of the BF16 evaluator (offsets from a 1024-aligned base).
+// Shared memory of the BF16 evaluator (offsets from a 1024-aligned base):
+// STAGES weight tiles, the B operand for up to NBMAX candidates, chi^2
+// partials.  The streaming of weight tiles from L2 is throughput-bound, not
+// latency-bound, so a few stages suffice.
+template <int NBMAX, int STAGES>
 struct MlpSmem {
+  static_assert(NBMAX % 16 == 0 && NBMAX <= kMlpNbMax && STAGES >= 2 && STAGES <= kMlpStagesMax, "");
   static constexpr int kStageOff = 0;
-  static constexpr int kActOff = kStageOff + kMlpStages * kMlpTileBytes;      // [kpad/64][kMlpNb][128 B]
-  static constexpr int kActBytes = (kMlpMaxK / 64) * kMlpNb * 128;
-  static constexpr int kChiOff = kActOff + kActBytes;                         // [4][kMlpNb] floats
-  static constexpr int kBytes = kChiOff + 4 * kMlpNb * 4;
+  static constexpr int kActOff = kStageOff + STAGES * kMlpTileBytes;  // [kpad/64][NBMAX][128 B]
+  static constexpr int kActBytes = (kMlpMaxK / 64) * NBMAX * 128;
+  static constexpr int kChiOff = kActOff + kActBytes;                 // [4][NBMAX] floats
+  static constexpr int kBytes = kChiOff + 4 * NBMAX * 4;
 };
 
-// Warp roles of the BF16 evaluator: warps 0-3 read the accumulators back
-// (warp w owns tensor-memory lanes 32w..32w+31), warp 4 streams the weight
-// tiles, warp 5 issues the MMAs.  The block needs at least kMlpThreads.
-constexpr int kMlpEpiWarps = 4;
-constexpr int kMlpProducerWarp = 4;
-constexpr int kMlpMmaWarp = 5;
-constexpr int kMlpThreads = 192;
+// Warp roles of the BF16 evaluator: warps 0-7 read the accumulators back
+// (warp w owns tensor-memory lanes 32(w%4)..32(w%4)+31 and every other
+// 16-column chunk, starting at chunk w/4), warp 8 streams the weight tiles,
+// warp 9 issues the MMAs.  The block needs at least kMlpThreads threads.
+constexpr int kMlpEpiWarps = 8;
+constexpr int kMlpProducerWarp = 8;
+constexpr int kMlpMmaWarp = 9;
+constexpr int kMlpThreads = 320;
 // tensor memory: two halves of 256 columns; an output-layer group of M-tiles
 // fills one half while the epilogue drains the other
 constexpr int kMlpHalfCols = 256;
-constexpr int kMlpOutGroup = kMlpHalfCols / kMlpNb;
 
 // Per-block state of the BF16 evaluator that outlives one call: the tensor
 // memory, the mbarriers of the weight-tile ring and of the two accumulator
@@ -194,7 +199,7 @@ constexpr int kMlpOutGroup = kMlpHalfCols / kMlpNb;
 // memory, set up once per block (mlp_ctx_init) and released before the
 // block exits (mlp_ctx_free).  An error (a wait that gave up) is sticky.
 struct MlpCtx {
-  uint64_t full[kMlpStages], empty[kMlpStages];
+  uint64_t full[kMlpStagesMax], empty[kMlpStagesMax];
   uint64_t acc_full[2], acc_free[2], drain;
   unsigned tmem;
   unsigned item;      // weight tiles consumed so far
@@ -216,7 +221,7 @@ inline __device__ void mlp_ctx_init(MlpCtx* c) {
   const int tid = threadIdx.x;
   if ((tid >> 5) == 0) tmem_alloc(&c->tmem, 512);
   if (tid == 0) {
-    for (int s = 0; s < kMlpStages; ++s) {
+    for (int s = 0; s < kMlpStagesMax; ++s) {
       mbar_init(&c->full[s], 1);
       mbar_init(&c->empty[s], 1);
     }
@@ -262,61 +267,67 @@ __device__ __forceinline__ float warp_sum16(const float (&s)[16], int lane) {
   return d + __shfl_xor_sync(kFull, d, 1);
 }
 
-// The order in which a network's M-tiles are grouped on the accumulator
-// halves.  Hidden layers: one group of all M-tiles from column 0 (the next
-// layer's input is written in place, so the layer's MMAs must all be done
-// first).  Output layer: groups of kMlpOutGroup M-tiles, alternating halves.
+// How a layer's M-tiles are grouped on the accumulator halves for a call
+// with N candidates.  Hidden layers: one group of all M-tiles from column 0
+// (the next layer's input is written in place, so the layer's MMAs must all
+// be done first; MT x N <= 512).  Output layer: groups of 256 / N M-tiles,
+// alternating halves.
 struct MlpGroup {
   int g0, g1, h0, nh;
 };
-__device__ __forceinline__ MlpGroup mlp_group(int MT, bool last, int gi) {
+__device__ __forceinline__ MlpGroup mlp_group(int MT, bool last, int gi, int N) {
   MlpGroup G;
   if (!last) {
     G.g0 = 0;
     G.g1 = MT;
     G.h0 = 0;
-    G.nh = (MT * kMlpNb > kMlpHalfCols) ? 2 : 1;
+    G.nh = (MT * N > kMlpHalfCols) ? 2 : 1;
   } else {
-    G.g0 = gi * kMlpOutGroup;
-    G.g1 = min(MT, G.g0 + kMlpOutGroup);
+    const int per = kMlpHalfCols / N;
+    G.g0 = gi * per;
+    G.g1 = min(MT, G.g0 + per);
     G.h0 = gi & 1;
     G.nh = 1;
   }
   return G;
 }
-__device__ __forceinline__ int mlp_n_groups(int MT, bool last) {
-  return last ? (MT + kMlpOutGroup - 1) / kMlpOutGroup : 1;
+__device__ __forceinline__ int mlp_n_groups(int MT, bool last, int N) {
+  const int per = kMlpHalfCols / N;
+  return last ? (MT + per - 1) / per : 1;
 }
 
-// Evaluates the batch x [n][d] (unit cube, n <= kMlpNb) with the BF16
-// tensor-core path into out[n] (log L).  Called by every thread of a block
-// of at least kMlpThreads threads, with the block's context `ctx`
-// (mlp_ctx_init).  `sm` is 1024-byte aligned and holds MlpSmem::kBytes.
-// Returns false (for every thread) if a wait gave up, now or before.
+// Evaluates the batch x [n][d] (unit cube, 1 <= n <= NBMAX) with the BF16
+// tensor-core path into out[n] (log L); the MMAs run with N = n rounded up
+// to 16.  Called by every thread of a block of at least kMlpThreads threads,
+// with the block's context `ctx` (mlp_ctx_init).  `sm` is 1024-byte aligned
+// and holds MlpSmem<NBMAX, STAGES>::kBytes.  Returns false (for every
+// thread) if a wait gave up, now or before.
+template <int NBMAX, int STAGES>
 inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict__ tiles,
                                      const float* __restrict__ f32, const float* x, int x_stride, int n,
                                      float* out, char* sm, MlpCtx* ctx) {
+  using L = MlpSmem<NBMAX, STAGES>;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  char* stages = sm + MlpSmem::kStageOff;
-  char* act = sm + MlpSmem::kActOff;
-  float* chi = reinterpret_cast<float*>(sm + MlpSmem::kChiOff);
-  constexpr int NB = kMlpNb;
-  constexpr unsigned S = kMlpStages;
+  char* stages = sm + L::kStageOff;
+  char* act = sm + L::kActOff;
+  float* chi = reinterpret_cast<float*>(sm + L::kChiOff);
+  constexpr unsigned S = STAGES;
   if (ctx_err(ctx)) return false;  // uniform: nothing writes it between calls
+  const int N = (n + 15) & ~15;
   const unsigned item0 = ctx->item, use0 = ctx->uses[0], use1 = ctx->uses[1];
   const unsigned tmem = ctx->tmem;
   const int last = M.n_layers - 1;
 
   // layer-0 input: theta = lo + span x in BF16, rows = candidates, K = d (pad 0)
   const int kb0 = M.kpad[0] / 64;
-  for (int q = tid; q < kb0 * NB * 64; q += blockDim.x) {
-    const int kb = q / (NB * 64), rem = q % (NB * 64), r = rem / 64, k = rem % 64;
+  for (int q = tid; q < kb0 * N * 64; q += blockDim.x) {
+    const int kb = q / (N * 64), rem = q % (N * 64), r = rem / 64, k = rem % 64;
     const int i = kb * 64 + k;
     float v = 0.f;
     if (r < n && i < M.d) v = fmaf(M.span[i], x[(size_t)r * x_stride + i], M.lo[i]);
-    *reinterpret_cast<__nv_bfloat16*>(act + kb * NB * 128 + sw128_offset(r, k)) = __float2bfloat16_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(act + kb * NBMAX * 128 + sw128_offset(r, k)) = __float2bfloat16_rn(v);
   }
-  for (int q = tid; q < 4 * NB; q += blockDim.x) chi[q] = 0.f;
+  for (int q = tid; q < 4 * NBMAX; q += blockDim.x) chi[q] = 0.f;
   fence_proxy_async();
   __syncthreads();
 
@@ -345,14 +356,14 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
     __syncwarp();
   } else if (warp == kMlpMmaWarp) {
     if (lane == 0) {
-      const unsigned idesc = idesc_bf16(128, NB);
+      const unsigned idesc = idesc_bf16(128, N);
       unsigned it = item0, uses[2] = {use0, use1};
       bool err = false;
       for (int l = 0; l <= last && !err; ++l) {
         const int KB = M.kpad[l] / 64, MT = M.mpad[l] / 128;
-        const int ng = mlp_n_groups(MT, l == last);
+        const int ng = mlp_n_groups(MT, l == last, N);
         for (int gi = 0; gi < ng && !err; ++gi) {
-          const MlpGroup G = mlp_group(MT, l == last, gi);
+          const MlpGroup G = mlp_group(MT, l == last, gi, N);
           // the previous user of each half has been drained; at a layer's
           // first group, of both halves (that epilogue also wrote this layer's input)
           for (int h = 0; h < 2 && !err; ++h) {
@@ -373,9 +384,9 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
                 break;
               }
               tc_fence_after();
-              const unsigned d_tmem = tmem + col0 + (unsigned)((t - G.g0) * NB);
+              const unsigned d_tmem = tmem + col0 + (unsigned)((t - G.g0) * N);
               const unsigned a0 = smem_u32(stages + s * kMlpTileBytes);
-              const unsigned b0 = smem_u32(act + kb * NB * 128);
+              const unsigned b0 = smem_u32(act + kb * NBMAX * 128);
 #pragma unroll
               for (int k = 0; k < 4; ++k)
                 umma_bf16(d_tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc,
@@ -402,16 +413,17 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
     }
     __syncwarp();
   } else if (warp < kMlpEpiWarps) {
-    const int q = warp;  // tensor-memory lane quadrant
+    const int q = warp & 3, ch = warp >> 2;  // lane quadrant, chunk parity
     const unsigned lane_base = (unsigned)(q * 32) << 16;
+    const int n_chunks = N / 16;
     unsigned uses[2] = {use0, use1};
     bool err = false;
     for (int l = 0; l <= last && !err; ++l) {
       const int MT = M.mpad[l] / 128;
       const bool is_last = (l == last);
-      const int ng = mlp_n_groups(MT, is_last);
+      const int ng = mlp_n_groups(MT, is_last, N);
       for (int gi = 0; gi < ng && !err; ++gi) {
-        const MlpGroup G = mlp_group(MT, is_last, gi);
+        const MlpGroup G = mlp_group(MT, is_last, gi, N);
         for (int h = G.h0; h < G.h0 + G.nh; ++h) {
           bool ok = true;
           if (lane == 0) ok = mbar_wait(&ctx->acc_full[h], uses[h] & 1);
@@ -426,10 +438,11 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
             const int f = t * 128 + q * 32 + lane;
             const float bias = f32[M.bias0[l] + f];
             const int kb = f >> 6, k = f & 63;
-            char* dst = act + kb * NB * 128;
-            for (int c0 = 0; c0 < NB; c0 += 16) {
+            char* dst = act + kb * NBMAX * 128;
+            for (int i = ch; i < n_chunks; i += 2) {
+              const int c0 = i * 16;
               float v[16];
-              tmem_ld16(tmem + lane_base + col0 + (unsigned)((t - G.g0) * NB + c0), v);
+              tmem_ld16(tmem + lane_base + col0 + (unsigned)((t - G.g0) * N + c0), v);
 #pragma unroll
               for (int c = 0; c < 16; ++c)
                 *reinterpret_cast<__nv_bfloat16*>(dst + sw128_offset(c0 + c, k)) =
@@ -439,33 +452,25 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
           fence_proxy_async();
         } else {
           // chi^2: per candidate column, summed over the group's features
-          float is_t[kMlpOutGroup], cb_t[kMlpOutGroup];
-#pragma unroll
-          for (int j = 0; j < kMlpOutGroup; ++j) {
-            const int f = (G.g0 + j) * 128 + q * 32 + lane;
-            const bool in = G.g0 + j < G.g1;
-            const float is = in ? f32[M.isig0 + f] : 0.f;
-            is_t[j] = is;
-            cb_t[j] = in ? (f32[M.bias0[l] + f] - f32[M.data0 + f]) * is : 0.f;
-          }
-          for (int c0 = 0; c0 < NB; c0 += 16) {
+          for (int i = ch; i < n_chunks; i += 2) {
+            const int c0 = i * 16;
             float sacc[16];
 #pragma unroll
             for (int c = 0; c < 16; ++c) sacc[c] = 0.f;
+            for (int t = G.g0; t < G.g1; ++t) {
+              const int f = t * 128 + q * 32 + lane;
+              const float is = f32[M.isig0 + f];
+              const float cb = (f32[M.bias0[l] + f] - f32[M.data0 + f]) * is;
+              float v[16];
+              tmem_ld16(tmem + lane_base + col0 + (unsigned)((t - G.g0) * N + c0), v);
 #pragma unroll
-            for (int j = 0; j < kMlpOutGroup; ++j) {
-              if (G.g0 + j < G.g1) {
-                float v[16];
-                tmem_ld16(tmem + lane_base + col0 + (unsigned)(j * NB + c0), v);
-#pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                  const float r = fmaf(v[c], is_t[j], cb_t[j]);
-                  sacc[c] = fmaf(r, r, sacc[c]);
-                }
+              for (int c = 0; c < 16; ++c) {
+                const float r = fmaf(v[c], is, cb);
+                sacc[c] = fmaf(r, r, sacc[c]);
               }
             }
             const float tot = warp_sum16(sacc, lane);
-            if ((lane & 1) == 0) chi[q * NB + c0 + ((lane >> 1) & 15)] += tot;
+            if ((lane & 1) == 0) chi[q * NBMAX + c0 + ((lane >> 1) & 15)] += tot;
           }
         }
         tc_fence_before();
@@ -478,7 +483,7 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
     if (err) ctx_set_err(ctx);
     epi_bar_sync();
     for (int r = tid; r < n; r += kMlpEpiWarps * 32)
-      out[r] = -0.5f * (chi[r] + chi[NB + r] + chi[2 * NB + r] + chi[3 * NB + r]);
+      out[r] = -0.5f * (chi[r] + chi[NBMAX + r] + chi[2 * NBMAX + r] + chi[3 * NBMAX + r]);
   }
   __syncthreads();
   return ctx_err(ctx) == 0u;

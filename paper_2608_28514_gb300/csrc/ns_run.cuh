@@ -68,7 +68,13 @@ struct RunDesc {
 struct Carve {
   size_t lik, scr, sel, chol, cent, mask, worst, W, seed, sel_slot, sel_key, candA, candB, candT, list, vals, slots,
       ctr, stage_cid, xbuf, lbuf, rlist, tile, acc, c64, l64, work, tree, mlp, total;
+  bool chol_global;  // MLP runs read the cluster Cholesky factors from global memory
 };
+
+// The BF16 evaluator inside the run kernel: up to 128 candidates per call,
+// three weight-tile stages.
+constexpr int kRunMlpStages = 3;
+using RunMlpSmem = MlpSmem<kMlpNbMax, kRunMlpStages>;
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
@@ -80,10 +86,12 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax,
     o = al16(o + bytes);
     return r;
   };
-  c.lik = take(sizeof(LikParams));
+  const size_t cand_bytes = (sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64;
+  c.chol_global = mlp;
+  c.lik = take(mlp ? 0 : sizeof(LikParams));
   c.scr = take(sizeof(BlockScratch));
   c.sel = take(sizeof(SelectScratch));
-  c.chol = take(sizeof(float) * n_nodes * d * d);
+  c.chol = take(mlp ? 0 : sizeof(float) * n_nodes * d * d);
   c.cent = take(sizeof(float) * n_nodes * d);
   c.mask = take(sizeof(int) * n_nodes);
   c.worst = take(sizeof(int) * m);
@@ -91,9 +99,11 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax,
   c.seed = take(sizeof(int) * m);
   c.sel_slot = take(sizeof(int) * m);
   c.sel_key = take(sizeof(uint32_t) * m);
-  c.candA = take((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
-  c.candB = take((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
-  c.candT = take((sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64);
+  if (!mlp) {
+    c.candA = take(cand_bytes);
+    c.candB = take(cand_bytes);
+    c.candT = take(cand_bytes);
+  }
   c.list = take(sizeof(int) * 2 * m);
   c.vals = take(sizeof(float) * m);
   c.slots = take(mlp ? 0 : sizeof(float) * (size_t)dir_row(dmax) * (m + 31) / 32 * 32);
@@ -103,20 +113,31 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax,
   c.xbuf = take(mlp ? sizeof(float) * (size_t)(m + kMlpF32Nb) * kMaxDim : 0);
   c.lbuf = take(mlp ? sizeof(float) * (size_t)(m + kMlpF32Nb) : 0);
   c.rlist = take(mlp ? sizeof(int) * (size_t)(m + kMlpF32Nb) : 0);
-  // from here on: the clustering scratch, which the MLP evaluators reuse
-  // (they run in the slice phase, never at the same time)
+  // from here on, scratch of one phase at a time: the clustering; for MLP
+  // runs also the evaluators (walker phase) and the batch-correction
+  // candidates (Algorithms 1-2 and the update), which never overlap
+  const size_t phase0 = o;
   c.tile = take(sizeof(float) * (d * kTile + d));
   c.acc = take(sizeof(double) * (d + d * d));
   c.c64 = take(sizeof(double) * d * d);
   c.l64 = take(sizeof(double) * d * d);
   c.work = take(sizeof(double) * (3 * d * d + d));
-  c.tree = take(tree_bytes(d, n_nodes, 8, tree_chol_warps(d, 8)));
-  c.mlp = c.tile;
+  // per-warp partials for every warp of the block (MLP blocks have kMlpThreads threads, others <= 256)
+  c.tree = take(tree_bytes(d, n_nodes, mlp ? kMlpThreads / 32 : 8, tree_chol_warps(d, 8)));
+  c.mlp = phase0;
   if (mlp) {
-    const size_t need = c.mlp + MlpSmem::kBytes + 1024;  // + alignment of the tensor-core region
-    const size_t f32 = c.mlp + mlp_f32_act_bytes(kMlpF32NbWide);
-    if (need > o) o = need;
-    if (f32 > o) o = f32;
+    const size_t end_cluster = o;
+    o = phase0;
+    c.candA = take(cand_bytes);
+    c.candB = take(cand_bytes);
+    c.candT = take(cand_bytes);
+    const size_t end_cand = o;
+    const size_t end_bf16 = phase0 + RunMlpSmem::kBytes + 1024;  // + alignment of the tensor-core region
+    const size_t end_f32 = phase0 + mlp_f32_act_bytes(kMlpF32NbWide);
+    o = end_cluster;
+    if (end_cand > o) o = end_cand;
+    if (end_bf16 > o) o = end_bf16;
+    if (end_f32 > o) o = end_f32;
   }
   c.total = o;
   return c;
@@ -160,7 +181,7 @@ inline __device__ void cluster_phase(const RunDesc& R, uint32_t t, char* sm, con
   double* C64 = reinterpret_cast<double*>(sm + cv.c64);
   double* L64 = reinterpret_cast<double*>(sm + cv.l64);
   double* work = reinterpret_cast<double*>(sm + cv.work);
-  float* s_chol = reinterpret_cast<float*>(sm + cv.chol);
+  float* s_chol = cv.chol_global ? R.chol : reinterpret_cast<float*>(sm + cv.chol);
   float* s_cent = reinterpret_cast<float*>(sm + cv.cent);
   int* s_mask = reinterpret_cast<int*>(sm + cv.mask);
   const int n = node_moments(R.live_x, R.n_pad, R.N, d, [](int) { return true; }, tile, acc, S);
@@ -287,10 +308,13 @@ inline __device__ bool mlp_batch_f32(const RunDesc& R, const float* xs, int n, f
 
 inline __device__ bool mlp_batch_bf16(const RunDesc& R, const float* xs, int n, float* ls, char* tsm,
                                       MlpCtx* ctx) {
+  // equal calls of at most kMlpNbMax candidates (each call streams every weight tile once)
+  const int calls = (n + kMlpNbMax - 1) / kMlpNbMax;
+  const int per = (n + calls - 1) / calls;
   bool ok = true;
-  for (int b0 = 0; b0 < n && ok; b0 += kMlpNb)
-    ok = mlp_eval_bf16(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, xs + (size_t)b0 * kMaxDim, kMaxDim, min(kMlpNb, n - b0),
-                       ls + b0, tsm, ctx);
+  for (int b0 = 0; b0 < n && ok; b0 += per)
+    ok = mlp_eval_bf16<kMlpNbMax, kRunMlpStages>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, xs + (size_t)b0 * kMaxDim,
+                                                 kMaxDim, min(per, n - b0), ls + b0, tsm, ctx);
   return ok;
 }
 
@@ -540,7 +564,7 @@ inline __device__ void init_live_mlp(const RunDesc& R, float* xbuf, float* lbuf,
 #define NS_MINB(D) ((D) <= 12 ? 2 : 1)
 #endif
 template <int DMAX, bool MLP = false>
-__global__ void __launch_bounds__(256, (MLP ? 1 : NS_MINB(DMAX))) k_run(const RunDesc* __restrict__ runs,
+__global__ void __launch_bounds__((MLP ? kMlpThreads : 256), (MLP ? 1 : NS_MINB(DMAX))) k_run(const RunDesc* __restrict__ runs,
                                                                         const int* __restrict__ ids, int chunk) {
   extern __shared__ __align__(16) char sm[];
   __shared__ RunDesc R;
@@ -571,7 +595,7 @@ __global__ void __launch_bounds__(256, (MLP ? 1 : NS_MINB(DMAX))) k_run(const Ru
   LikParams& P = *reinterpret_cast<LikParams*>(sm + cv.lik);
   BlockScratch& S = *reinterpret_cast<BlockScratch*>(sm + cv.scr);
   SelectScratch& X = *reinterpret_cast<SelectScratch*>(sm + cv.sel);
-  float* s_chol = reinterpret_cast<float*>(sm + cv.chol);
+  float* s_chol = MLP ? R.chol : reinterpret_cast<float*>(sm + cv.chol);
   float* s_cent = reinterpret_cast<float*>(sm + cv.cent);
   int* s_mask = reinterpret_cast<int*>(sm + cv.mask);
   int* s_worst = reinterpret_cast<int*>(sm + cv.worst);
@@ -587,7 +611,7 @@ __global__ void __launch_bounds__(256, (MLP ? 1 : NS_MINB(DMAX))) k_run(const Ru
   int* s_ctr = reinterpret_cast<int*>(sm + cv.ctr);
   int* s_stage_cid = reinterpret_cast<int*>(sm + cv.stage_cid);
 
-  {  // likelihood parameters into shared memory
+  if constexpr (!MLP) {  // likelihood parameters into shared memory
     const int* src = reinterpret_cast<const int*>(R.lik);
     int* dst = reinterpret_cast<int*>(&P);
     for (int i = tid; i < (int)(sizeof(LikParams) / 4); i += B) dst[i] = src[i];
@@ -606,7 +630,8 @@ __global__ void __launch_bounds__(256, (MLP ? 1 : NS_MINB(DMAX))) k_run(const Ru
     }
   }
   if (RS.t > 0) {  // cluster tables of the last re-clustering
-    for (int i = tid; i < R.n_nodes * d * d; i += B) s_chol[i] = R.chol[i];
+    if constexpr (!MLP)
+      for (int i = tid; i < R.n_nodes * d * d; i += B) s_chol[i] = R.chol[i];
     for (int i = tid; i < R.n_nodes * d; i += B) s_cent[i] = R.centres[i];
     for (int i = tid; i < R.n_nodes; i += B) s_mask[i] = R.mask[i];
   }
