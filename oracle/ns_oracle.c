@@ -548,10 +548,14 @@ static void jacobi_eigen(int d, const double* A0, double* lam, double* Q)
     for (int i = 0; i < d * d; ++i) Q[i] = 0.0;
     for (int i = 0; i < d; ++i) Q[i * d + i] = 1.0;
     for (int sweep = 0; sweep < 100; ++sweep) {
-        double off = 0.0;
-        for (int p = 0; p < d; ++p)
+        /* converged once the off-diagonal mass is at FP64 rounding level
+         * relative to the diagonal */
+        double off = 0.0, dia = 0.0;
+        for (int p = 0; p < d; ++p) {
+            dia += A[p * d + p] * A[p * d + p];
             for (int q = p + 1; q < d; ++q) off += A[p * d + q] * A[p * d + q];
-        if (off < 1e-300) break;
+        }
+        if (!(off > 1e-30 * dia)) break;
         for (int p = 0; p < d; ++p) {
             for (int q = p + 1; q < d; ++q) {
                 double apq = A[p * d + q];
