@@ -17,7 +17,12 @@ Reported (one JSON line from rank 0):
             ns_create (host->device) + ns_run + ns_result for every run
             (device->host of all samples) + ns_destroy;
   roofline  the run kernel against the FP32 ALU peak;
-  cpu_baseline  the CPU oracle on the host cores, on a bounded sample.
+  cpu_baseline  the CPU oracle on the host cores, on a bounded sample;
+  emulator_bf16_vs_fp32  the 27-D emulator-style MLP likelihood (N_live
+            1500, m 150, 135 slice steps, one run per SM, first iterations):
+            whole-run evals/s of the BF16 tensor-core path (FP32
+            re-evaluation near the threshold) and of the FP32 path, and the
+            tensor-core evaluator alone against the measured BF16 peak.
 
 ``--impl reference`` times the CPU oracle as the reference arm instead.
 """
@@ -46,6 +51,14 @@ FLOP_PER_EVAL = 2 * (3 * D + D * (D + 1) // 2)
 SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
 
 
+# the 27-D emulator-style likelihood (MLP 27 -> 512 x 4 -> 2000, SiLU),
+# N_live = 1500, m = 150, 135 slice steps: BF16 tensor-core path with FP32
+# re-evaluation near the threshold against the plain FP32 path, on the first
+# EMU_ITERS iterations of one run per SM
+EMU_N, EMU_M, EMU_STEPS, EMU_ITERS = 1500, 150, 135, 2
+EMU_FLOP = 2 * (27 * 512 + 3 * 512 * 512 + 512 * 2000)
+
+
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -62,6 +75,7 @@ def parse():
                     help="profiling case: short launches (--chunk), dead buffers of --dead-cap, run "
                          "status ignored; prints no bench line")
     ap.add_argument("--dead-cap", type=int, default=0)
+    ap.add_argument("--no-emulator", action="store_true")
     return ap.parse_args()
 
 
@@ -159,6 +173,68 @@ class ClockSampler:
                     reasons.add(nm)
         return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
                 "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# --------------------------------------------------------------------------
+# the emulator likelihood: BF16 vs FP32 path
+# --------------------------------------------------------------------------
+def emulator_compare(nat, W, torch, n_sm, peaks):
+    p = W.mlp_emulator(1)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    runs = [(p, EMU_N, EMU_M, EMU_STEPS, 1e-3, s) for s in range(1, n_sm + 1)]
+    out = {"workload": f"27-D emulator MLP 27-512x4-2000 (SiLU, BF16-exact weights), N_live={EMU_N}, m={EMU_M}, "
+                       f"{EMU_STEPS} slice steps, {n_sm} runs (one per SM), first {EMU_ITERS} iterations of each",
+           "reeval": "FP32 re-evaluation when |logL - threshold| < 2 + 4e-3 |threshold| (library defaults)"}
+    for name, prec in (("bf16", 1), ("fp32", 0)):
+        opt = nat.ns_default_options(precision=prec, max_iter=EMU_ITERS, chunk_iters=EMU_ITERS)
+        h = nat.ns_create_batch(runs, opt)
+        nat.ns_run(h, check=False)  # warm-up
+        nat.ns_reset(h)
+        flush.zero_()
+        torch.cuda.synchronize()
+        nat.ns_run(h, check=False)
+        st = nat.ns_get_stats(h)
+        res = [nat.ns_summary(h, r) for r in range(len(runs))]
+        nat.ns_destroy(h)
+        ev = sum(r["n_evals"] for r in res) - EMU_N * len(runs)  # slice-step evaluations (initial set excluded)
+        re = sum(r["n_reeval"] for r in res)
+        out[name] = {"evals_per_s": ev / (st["run_ms"] / 1e3), "ms": st["run_ms"], "evals": ev, "fp32_reevals": re,
+                     "effective_tflops": ev * EMU_FLOP / (st["run_ms"] / 1e3) / 1e12}
+    out["bf16_over_fp32"] = out["bf16"]["evals_per_s"] / out["fp32"]["evals_per_s"]
+    # the tensor-core evaluator alone on a large batch (8 calls of 128 candidates per SM)
+    nb = nat.ns_mlp_image_bytes(p)
+    img = torch.empty(nb + 1024, dtype=torch.uint8, device="cuda")
+    off = (-img.data_ptr()) % 1024
+    img = img[off:off + nb]
+    nat.ns_mlp_pack(p, img)
+    n = n_sm * 128 * 8
+    x = torch.rand(n, p.d, device="cuda", generator=torch.Generator(device="cuda").manual_seed(7))
+    lo = torch.empty(n, device="cuda")
+    for _ in range(3):
+        nat.ns_mlp_loglike(p, img, x, lo, precision=1)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 5
+    stream = torch.cuda.current_stream()
+    e0.record(stream)
+    for _ in range(reps):
+        nat.ns_mlp_loglike(p, img, x, lo, precision=1, stream=stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    achieved = n * EMU_FLOP / (ms / 1e3) / 1e12
+    peak = peaks.get("bf16_tflops") if peaks else None
+    out["evaluator_roofline"] = {"bound": "tensor", "kernel": "k_mlp_bf16", "achieved": achieved,
+                                 "peak": peak, "unit": "TFLOP/s", "frac": (achieved / peak) if peak else None,
+                                 "peak_basis": "measured bf16 burst (cuBLAS 8192^3)" if peak else None,
+                                 "candidates": n, "flop_per_eval": EMU_FLOP, "ms_per_launch": ms}
+    return out
+
+
+def measured_peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        return None
 
 
 # --------------------------------------------------------------------------
@@ -352,6 +428,10 @@ def main():
                "d2h_bytes_per_step": int(d2h), "includes": "ns_create + ns_run + ns_result(all runs) + ns_destroy"}
 
     nat.ns_destroy(h)
+    emulator = None
+    if not args.no_emulator:
+        emulator = emulator_compare(nat, W, torch, torch.cuda.get_device_properties(local).multi_processor_count,
+                                    measured_peaks())
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
@@ -359,7 +439,7 @@ def main():
                 "config": dict(workload_config(args, R), parallelism=f"replicas x{world} (runs sharded by seed)"),
                 "wall_time_to_logz_s": t_dev / args.steps, "accuracy": acc, "clocks": clocks,
                 "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-                "phase_cycle_share": phase_frac}
+                "phase_cycle_share": phase_frac, "emulator_bf16_vs_fp32": emulator}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()

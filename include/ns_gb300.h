@@ -104,7 +104,8 @@ typedef struct {
     long long dead_cap;   /* dead-point capacity per run; 0 = 400 * N + 4 * m */
     int chunk_iters;      /* iterations per persistent launch (1000) */
     int precision;        /* MLP only: 0 FP32, 1 BF16 with FP32 re-evaluation */
-    double reeval_margin; /* MLP only: re-evaluate in FP32 when |logL - threshold| < margin */
+    double reeval_margin; /* MLP only: re-evaluate in FP32 when |logL - threshold| <   */
+    double reeval_rel;    /*   reeval_margin + reeval_rel |threshold| (2.0 and 4e-3) */
 } ns_options;
 
 /* One run of a batch. */

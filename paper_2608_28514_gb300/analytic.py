@@ -80,27 +80,38 @@ def logz_rosenbrock_grid2d(a, b, lo, hi, n=4096):
     return math.log(tot * h * h) - 2 * math.log(hi - lo)
 
 
+_CHAIN_CACHE = {}
+
+
 def logz_rosenbrock_chain(d, a, b, lo, hi, h=0.002):
     """Chained Rosenbrock, L = prod_i exp(-(a-x_i)^2 - b (x_{i+1}-x_i^2)^2),
     by the transfer operator f_{i+1}(y) = int f_i(x) K(x, y) dx on a
-    midpoint grid of spacing h."""
-    n = int(round((hi - lo) / h))
-    h = (hi - lo) / n
-    xs = lo + (np.arange(n) + 0.5) * h
-    f = np.ones(n)
-    logscale = 0.0
-    ex = np.exp(-(a - xs) ** 2)
-    for _ in range(d - 1):
+    midpoint grid of spacing h.  One pass of the chain gives log Z for every
+    dimension along the way; the pass is kept and extended on demand."""
+    key = (float(a), float(b), float(lo), float(hi), float(h))
+    st = _CHAIN_CACHE.get(key)
+    if st is None:
+        n = int(round((hi - lo) / h))
+        hh = (hi - lo) / n
+        xs = lo + (np.arange(n) + 0.5) * hh
+        st = {"xs": xs, "h": hh, "f": np.ones(n), "logscale": 0.0, "ex": np.exp(-(a - xs) ** 2), "logz": {}}
+        _CHAIN_CACHE[key] = st
+    xs, hh, ex = st["xs"], st["h"], st["ex"]
+    n = len(xs)
+    while d not in st["logz"]:
         g = np.zeros(n)
         blk = 512
+        f = st["f"]
         for j0 in range(0, n, blk):
             y = xs[j0:j0 + blk][None, :]
             K = np.exp(-b * (y - (xs * xs)[:, None]) ** 2)
-            g[j0:j0 + blk] = (f * ex) @ K * h
+            g[j0:j0 + blk] = (f * ex) @ K * hh
         s = g.max()
-        logscale += math.log(s)
-        f = g / s
-    return math.log(f.sum() * h) + logscale - d * math.log(hi - lo)
+        st["logscale"] += math.log(s)
+        st["f"] = g / s
+        dim = len(st["logz"]) + 2  # the chain after k steps covers k + 1 variables
+        st["logz"][dim] = math.log(st["f"].sum() * hh) + st["logscale"] - dim * math.log(hi - lo)
+    return st["logz"][d]
 
 
 def logz(p):

@@ -120,7 +120,8 @@ __device__ __forceinline__ int depth_of(int nd) {
 }
 
 // One warp: regularised Cholesky (section 2.1) of C (d x d FP64) into L;
-// work: [3 d d + d] FP64.  Same rule as reg_cholesky.
+// work: [3 d d + d] FP64.  Same rule as reg_cholesky (eigen-clip fallback
+// by warp_eigen_clip).
 __device__ inline void warp_reg_cholesky(int d, const double* C, double* L, double* work) {
   const int lane = threadIdx.x & 31;
   double tr = 0.0;
@@ -137,23 +138,7 @@ __device__ inline void warp_reg_cholesky(int d, const double* C, double* L, doub
   for (int i = lane; i < d * d; i += 32) A[i] = C[i] + (((i / d) == (i % d)) ? delta : 0.0);
   __syncwarp();
   if (warp_cholesky(d, A, L)) return;
-  if (lane == 0) {
-    double* Q = work + d * d;
-    double* lam = work + 2 * d * d;
-    double* Tm = work + 2 * d * d + d;  // d*d more (work holds 3 d d + d)
-    for (int i = 0; i < d * d; ++i) Tm[i] = C[i];
-    jacobi_eigen_serial(d, Tm, Q, lam);
-    double lmax = 0.0;
-    for (int i = 0; i < d; ++i) lmax = fmax(lmax, lam[i]);
-    for (int i = 0; i < d; ++i) lam[i] = fmax(lam[i], 1e-10 * lmax);
-    for (int i = 0; i < d; ++i)
-      for (int j = 0; j < d; ++j) {
-        double s = 0.0;
-        for (int k = 0; k < d; ++k) s += Q[i * d + k] * lam[k] * Q[j * d + k];
-        A[i * d + j] = s + (i == j ? delta : 0.0);
-      }
-  }
-  __syncwarp();
+  warp_eigen_clip(d, C, delta, A, work + d * d, work + 2 * d * d + d);
   if (!warp_cholesky(d, A, L)) {
     if (lane == 0) {
       for (int i = 0; i < d * d; ++i) L[i] = 0.0;

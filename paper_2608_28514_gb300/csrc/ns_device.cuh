@@ -501,11 +501,14 @@ __device__ __forceinline__ void draw_directions(const SliceCfg& S, int walker, c
       if (2 * p < d) {
         const float u1 = u24_open0(st.next());
         const float u2 = u24(st.next());
+        // Box-Muller; the angle on the special-function unit: 2 pi u2 - pi
+        // stays in [-pi, pi), where the intrinsics are accurate to ~1e-6
+        // absolute, and (cos, sin)(2 pi u2) = -(cos, sin)(2 pi u2 - pi).  The
+        // radius keeps the accurate logarithm (relative accuracy near u1 = 1).
         const float rho = sqrtf(-2.f * logf(u1));
-        float sn, cs;
-        sincospif(2.f * u2, &sn, &cs);
-        z[2 * p] = rho * cs;
-        if (2 * p + 1 < DMAX && 2 * p + 1 < d) z[2 * p + 1] = rho * sn;
+        const float th = fmaf(u2, 6.28318530717958648f, -3.14159265358979324f);
+        z[2 * p] = -rho * __cosf(th);
+        if (2 * p + 1 < DMAX && 2 * p + 1 < d) z[2 * p + 1] = -rho * __sinf(th);
       }
     float nz = 0.f;
 #pragma unroll
@@ -962,17 +965,31 @@ inline __device__ bool warp_cholesky(int d, const double* A, double* L) {
   return true;
 }
 
-// Single-thread cyclic Jacobi (rare path: a covariance that is not
-// numerically positive definite).  A: d x d, destroyed; Q: eigenvectors in
-// columns; lam: eigenvalues.
-inline __device__ void jacobi_eigen_serial(int d, double* A, double* Q, double* lam) {
-  for (int i = 0; i < d * d; ++i) Q[i] = 0.0;
-  for (int i = 0; i < d; ++i) Q[i * d + i] = 1.0;
+// Cyclic Jacobi eigendecomposition, one warp (the rare path of the
+// regularised Cholesky: a covariance that is not numerically positive
+// definite).  The rotations follow the serial cyclic order p < q; each
+// rotation's column, row and eigenvector updates are spread over the lanes.
+// Sweeps stop once the off-diagonal mass is below 1e-30 of the diagonal
+// mass (converged to FP64 rounding).  A: d x d, destroyed; Q: eigenvectors
+// in columns; lam: eigenvalues.  Every lane of the warp calls it.
+inline __device__ void jacobi_eigen_warp(int d, double* A, double* Q, double* lam) {
+  const int lane = threadIdx.x & 31;
+  for (int i = lane; i < d * d; i += 32) Q[i] = ((i / d) == (i % d)) ? 1.0 : 0.0;
+  __syncwarp();
   for (int sweep = 0; sweep < 100; ++sweep) {
-    double off = 0.0;
-    for (int p = 0; p < d; ++p)
-      for (int q = p + 1; q < d; ++q) off += A[p * d + q] * A[p * d + q];
-    if (off < 1e-300) break;
+    double off = 0.0, dia = 0.0;
+    for (int i = lane; i < d * d; i += 32) {
+      const int a = i / d, b = i % d;
+      const double v = A[i];
+      if (b > a) off += v * v;
+      else if (a == b) dia += v * v;
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      off += __shfl_xor_sync(kFull, off, o);
+      dia += __shfl_xor_sync(kFull, dia, o);
+    }
+    if (!(off > 1e-30 * dia)) break;
     for (int p = 0; p < d; ++p)
       for (int q = p + 1; q < d; ++q) {
         const double apq = A[p * d + q];
@@ -980,24 +997,47 @@ inline __device__ void jacobi_eigen_serial(int d, double* A, double* Q, double* 
         const double th = (A[q * d + q] - A[p * d + p]) / (2.0 * apq);
         const double tt = (th >= 0 ? 1.0 : -1.0) / (fabs(th) + sqrt(th * th + 1.0));
         const double c = 1.0 / sqrt(tt * tt + 1.0), s = tt * c;
-        for (int k = 0; k < d; ++k) {
+        __syncwarp();
+        for (int k = lane; k < d; k += 32) {
           const double akp = A[k * d + p], akq = A[k * d + q];
           A[k * d + p] = c * akp - s * akq;
           A[k * d + q] = s * akp + c * akq;
         }
-        for (int k = 0; k < d; ++k) {
+        __syncwarp();
+        for (int k = lane; k < d; k += 32) {
           const double apk = A[p * d + k], aqk = A[q * d + k];
           A[p * d + k] = c * apk - s * aqk;
           A[q * d + k] = s * apk + c * aqk;
-        }
-        for (int k = 0; k < d; ++k) {
           const double qkp = Q[k * d + p], qkq = Q[k * d + q];
           Q[k * d + p] = c * qkp - s * qkq;
           Q[k * d + q] = s * qkp + c * qkq;
         }
+        __syncwarp();
       }
   }
-  for (int i = 0; i < d; ++i) lam[i] = A[i * d + i];
+  for (int i = lane; i < d; i += 32) lam[i] = A[i * d + i];
+  __syncwarp();
+}
+
+// The eigen-clip of the regularised Cholesky, one warp: A <- Q diag(max(lam,
+// 1e-10 lam_max)) Q^T + delta I from the covariance C.  work: [2 d d + d]
+// FP64 (Q, lam), T: [d d] FP64 scratch.
+inline __device__ void warp_eigen_clip(int d, const double* C, double delta, double* A, double* work, double* T) {
+  const int lane = threadIdx.x & 31;
+  double* Q = work;
+  double* lam = work + d * d;
+  for (int i = lane; i < d * d; i += 32) T[i] = C[i];
+  __syncwarp();
+  jacobi_eigen_warp(d, T, Q, lam);
+  double lmax = 0.0;
+  for (int i = 0; i < d; ++i) lmax = fmax(lmax, lam[i]);
+  for (int q = lane; q < d * d; q += 32) {
+    const int i = q / d, j = q % d;
+    double s = 0.0;
+    for (int k = 0; k < d; ++k) s += Q[i * d + k] * fmax(lam[k], 1e-10 * lmax) * Q[j * d + k];
+    A[q] = s + (i == j ? delta : 0.0);
+  }
+  __syncwarp();
 }
 
 // Regularised Cholesky of the covariance in C (smem FP64, d x d):
@@ -1031,22 +1071,7 @@ inline __device__ void reg_cholesky(int d, double* C, double* L, double* work, B
   const int ok = S.iw[0];
   __syncthreads();
   if (ok) return;
-  if (tid == 0) {
-    double* Q = work + d * d;
-    double* lam = work + 2 * d * d;
-    double* T = work + 2 * d * d + d;  // d*d
-    for (int i = 0; i < d * d; ++i) T[i] = C[i];
-    jacobi_eigen_serial(d, T, Q, lam);
-    double lmax = 0.0;
-    for (int i = 0; i < d; ++i) lmax = fmax(lmax, lam[i]);
-    for (int i = 0; i < d; ++i) lam[i] = fmax(lam[i], 1e-10 * lmax);
-    for (int i = 0; i < d; ++i)
-      for (int j = 0; j < d; ++j) {
-        double s = 0.0;
-        for (int k = 0; k < d; ++k) s += Q[i * d + k] * lam[k] * Q[j * d + k];
-        A[i * d + j] = s + (i == j ? delta : 0.0);
-      }
-  }
+  if (tid < 32) warp_eigen_clip(d, C, delta, A, work + d * d, work + 2 * d * d + d);
   __syncthreads();
   if (tid < 32) {
     const bool ok2 = warp_cholesky(d, A, L);

@@ -180,6 +180,16 @@ bool same_network(const ns_likelihood& a, const ns_likelihood& b) {
          eq(a.sigma_out, b.sigma_out, no);
 }
 
+// Dynamic shared memory a run kernel may take (the static part stays below 2 KB).
+constexpr size_t kRunSmemBudget = 227 * 1024 - 2048;
+
+// A run whose cluster tables do not fit in shared memory keeps them in
+// global memory (make_carve's spill).
+bool run_spills(const ns_problem& p, int n_nodes) {
+  if (p.lik->kind == NS_LIK_MLP) return false;
+  return make_carve(p.d, p.m, n_nodes, dmax_class(p.d), false, false).total > kRunSmemBudget;
+}
+
 int block_for_m(int m) {
   int b = ((m + 31) / 32) * 32;
   if (b < 128) b = 128;
@@ -265,7 +275,7 @@ ns_status check_opts(const ns_options& o, std::string* err) {
       o.t_max < 1 || o.t_max > NS_MAX_HISTORY || !(o.width > 0) || !std::isfinite(o.width) ||
       o.correction < 0 || o.correction > 3 || o.max_iter < 1 || o.dead_cap < 0 || o.chunk_iters < 0 ||
       !(o.vol_frac >= 0 && o.vol_frac < 1) || o.precision < 0 || o.precision > 1 || !(o.reeval_margin >= 0) ||
-      !std::isfinite(o.reeval_margin)) {
+      !std::isfinite(o.reeval_margin) || !(o.reeval_rel >= 0) || !std::isfinite(o.reeval_rel)) {
     set_err(err, "an option is out of range");
     return NS_ERR_ARG;
   }
@@ -380,6 +390,11 @@ struct ns_handle {
   std::vector<RunDesc> runs;
   std::vector<HostRun> host;
   std::vector<ClassGroup> groups;
+  // several groups (register classes, MLP) run concurrently: each on its own
+  // stream, forked from and joined back into the caller's stream
+  std::vector<cudaStream_t> gstreams;
+  std::vector<cudaEvent_t> gjoin;
+  cudaEvent_t gfork = nullptr;
   bool ran = false;
   double last_ms = 0;
   double kernel_ms = 0;
@@ -409,7 +424,10 @@ ns_status ns_default_options(ns_options* o) {
   o->dead_cap = 0;
   o->chunk_iters = 1000;
   o->precision = 0;
-  o->reeval_margin = 0.0;
+  // the BF16 emulator path's log L error is relative in nature (about 0.1 %
+  // at the 99th percentile, 0.35 % at most, on the 27-D emulator network)
+  o->reeval_margin = 2.0;
+  o->reeval_rel = 4e-3;
   return NS_OK;
 }
 
@@ -454,6 +472,8 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
   };
   struct Off {
     int mlp_owner;  // the run whose MLP image this run reads (itself if it owns one)
+    int spill;      // cluster tables in global memory
+    size_t tree_ws;
     size_t lik, mlp_img, mlp_desc, live_x, live_l, live_cid, new_x, new_l, hist_l, hist_x, hist_len, stage_x, dirs, wsp, side, dead_x,
         dead_l, dead_logw, centres, chol, chol64, logvol, count, split, mask;
   };
@@ -506,6 +526,8 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     o.count = take(sizeof(int) * n_nodes);
     o.split = take(sizeof(int) * n_nodes);
     o.mask = take(sizeof(int) * n_nodes);
+    o.spill = run_spills(p, n_nodes) ? 1 : 0;
+    o.tree_ws = o.spill ? take(tree_bytes(d, n_nodes, 8, tree_chol_warps(d, 8))) : 0;
     HostRun& hr = h->host[r];
     hr.d = d;
     hr.N = N;
@@ -593,7 +615,10 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     R.mask = reinterpret_cast<int*>(base + o.mask);
     R.st = reinterpret_cast<RunState*>(base + off_state) + r;
     R.precision = opt.precision;
+    R.spill = o.spill;
+    R.tree_ws = o.spill ? reinterpret_cast<char*>(base + o.tree_ws) : nullptr;
     R.reeval_margin = (float)opt.reeval_margin;
+    R.reeval_rel = (float)opt.reeval_rel;
     if (p.lik->kind == NS_LIK_MLP) {
       R.mlp_tiles = reinterpret_cast<const uint8_t*>(base + o.mlp_img);
       R.mlp_desc = reinterpret_cast<const MlpDesc*>(base + o.mlp_desc);
@@ -655,12 +680,12 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     size_t smem = 0;
     for (int r : members[ci]) {
       maxm = std::max(maxm, runs[r].m);
-      smem = std::max(smem, make_carve(runs[r].d, runs[r].m, n_nodes, g.dmax, g.mlp).total);
+      smem = std::max(smem, make_carve(runs[r].d, runs[r].m, n_nodes, g.dmax, g.mlp, off[r].spill != 0).total);
     }
     g.block = block_for_m(maxm);
     if (g.mlp) g.block = std::max(g.block, kMlpThreads);  // the BF16 evaluator's warp roles
     g.smem = smem;
-    if (smem > 227 * 1024) {
+    if (smem > kRunSmemBudget) {
       set_err(nullptr, "runs of dimension class %d need %zu bytes of shared memory (limit 227 KB): "
               "lower the tree depth or m", g.dmax, smem);
       return fail(NS_ERR_ARG);
@@ -672,6 +697,24 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
       return fail(NS_ERR_CUDA);
     }
     h->groups.push_back(g);
+  }
+  if (h->groups.size() > 1) {
+    e = cudaEventCreateWithFlags(&h->gfork, cudaEventDisableTiming);
+    for (size_t gi = 0; gi < h->groups.size() && e == cudaSuccess; ++gi) {
+      cudaStream_t gs = nullptr;
+      cudaEvent_t ge = nullptr;
+      e = cudaStreamCreateWithFlags(&gs, cudaStreamNonBlocking);
+      if (e == cudaSuccess) h->gstreams.push_back(gs);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ge, cudaEventDisableTiming);
+      if (e == cudaSuccess) h->gjoin.push_back(ge);
+    }
+    if (e != cudaSuccess) {
+      set_err(nullptr, "stream setup failed: %s", cudaGetErrorString(e));
+      for (cudaStream_t gs : h->gstreams) cudaStreamDestroy(gs);
+      for (cudaEvent_t ge : h->gjoin) cudaEventDestroy(ge);
+      if (h->gfork) cudaEventDestroy(h->gfork);
+      return fail(NS_ERR_CUDA);
+    }
   }
   *out = h;
   return NS_OK;
@@ -741,8 +784,14 @@ ns_status ns_run(ns_handle* h, void* stream_v) {
   h->d2h_bytes = 0;
   for (;;) {
     NS_CUDA(cudaEventRecord(k0, s), &h->err);
-    for (const ClassGroup& g : h->groups) {
-      cudaError_t e = launch_class(g, h->d_runs, chunk, s);
+    const bool fork = h->groups.size() > 1;
+    if (fork) NS_CUDA(cudaEventRecord(h->gfork, s), &h->err);
+    for (size_t gi = 0; gi < h->groups.size(); ++gi) {
+      cudaStream_t gs = fork ? h->gstreams[gi] : s;
+      cudaError_t e = fork ? cudaStreamWaitEvent(gs, h->gfork, 0) : cudaSuccess;
+      if (e == cudaSuccess) e = launch_class(h->groups[gi], h->d_runs, chunk, gs);
+      if (e == cudaSuccess && fork) e = cudaEventRecord(h->gjoin[gi], gs);
+      if (e == cudaSuccess && fork) e = cudaStreamWaitEvent(s, h->gjoin[gi], 0);
       if (e != cudaSuccess) {
         set_err(&h->err, "run kernel launch failed: %s", cudaGetErrorString(e));
         cleanup();
@@ -874,6 +923,9 @@ const char* ns_last_error(const ns_handle* h) {
 
 void ns_destroy(ns_handle* h) {
   if (!h) return;
+  for (cudaStream_t gs : h->gstreams) cudaStreamDestroy(gs);
+  for (cudaEvent_t ge : h->gjoin) cudaEventDestroy(ge);
+  if (h->gfork) cudaEventDestroy(h->gfork);
   if (h->h_states) cudaFreeHost(h->h_states);
   if (h->arena) cudaFree(h->arena);
   delete h;

@@ -60,7 +60,10 @@ struct RunDesc {
   const float* mlp_f32;
   const MlpDesc* mlp_desc;
   int precision;          // 0 FP32 CUDA cores, 1 BF16 tensor cores + FP32 re-evaluation
-  float reeval_margin;    // re-evaluate in FP32 when |logL_bf16 - threshold| < margin
+  int spill;              // cluster tables in global memory (make_carve)
+  char* tree_ws;          // the cluster-tree scratch of a spilled run
+  float reeval_margin;    // re-evaluate in FP32 when |logL_bf16 - threshold| <
+  float reeval_rel;       //   reeval_margin + reeval_rel |threshold|
 };
 
 // Shared-memory carve of the run kernel, computed identically on host and
@@ -68,7 +71,8 @@ struct RunDesc {
 struct Carve {
   size_t lik, scr, sel, chol, cent, mask, worst, W, seed, sel_slot, sel_key, candA, candB, candT, list, vals, slots,
       ctr, stage_cid, xbuf, lbuf, rlist, tile, acc, c64, l64, work, tree, mlp, total;
-  bool chol_global;  // MLP runs read the cluster Cholesky factors from global memory
+  bool chol_global;  // the cluster Cholesky factors live in global memory (MLP runs, spilled runs)
+  bool tree_global;  // the cluster-tree scratch lives in global memory (spilled runs)
 };
 
 // The BF16 evaluator inside the run kernel: up to 128 candidates per call,
@@ -78,7 +82,11 @@ using RunMlpSmem = MlpSmem<kMlpNbMax, kRunMlpStages>;
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-__host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax, bool mlp = false) {
+// spill: the run's cluster tables do not fit next to the rest (large d at
+// depth 3); the Cholesky factors and the tree scratch then stay in global
+// memory (only the clustering and the direction draws read them).
+__host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax, bool mlp = false,
+                                            bool spill = false) {
   Carve c;
   size_t o = 0;
   auto take = [&](size_t bytes) {
@@ -87,11 +95,12 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax,
     return r;
   };
   const size_t cand_bytes = (sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64;
-  c.chol_global = mlp;
+  c.chol_global = mlp || spill;
+  c.tree_global = spill && !mlp;
   c.lik = take(mlp ? 0 : sizeof(LikParams));
   c.scr = take(sizeof(BlockScratch));
   c.sel = take(sizeof(SelectScratch));
-  c.chol = take(mlp ? 0 : sizeof(float) * n_nodes * d * d);
+  c.chol = take(c.chol_global ? 0 : sizeof(float) * n_nodes * d * d);
   c.cent = take(sizeof(float) * n_nodes * d);
   c.mask = take(sizeof(int) * n_nodes);
   c.worst = take(sizeof(int) * m);
@@ -123,7 +132,7 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax,
   c.l64 = take(sizeof(double) * d * d);
   c.work = take(sizeof(double) * (3 * d * d + d));
   // per-warp partials for every warp of the block (MLP blocks have kMlpThreads threads, others <= 256)
-  c.tree = take(tree_bytes(d, n_nodes, mlp ? kMlpThreads / 32 : 8, tree_chol_warps(d, 8)));
+  c.tree = take(c.tree_global ? 0 : tree_bytes(d, n_nodes, mlp ? kMlpThreads / 32 : 8, tree_chol_warps(d, 8)));
   c.mlp = phase0;
   if (mlp) {
     const size_t end_cluster = o;
@@ -212,7 +221,7 @@ inline __device__ void cluster_phase(const RunDesc& R, uint32_t t, char* sm, con
   }
   const int nw = blockDim.x >> 5;
   const int nw_chol = tree_chol_warps(d, 8) < nw ? tree_chol_warps(d, 8) : nw;
-  const TreeScratch T = tree_carve(sm + cv.tree, d, nw, tree_chol_warps(d, 8));
+  const TreeScratch T = tree_carve(cv.tree_global ? R.tree_ws : sm + cv.tree, d, nw, tree_chol_warps(d, 8));
   if (threadIdx.x == 0) T.node_n[0] = n;
   __syncthreads();
   TreeIO io;
@@ -294,10 +303,11 @@ __device__ __noinline__ void walker_phase(const RunDesc& R, const LikParams& P, 
 // a4-a7 for MLP runs: the walkers advance in lock step, one round at a time;
 // each round the block evaluates every walker's candidate as one batch (on
 // the tensor cores in BF16, or on the CUDA cores in FP32).  In BF16 mode a
-// candidate whose log L falls within reeval_margin of the threshold it is
-// compared with is re-evaluated in FP32 before the decision; each walker's
-// final point and its history samples are re-evaluated in FP32 afterwards,
-// so every log L that is stored (dead points, Algorithm 2) is an FP32 value.
+// candidate whose log L falls within reeval_margin + reeval_rel |threshold|
+// of the threshold it is compared with is re-evaluated in FP32 before the
+// decision; each walker's final point and its history samples are
+// re-evaluated in FP32 afterwards, so every log L that is stored (dead
+// points, Algorithm 2) is an FP32 value.
 // Called by every thread of the block.
 inline __device__ bool mlp_batch_f32(const RunDesc& R, const float* xs, int n, float* ls, float* act) {
   for (int b0 = 0; b0 < n; b0 += kMlpF32NbWide)
@@ -405,7 +415,8 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
       if (!mlp_batch_bf16(R, xbuf, m, lbuf, tsm, ctx)) err = 1;
       // re-evaluate in FP32 the candidates close to their threshold
       const float thr = (phase == 2) ? thr_in : thr_out;
-      const bool need = active && in && R.reeval_margin > 0.f && fabsf(lbuf[tid] - thr) < R.reeval_margin;
+      const float margin = fmaf(R.reeval_rel, fabsf(thr), R.reeval_margin);
+      const bool need = active && in && margin > 0.f && fabsf(lbuf[tid] - thr) < margin;
       int cnt;
       const int pos = block_exclusive_scan(need ? 1 : 0, BS, &cnt);
       if (need) rlist[pos] = tid;
@@ -586,7 +597,7 @@ __global__ void __launch_bounds__((MLP ? kMlpThreads : 256), (MLP ? 1 : NS_MINB(
     if (R.precision == 1) mlp_ctx_init(&mlp_ctx);
   }
   const int d = R.d, N = R.N, m = R.m;
-  const Carve cv = make_carve(d, m, R.n_nodes, DMAX, MLP);
+  const Carve cv = make_carve(d, m, R.n_nodes, DMAX, MLP, R.spill != 0);
   float* s_slots = reinterpret_cast<float*>(sm + cv.slots);
   float* s_xbuf = reinterpret_cast<float*>(sm + cv.xbuf);
   float* s_lbuf = reinterpret_cast<float*>(sm + cv.lbuf);
@@ -595,7 +606,7 @@ __global__ void __launch_bounds__((MLP ? kMlpThreads : 256), (MLP ? 1 : NS_MINB(
   LikParams& P = *reinterpret_cast<LikParams*>(sm + cv.lik);
   BlockScratch& S = *reinterpret_cast<BlockScratch*>(sm + cv.scr);
   SelectScratch& X = *reinterpret_cast<SelectScratch*>(sm + cv.sel);
-  float* s_chol = MLP ? R.chol : reinterpret_cast<float*>(sm + cv.chol);
+  float* s_chol = cv.chol_global ? R.chol : reinterpret_cast<float*>(sm + cv.chol);
   float* s_cent = reinterpret_cast<float*>(sm + cv.cent);
   int* s_mask = reinterpret_cast<int*>(sm + cv.mask);
   int* s_worst = reinterpret_cast<int*>(sm + cv.worst);
@@ -630,7 +641,7 @@ __global__ void __launch_bounds__((MLP ? kMlpThreads : 256), (MLP ? 1 : NS_MINB(
     }
   }
   if (RS.t > 0) {  // cluster tables of the last re-clustering
-    if constexpr (!MLP)
+    if (!cv.chol_global)
       for (int i = tid; i < R.n_nodes * d * d; i += B) s_chol[i] = R.chol[i];
     for (int i = tid; i < R.n_nodes * d; i += B) s_cent[i] = R.centres[i];
     for (int i = tid; i < R.n_nodes; i += B) s_mask[i] = R.mask[i];
