@@ -300,12 +300,18 @@ def ns_get_stats(h):
 
 
 PHASES = ("cluster", "select", "slice", "correct", "update", "evidence")
+MLP_PHASES = ("mlp_eval", "mlp_reeval")  # inside the slice phase of MLP runs
 
 
-def ns_phase_cycles(h, run=0):
+def ns_phase_cycles(h, run=0, mlp=False):
+    """SM cycles per phase of one run; mlp=True adds the MLP evaluation and
+    re-evaluation cycles (a part of the slice phase)."""
     arr = (C.c_longlong * 8)()
     _check(lib().ns_phase_cycles(h.ptr, int(run), arr), h.ptr)
-    return {name: int(arr[i]) for i, name in enumerate(PHASES)}
+    out = {name: int(arr[i]) for i, name in enumerate(PHASES)}
+    if mlp:
+        out.update({name: int(arr[6 + i]) for i, name in enumerate(MLP_PHASES)})
+    return out
 
 
 def ns_summary(h, run=0):

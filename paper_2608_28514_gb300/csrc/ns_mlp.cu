@@ -95,9 +95,19 @@ bool make_desc(const ns_likelihood& L, const double* lo, const double* hi, int d
   f += M->mpad[last];
   M->isig0 = f;
   f += M->mpad[last];
+  // FP32 weights stored as BF16 when every weight is a BF16 value (low 16 bits zero)
+  long long n_w = 0;
+  for (int l = 0; l < L.n_layers; ++l) n_w += (long long)M->in[l] * M->out[l];
+  M->w_bf16 = 1;
+  for (long long i = 0; i < n_w && M->w_bf16; ++i) {
+    uint32_t u;
+    std::memcpy(&u, L.weights + i, 4);
+    if ((u & 0xFFFFu) != 0u || !std::isfinite(L.weights[i])) M->w_bf16 = 0;
+  }
   for (int l = 0; l < L.n_layers; ++l) {
     M->w32_0[l] = f;
-    f += (long long)M->in[l] * M->out[l];
+    const long long cnt = (long long)M->in[l] * M->out[l];
+    f += M->w_bf16 ? (cnt + 1) / 2 : cnt;
   }
   M->n_tiles = tiles;
   M->tile_bytes = (long long)tiles * kMlpTileBytes;
@@ -146,8 +156,18 @@ void ns_mlp_pack_host(const ns_likelihood& L, const MlpDesc& M, std::vector<uint
       }
     float* f32 = reinterpret_cast<float*>(img.data() + M.tile_bytes);
     for (int o = 0; o < out; ++o) f32[M.bias0[l] + o] = Bv[o];
+    uint16_t* w16 = reinterpret_cast<uint16_t*>(f32 + M.w32_0[l]);
     for (int o = 0; o < out; ++o)  // transposed: [in][out]
-      for (int i = 0; i < in; ++i) f32[M.w32_0[l] + (size_t)i * out + o] = W[(size_t)o * in + i];
+      for (int i = 0; i < in; ++i) {
+        const float w = W[(size_t)o * in + i];
+        if (M.w_bf16) {
+          uint32_t u;
+          std::memcpy(&u, &w, 4);
+          w16[(size_t)i * out + o] = (uint16_t)(u >> 16);
+        } else {
+          f32[M.w32_0[l] + (size_t)i * out + o] = w;
+        }
+      }
     W += (size_t)in * out;
     Bv += out;
   }

@@ -38,7 +38,9 @@ constexpr unsigned kMlpWaitCap = 1u << 22;
 //   tiles  : BF16 swizzled weight tiles, layer by layer, M-tile by M-tile,
 //            K-block by K-block (16 KB each);
 //   f32    : per layer bias (padded out), then data and 1/sigma of the last
-//            layer (padded out), then the FP32 weights transposed, [in][out].
+//            layer (padded out), then the FP32 weights transposed, [in][out]
+//            (as BF16 bit patterns, two per float slot, when every weight is
+//            a BF16 value: the FP32 arithmetic then reads half the bytes).
 struct MlpDesc {
   int n_layers, d;
   int in[kMlpMaxLayers], out[kMlpMaxLayers];        // true widths
@@ -48,6 +50,7 @@ struct MlpDesc {
   long long w32_0[kMlpMaxLayers];                    // float offset of the layer's FP32 weights
   long long data0, isig0;                            // float offsets (last layer, padded)
   int n_tiles;
+  int w_bf16;  // the FP32 master weights are all BF16 values: stored as BF16 (exact), read as FP32
   long long tile_bytes, f32_floats;
   float lo[kMaxDim], span[kMaxDim];
 };
@@ -505,9 +508,9 @@ __host__ __device__ constexpr size_t mlp_f32_act_bytes(int nb) {
   return sizeof(float) * 2 * (size_t)kMlpMaxK * (size_t)mlp_f32_stride(nb);
 }
 
-template <int NB>
-__device__ __noinline__ void mlp_eval_f32(const MlpDesc& M, const float* __restrict__ f32, const float* x,
-                                          int x_stride, int n, float* out, float* act) {
+template <int NB, bool W16>
+__device__ __noinline__ void mlp_eval_f32_w(const MlpDesc& M, const float* __restrict__ f32, const float* x,
+                                            int x_stride, int n, float* out, float* act) {
   static_assert(NB % 4 == 0, "NB must be a multiple of 4");
   constexpr int S = mlp_f32_stride(NB);
   constexpr int KU = kMlpF32Ku;
@@ -526,6 +529,11 @@ __device__ __noinline__ void mlp_eval_f32(const MlpDesc& M, const float* __restr
     const int nin = M.in[l], nout = M.out[l];
     const bool last = (l == M.n_layers - 1);
     const float* WT = f32 + M.w32_0[l];
+    const uint16_t* WT16 = reinterpret_cast<const uint16_t*>(WT);
+    auto wld = [&](size_t idx) -> float {
+      if constexpr (W16) return __uint_as_float((uint32_t)WT16[idx] << 16);
+      else return WT[idx];
+    };
     const float* bias = f32 + M.bias0[l];
     for (int o0 = 0; o0 < nout; o0 += 2 * B) {
       const int oa = o0 + tid, ob = oa + B;
@@ -543,16 +551,16 @@ __device__ __noinline__ void mlp_eval_f32(const MlpDesc& M, const float* __restr
       float wa[KU], wb[KU];
 #pragma unroll
       for (int u = 0; u < KU; ++u) {
-        wa[u] = (u < nin) ? WT[(size_t)u * nout + ca] : 0.f;
-        wb[u] = (u < nin) ? WT[(size_t)u * nout + cb] : 0.f;
+        wa[u] = (u < nin) ? wld((size_t)u * nout + ca) : 0.f;
+        wb[u] = (u < nin) ? wld((size_t)u * nout + cb) : 0.f;
       }
       for (int i0 = 0; i0 < nin; i0 += KU) {
         float na[KU], nb[KU];
 #pragma unroll
         for (int u = 0; u < KU; ++u) {
           const int i = i0 + KU + u;
-          na[u] = (i < nin) ? WT[(size_t)i * nout + ca] : 0.f;
-          nb[u] = (i < nin) ? WT[(size_t)i * nout + cb] : 0.f;
+          na[u] = (i < nin) ? wld((size_t)i * nout + ca) : 0.f;
+          nb[u] = (i < nin) ? wld((size_t)i * nout + cb) : 0.f;
         }
 #pragma unroll
         for (int u = 0; u < KU; ++u) {
@@ -631,6 +639,14 @@ __device__ __noinline__ void mlp_eval_f32(const MlpDesc& M, const float* __restr
     out[r] = -0.5f * s;
   }
   __syncthreads();
+}
+
+// The FP32 evaluator for the image's weight storage.
+template <int NB>
+__device__ __forceinline__ void mlp_eval_f32(const MlpDesc& M, const float* __restrict__ f32, const float* x,
+                                             int x_stride, int n, float* out, float* act) {
+  if (M.w_bf16) mlp_eval_f32_w<NB, true>(M, f32, x, x_stride, n, out, act);
+  else mlp_eval_f32_w<NB, false>(M, f32, x, x_stride, n, out, act);
 }
 
 }  // namespace nsd

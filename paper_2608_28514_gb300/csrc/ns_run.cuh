@@ -347,7 +347,8 @@ template <int DMAX>
 __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& S, const float* s_W, const int* s_seed,
                                               const float* s_chol, float* xbuf, float* lbuf, int* rlist, char* msm,
                                               MlpCtx* ctx, BlockScratch& BS, long long& ev_out, int& fl_out,
-                                              long long& re_out, int& err_out) {
+                                              long long& re_out, int& err_out, long long& cyc_eval,
+                                              long long& cyc_reeval) {
   constexpr int RW = dir_row(DMAX);
   const int tid = threadIdx.x, m = R.m, d = S.d;
   const bool bf16 = (R.precision == 1);
@@ -387,6 +388,7 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   bool active = mine && S.n_steps > 0;
   if (active) load_step(0);
   int err = 0;
+  long long ce = 0, cr = 0;  // thread 0: cycles in the batch evaluations and the FP32 re-evaluations
   for (;;) {
     if (!__syncthreads_or(active ? 1 : 0)) break;
     float tp = 0.f;
@@ -411,8 +413,12 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
       for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = 0.5f;
     }
     __syncthreads();
+    long long c0 = clock64();
     if (bf16) {
       if (!mlp_batch_bf16(R, xbuf, m, lbuf, tsm, ctx)) err = 1;
+      long long c1 = clock64();
+      ce += c1 - c0;
+      c0 = c1;
       // re-evaluate in FP32 the candidates close to their threshold
       const float thr = (phase == 2) ? thr_in : thr_out;
       const float margin = fmaf(R.reeval_rel, fabsf(thr), R.reeval_margin);
@@ -425,8 +431,10 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
         mlp_reeval(R, xbuf, lbuf, rlist, cnt, xg, lg, act);
         reevals += (tid == 0) ? cnt : 0;
       }
+      cr += clock64() - c0;
     } else {
       mlp_batch_f32(R, xbuf, m, lbuf, act);
+      ce += clock64() - c0;
     }
     __syncthreads();
     if (active) {
@@ -493,13 +501,14 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
     }
   }
   __syncthreads();
-  // stored values in FP32: each walker's final point, then its history samples
+  // stored values in FP32: each walker's final point, then its history
+  // samples (rows of xbuf in order: the wide FP32 evaluator)
+  const long long c_end = clock64();
   if (bf16 && !err) {
     if (mine)
       for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = x[k];
-    if (tid < m) rlist[tid] = tid;
     __syncthreads();
-    mlp_reeval(R, xbuf, lbuf, rlist, m, xg, lg, act);
+    mlp_batch_f32(R, xbuf, m, lbuf, act);
     if (mine) l = lbuf[tid];
     reevals += (tid == 0) ? m : 0;
     // history: rows (walker, slot) with an in-box sample
@@ -516,9 +525,8 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
           for (int k = 0; k < d; ++k) xbuf[(size_t)gidx * kMaxDim + k] = hx[k];
         }
       }
-      for (int q = tid; q < nb; q += blockDim.x) rlist[q] = q;
       __syncthreads();
-      mlp_reeval(R, xbuf, lbuf, rlist, nb, xg, lg, act);
+      mlp_batch_f32(R, xbuf, nb, lbuf, act);
       for (int h = 0; h < nh; ++h) {
         const int gidx = base + h - h0;
         if (gidx >= 0 && gidx < nb) {
@@ -535,10 +543,13 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
     R.new_l[i] = l;
     R.hist_len[i] = hlen;
   }
+  cr += clock64() - c_end;
   ev_out = mine ? evals : 0;
   fl_out = mine ? flags : 0;
   re_out = reevals;
   err_out = err;
+  cyc_eval = ce;
+  cyc_reeval = cr;
 }
 
 // Initial live points of an MLP run, evaluated in FP32.
@@ -682,11 +693,12 @@ __global__ void __launch_bounds__((MLP ? kMlpThreads : 256), (MLP ? 1 : NS_MINB(
     select_worst(R.live_l, N, m, R.k0, R.k1, t, s_sel_slot, s_sel_key, s_worst, s_W, s_seed, X, S);
     tick(kPhSelect);
     // a4-a7: slice-sampling walkers
-    long long ev = 0, re = 0;
+    long long ev = 0, re = 0, cyc_eval = 0, cyc_reeval = 0;
     int fl = 0, werr = 0;
     SC.t = t;
     if constexpr (MLP) {
-      walker_phase_mlp<DMAX>(R, SC, s_W, s_seed, s_chol, s_xbuf, s_lbuf, s_rlist, s_mlp, &mlp_ctx, S, ev, fl, re, werr);
+      walker_phase_mlp<DMAX>(R, SC, s_W, s_seed, s_chol, s_xbuf, s_lbuf, s_rlist, s_mlp, &mlp_ctx, S, ev, fl, re, werr,
+                             cyc_eval, cyc_reeval);
     } else {
       if ((tid & ~31) < m) walker_phase<DMAX>(R, P, SC, s_W, s_seed, s_chol, s_slots, ev, fl);
     }
@@ -694,7 +706,11 @@ __global__ void __launch_bounds__((MLP ? kMlpThreads : 256), (MLP ? 1 : NS_MINB(
     tick(kPhSlice);
     if constexpr (MLP) {
       const long long re_sum = block_sum_ll(re, S);
-      if (tid == 0) RS.n_reeval += re_sum;
+      if (tid == 0) {
+        RS.n_reeval += re_sum;
+        RS.cycles[6] += cyc_eval;
+        RS.cycles[7] += cyc_reeval;
+      }
       if (__syncthreads_or(werr)) {
         if (tid == 0) RS.status = NS_ERR_BUDGET;
         __syncthreads();

@@ -79,6 +79,25 @@ def test_mlp_fp32_matches_oracle(nat, oracle, widths, n):
     np.testing.assert_allclose(got, want, rtol=2e-5, atol=1e-3)
 
 
+def test_mlp_fp32_general_weights(nat, oracle):
+    """FP32 master weights that are not BF16 values are stored and read as
+    FP32 (BF16-valued ones as BF16, exactly): both match the FP64 oracle."""
+    for perturb in (False, True):
+        p = _problem((5, 128, 200, 300), 4, unit_sigma=False)
+        if perturb:
+            rng = np.random.default_rng(9)
+            p.mlp.weights = [(w * (1.0 + 1e-3 * rng.standard_normal(w.shape))).astype(np.float32)
+                             for w in p.mlp.weights]
+            assert any(np.any(w.view(np.uint32) & 0xFFFF) for w in p.mlp.weights)
+        img = _image(nat, p)
+        x = np.random.default_rng(5).uniform(0, 1, size=(97, p.d)).astype(np.float32)
+        out = torch.zeros(97, device="cuda")
+        nat.ns_mlp_loglike(p, img, torch.tensor(x, device="cuda"), out, precision=0)
+        torch.cuda.synchronize()
+        want = oracle.loglike(oracle.Lik(p), x.astype(np.float64))
+        np.testing.assert_allclose(out.cpu().numpy().astype(np.float64), want, rtol=2e-5, atol=1e-3)
+
+
 @pytest.mark.parametrize("widths,n", [((5, 128, 200, 300), 64), ((27, 512, 512, 512, 512, 2000), 150),
                                       ((3, 64, 100), 1), ((27, 512, 512, 512, 512, 2000), 257)])
 def test_mlp_bf16_tensor_cores(nat, oracle, widths, n):
