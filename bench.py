@@ -76,6 +76,12 @@ def parse():
                          "status ignored; prints no bench line")
     ap.add_argument("--dead-cap", type=int, default=0)
     ap.add_argument("--no-emulator", action="store_true")
+    ap.add_argument("--profile-mlp", type=int, default=0, metavar="N",
+                    help="profiling case: the BF16 and FP32 MLP evaluators on N candidates of the 27-D emulator "
+                         "network, three launches each; prints no bench line")
+    ap.add_argument("--correction-sweep", type=int, default=0, metavar="SEEDS",
+                    help="run the batching-error study (correction schemes x m/N) with SEEDS runs per point, "
+                         "print its JSON table and exit")
     return ap.parse_args()
 
 
@@ -230,6 +236,52 @@ def emulator_compare(nat, W, torch, n_sm, peaks):
     return out
 
 
+# --------------------------------------------------------------------------
+# the batching-error study (section 3.2): correction schemes x m/N
+# --------------------------------------------------------------------------
+CORRECTION_SCHEMES = (("naive", 0, 1), ("sorting", 1, 1), ("history_K1", 2, 1), ("history_K2", 2, 2),
+                      ("history_K10", 2, 10), ("best_of_worst", 3, 1))
+SWEEP_M = (1, 2, 5, 10, 20, 50, 100, 200)
+
+
+def correction_sweep(n_seeds, n_live=1000):
+    """The 2-D unit Gaussian on [-7, 7]^2, N_live = 1000, 5 d = 10 slice steps:
+    for every correction scheme and m/N in {0.001 .. 0.2}, the mean and
+    standard deviation of log Z - log Z_true over n_seeds runs, all runs of a
+    scheme in one batch.  m/N = 0.5 and 1 lie outside the library's limits
+    (m <= 256 walkers per run; m = N leaves no survivor to seed a walker)."""
+    import numpy as np
+    import torch
+
+    from paper_2608_28514_gb300 import _native as nat
+    from paper_2608_28514_gb300 import analytic
+    from paper_2608_28514_gb300 import workloads as W
+
+    p = W.gauss2d_unit_box7()
+    truth = analytic.logz(p)
+    table = {}
+    t_all = 0.0
+    for name, corr, K in CORRECTION_SCHEMES:
+        opt = nat.ns_default_options(correction=corr, history_iters=K)
+        runs = [(p, n_live, m, 10, 1e-3, 1000 * m + s) for m in SWEEP_M for s in range(1, n_seeds + 1)]
+        h = nat.ns_create_batch(runs, opt)
+        nat.ns_run(h)
+        t_all += nat.ns_get_stats(h)["run_ms"]
+        res = [nat.ns_summary(h, r) for r in range(len(runs))]
+        nat.ns_destroy(h)
+        rows = {}
+        for i, m in enumerate(SWEEP_M):
+            z = np.array([r["log_z"] for r in res[i * n_seeds:(i + 1) * n_seeds]]) - truth
+            rel = sum(r["n_relaxed"] for r in res[i * n_seeds:(i + 1) * n_seeds])
+            rows[f"{m / n_live:g}"] = {"m": m, "mean_dlogz": float(z.mean()), "std": float(z.std(ddof=1)),
+                                       "sem": float(z.std(ddof=1) / np.sqrt(n_seeds)), "relaxed_points": int(rel)}
+        table[name] = rows
+    torch.cuda.synchronize()
+    return {"study": "batching error vs m/N (section 3.2): 2-D unit Gaussian, prior [-7,7]^2, N_live=%d, "
+                     "10 slice steps, %d seeds per point" % (n_live, n_seeds),
+            "log_z_true": truth, "device_ms": t_all, "schemes": table}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -275,6 +327,27 @@ def main():
     args = parse()
     if args.impl == "reference":
         run_reference(args)
+        return
+    if args.profile_mlp > 0:
+        import torch
+        from paper_2608_28514_gb300 import _native as nat
+        from paper_2608_28514_gb300 import workloads as W
+        p = W.mlp_emulator(1)
+        nb = nat.ns_mlp_image_bytes(p)
+        img = torch.empty(nb + 1024, dtype=torch.uint8, device="cuda")
+        img = img[(-img.data_ptr()) % 1024:][:nb]
+        nat.ns_mlp_pack(p, img)
+        x = torch.rand(args.profile_mlp, p.d, device="cuda", generator=torch.Generator(device="cuda").manual_seed(7))
+        out = torch.empty(args.profile_mlp, device="cuda")
+        for prec in (1, 0):
+            for _ in range(3):
+                nat.ns_mlp_loglike(p, img, x, out, precision=prec)
+        torch.cuda.synchronize()
+        print("profile case done", float(out[:8].sum()))
+        return
+    if args.correction_sweep > 0:
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps(correction_sweep(args.correction_sweep)), flush=True)
         return
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))

@@ -448,10 +448,31 @@ def ns_mlp_pack(problem, image, stream=None):
     _check(lib().ns_mlp_pack(C.byref(lik), int(problem.d), _ptr(image), _stream_ptr(stream)))
 
 
-def ns_mlp_loglike(problem, image, x, logl, precision=1, stream=None):
+_LIK_CACHE = {}
+
+
+def _cached_likelihood(problem):
+    """The marshalled likelihood of a problem object, kept while the object
+    lives (batch evaluations are called many times on one network)."""
+    key = id(problem)
+    hit = _LIK_CACHE.get(key)
+    if hit is not None and hit[0]() is problem:
+        return hit[1], hit[2]
+    import weakref
     keep = _Keep()
     lik = likelihood_struct(problem, keep)
-    _check(lib().ns_mlp_loglike(C.byref(lik), keep.dptr(problem.lo), keep.dptr(problem.hi), int(problem.d),
+    try:
+        ref = weakref.ref(problem, lambda _r, k=key: _LIK_CACHE.pop(k, None))
+    except TypeError:
+        return lik, keep
+    _LIK_CACHE[key] = (ref, lik, keep)
+    return lik, keep
+
+
+def ns_mlp_loglike(problem, image, x, logl, precision=1, stream=None):
+    lik, _ = _cached_likelihood(problem)
+    box = _Keep()
+    _check(lib().ns_mlp_loglike(C.byref(lik), box.dptr(problem.lo), box.dptr(problem.hi), int(problem.d),
                                 _ptr(image), int(x.shape[0]), _ptr(x), _ptr(logl), int(precision),
                                 _stream_ptr(stream)))
 

@@ -6,7 +6,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <string>
+#include <unordered_map>
 #include <vector>
 
 #include "../../include/ns_gb300.h"
@@ -129,6 +131,18 @@ uint16_t bf16_bits(float v) {
 
 std::string g_mlp_err;
 
+// Descriptions of the images packed by ns_mlp_pack, by image address: a batch
+// evaluation then needs no pass over the weights on the host.
+std::mutex g_desc_mu;
+std::unordered_map<const void*, MlpDesc> g_desc;
+
+bool same_widths(const ns_likelihood& L, const MlpDesc& M) {
+  if (L.n_layers != M.n_layers || !L.widths) return false;
+  for (int l = 0; l < M.n_layers; ++l)
+    if (L.widths[l] != M.in[l] || L.widths[l + 1] != M.out[l]) return false;
+  return true;
+}
+
 }  // namespace
 
 // Shared with ns_lib.cu (validation of MLP runs).
@@ -229,6 +243,10 @@ ns_status ns_mlp_pack(const ns_likelihood* lik, int d, void* image, void* stream
   ns_mlp_pack_host(*lik, M, img);
   cudaError_t e = cudaMemcpyAsync(image, img.data(), img.size(), cudaMemcpyHostToDevice, (cudaStream_t)stream);
   if (e == cudaSuccess) e = cudaStreamSynchronize((cudaStream_t)stream);
+  if (e == cudaSuccess) {
+    std::lock_guard<std::mutex> lk(g_desc_mu);
+    g_desc[image] = M;
+  }
   return e == cudaSuccess ? NS_OK : NS_ERR_CUDA;
 }
 
@@ -237,10 +255,27 @@ ns_status ns_mlp_loglike(const ns_likelihood* lik, const double* lo, const doubl
   if (!lik || !lo || !hi || !image || n < 0 || (n > 0 && (!x || !logl)) || precision < 0 || precision > 1)
     return NS_ERR_ARG;
   MlpDesc M;
-  std::string msg;
-  if (!make_desc(*lik, lo, hi, d, &M, &msg)) {
-    g_mlp_err = msg;
-    return NS_ERR_ARG;
+  bool cached = false;
+  {
+    std::lock_guard<std::mutex> lk(g_desc_mu);
+    auto it = g_desc.find(image);
+    if (it != g_desc.end() && it->second.d == d && same_widths(*lik, it->second)) {
+      M = it->second;
+      cached = true;
+    }
+  }
+  if (cached) {
+    for (int i = 0; i < d; ++i) {
+      if (!(lo[i] < hi[i]) || !std::isfinite(lo[i]) || !std::isfinite(hi[i])) return NS_ERR_ARG;
+      M.lo[i] = (float)lo[i];
+      M.span[i] = (float)(hi[i] - lo[i]);
+    }
+  } else {
+    std::string msg;
+    if (!make_desc(*lik, lo, hi, d, &M, &msg)) {
+      g_mlp_err = msg;
+      return NS_ERR_ARG;
+    }
   }
   if (n == 0) return NS_OK;
   return ns_mlp_launch(M, image, n, x, logl, precision, (cudaStream_t)stream) == cudaSuccess ? NS_OK

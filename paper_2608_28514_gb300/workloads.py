@@ -146,6 +146,12 @@ def gauss2d_sigma05():
     return gauss_iso(2, 0.5, -5.0, 5.0, name="gauss_iso_d2_sigma0.5_box5")
 
 
+def gauss2d_unit_box7():
+    """2-D unit Gaussian, log L = -|x|^2 / 2, prior [-7, 7]^2 (the batching
+    error study, section 3.2)."""
+    return gauss_iso(2, 1.0, -7.0, 7.0, name="gauss_iso_d2_sigma1_box7")
+
+
 def corr_gauss10(seed):
     """10-D correlated Gaussian on [-10, 10]^10."""
     return gauss_corr(10, seed)

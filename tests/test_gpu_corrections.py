@@ -1,0 +1,72 @@
+"""The batching error and its corrections (section 3.1 Algorithms 1-2,
+section 3.2) on the 2-D unit Gaussian in [-7, 7]^2, through the C ABI.
+
+Pins: at m = 1 every correction scheme is sequential nested sampling, so all
+schemes give the same run bit for bit; the closed-form log Z (erf products)
+of the unit Gaussian; and the paper's findings -- the schemes agree at small
+m/N, the history correction keeps log Z unbiased at m/N = 0.1-0.2, and the
+best-of-worst threshold inflates Z more and more as m/N grows.
+"""
+import numpy as np
+import pytest
+
+from paper_2608_28514_gb300 import analytic as A
+from paper_2608_28514_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+SCHEMES = {"naive": (0, 1), "sorting": (1, 1), "history_K1": (2, 1), "history_K2": (2, 2),
+           "history_K10": (2, 10), "best_of_worst": (3, 1)}
+
+
+@pytest.fixture(scope="module")
+def nat():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2608_28514_gb300 import _native
+    _native.lib()
+    return _native
+
+
+def _runs(nat, scheme, m, seeds, N=1000):
+    corr, K = SCHEMES[scheme]
+    p = W.gauss2d_unit_box7()
+    h = nat.ns_create_batch([(p, N, m, 10, 1e-3, s) for s in seeds],
+                            nat.ns_default_options(correction=corr, history_iters=K))
+    nat.ns_run(h)
+    out = [nat.ns_result(h, r) for r in range(len(seeds))]
+    nat.ns_destroy(h)
+    return out
+
+
+def test_m1_every_scheme_is_sequential(nat):
+    seeds = [3, 4, 5]
+    ref = _runs(nat, "naive", 1, seeds, N=200)
+    for name in SCHEMES:
+        if name == "naive":
+            continue
+        got = _runs(nat, name, 1, seeds, N=200)
+        for a, b in zip(ref, got):
+            assert a["log_z"] == b["log_z"] and a["n_evals"] == b["n_evals"], name
+            np.testing.assert_array_equal(a["dead_l"], b["dead_l"])
+            assert b["n_relaxed"] == 0
+
+
+def test_batching_error_against_m_over_n(nat):
+    truth = A.logz(W.gauss2d_unit_box7())
+    seeds = list(range(1, 25))
+    stats = {}
+    for name in ("naive", "sorting", "history_K1", "best_of_worst"):
+        for m in (10, 100, 200):
+            z = np.array([r["log_z"] for r in _runs(nat, name, m, [1000 * m + s for s in seeds])]) - truth
+            stats[name, m] = (z.mean(), z.std(ddof=1) / np.sqrt(len(z)))
+    for name in ("naive", "sorting", "history_K1", "best_of_worst"):
+        mu, se = stats[name, 10]
+        assert abs(mu) < 4 * se + 0.02, (name, mu, se)
+    for m in (100, 200):
+        mu, se = stats["history_K1", m]
+        assert abs(mu) < 4 * se + 0.02, (m, mu, se)
+    b10, b100, b200 = (stats["best_of_worst", m][0] for m in (10, 100, 200))
+    assert b200 > 0.15 and b200 > b100 > b10, (b10, b100, b200)
