@@ -440,11 +440,11 @@ def main():
         evals_all = float(evals)
     value = evals_all / t_dev
 
-    phase = {k: 0 for k in nat.PHASES}
+    phase = {k: 0 for k in nat.PHASES + nat.WALK_PHASES}
     for r in range(R):
-        for k, v in nat.ns_phase_cycles(h, r).items():
+        for k, v in nat.ns_phase_cycles(h, r, walk=True).items():
             phase[k] += v
-    tot_c = max(1, sum(phase.values()))
+    tot_c = max(1, sum(v for k, v in phase.items() if k in nat.PHASES))
     phase_frac = {k: round(v / tot_c, 4) for k, v in phase.items()}
     status = [r["status"] for r in last_res]
     logz = np.array([r["log_z"] for r in last_res])

@@ -182,8 +182,9 @@ ns_status ns_summary(const ns_handle* h, int run, ns_result_t* out);
  * accumulated over all its iterations since creation or ns_reset, as seen
  * by thread 0 of its block between barriers.  out[0..5] = clustering,
  * selection, slice walkers, Algorithms 1-2, live/dead update, evidence and
- * stop test; out[6..7] = MLP runs: within the slice phase, the batch
- * evaluations (BF16 or FP32 path) and the FP32 re-evaluations; 0 otherwise.
+ * stop test; out[6..7] = within the slice phase: MLP runs, the batch
+ * evaluations (BF16 or FP32 path) and the FP32 re-evaluations; other runs,
+ * the first warp's direction draws and its walk.
  * Valid after ns_run. */
 ns_status ns_phase_cycles(const ns_handle* h, int run, long long* out);
 

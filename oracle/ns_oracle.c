@@ -143,6 +143,38 @@ double orc_loglike(const orc_lik* L, const double* x)
         ll = emax + log(acc / (double)K);
         break;
     }
+    case ORC_LIK_GMM: {
+        /* Test 1 / Test 2 of section 2.3: log sum_k w_k exp(-1/2 sum_i
+         * (theta_i - mu_ki)^2 / s_ki^2), weights as given (eqs. array and
+         * separation) */
+        int K = L->n_modes;
+        double e[256];
+        double emax = -INFINITY;
+        for (int k = 0; k < K && k < 256; ++k) {
+            double s = 0.0;
+            for (int i = 0; i < d; ++i) {
+                double u = th[i] - L->centres[k * d + i];
+                s += u * u / L->mode_var[k * d + i];
+            }
+            e[k] = L->mode_logw[k] - 0.5 * s;
+            if (e[k] > emax) emax = e[k];
+        }
+        double acc = 0.0;
+        for (int k = 0; k < K && k < 256; ++k) acc += exp(e[k] - emax);
+        ll = emax + log(acc);
+        break;
+    }
+    case ORC_LIK_SHELL: {
+        /* Test 3 of section 2.3: -1/2 ((|theta - c| - r0) / w)^2 */
+        double r2 = 0.0;
+        for (int i = 0; i < d; ++i) {
+            double u = th[i] - L->mean[i];
+            r2 += u * u;
+        }
+        double z = (sqrt(r2) - L->a) / L->sigma;
+        ll = -0.5 * z * z;
+        break;
+    }
     case ORC_LIK_MLP: {
         int maxw = 0;
         for (int l = 0; l <= L->n_layers; ++l)
@@ -179,6 +211,11 @@ double orc_loglike(const orc_lik* L, const double* x)
     }
     if (ll != ll) ll = -INFINITY; /* NaN counts as outside the constraint */
     return ll;
+}
+
+void orc_loglike_batch(const orc_lik* L, int n, const double* x_unit, double* out)
+{
+    for (int j = 0; j < n; ++j) out[j] = orc_loglike(L, x_unit + (size_t)j * L->d);
 }
 
 /* ======================================================================= */

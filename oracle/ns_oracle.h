@@ -32,7 +32,7 @@ void orc_stream_draws(const uint32_t key[2], uint32_t t, uint32_t walker, uint32
 
 /* ---- likelihoods ------------------------------------------------------- */
 enum { ORC_LIK_GAUSS_ISO = 0, ORC_LIK_GAUSS_CORR = 1, ORC_LIK_ROSENBROCK = 2,
-       ORC_LIK_MIXTURE = 3, ORC_LIK_MLP = 4 };
+       ORC_LIK_MIXTURE = 3, ORC_LIK_MLP = 4, ORC_LIK_GMM = 5, ORC_LIK_SHELL = 6 };
 
 typedef struct {
     int kind;
@@ -51,9 +51,13 @@ typedef struct {
     const double* biases;      /* concatenated [out] blocks */
     const double* data;        /* [widths[n_layers]] */
     const double* sigma_out;   /* [widths[n_layers]] */
+    const double* mode_var;    /* [n_modes*d] GMM: per-mode diagonal variances */
+    const double* mode_logw;   /* [n_modes]   GMM: log weights (not normalised) */
 } orc_lik;
 
 double orc_loglike(const orc_lik* L, const double* x_unit);
+/* out[j] = orc_loglike(L, x + j d), j < n */
+void orc_loglike_batch(const orc_lik* L, int n, const double* x_unit, double* out);
 
 /* ---- sampler options ---------------------------------------------------- */
 typedef struct {

@@ -35,6 +35,7 @@ class OrcLik(C.Structure):
         ("n_layers", C.c_int), ("widths", C.POINTER(C.c_int)),
         ("weights", C.POINTER(C.c_double)), ("biases", C.POINTER(C.c_double)),
         ("data", C.POINTER(C.c_double)), ("sigma_out", C.POINTER(C.c_double)),
+        ("mode_var", C.POINTER(C.c_double)), ("mode_logw", C.POINTER(C.c_double)),
     ]
 
 
@@ -73,6 +74,8 @@ def lib():
         L.orc_stream_draws.argtypes = [_up, C.c_uint32, C.c_uint32, C.c_uint32, C.c_uint32, C.c_int, _up]
         L.orc_loglike.argtypes = [C.POINTER(OrcLik), _dp]
         L.orc_loglike.restype = C.c_double
+        L.orc_loglike_batch.argtypes = [C.POINTER(OrcLik), C.c_int, _dp, _dp]
+        L.orc_loglike_batch.restype = None
         L.orc_default_opts.argtypes = [C.POINTER(OrcOpts), C.c_int, C.c_int]
         L.orc_select.argtypes = [C.c_int, C.c_int, _dp, _up, C.c_uint32, _ip, _ip]
         L.orc_slice_walker.argtypes = [C.POINTER(OrcLik), C.POINTER(OrcOpts), C.c_int, _up, C.c_uint32,
@@ -144,6 +147,8 @@ class Lik:
             s.biases = ptr(np.concatenate([np.ravel(b) for b in p.mlp.biases]))
             s.data = ptr(p.mlp.data)
             s.sigma_out = ptr(p.mlp.sigma_out)
+        s.mode_var = ptr(p.mode_var)
+        s.mode_logw = ptr(p.mode_logw)
         self.struct = s
         self.d = int(p.d)
 
@@ -179,8 +184,10 @@ def stream_draws(seed, t, walker, purpose, first, n):
 
 
 def loglike(lik, X):
-    X = _f64(X).reshape(-1, lik.d)
-    return np.array([lib().orc_loglike(lik.ref(), np.ascontiguousarray(x)) for x in X])
+    X = np.ascontiguousarray(_f64(X).reshape(-1, lik.d))
+    out = np.empty(len(X))
+    lib().orc_loglike_batch(lik.ref(), len(X), X, out)
+    return out
 
 
 def select(logl, m, seed, t):

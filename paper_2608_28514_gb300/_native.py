@@ -301,16 +301,20 @@ def ns_get_stats(h):
 
 PHASES = ("cluster", "select", "slice", "correct", "update", "evidence")
 MLP_PHASES = ("mlp_eval", "mlp_reeval")  # inside the slice phase of MLP runs
+WALK_PHASES = ("draw", "walk")           # inside the slice phase of other runs (first warp)
 
 
-def ns_phase_cycles(h, run=0, mlp=False):
+def ns_phase_cycles(h, run=0, mlp=False, walk=False):
     """SM cycles per phase of one run; mlp=True adds the MLP evaluation and
-    re-evaluation cycles (a part of the slice phase)."""
+    re-evaluation cycles, walk=True the direction-draw and walk cycles of the
+    first warp (both parts of the slice phase)."""
     arr = (C.c_longlong * 8)()
     _check(lib().ns_phase_cycles(h.ptr, int(run), arr), h.ptr)
     out = {name: int(arr[i]) for i, name in enumerate(PHASES)}
     if mlp:
         out.update({name: int(arr[6 + i]) for i, name in enumerate(MLP_PHASES)})
+    if walk:
+        out.update({name: int(arr[6 + i]) for i, name in enumerate(WALK_PHASES)})
     return out
 
 

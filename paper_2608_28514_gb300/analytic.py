@@ -53,6 +53,35 @@ def logz_mixture(p):
     return mx + math.log(np.mean(np.exp(terms - mx))) - _log_box_volume(p)
 
 
+def logz_gmm(p):
+    """Weighted diagonal Gaussian mixture: each mode integrates to its weight
+    times a product of truncated 1-D Gaussian integrals (erf)."""
+    terms = []
+    for c, v, lw in zip(p.centres, p.mode_var, p.mode_logw):
+        terms.append(lw + sum(_log_gauss_1d(c[i], math.sqrt(v[i]), p.lo[i], p.hi[i]) for i in range(p.d)))
+    terms = np.array(terms)
+    mx = terms.max()
+    return mx + math.log(np.sum(np.exp(terms - mx))) - _log_box_volume(p)
+
+
+def logz_shell2d(p):
+    """2-D Gaussian shell centred in a square box [lo, hi]^2: radial
+    quadrature of 2 pi r exp(-(r - r0)^2 / (2 w^2)) over the inscribed disc,
+    plus the corner annulus r in (h, h sqrt 2) weighted by the angle
+    2 pi - 8 arccos(h / r) that stays in the box (h = half-width)."""
+    assert p.d == 2
+    c = np.asarray(p.mean)
+    h = 0.5 * (p.hi[0] - p.lo[0])
+    assert np.allclose(c, 0.5 * (p.hi + p.lo)) and np.isclose(p.hi[1] - p.lo[1], 2 * h)
+    r0, w = p.a, p.sigma
+    f = lambda r: math.exp(-0.5 * ((r - r0) / w) ** 2)
+    inner = integrate.quad(lambda r: 2.0 * math.pi * r * f(r), 0.0, h, points=[r0], epsabs=0, epsrel=1e-12,
+                           limit=400)[0]
+    outer = integrate.quad(lambda r: (2.0 * math.pi - 8.0 * math.acos(h / r)) * r * f(r), h, h * _SQ2,
+                           epsabs=0, epsrel=1e-12, limit=400)[0]
+    return math.log(inner + outer) - _log_box_volume(p)
+
+
 def logz_rosenbrock_2d(a, b, lo, hi):
     """log (1/V) int int exp(-(a-x)^2 - b (y-x^2)^2) dy dx over [lo,hi]^2,
     the inner integral in closed form (erf), the outer by adaptive
@@ -122,6 +151,10 @@ def logz(p):
         return logz_gauss_corr(p)
     if p.kind == W.MIXTURE:
         return logz_mixture(p)
+    if p.kind == W.GMM:
+        return logz_gmm(p)
+    if p.kind == W.SHELL and p.d == 2:
+        return logz_shell2d(p)
     if p.kind == W.ROSENBROCK:
         if p.d == 2:
             return logz_rosenbrock_2d(p.a, p.b, float(p.lo[0]), float(p.hi[0]))

@@ -37,6 +37,8 @@ def _compile(src, obj, extra, nvcc, verbose):
     cmd = [nvcc, *ARCH, *FLAGS, *extra, "-c", src, "-o", obj]
     if os.environ.get("NS_RUN_MINB"):
         cmd.insert(1, "-DNS_RUN_MINB=" + str(int(os.environ["NS_RUN_MINB"])))
+    if os.environ.get("NS_RUN_MAXNREG"):
+        cmd.insert(1, "-DNS_RUN_MAXNREG=" + str(int(os.environ["NS_RUN_MAXNREG"])))
     if verbose:
         cmd.insert(1, "-Xptxas=-v")
     r = subprocess.run(cmd, capture_output=True, text=True)

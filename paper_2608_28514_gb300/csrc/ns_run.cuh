@@ -276,7 +276,7 @@ inline __device__ int nearest_leaf(const float* x, int d, int n_nodes, const flo
 template <int DMAX>
 __device__ __noinline__ void walker_phase(const RunDesc& R, const LikParams& P, const SliceCfg& SC,
                                           const float* s_W, const int* s_seed, const float* s_chol, float* s_slots,
-                                          long long& ev, int& fl) {
+                                          long long& ev, int& fl, long long& cyc_draw, long long& cyc_walk) {
   const int tid = threadIdx.x, m = R.m, d = R.d;
   const bool act = tid < m;
   const int i = act ? tid : 0;
@@ -291,13 +291,17 @@ __device__ __noinline__ void walker_phase(const RunDesc& R, const LikParams& P, 
   O.hist_x = R.hist_x + (size_t)i * R.t_max * d;
   O.hist_len = R.hist_len + i;
   float* my_dirs = R.dirs + (size_t)i * R.n_steps * dir_row(DMAX);
+  const long long c0 = clock64();
   if (act) draw_directions<DMAX>(SC, i, s_chol + (size_t)cid * d * d, my_dirs);
+  const long long c1 = clock64();
   long long e = 0;
   int f = 0;
   slice_walker<DMAX>(P, SC, i, act, R.live_x + sd, R.n_pad, R.live_l[sd], my_dirs, s_slots + (size_t)tid * dir_row(DMAX),
                      thr_out, thr_in, O, e, f);
   ev = act ? e : 0;
   fl = act ? f : 0;
+  cyc_draw = c1 - c0;  // this warp's direction draws and walk
+  cyc_walk = clock64() - c1;
 }
 
 // a4-a7 for MLP runs: the walkers advance in lock step, one round at a time;
@@ -585,9 +589,15 @@ inline __device__ void init_live_mlp(const RunDesc& R, float* xbuf, float* lbuf,
 #else
 #define NS_MINB(D) ((D) <= 12 ? 2 : 1)
 #endif
+// NS_RUN_MAXNREG (build time) caps the analytic run kernels' registers per
+// thread directly instead (finer than whole blocks per SM).
+#ifdef NS_RUN_MAXNREG
+#define NS_RUN_BOUNDS(MLP, D) __launch_bounds__((MLP ? kMlpThreads : 256)) __maxnreg__(MLP ? 200 : NS_RUN_MAXNREG)
+#else
+#define NS_RUN_BOUNDS(MLP, D) __launch_bounds__((MLP ? kMlpThreads : 256), (MLP ? 1 : NS_MINB(D)))
+#endif
 template <int DMAX, bool MLP = false>
-__global__ void __launch_bounds__((MLP ? kMlpThreads : 256), (MLP ? 1 : NS_MINB(DMAX))) k_run(const RunDesc* __restrict__ runs,
-                                                                        const int* __restrict__ ids, int chunk) {
+__global__ void NS_RUN_BOUNDS(MLP, DMAX) k_run(const RunDesc* __restrict__ runs, const int* __restrict__ ids, int chunk) {
   extern __shared__ __align__(16) char sm[];
   __shared__ RunDesc R;
   __shared__ RunState RS;
@@ -700,7 +710,11 @@ __global__ void __launch_bounds__((MLP ? kMlpThreads : 256), (MLP ? 1 : NS_MINB(
       walker_phase_mlp<DMAX>(R, SC, s_W, s_seed, s_chol, s_xbuf, s_lbuf, s_rlist, s_mlp, &mlp_ctx, S, ev, fl, re, werr,
                              cyc_eval, cyc_reeval);
     } else {
-      if ((tid & ~31) < m) walker_phase<DMAX>(R, P, SC, s_W, s_seed, s_chol, s_slots, ev, fl);
+      if ((tid & ~31) < m) walker_phase<DMAX>(R, P, SC, s_W, s_seed, s_chol, s_slots, ev, fl, cyc_eval, cyc_reeval);
+      if (tid == 0) {
+        RS.cycles[6] += cyc_eval;
+        RS.cycles[7] += cyc_reeval;
+      }
     }
     __syncthreads();
     tick(kPhSlice);

@@ -11,6 +11,9 @@ Shapes follow the paper's workloads:
   - Rosenbrock, a = 1, b = 100 (section 4.2), chained for d > 2;
   - equal-weight mixture of isotropic Gaussians (the multimodal tests of
     sections 2.3 and 4.3);
+  - the clustering tests of section 2.3: an array of 49 unit Gaussians
+    (Test 1), two separated 10-D diagonal Gaussians of different heights
+    (Test 2), a 2-D Gaussian shell (Test 3);
   - a 27-input SiLU MLP with a chi^2 likelihood standing in for the
     cosmological emulator of section 5 (whose weights and data are not
     available).
@@ -20,9 +23,9 @@ from typing import List, Optional
 
 import numpy as np
 
-GAUSS_ISO, GAUSS_CORR, ROSENBROCK, MIXTURE, MLP = 0, 1, 2, 3, 4
+GAUSS_ISO, GAUSS_CORR, ROSENBROCK, MIXTURE, MLP, GMM, SHELL = 0, 1, 2, 3, 4, 5, 6
 KIND_NAMES = {GAUSS_ISO: "gauss_iso", GAUSS_CORR: "gauss_corr", ROSENBROCK: "rosenbrock",
-              MIXTURE: "mixture", MLP: "mlp"}
+              MIXTURE: "mixture", MLP: "mlp", GMM: "gmm", SHELL: "shell"}
 
 
 @dataclass
@@ -46,6 +49,8 @@ class Problem:
     cov: Optional[np.ndarray] = None         # kept for closed forms
     sigma: Optional[float] = None
     centres: Optional[np.ndarray] = None     # [n_modes, d]
+    mode_var: Optional[np.ndarray] = None    # [n_modes, d] GMM diagonal variances
+    mode_logw: Optional[np.ndarray] = None   # [n_modes] GMM log weights
     a: Optional[float] = None
     b: Optional[float] = None
     mlp: Optional[MLPSpec] = None
@@ -144,6 +149,47 @@ def mlp_emulator(seed, widths=(27, 512, 512, 512, 512, 2000), sig_lo=1e-3, sig_h
 def gauss2d_sigma05():
     """2-D isotropic Gaussian, mean 0, sigma 0.5, prior [-5, 5]^2."""
     return gauss_iso(2, 0.5, -5.0, 5.0, name="gauss_iso_d2_sigma0.5_box5")
+
+
+def gmm(d, centres, variances, log_weights, lo, hi, name=""):
+    """Weighted Gaussian mixture with diagonal covariances:
+    log L = log sum_k w_k exp(-1/2 sum_i (theta_i - mu_ki)^2 / s_ki^2)."""
+    c = np.asarray(centres, dtype=np.float64).reshape(-1, d)
+    v = np.asarray(variances, dtype=np.float64).reshape(c.shape)
+    w = np.asarray(log_weights, dtype=np.float64).reshape(c.shape[0])
+    l, h = _box(d, lo, hi)
+    return Problem(GMM, d, l, h, centres=c, mode_var=v, mode_logw=w, name=name or f"gmm_d{d}_k{len(c)}")
+
+
+def shell(d, radius, width, lo, hi, centre=0.0, name=""):
+    """Gaussian shell: log L = -1/2 ((|theta - c| - r0) / w)^2."""
+    l, h = _box(d, lo, hi)
+    return Problem(SHELL, d, l, h, mean=np.full(d, float(centre)), a=float(radius), sigma=float(width),
+                   name=name or f"shell_d{d}")
+
+
+def array49():
+    """Test 1 (section 2.3): 49 unit Gaussians at (4i, 4j), i, j = -3..3, each
+    of weight 1, prior [-20, 20]^2."""
+    c = np.array([[4.0 * i, 4.0 * j] for i in range(-3, 4) for j in range(-3, 4)])
+    return gmm(2, c, np.ones_like(c), np.zeros(len(c)), -20.0, 20.0, name="array49_d2")
+
+
+def bimodal(d=10):
+    """Test 2 (section 2.3): weights 1/10 and 1, means -10 and +10 in every
+    coordinate, diagonal variances alternating 0.1 / 1 (mode 1) and 1 / 0.1
+    (mode 2), prior [-20, 20]^d.  d < 10 truncates the coordinates."""
+    odd = np.arange(1, d + 1) % 2 == 1  # coordinate numbers 1, 3, 5, ... (1-based)
+    v1 = np.where(odd, 0.1, 1.0)
+    v2 = np.where(odd, 1.0, 0.1)
+    c = np.array([np.full(d, -10.0), np.full(d, 10.0)])
+    return gmm(d, c, np.array([v1, v2]), np.log([0.1, 1.0]), -20.0, 20.0, name=f"bimodal_d{d}")
+
+
+def shell2d():
+    """Test 3 (section 2.3): 2-D Gaussian shell of radius 5 and width 1 about
+    the origin, prior [-10, 10]^2."""
+    return shell(2, 5.0, 1.0, -10.0, 10.0, name="shell_d2")
 
 
 def gauss2d_unit_box7():
