@@ -79,6 +79,9 @@ def parse():
     ap.add_argument("--profile-mlp", type=int, default=0, metavar="N",
                     help="profiling case: the BF16 and FP32 MLP evaluators on N candidates of the 27-D emulator "
                          "network, three launches each; prints no bench line")
+    ap.add_argument("--clustering-tests", type=int, default=0, metavar="SEEDS",
+                    help="run the clustering tests of Table 1 with SEEDS runs per configuration (m = 1), print "
+                         "the JSON table and exit")
     ap.add_argument("--correction-sweep", type=int, default=0, metavar="SEEDS",
                     help="run the batching-error study (correction schemes x m/N) with SEEDS runs per point, "
                          "print its JSON table and exit")
@@ -282,6 +285,44 @@ def correction_sweep(n_seeds, n_live=1000):
             "log_z_true": truth, "device_ms": t_all, "schemes": table}
 
 
+# --------------------------------------------------------------------------
+# the clustering tests of section 2.3 (Table 1)
+# --------------------------------------------------------------------------
+def clustering_tests(n_seeds, m=1, n_live=1000):
+    """Table 1: Test 1 (49 Gaussians, tree depth 6 in the paper, 3 here:
+    the library's deepest tree), Test 2 (two separated 10-D Gaussians, depth
+    1), Test 3 (Gaussian shell, depth 4 in the paper, 3 here), each with (+)
+    and without (-) the cluster tree, re-clustering every 100 iterations,
+    5 d slice steps; all seeds of one configuration in one batch."""
+    import numpy as np
+    import torch
+
+    from paper_2608_28514_gb300 import _native as nat
+    from paper_2608_28514_gb300 import analytic
+    from paper_2608_28514_gb300 import workloads as W
+
+    tests = (("test1_array49", W.array49(), 3), ("test2_bimodal10", W.bimodal(10), 1),
+             ("test3_shell", W.shell2d(), 3))
+    out = {}
+    for name, p, depth in tests:
+        row = {"log_z_true": analytic.logz(p)}
+        for tag, dep in (("+", depth), ("-", 0)):
+            h = nat.ns_create_batch([(p, n_live, m, 5 * p.d, 1e-3, 7000 + s) for s in range(n_seeds)],
+                                    nat.ns_default_options(depth=dep, recluster_every=100))
+            nat.ns_run(h)
+            st = nat.ns_get_stats(h)
+            res = [nat.ns_summary(h, r) for r in range(n_seeds)]
+            nat.ns_destroy(h)
+            z = np.array([r["log_z"] for r in res])
+            row[tag] = {"depth": dep, "log_z_mean": float(z.mean()), "log_z_std": float(z.std(ddof=1)),
+                        "evaluations_mean": float(np.mean([r["n_evals"] for r in res])),
+                        "device_ms_all_runs": st["run_ms"], "runs_concurrent": n_seeds}
+        out[name] = row
+    torch.cuda.synchronize()
+    return {"study": "clustering tests (section 2.3, Table 1): N_live=%d, m=%d, %d runs per configuration"
+                     % (n_live, m, n_seeds), "tests": out}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -344,6 +385,10 @@ def main():
                 nat.ns_mlp_loglike(p, img, x, out, precision=prec)
         torch.cuda.synchronize()
         print("profile case done", float(out[:8].sum()))
+        return
+    if args.clustering_tests > 0:
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps(clustering_tests(args.clustering_tests)), flush=True)
         return
     if args.correction_sweep > 0:
         if int(os.environ.get("RANK", "0")) == 0:

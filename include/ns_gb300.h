@@ -44,7 +44,9 @@ extern "C" {
 #endif
 
 #define NS_MAX_DIM 32          /* largest d a run may have */
-#define NS_MAX_MODES 8         /* mixture components */
+#define NS_MAX_MODES 8         /* MIXTURE components */
+#define NS_MAX_GMM_MODES 64    /* GMM components */
+#define NS_GMM_CAPACITY 512    /* GMM: n_modes x (d rounded up to its register class) */
 #define NS_MAX_DEPTH 3         /* cluster tree depth: up to 8 leaves, 15 nodes */
 #define NS_MAX_BATCH 256       /* m, walkers per run (one thread each) */
 #define NS_MAX_LIVE 65536      /* N_live per run */
@@ -68,24 +70,28 @@ typedef enum {
     NS_LIK_GAUSS_CORR = 1,  /* -1/2 |L^T (theta-mean)|^2, L L^T = Sigma^-1 */
     NS_LIK_ROSENBROCK = 2,  /* -sum_i (a-theta_i)^2 + b (theta_{i+1}-theta_i^2)^2 (section 4.2) */
     NS_LIK_MIXTURE = 3,     /* log (1/K) sum_k exp(-|theta-c_k|^2 / (2 sigma^2)) (eq. array form) */
-    NS_LIK_MLP = 4          /* -1/2 sum_k ((MLP(theta)_k - data_k)/sigma_k)^2 (section 5 stand-in) */
+    NS_LIK_MLP = 4,         /* -1/2 sum_k ((MLP(theta)_k - data_k)/sigma_k)^2 (section 5 stand-in) */
+    NS_LIK_GMM = 5,         /* log sum_k w_k exp(-1/2 sum_i (theta_i-mu_ki)^2 / s_ki^2) (section 2.3, eqs. array, separation) */
+    NS_LIK_SHELL = 6        /* -1/2 ((|theta-c| - r0) / w)^2 (section 2.3, eq. shell) */
 } ns_lik_kind;
 
 /* Likelihood description; host pointers, copied by ns_create*. */
 typedef struct {
     int kind;                  /* ns_lik_kind */
-    const double* mean;        /* [d]   GAUSS_ISO, GAUSS_CORR */
+    const double* mean;        /* [d]   GAUSS_ISO, GAUSS_CORR; SHELL: the centre c */
     const double* prec_chol;   /* [d*d] GAUSS_CORR: row-major lower L with L L^T = Sigma^-1 */
-    double sigma;              /*       GAUSS_ISO, MIXTURE (> 0) */
-    int n_modes;               /*       MIXTURE, 1..NS_MAX_MODES */
-    const double* centres;     /* [n_modes*d] MIXTURE */
-    double a, b;               /*       ROSENBROCK */
+    double sigma;              /*       GAUSS_ISO, MIXTURE (> 0); SHELL: the width w (> 0) */
+    int n_modes;               /*       MIXTURE 1..NS_MAX_MODES; GMM 1..NS_MAX_GMM_MODES */
+    const double* centres;     /* [n_modes*d] MIXTURE, GMM */
+    double a, b;               /*       ROSENBROCK; SHELL: a = the radius r0 (>= 0) */
     int n_layers;              /*       MLP: affine layers */
     const int* widths;         /* [n_layers+1], widths[0] = d */
     const float* weights;      /* concatenated [out][in] row-major blocks */
     const float* biases;       /* concatenated [out] blocks */
     const float* data;         /* [widths[n_layers]] */
     const float* sigma_out;    /* [widths[n_layers]] (> 0) */
+    const double* mode_var;    /* [n_modes*d] GMM: per-mode diagonal variances (> 0) */
+    const double* mode_logw;   /* [n_modes]   GMM: log weights (finite; not normalised) */
 } ns_likelihood;
 
 typedef struct {

@@ -35,6 +35,7 @@ class NsLikelihood(C.Structure):
         ("a", C.c_double), ("b", C.c_double), ("n_layers", C.c_int), ("widths", C.POINTER(C.c_int)),
         ("weights", C.POINTER(C.c_float)), ("biases", C.POINTER(C.c_float)),
         ("data", C.POINTER(C.c_float)), ("sigma_out", C.POINTER(C.c_float)),
+        ("mode_var", C.POINTER(C.c_double)), ("mode_logw", C.POINTER(C.c_double)),
     ]
 
 
@@ -193,6 +194,8 @@ def likelihood_struct(problem, keep):
         s.biases = keep.fptr(np.concatenate([np.ravel(b) for b in p.mlp.biases]))
         s.data = keep.fptr(p.mlp.data)
         s.sigma_out = keep.fptr(p.mlp.sigma_out)
+    s.mode_var = keep.dptr(p.mode_var)
+    s.mode_logw = keep.dptr(p.mode_logw)
     keep.bufs.append(s)
     return s
 

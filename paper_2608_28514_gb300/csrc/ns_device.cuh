@@ -21,7 +21,9 @@ constexpr uint32_t kPurposeKmeans = 0x20000u;
 constexpr uint32_t kTInit = 0xFFFFFFFFu;
 constexpr unsigned kFull = 0xFFFFFFFFu;
 
-enum LikKind { kIso = 0, kCorr = 1, kRosen = 2, kMix = 3, kMlp = 4 };
+enum LikKind { kIso = 0, kCorr = 1, kRosen = 2, kMix = 3, kMlp = 4, kGmm = 5, kShell = 6 };
+constexpr int kMaxGmmModes = 64;
+constexpr int kGmmCap = 512;  // GMM modes x DMAX
 
 // ---------------------------------------------------------------------------
 // Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
@@ -113,6 +115,10 @@ struct LikParams {
   float rw[kMaxDim];               // Rosenbrock: 1 for the d-1 chain links, else 0
   float2 LpP[(kMaxDim / 2) * kMaxDim];  // [jp*kMaxDim + i] = (L[i][2jp], L[i][2jp+1]), L L^T = inverse covariance
   float cm[kMaxModes * kMaxDim];   // [k*kMaxDim + i]
+  // GMM, rows of DMAX floats (the run's register class), zero-padded:
+  float gm[kGmmCap];               // lo_i - mu_ki
+  float giv[kGmmCap];              // 1 / (2 s_ki^2), 0 beyond d
+  float glw[kMaxGmmModes];         // log w_k
 };
 
 __device__ __forceinline__ float2 f2(float a, float b) { return make_float2(a, b); }
@@ -215,6 +221,41 @@ __device__ __forceinline__ float loglike_u(const LikParams& P, const float (&u)[
       for (int k = 0; k < kMaxModes; ++k)
         if (k < P.n_modes) acc += expf(e[k] - emax);
       ll = emax + logf(acc) - P.log_k;
+      break;
+    }
+    case kGmm: {
+      // log sum_k w_k exp(-sum_i (theta_i - mu_ki)^2 / (2 s_ki^2)), online
+      // max-shifted sum over the modes
+      float mx = -CUDART_INF_F, acc = 0.f;
+      for (int k = 0; k < P.n_modes; ++k) {
+        const float* g = P.gm + k * DMAX;
+        const float* w = P.giv + k * DMAX;
+        float2 s = f2(0.f, 0.f);
+#pragma unroll
+        for (int i = 0; i < DMAX; i += 2) {
+          const float2 y = __ffma2_rn(ld2(P.span + i), f2(u[i], u[i + 1]), ld2(g + i));
+          s = __ffma2_rn(__fmul2_rn(y, ld2(w + i)), y, s);
+        }
+        const float e = P.glw[k] - (s.x + s.y);
+        if (e > mx) {
+          acc = fmaf(acc, expf(mx - e), 1.f);
+          mx = e;
+        } else {
+          acc += expf(e - mx);
+        }
+      }
+      ll = mx + logf(acc);
+      break;
+    }
+    case kShell: {
+      float2 acc = f2(0.f, 0.f);
+#pragma unroll
+      for (int i = 0; i < DMAX; i += 2) {
+        const float2 y = __ffma2_rn(ld2(P.span + i), f2(u[i], u[i + 1]), ld2(P.c + i));
+        acc = __ffma2_rn(y, y, acc);
+      }
+      const float z = sqrtf(acc.x + acc.y) - P.a;
+      ll = -z * z * P.inv2s2;
       break;
     }
     default:

@@ -250,6 +250,36 @@ ns_status check_lik(const ns_likelihood* L, int d, std::string* err) {
           return NS_ERR_ARG;
         }
       return NS_OK;
+    case NS_LIK_GMM:
+      if (!L->centres || !L->mode_var || !L->mode_logw || L->n_modes < 1 || L->n_modes > NS_MAX_GMM_MODES ||
+          L->n_modes * dmax_class(d) > NS_GMM_CAPACITY) {
+        set_err(err, "GMM needs centres, mode_var, mode_logw and 1..%d modes with n_modes x %d <= %d",
+                NS_MAX_GMM_MODES, dmax_class(d), NS_GMM_CAPACITY);
+        return NS_ERR_ARG;
+      }
+      for (int k = 0; k < L->n_modes; ++k) {
+        if (!std::isfinite(L->mode_logw[k])) {
+          set_err(err, "mode_logw[%d] is not finite", k);
+          return NS_ERR_ARG;
+        }
+        for (int i = 0; i < d; ++i)
+          if (!std::isfinite(L->centres[k * d + i]) || !finite_pos(L->mode_var[k * d + i])) {
+            set_err(err, "GMM mode %d: centre not finite or variance not positive", k);
+            return NS_ERR_ARG;
+          }
+      }
+      return NS_OK;
+    case NS_LIK_SHELL:
+      if (!L->mean || !finite_pos(L->sigma) || !std::isfinite(L->a) || L->a < 0) {
+        set_err(err, "SHELL needs the centre (mean), a radius a >= 0 and a width sigma > 0");
+        return NS_ERR_ARG;
+      }
+      for (int i = 0; i < d; ++i)
+        if (!std::isfinite(L->mean[i])) {
+          set_err(err, "mean[%d] is not finite", i);
+          return NS_ERR_ARG;
+        }
+      return NS_OK;
     case NS_LIK_MLP: {
       MlpDesc M;
       std::string msg;
@@ -350,6 +380,23 @@ LikParams make_lik(const ns_likelihood& L, const double* lo, const double* hi, i
       P.log_k = (float)std::log((double)L.n_modes);
       for (int k = 0; k < L.n_modes; ++k)
         for (int i = 0; i < d; ++i) P.cm[k * kMaxDim + i] = (float)(lo[i] - L.centres[k * d + i]);
+      break;
+    case NS_LIK_GMM: {
+      const int row = dmax_class(d);
+      P.n_modes = L.n_modes;
+      for (int k = 0; k < L.n_modes; ++k) {
+        P.glw[k] = (float)L.mode_logw[k];
+        for (int i = 0; i < d; ++i) {
+          P.gm[k * row + i] = (float)(lo[i] - L.centres[k * d + i]);
+          P.giv[k * row + i] = (float)(0.5 / L.mode_var[k * d + i]);
+        }
+      }
+      break;
+    }
+    case NS_LIK_SHELL:
+      P.a = (float)L.a;
+      P.inv2s2 = (float)(1.0 / (2.0 * L.sigma * L.sigma));
+      for (int i = 0; i < d; ++i) P.c[i] = (float)(lo[i] - L.mean[i]);
       break;
     default:
       break;
