@@ -323,6 +323,18 @@ def clustering_tests(n_seeds, m=1, n_live=1000):
                      % (n_live, m, n_seeds), "tests": out}
 
 
+def csrc_hash():
+    """First 16 hex digits of the SHA-256 of the kernel sources (names and
+    contents), identifying the build that a stored ncu figure belongs to."""
+    import glob
+    import hashlib
+    h = hashlib.sha256()
+    for f in sorted(glob.glob(os.path.join(ROOT, "paper_2608_28514_gb300", "csrc", "*"))):
+        h.update(os.path.basename(f).encode())
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -505,13 +517,16 @@ def main():
     flops_per_launch = FLOP_PER_EVAL * evals / max(1, launches)
     achieved = flops_per_launch / avg_launch_s / 1e12
     peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    # DRAM bytes per launch from the ncu record of this kernel, scaled by the
+    # run-iterations of a launch; null once the kernel sources have changed
     traffic = None
     tf = os.path.join(ROOT, "profiles", "traffic_k_run.json")
     if os.path.exists(tf):
         try:
             tj = json.load(open(tf))
-            if tj.get("runs") and tj.get("bytes_per_run_per_launch"):
-                traffic = tj["bytes_per_run_per_launch"] * R
+            if tj.get("csrc_sha256_16") == csrc_hash():
+                iters = sum(r["n_iter"] for r in last_res)
+                traffic = tj["bytes_per_run_iteration"] * iters * args.steps / max(1, launches)
         except (ValueError, KeyError):
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
