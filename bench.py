@@ -323,6 +323,28 @@ def clustering_tests(n_seeds, m=1, n_live=1000):
                      % (n_live, m, n_seeds), "tests": out}
 
 
+# --------------------------------------------------------------------------
+# replicas over ranks: runs are independent, so ranks shard them by seed and
+# exchange only the timing and the counts (no data-path collective)
+# --------------------------------------------------------------------------
+def rank_seeds(rank, runs_per_rank):
+    """Seeds of this rank's runs: disjoint across ranks."""
+    return [1 + rank * runs_per_rank + r for r in range(runs_per_rank)]
+
+
+def combine_ranks(t_seconds, evals, dist, device):
+    """Whole-job figures over the ranks of a process group (or one process
+    when dist is None): the slowest rank's time and the total evaluations."""
+    if dist is None:
+        return float(t_seconds), float(evals)
+    import torch
+    tt = torch.tensor([float(t_seconds)], dtype=torch.float64, device=device)
+    ee = torch.tensor([float(evals)], dtype=torch.float64, device=device)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    dist.all_reduce(ee, op=dist.ReduceOp.SUM)
+    return float(tt.item()), float(ee.item())
+
+
 def csrc_hash():
     """First 16 hex digits of the SHA-256 of the kernel sources (names and
     contents), identifying the build that a stored ncu figure belongs to."""
@@ -435,7 +457,7 @@ def main():
     if R <= 0:
         per_sm = nat.ns_resident_runs_per_sm(D, args.m, 0)
         R = max(1, per_sm) * torch.cuda.get_device_properties(local).multi_processor_count
-    seeds = [1 + rank * R + r for r in range(R)]
+    seeds = rank_seeds(rank, R)
     probs = [W.corr_gauss10(s) for s in seeds]
     truths = np.array([analytic.logz(p) for p in probs])
     runs = [(p, N_LIVE, args.m, N_STEPS, STOP, s) for p, s in zip(probs, seeds)]
@@ -486,15 +508,7 @@ def main():
     barrier()
     clocks = sampler.stop()
 
-    t_dev = dev_ms / 1e3
-    if world > 1:
-        tt = torch.tensor([t_dev], dtype=torch.float64, device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        ee = torch.tensor([float(evals)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(ee, op=dist.ReduceOp.SUM)
-        t_dev, evals_all = float(tt.item()), float(ee.item())
-    else:
-        evals_all = float(evals)
+    t_dev, evals_all = combine_ranks(dev_ms / 1e3, evals, dist if world > 1 else None, "cuda")
     value = evals_all / t_dev
 
     phase = {k: 0 for k in nat.PHASES + nat.WALK_PHASES}
@@ -551,12 +565,7 @@ def main():
             e2e_evals += sum(r["n_evals"] for r in res)
             h2d, d2h = st2["h2d_bytes"], st2["d2h_bytes"]
             del res
-        if world > 1:
-            tt = torch.tensor([e2e_t], dtype=torch.float64, device="cuda")
-            dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-            ee = torch.tensor([float(e2e_evals)], dtype=torch.float64, device="cuda")
-            dist.all_reduce(ee, op=dist.ReduceOp.SUM)
-            e2e_t, e2e_evals = float(tt.item()), float(ee.item())
+        e2e_t, e2e_evals = combine_ranks(e2e_t, e2e_evals, dist if world > 1 else None, "cuda")
         e2e = {"value": e2e_evals / e2e_t, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
                "d2h_bytes_per_step": int(d2h), "includes": "ns_create + ns_run + ns_result(all runs) + ns_destroy"}
 
