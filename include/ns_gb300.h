@@ -172,6 +172,27 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
  * word per run. */
 ns_status ns_run(ns_handle* h, void* stream);
 
+/* Advances every unfinished run of the handle by at most n_iters iterations
+ * (one persistent launch per register class), queued on `stream`, and waits
+ * for it; ns_run or further ns_step calls continue from there.  The result
+ * of a run does not depend on how its iterations were split into calls.
+ * NS_ERR_ARG for n_iters < 1. */
+ns_status ns_step(ns_handle* h, int n_iters, void* stream);
+
+/* Checkpoint / resume.  Every random number of a run is a Philox draw keyed
+ * by (seed, iteration, walker, step), so a run's whole state is its device
+ * memory: ns_checkpoint copies it (with a fingerprint of the batch's shapes
+ * and options) into the caller's host buffer of ns_checkpoint_bytes(h)
+ * bytes; ns_restore loads such a checkpoint into a handle created by
+ * ns_create_batch with the same runs and options (in this or another
+ * process), after which ns_run finishes every run exactly as the
+ * checkpointed handle would have.  NS_ERR_ARG if the buffer is too small or
+ * the checkpoint comes from a batch of another shape.  Both wait for
+ * `stream`. */
+size_t ns_checkpoint_bytes(const ns_handle* h);
+ns_status ns_checkpoint(ns_handle* h, void* host_buf, size_t bytes, void* stream);
+ns_status ns_restore(ns_handle* h, const void* host_buf, size_t bytes, void* stream);
+
 /* Returns every run of the handle to its initial state (same seeds) so that
  * ns_run can be repeated on the allocated memory; asynchronous on `stream`. */
 ns_status ns_reset(ns_handle* h, void* stream);

@@ -92,6 +92,11 @@ def lib():
     L.ns_create_batch.argtypes = [C.c_int, C.POINTER(NsProblem), C.POINTER(NsOptions), C.POINTER(_vp)]
     L.ns_run.argtypes = [_vp, _vp]
     L.ns_reset.argtypes = [_vp, _vp]
+    L.ns_step.argtypes = [_vp, C.c_int, _vp]
+    L.ns_checkpoint_bytes.argtypes = [_vp]
+    L.ns_checkpoint_bytes.restype = C.c_size_t
+    L.ns_checkpoint.argtypes = [_vp, _vp, C.c_size_t, _vp]
+    L.ns_restore.argtypes = [_vp, _vp, C.c_size_t, _vp]
     L.ns_result.argtypes = [_vp, C.c_int, C.POINTER(NsResult)]
     L.ns_summary.argtypes = [_vp, C.c_int, C.POINTER(NsResult)]
     L.ns_phase_cycles.argtypes = [_vp, C.c_int, C.POINTER(C.c_longlong)]
@@ -131,7 +136,7 @@ def lib():
     L.ns_cluster_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
     L.ns_cluster_scratch_bytes.restype = C.c_size_t
     for name in ("ns_default_options", "ns_create", "ns_create_batch", "ns_run", "ns_reset", "ns_result", "ns_summary",
-                 "ns_phase_cycles", "ns_run_noalloc",
+                 "ns_phase_cycles", "ns_run_noalloc", "ns_step", "ns_checkpoint", "ns_restore",
                  "ns_last_run_ms", "ns_get_stats", "ns_philox4x32_10", "ns_loglike", "ns_select_worst", "ns_slice_replace",
                  "ns_batch_correct", "ns_evidence_update", "ns_cluster"):
         getattr(L, name).restype = C.c_int
@@ -279,6 +284,28 @@ def ns_run(h, stream=None, check=True):
     if check:
         _check(st, h.ptr)
     return st
+
+
+def ns_step(h, n_iters, stream=None, check=True):
+    """Advance every unfinished run by at most n_iters iterations."""
+    st = lib().ns_step(h.ptr, int(n_iters), _stream_ptr(stream))
+    if check:
+        _check(st, h.ptr)
+    return st
+
+
+def ns_checkpoint(h, stream=None):
+    """The handle's whole state as bytes (see ns_restore)."""
+    n = int(lib().ns_checkpoint_bytes(h.ptr))
+    buf = (C.c_char * n)()
+    _check(lib().ns_checkpoint(h.ptr, buf, n, _stream_ptr(stream)), h.ptr)
+    return bytes(buf)
+
+
+def ns_restore(h, data, stream=None):
+    """Load a checkpoint taken from a batch of the same runs and options."""
+    buf = C.create_string_buffer(bytes(data), len(data))
+    _check(lib().ns_restore(h.ptr, buf, len(data), _stream_ptr(stream)), h.ptr)
 
 
 def ns_reset(h, stream=None):

@@ -190,6 +190,38 @@ bool run_spills(const ns_problem& p, int n_nodes) {
   return make_carve(p.d, p.m, n_nodes, dmax_class(p.d), false, false).total > kRunSmemBudget;
 }
 
+// FNV-1a over the shape of a batch (what fixes the arena layout): a
+// checkpoint restores only into a handle of the same shape.
+uint64_t batch_fingerprint(int n_runs, const ns_problem* runs, const ns_options& o, size_t total) {
+  uint64_t h = 1469598103934665603ull;
+  auto mix = [&](const void* p, size_t n) {
+    const unsigned char* b = static_cast<const unsigned char*>(p);
+    for (size_t i = 0; i < n; ++i) h = (h ^ b[i]) * 1099511628211ull;
+  };
+  mix(&n_runs, sizeof(n_runs));
+  mix(&total, sizeof(total));
+  for (int r = 0; r < n_runs; ++r) {
+    const ns_problem& p = runs[r];
+    const int v[6] = {p.d, p.n_live, p.m, p.n_slice_steps, p.lik->kind,
+                      p.lik->kind == NS_LIK_MLP ? p.lik->n_layers : p.lik->n_modes};
+    mix(v, sizeof(v));
+    mix(&p.seed, sizeof(p.seed));
+    mix(&p.stop_frac, sizeof(p.stop_frac));
+  }
+  const long long w[12] = {o.depth, o.recluster_every, o.n_min, o.kmeans_iters, o.correction, o.history_iters,
+                           o.t_max, o.e_max, o.s_max, o.max_iter, o.dead_cap, o.precision};
+  mix(w, sizeof(w));
+  return h;
+}
+
+// Header of a checkpoint (ns_checkpoint).
+struct CheckpointHeader {
+  char magic[8];
+  uint64_t fingerprint, total, off_desc, desc_bytes, off_state;
+  int n_runs, pad;
+};
+constexpr char kCkptMagic[8] = {'N', 'S', 'C', 'K', 'P', 'T', '0', '1'};
+
 int block_for_m(int m) {
   int b = ((m + 31) / 32) * 32;
   if (b < 128) b = 128;
@@ -442,6 +474,11 @@ struct ns_handle {
   std::vector<cudaStream_t> gstreams;
   std::vector<cudaEvent_t> gjoin;
   cudaEvent_t gfork = nullptr;
+  // the arena's meaningful bytes: everything but the run descriptors (device
+  // pointers into this arena) is position independent and forms a checkpoint
+  char* base = nullptr;
+  size_t total = 0, off_desc = 0, desc_bytes = 0, off_state = 0;
+  uint64_t fingerprint = 0;
   bool ran = false;
   double last_ms = 0;
   double kernel_ms = 0;
@@ -602,6 +639,12 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     return e == cudaErrorMemoryAllocation ? NS_ERR_OOM : NS_ERR_CUDA;
   }
   char* base = reinterpret_cast<char*>((reinterpret_cast<uintptr_t>(h->arena) + 1023) & ~(uintptr_t)1023);
+  h->base = base;
+  h->total = total;
+  h->off_desc = off_desc;
+  h->desc_bytes = sizeof(RunDesc) * n_runs;
+  h->off_state = off_state;
+  h->fingerprint = batch_fingerprint(n_runs, runs, opt, total);
   e = cudaMallocHost(&h->h_states, sizeof(RunState) * n_runs);
   if (e != cudaSuccess) {
     set_err(&h->err, "cudaMallocHost failed: %s", cudaGetErrorString(e));
@@ -808,8 +851,11 @@ ns_status ns_reset(ns_handle* h, void* stream) {
   return NS_OK;
 }
 
-ns_status ns_run(ns_handle* h, void* stream_v) {
-  if (!h) return NS_ERR_ARG;
+namespace {
+
+// Launches every unfinished run for `chunk` iterations per pass; until_done:
+// repeat passes until every run has stopped (ns_run), else one pass (ns_step).
+ns_status run_impl(ns_handle* h, void* stream_v, int chunk_in, bool until_done) {
   cudaStream_t s = (cudaStream_t)stream_v;
   cudaEvent_t e0, e1, k0, k1;
   NS_CUDA(cudaEventCreate(&e0), &h->err);
@@ -823,7 +869,7 @@ ns_status ns_run(ns_handle* h, void* stream_v) {
     cudaEventDestroy(k1);
   };
   NS_CUDA(cudaEventRecord(e0, s), &h->err);
-  const int chunk = h->opt.chunk_iters > 0 ? h->opt.chunk_iters : 1000;
+  const int chunk = chunk_in;
   long long rounds = 0;
   const long long max_rounds = h->opt.max_iter / chunk + 2;
   h->kernel_ms = 0;
@@ -858,7 +904,7 @@ ns_status ns_run(ns_handle* h, void* stream_v) {
     bool done = true;
     for (int r = 0; r < h->n_runs; ++r)
       if (!h->h_states[r].stopped && h->h_states[r].status == 0) done = false;
-    if (done || rounds > max_rounds) break;
+    if (done || rounds > max_rounds || !until_done) break;
   }
   NS_CUDA(cudaEventRecord(e1, s), &h->err);
   NS_CUDA(cudaEventSynchronize(e1), &h->err);
@@ -873,6 +919,62 @@ ns_status ns_run(ns_handle* h, void* stream_v) {
     if (h->h_states[r].status != 0) worst = (ns_status)h->h_states[r].status;
   if (worst != NS_OK) set_err(&h->err, "a run ended with status %d", (int)worst);
   return worst;
+}
+
+}  // namespace
+
+ns_status ns_run(ns_handle* h, void* stream) {
+  if (!h) return NS_ERR_ARG;
+  return run_impl(h, stream, h->opt.chunk_iters > 0 ? h->opt.chunk_iters : 1000, true);
+}
+
+ns_status ns_step(ns_handle* h, int n_iters, void* stream) {
+  if (!h || n_iters < 1) return NS_ERR_ARG;
+  return run_impl(h, stream, n_iters, false);
+}
+
+size_t ns_checkpoint_bytes(const ns_handle* h) { return h ? sizeof(CheckpointHeader) + h->total : 0; }
+
+ns_status ns_checkpoint(ns_handle* h, void* host_buf, size_t bytes, void* stream) {
+  if (!h || !host_buf || bytes < ns_checkpoint_bytes(h)) return NS_ERR_ARG;
+  CheckpointHeader hd;
+  std::memset(&hd, 0, sizeof(hd));
+  std::memcpy(hd.magic, kCkptMagic, 8);
+  hd.fingerprint = h->fingerprint;
+  hd.total = h->total;
+  hd.off_desc = h->off_desc;
+  hd.desc_bytes = h->desc_bytes;
+  hd.off_state = h->off_state;
+  hd.n_runs = h->n_runs;
+  std::memcpy(host_buf, &hd, sizeof(hd));
+  char* dst = static_cast<char*>(host_buf) + sizeof(hd);
+  cudaStream_t s = (cudaStream_t)stream;
+  NS_CUDA(cudaMemcpyAsync(dst, h->base, h->total, cudaMemcpyDeviceToHost, s), &h->err);
+  NS_CUDA(cudaStreamSynchronize(s), &h->err);
+  return NS_OK;
+}
+
+ns_status ns_restore(ns_handle* h, const void* host_buf, size_t bytes, void* stream) {
+  if (!h || !host_buf || bytes < sizeof(CheckpointHeader)) return NS_ERR_ARG;
+  CheckpointHeader hd;
+  std::memcpy(&hd, host_buf, sizeof(hd));
+  if (std::memcmp(hd.magic, kCkptMagic, 8) != 0 || hd.fingerprint != h->fingerprint || hd.total != h->total ||
+      hd.off_desc != h->off_desc || hd.desc_bytes != h->desc_bytes || hd.n_runs != h->n_runs ||
+      bytes < sizeof(hd) + hd.total) {
+    set_err(&h->err, "ns_restore: the checkpoint was not taken from a batch of this shape");
+    return NS_ERR_ARG;
+  }
+  const char* src = static_cast<const char*>(host_buf) + sizeof(hd);
+  cudaStream_t s = (cudaStream_t)stream;
+  // everything but the run descriptors, which hold this handle's own pointers
+  NS_CUDA(cudaMemcpyAsync(h->base, src, h->off_desc, cudaMemcpyHostToDevice, s), &h->err);
+  const size_t tail = h->off_desc + h->desc_bytes;
+  NS_CUDA(cudaMemcpyAsync(h->base + tail, src + tail, h->total - tail, cudaMemcpyHostToDevice, s), &h->err);
+  NS_CUDA(cudaStreamSynchronize(s), &h->err);
+  std::memcpy(h->h_states, src + h->off_state, sizeof(RunState) * h->n_runs);
+  for (auto& hr : h->host) hr.fetched = false;
+  h->ran = true;
+  return NS_OK;
 }
 
 ns_status ns_get_stats(const ns_handle* h, ns_stats* out) {
