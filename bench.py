@@ -82,6 +82,9 @@ def parse():
     ap.add_argument("--clustering-tests", type=int, default=0, metavar="SEEDS",
                     help="run the clustering tests of Table 1 with SEEDS runs per configuration (m = 1), print "
                          "the JSON table and exit")
+    ap.add_argument("--comparison-shapes", type=int, default=0, metavar="SEEDS",
+                    help="run the section-4 comparison shapes (Gaussian d = 2..32, Rosenbrock and the 49-Gaussian "
+                         "array at N = 100..1000) with SEEDS runs each, print the JSON table and exit")
     ap.add_argument("--correction-sweep", type=int, default=0, metavar="SEEDS",
                     help="run the batching-error study (correction schemes x m/N) with SEEDS runs per point, "
                          "print its JSON table and exit")
@@ -357,6 +360,43 @@ def csrc_hash():
     return h.hexdigest()[:16]
 
 
+# --------------------------------------------------------------------------
+# the comparison shapes of section 4 (the paper's own sampler settings)
+# --------------------------------------------------------------------------
+def comparison_shapes(n_seeds, m=1):
+    """Section 4: the unit Gaussian on [-7, 7]^d for d in {2, 4, 8, 16, 32}
+    (N = 1000); the 2-D Rosenbrock on [-10, 10]^2 and the array of 49
+    Gaussians for N in {100, 200, 500, 1000}; sequential (m = 1), 5 d slice
+    steps, stop 1e-3; all seeds of a configuration concurrently.  Reported:
+    mean and spread of log Z - log Z_true, evaluations and device time."""
+    import numpy as np
+    import torch
+
+    from paper_2608_28514_gb300 import _native as nat
+    from paper_2608_28514_gb300 import analytic
+    from paper_2608_28514_gb300 import workloads as W
+
+    cases = [(f"gauss_d{d}", W.gauss_unit_box7(d), 1000) for d in (2, 4, 8, 16, 32)]
+    cases += [(f"rosenbrock_N{n}", W.rosenbrock2d_box10(), n) for n in (100, 200, 500, 1000)]
+    cases += [(f"array49_N{n}", W.array49(), n) for n in (100, 200, 500, 1000)]
+    out = {}
+    for name, p, n_live in cases:
+        truth = analytic.logz(p)
+        h = nat.ns_create_batch([(p, n_live, m, 5 * p.d, 1e-3, 3000 + s) for s in range(n_seeds)])
+        nat.ns_run(h)
+        st = nat.ns_get_stats(h)
+        res = [nat.ns_summary(h, r) for r in range(n_seeds)]
+        nat.ns_destroy(h)
+        dz = np.array([r["log_z"] for r in res]) - truth
+        out[name] = {"log_z_true": truth, "mean_dlogz": float(dz.mean()), "std_dlogz": float(dz.std(ddof=1)),
+                     "mean_reported_err": float(np.mean([r["log_z_err"] for r in res])),
+                     "evaluations_mean": float(np.mean([r["n_evals"] for r in res])),
+                     "device_ms_all_runs": st["run_ms"], "runs_concurrent": n_seeds, "n_live": n_live}
+    torch.cuda.synchronize()
+    return {"study": "comparison shapes (section 4): m=%d, %d runs per configuration" % (m, n_seeds),
+            "cases": out}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -419,6 +459,10 @@ def main():
                 nat.ns_mlp_loglike(p, img, x, out, precision=prec)
         torch.cuda.synchronize()
         print("profile case done", float(out[:8].sum()))
+        return
+    if args.comparison_shapes > 0:
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps(comparison_shapes(args.comparison_shapes)), flush=True)
         return
     if args.clustering_tests > 0:
         if int(os.environ.get("RANK", "0")) == 0:

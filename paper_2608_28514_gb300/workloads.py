@@ -192,6 +192,16 @@ def shell2d():
     return shell(2, 5.0, 1.0, -10.0, 10.0, name="shell_d2")
 
 
+def gauss_unit_box7(d):
+    """The comparison Gaussian of section 4.1: log L = -|x|^2 / 2 on [-7, 7]^d."""
+    return gauss_iso(d, 1.0, -7.0, 7.0, name=f"gauss_iso_d{d}_sigma1_box7")
+
+
+def rosenbrock2d_box10():
+    """The comparison Rosenbrock of section 4.2: a = 1, b = 100 on [-10, 10]^2."""
+    return rosenbrock(2, box=10.0, name="rosenbrock_d2_box10")
+
+
 def gauss2d_unit_box7():
     """2-D unit Gaussian, log L = -|x|^2 / 2, prior [-7, 7]^2 (the batching
     error study, section 3.2)."""
