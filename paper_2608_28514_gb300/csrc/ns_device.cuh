@@ -503,7 +503,7 @@ inline __device__ void select_worst(const float* __restrict__ logl, int N, int m
 //
 // Each iteration first draws, for every walker and every slice step, the
 // direction v = L_c z/|z| (z: Box-Muller normals from the step's stream) and
-// the bracket offset r, all lanes in step (draw_directions).  The walk then
+// the bracket offset r, all threads of the block in step (draw_directions_block).  The walk then
 // runs as a state machine in which a round evaluates one candidate per
 // active walker: expansion to the left, expansion to the right, shrinkage;
 // after the direction draws a step's stream continues with the shrink draws.
@@ -524,64 +524,79 @@ constexpr int kPreShrink = 3;
 // padded to a multiple of 4 floats (16-byte rows).
 __host__ __device__ constexpr int dir_row(int dmax) { return ((dmax + 1 + kPreShrink) + 3) & ~3; }
 
-// dirs: this walker's [n_steps][dir_row(DMAX)] table (zero beyond d).
-// chol: the walker's cluster factor, [d][d] row-major lower.
+// One row of the per-step table: walker `walker`'s step s, from the step's
+// stream; chol: the walker's cluster factor, [d][d] row-major lower; out:
+// dir_row(DMAX) floats (zero beyond d).
 template <int DMAX>
-__device__ __forceinline__ void draw_directions(const SliceCfg& S, int walker, const float* __restrict__ chol,
-                                                float* __restrict__ dirs) {
+__device__ __forceinline__ void draw_row(const SliceCfg& S, int walker, int s, const float* __restrict__ chol,
+                                         float* __restrict__ out) {
   constexpr int RW = dir_row(DMAX);
   const int d = S.d;
-  for (int s = 0; s < S.n_steps; ++s) {
-    Stream st;
-    st.init(S.k0, S.k1, S.t, (uint32_t)walker, (uint32_t)s);
-    float z[DMAX];
+  Stream st;
+  st.init(S.k0, S.k1, S.t, (uint32_t)walker, (uint32_t)s);
+  float z[DMAX];
 #pragma unroll
-    for (int i = 0; i < DMAX; ++i) z[i] = 0.f;
+  for (int i = 0; i < DMAX; ++i) z[i] = 0.f;
 #pragma unroll
-    for (int p = 0; p < (DMAX + 1) / 2; ++p)
-      if (2 * p < d) {
-        const float u1 = u24_open0(st.next());
-        const float u2 = u24(st.next());
-        // Box-Muller; the angle on the special-function unit: 2 pi u2 - pi
-        // stays in [-pi, pi), where the intrinsics are accurate to ~1e-6
-        // absolute, and (cos, sin)(2 pi u2) = -(cos, sin)(2 pi u2 - pi).  The
-        // radius keeps the accurate logarithm (relative accuracy near u1 = 1).
-        const float rho = sqrtf(-2.f * logf(u1));
-        const float th = fmaf(u2, 6.28318530717958648f, -3.14159265358979324f);
-        z[2 * p] = -rho * __cosf(th);
-        if (2 * p + 1 < DMAX && 2 * p + 1 < d) z[2 * p + 1] = -rho * __sinf(th);
-      }
-    float nz = 0.f;
-#pragma unroll
-    for (int i = 0; i < DMAX; ++i) nz = fmaf(z[i], z[i], nz);
-    if (nz > 0.f) {
-      const float inv = rsqrtf(nz);
-#pragma unroll
-      for (int i = 0; i < DMAX; ++i) z[i] *= inv;
-    } else {
-#pragma unroll
-      for (int i = 0; i < DMAX; ++i) z[i] = (i == 0) ? 1.f : 0.f;
+  for (int p = 0; p < (DMAX + 1) / 2; ++p)
+    if (2 * p < d) {
+      const float u1 = u24_open0(st.next());
+      const float u2 = u24(st.next());
+      // Box-Muller; the angle on the special-function unit: 2 pi u2 - pi
+      // stays in [-pi, pi), where the intrinsics are accurate to ~1e-6
+      // absolute, and (cos, sin)(2 pi u2) = -(cos, sin)(2 pi u2 - pi).  The
+      // radius keeps the accurate logarithm (relative accuracy near u1 = 1).
+      const float rho = sqrtf(-2.f * logf(u1));
+      const float th = fmaf(u2, 6.28318530717958648f, -3.14159265358979324f);
+      z[2 * p] = -rho * __cosf(th);
+      if (2 * p + 1 < DMAX && 2 * p + 1 < d) z[2 * p + 1] = -rho * __sinf(th);
     }
-    float row[RW];
+  float nz = 0.f;
 #pragma unroll
-    for (int i = 0; i < RW; ++i) row[i] = 0.f;
+  for (int i = 0; i < DMAX; ++i) nz = fmaf(z[i], z[i], nz);
+  if (nz > 0.f) {
+    const float inv = rsqrtf(nz);
 #pragma unroll
-    for (int i = 0; i < DMAX; ++i) {
-      float acc = 0.f;
-      if (i < d) {
+    for (int i = 0; i < DMAX; ++i) z[i] *= inv;
+  } else {
 #pragma unroll
-        for (int k = 0; k <= i; ++k) acc = fmaf(chol[i * d + k], z[k], acc);
-      }
-      row[i] = acc;
-    }
-    row[DMAX] = u24(st.next());
-#pragma unroll
-    for (int j = 0; j < kPreShrink; ++j) row[DMAX + 1 + j] = u24(st.next());
-    float* out = dirs + (size_t)s * RW;
-#pragma unroll
-    for (int i = 0; i < RW; i += 4)
-      *reinterpret_cast<float4*>(out + i) = make_float4(row[i], row[i + 1], row[i + 2], row[i + 3]);
+    for (int i = 0; i < DMAX; ++i) z[i] = (i == 0) ? 1.f : 0.f;
   }
+  float row[RW];
+#pragma unroll
+  for (int i = 0; i < RW; ++i) row[i] = 0.f;
+#pragma unroll
+  for (int i = 0; i < DMAX; ++i) {
+    float acc = 0.f;
+    if (i < d) {
+#pragma unroll
+      for (int k = 0; k <= i; ++k) acc = fmaf(chol[i * d + k], z[k], acc);
+    }
+    row[i] = acc;
+  }
+  row[DMAX] = u24(st.next());
+#pragma unroll
+  for (int j = 0; j < kPreShrink; ++j) row[DMAX + 1 + j] = u24(st.next());
+#pragma unroll
+  for (int i = 0; i < RW; i += 4)
+    *reinterpret_cast<float4*>(out + i) = make_float4(row[i], row[i + 1], row[i + 2], row[i + 3]);
+}
+
+// The rows of walkers [w0, w1) (every step), spread over all threads of the
+// block: consecutive threads take consecutive steps of a walker (so a warp
+// mostly reads one cluster factor).  dirs: [walkers][n_steps][dir_row(DMAX)];
+// chol_of(i): walker i's cluster factor.  Called by every thread; ends with a
+// block barrier.
+template <int DMAX, typename CholOf>
+__device__ __forceinline__ void draw_directions_block(const SliceCfg& S, int w0, int w1, CholOf chol_of,
+                                                      float* __restrict__ dirs) {
+  constexpr int RW = dir_row(DMAX);
+  const int rows = (w1 - w0) * S.n_steps;
+  for (int q = threadIdx.x; q < rows; q += blockDim.x) {
+    const int i = w0 + q / S.n_steps, s = q - (i - w0) * S.n_steps;
+    draw_row<DMAX>(S, i, s, chol_of(i), dirs + ((size_t)i * S.n_steps + s) * RW);
+  }
+  __syncthreads();
 }
 
 struct WalkerOut {
@@ -627,7 +642,7 @@ __device__ __forceinline__ void take_row(const float* slot, float (&v)[DMAX], fl
 }
 
 // All lanes of a warp must call it.  dirs: this walker's table from
-// draw_directions; slot: dir_row(DMAX) floats of shared memory (16-byte
+// draw_directions_block; slot: dir_row(DMAX) floats of shared memory (16-byte
 // aligned) private to this walker, used to prefetch the next step's row.
 template <int DMAX>
 inline __device__ void slice_walker(const LikParams& P, const SliceCfg& S, int walker, bool active,

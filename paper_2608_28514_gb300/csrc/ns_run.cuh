@@ -281,7 +281,6 @@ __device__ __noinline__ void walker_phase(const RunDesc& R, const LikParams& P, 
   const bool act = tid < m;
   const int i = act ? tid : 0;
   const int sd = s_seed[i];
-  const int cid = R.live_cid[sd];
   const float thr_out = (R.correction == 3) ? s_W[m - 1] : s_W[0];
   const float thr_in = (R.correction == 3) ? s_W[m - 1] : s_W[i];
   WalkerOut O;
@@ -291,8 +290,6 @@ __device__ __noinline__ void walker_phase(const RunDesc& R, const LikParams& P, 
   O.hist_x = R.hist_x + (size_t)i * R.t_max * d;
   O.hist_len = R.hist_len + i;
   float* my_dirs = R.dirs + (size_t)i * R.n_steps * dir_row(DMAX);
-  const long long c0 = clock64();
-  if (act) draw_directions<DMAX>(SC, i, s_chol + (size_t)cid * d * d, my_dirs);
   const long long c1 = clock64();
   long long e = 0;
   int f = 0;
@@ -300,7 +297,7 @@ __device__ __noinline__ void walker_phase(const RunDesc& R, const LikParams& P, 
                      thr_out, thr_in, O, e, f);
   ev = act ? e : 0;
   fl = act ? f : 0;
-  cyc_draw = c1 - c0;  // this warp's direction draws and walk
+  cyc_draw = 0;  // the draws happen before, block-wide (k_run)
   cyc_walk = clock64() - c1;
 }
 
@@ -363,11 +360,11 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   const bool mine = tid < m;
   const int i = mine ? tid : 0;
   const int sd = s_seed[i];
-  const int cid = R.live_cid[sd];
   const float thr_out = (R.correction == 3) ? s_W[m - 1] : s_W[0];
   const float thr_in = (R.correction == 3) ? s_W[m - 1] : s_W[i];
   const float* dirs = R.dirs + (size_t)i * S.n_steps * RW;
-  if (mine) draw_directions<DMAX>(S, i, s_chol + (size_t)cid * d * d, const_cast<float*>(dirs));
+  draw_directions_block<DMAX>(S, 0, m, [&](int w) { return s_chol + (size_t)R.live_cid[s_seed[w]] * d * d; },
+                              R.dirs);
   const uint32_t n0 = shrink_draw0(d);
   float x[DMAX], v[DMAX], pre[kPreShrink];
   float l = mine ? R.live_l[sd] : 0.f;
@@ -710,9 +707,14 @@ __global__ void NS_RUN_BOUNDS(MLP, DMAX) k_run(const RunDesc* __restrict__ runs,
       walker_phase_mlp<DMAX>(R, SC, s_W, s_seed, s_chol, s_xbuf, s_lbuf, s_rlist, s_mlp, &mlp_ctx, S, ev, fl, re, werr,
                              cyc_eval, cyc_reeval);
     } else {
+      // every walker's rows of the iteration, spread over the whole block
+      const long long cd = clock64();
+      draw_directions_block<DMAX>(SC, 0, m, [&](int w) { return s_chol + (size_t)R.live_cid[s_seed[w]] * d * d; },
+                                  R.dirs);
+      const long long cd1 = clock64();
       if ((tid & ~31) < m) walker_phase<DMAX>(R, P, SC, s_W, s_seed, s_chol, s_slots, ev, fl, cyc_eval, cyc_reeval);
       if (tid == 0) {
-        RS.cycles[6] += cyc_eval;
+        RS.cycles[6] += cd1 - cd;
         RS.cycles[7] += cyc_reeval;
       }
     }
@@ -850,7 +852,6 @@ __global__ void k_slice(const LikParams P, SliceCfg SC, int m, int n_pad, int co
   const int i = act ? i0 : 0;
   const int d = SC.d;
   const int sd = seed_slot[i];
-  const int c = cid[sd];
   const float thr_out = (correction == 3) ? W[m - 1] : W[0];
   const float thr_in = (correction == 3) ? W[m - 1] : W[i];
   WalkerOut O;
@@ -860,7 +861,12 @@ __global__ void k_slice(const LikParams P, SliceCfg SC, int m, int n_pad, int co
   O.hist_x = hist_x + (size_t)i * SC.t_max * d;
   O.hist_len = hist_len + i;
   float* my_dirs = dir_scratch + (size_t)i * SC.n_steps * dir_row(DMAX);
-  if (act) draw_directions<DMAX>(SC, i, chol + (size_t)c * d * d, my_dirs);
+  {  // this block's walkers' rows, spread over the block
+    const int w0 = blockIdx.x * blockDim.x, w1 = min(m, w0 + (int)blockDim.x);
+    if (w0 < w1)
+      draw_directions_block<DMAX>(SC, w0, w1, [&](int w) { return chol + (size_t)cid[seed_slot[w]] * d * d; },
+                                  dir_scratch);
+  }
   long long ev = 0;
   int fl = 0;
   float* slot = reinterpret_cast<float*>(sm) + (size_t)threadIdx.x * dir_row(DMAX);
