@@ -995,6 +995,7 @@ inline __device__ void evidence_add(EvidState& E, int N, int n, const float* __r
 // tile, FP64 across tiles; FP64 regularised Cholesky.
 // ---------------------------------------------------------------------------
 constexpr int kTile = 128;
+constexpr int kTileS = kTile + 2;  // row stride of a moments tile: rows start on different banks
 
 // One warp: L = chol(A) for a d x d FP64 matrix (smem, row-major).  Returns
 // false (uniformly) if a pivot is not positive.
@@ -1146,14 +1147,14 @@ inline __device__ void reg_cholesky(int d, double* C, double* L, double* work, B
 // member x_ref (so that E[(x - x_ref)(x - x_ref)^T] - (mu - x_ref)(mu -
 // x_ref)^T suffers no cancellation), products accumulate in FP32 within a
 // tile of kTile points and in FP64 across tiles.  tile: smem float
-// [d][kTile] + d; acc: smem FP64 [d + d*d]; returns n.  Results: mean in
+// [d][kTileS] + d; acc: smem FP64 [d + d*d]; returns n.  Results: mean in
 // acc[0:d], covariance in acc[d:d+d*d].
 template <class Member>
 inline __device__ int node_moments(const float* __restrict__ live_x, int n_pad, int N, int d, Member member,
                                    float* tile, double* acc, BlockScratch& S) {
   const int tid = threadIdx.x, B = blockDim.x;
   const int ne = d * (d + 1) / 2;
-  float* ref = tile + d * kTile;
+  float* ref = tile + d * kTileS;
   for (int i = tid; i < d + d * d; i += B) acc[i] = 0.0;
   if (tid == 0) {
     int j0 = 0;
@@ -1168,7 +1169,7 @@ inline __device__ int node_moments(const float* __restrict__ live_x, int n_pad, 
   for (int j0 = 0; j0 < N; j0 += kTile) {
     for (int q = tid; q < d * kTile; q += B) {
       const int i = q / kTile, jj = q % kTile, j = j0 + jj;
-      tile[q] = (j < N && member(j)) ? live_x[(size_t)i * n_pad + j] - ref[i] : 0.f;
+      tile[i * kTileS + jj] = (j < N && member(j)) ? live_x[(size_t)i * n_pad + j] - ref[i] : 0.f;
     }
     if (tid < kTile) cnt += (j0 + tid < N && member(j0 + tid)) ? 1 : 0;
     __syncthreads();
@@ -1177,18 +1178,31 @@ inline __device__ int node_moments(const float* __restrict__ live_x, int n_pad, 
         int a = 0;
         while ((a + 1) * (a + 2) / 2 <= e) ++a;
         const int bcol = e - a * (a + 1) / 2;
-        const float* ta = tile + a * kTile;
-        const float* tb = tile + bcol * kTile;
-        float2 s2 = f2(0.f, 0.f);
-#pragma unroll 8
-        for (int jj = 0; jj < kTile; jj += 2) s2 = __ffma2_rn(ld2(ta + jj), ld2(tb + jj), s2);
-        acc[d + a * d + bcol] += (double)(s2.x + s2.y);
+        const float* ta = tile + a * kTileS;
+        const float* tb = tile + bcol * kTileS;
+        // four independent packed accumulators
+        float2 s0 = f2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+#pragma unroll 4
+        for (int jj = 0; jj < kTile; jj += 8) {
+          s0 = __ffma2_rn(ld2(ta + jj), ld2(tb + jj), s0);
+          s1 = __ffma2_rn(ld2(ta + jj + 2), ld2(tb + jj + 2), s1);
+          s2 = __ffma2_rn(ld2(ta + jj + 4), ld2(tb + jj + 4), s2);
+          s3 = __ffma2_rn(ld2(ta + jj + 6), ld2(tb + jj + 6), s3);
+        }
+        s0 = __fadd2_rn(__fadd2_rn(s0, s1), __fadd2_rn(s2, s3));
+        acc[d + a * d + bcol] += (double)(s0.x + s0.y);
       } else {
-        const float* ta = tile + (e - ne) * kTile;
-        float2 s2 = f2(0.f, 0.f);
-#pragma unroll 8
-        for (int jj = 0; jj < kTile; jj += 2) s2 = __fadd2_rn(ld2(ta + jj), s2);
-        acc[e - ne] += (double)(s2.x + s2.y);
+        const float* ta = tile + (e - ne) * kTileS;
+        float2 s0 = f2(0.f, 0.f), s1 = s0, s2 = s0, s3 = s0;
+#pragma unroll 4
+        for (int jj = 0; jj < kTile; jj += 8) {
+          s0 = __fadd2_rn(ld2(ta + jj), s0);
+          s1 = __fadd2_rn(ld2(ta + jj + 2), s1);
+          s2 = __fadd2_rn(ld2(ta + jj + 4), s2);
+          s3 = __fadd2_rn(ld2(ta + jj + 6), s3);
+        }
+        s0 = __fadd2_rn(__fadd2_rn(s0, s1), __fadd2_rn(s2, s3));
+        acc[e - ne] += (double)(s0.x + s0.y);
       }
     }
     __syncthreads();

@@ -126,7 +126,7 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax,
   // runs also the evaluators (walker phase) and the batch-correction
   // candidates (Algorithms 1-2 and the update), which never overlap
   const size_t phase0 = o;
-  c.tile = take(sizeof(float) * (d * kTile + d));
+  c.tile = take(sizeof(float) * (d * kTileS + d));
   c.acc = take(sizeof(double) * (d + d * d));
   c.c64 = take(sizeof(double) * d * d);
   c.l64 = take(sizeof(double) * d * d);
