@@ -112,6 +112,8 @@ typedef struct {
     int precision;        /* MLP only: 0 FP32, 1 BF16 with FP32 re-evaluation */
     double reeval_margin; /* MLP only: re-evaluate in FP32 when |logL - threshold| <   */
     double reeval_rel;    /*   reeval_margin + reeval_rel |threshold| (2.0 and 4e-3) */
+    int reeval_defer;     /* MLP only: rounds a near-threshold candidate may wait so that several are
+                           * re-evaluated in one FP32 pass, 0..64 (4; 0 = at once); results do not depend on it */
 } ns_options;
 
 /* One run of a batch. */

@@ -45,7 +45,7 @@ class NsOptions(C.Structure):
         ("kmeans_iters", C.c_int), ("correction", C.c_int), ("history_iters", C.c_int), ("t_max", C.c_int),
         ("e_max", C.c_int), ("s_max", C.c_int), ("width", C.c_double), ("max_iter", C.c_longlong),
         ("dead_cap", C.c_longlong), ("chunk_iters", C.c_int), ("precision", C.c_int),
-        ("reeval_margin", C.c_double), ("reeval_rel", C.c_double),
+        ("reeval_margin", C.c_double), ("reeval_rel", C.c_double), ("reeval_defer", C.c_int),
     ]
 
 

@@ -337,7 +337,8 @@ ns_status check_opts(const ns_options& o, std::string* err) {
       o.t_max < 1 || o.t_max > NS_MAX_HISTORY || !(o.width > 0) || !std::isfinite(o.width) ||
       o.correction < 0 || o.correction > 3 || o.max_iter < 1 || o.dead_cap < 0 || o.chunk_iters < 0 ||
       !(o.vol_frac >= 0 && o.vol_frac < 1) || o.precision < 0 || o.precision > 1 || !(o.reeval_margin >= 0) ||
-      !std::isfinite(o.reeval_margin) || !(o.reeval_rel >= 0) || !std::isfinite(o.reeval_rel)) {
+      !std::isfinite(o.reeval_margin) || !(o.reeval_rel >= 0) || !std::isfinite(o.reeval_rel) ||
+      o.reeval_defer < 0 || o.reeval_defer > 64) {
     set_err(err, "an option is out of range");
     return NS_ERR_ARG;
   }
@@ -512,6 +513,7 @@ ns_status ns_default_options(ns_options* o) {
   // at the 99th percentile, 0.35 % at most, on the 27-D emulator network)
   o->reeval_margin = 2.0;
   o->reeval_rel = 4e-3;
+  o->reeval_defer = 4;
   return NS_OK;
 }
 
@@ -709,6 +711,7 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     R.tree_ws = o.spill ? reinterpret_cast<char*>(base + o.tree_ws) : nullptr;
     R.reeval_margin = (float)opt.reeval_margin;
     R.reeval_rel = (float)opt.reeval_rel;
+    R.reeval_defer = opt.reeval_defer;
     if (p.lik->kind == NS_LIK_MLP) {
       R.mlp_tiles = reinterpret_cast<const uint8_t*>(base + o.mlp_img);
       R.mlp_desc = reinterpret_cast<const MlpDesc*>(base + o.mlp_desc);

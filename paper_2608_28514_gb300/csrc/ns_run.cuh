@@ -64,6 +64,7 @@ struct RunDesc {
   char* tree_ws;          // the cluster-tree scratch of a spilled run
   float reeval_margin;    // re-evaluate in FP32 when |logL_bf16 - threshold| <
   float reeval_rel;       //   reeval_margin + reeval_rel |threshold|
+  int reeval_defer;       // rounds a near-threshold candidate may wait for a shared FP32 pass
 };
 
 // Shared-memory carve of the run kernel, computed identically on host and
@@ -390,11 +391,79 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   if (active) load_step(0);
   int err = 0;
   long long ce = 0, cr = 0;  // thread 0: cycles in the batch evaluations and the FP32 re-evaluations
+  // A walker whose BF16 log L is near its threshold waits (pending) for the
+  // FP32 value, holding its candidate in its xbuf row; the pending
+  // candidates are re-evaluated together once kMlpF32Nb of them wait, one has
+  // waited reeval_defer rounds, or no walker is left to move.  A decision is
+  // only delayed, never changed: the runs equal those of immediate
+  // re-evaluation (reeval_defer = 0) bit for bit.
+  bool pend = false;
+  int age = 0;           // rounds the oldest pending candidate has waited (uniform)
+  float ptp = 0.f;       // the pending candidate's position on the line
+  // the slice-sampling step on the outcome of this walker's candidate at tp
+  auto decide = [&](bool in, float lp, float tp) {
+    if (in) ++evals;
+    const bool ok = in && (lp > ((phase == 2) ? thr_in : thr_out));
+    if (phase < 2) {
+      const bool expand = ok && (nexp < S.e_max);
+      a = (expand && phase == 0) ? a - S.width : a;
+      b = (expand && phase == 1) ? b + S.width : b;
+      flags |= (ok && !expand) ? 1 : 0;
+      nexp = expand ? nexp + 1 : 0;
+      phase = expand ? phase : phase + 1;
+    } else {
+      if (step == S.n_steps - 1) {
+        int hs = -1;
+        if (nsh < S.t_max - 1) {
+          hs = nsh;
+          hlen = nsh + 1;
+        } else if (ok) {
+          hs = S.t_max - 1;
+          hlen = S.t_max;
+        }
+        if (hs >= 0) {
+          float u[DMAX];
+          candidate<DMAX>(x, v, tp, u);
+          R.hist_l[(size_t)i * S.t_max + hs] = lp;
+          for (int k = 0; k < d; ++k) R.hist_x[((size_t)i * S.t_max + hs) * d + k] = u[k];
+        }
+      }
+      bool advance = ok;
+      if (ok) {
+        float u[DMAX];
+        candidate<DMAX>(x, v, tp, u);
+#pragma unroll
+        for (int k = 0; k < DMAX; ++k) x[k] = u[k];
+        l = lp;
+      } else {
+        if (tp < 0.f) a = tp;
+        else b = tp;
+        if (++nsh >= S.s_max) {
+          flags |= 2;
+          advance = true;
+        }
+      }
+      if (advance) {
+        ++step;
+        if (step < S.n_steps) {
+          load_step(step);
+          st.init(S.k0, S.k1, S.t, (uint32_t)i, (uint32_t)step);
+          st.n = n0 + kPreShrink;
+          phase = 0;
+          nsh = 0;
+          nexp = 0;
+        } else {
+          active = false;
+        }
+      }
+    }
+  };
   for (;;) {
     if (!__syncthreads_or(active ? 1 : 0)) break;
+    const bool moving = active && !pend;  // proposes a candidate this round
     float tp = 0.f;
     bool in = false;
-    if (active) {
+    if (moving) {
       tp = (phase == 0) ? a : b;
       if (phase == 2) {
         float uu = pre[0];
@@ -410,7 +479,7 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
       float u[DMAX];
       in = candidate<DMAX>(x, v, tp, u);
       for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = in ? u[k] : 0.5f;
-    } else if (mine) {
+    } else if (mine && !pend) {
       for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = 0.5f;
     }
     __syncthreads();
@@ -420,81 +489,36 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
       long long c1 = clock64();
       ce += c1 - c0;
       c0 = c1;
-      // re-evaluate in FP32 the candidates close to their threshold
+      // candidates close to their threshold wait for their FP32 value
       const float thr = (phase == 2) ? thr_in : thr_out;
       const float margin = fmaf(R.reeval_rel, fabsf(thr), R.reeval_margin);
-      const bool need = active && in && margin > 0.f && fabsf(lbuf[tid] - thr) < margin;
+      const bool need = moving && in && margin > 0.f && fabsf(lbuf[tid] - thr) < margin;
+      if (need) {
+        pend = true;
+        ptp = tp;
+      }
+      if (moving && !need) decide(in, in ? lbuf[tid] : -CUDART_INF_F, tp);
       int cnt;
-      const int pos = block_exclusive_scan(need ? 1 : 0, BS, &cnt);
-      if (need) rlist[pos] = tid;
-      __syncthreads();
-      if (cnt > 0) {
+      const int pos = block_exclusive_scan(pend ? 1 : 0, BS, &cnt);
+      const int still = __syncthreads_or((active && !pend) ? 1 : 0);
+      age = (cnt > 0) ? age + 1 : 0;
+      if (cnt > 0 && (cnt >= kMlpF32Nb || !still || age > R.reeval_defer)) {
+        if (pend) rlist[pos] = tid;
+        __syncthreads();
         mlp_reeval(R, xbuf, lbuf, rlist, cnt, xg, lg, act);
         reevals += (tid == 0) ? cnt : 0;
+        if (pend) {
+          pend = false;
+          decide(true, lbuf[tid], ptp);
+        }
+        age = 0;
       }
       cr += clock64() - c0;
     } else {
       mlp_batch_f32(R, xbuf, m, lbuf, act);
       ce += clock64() - c0;
-    }
-    __syncthreads();
-    if (active) {
-      const float lp = in ? lbuf[tid] : -CUDART_INF_F;
-      if (in) ++evals;
-      const bool ok = in && (lp > ((phase == 2) ? thr_in : thr_out));
-      if (phase < 2) {
-        const bool expand = ok && (nexp < S.e_max);
-        a = (expand && phase == 0) ? a - S.width : a;
-        b = (expand && phase == 1) ? b + S.width : b;
-        flags |= (ok && !expand) ? 1 : 0;
-        nexp = expand ? nexp + 1 : 0;
-        phase = expand ? phase : phase + 1;
-      } else {
-        if (step == S.n_steps - 1) {
-          int hs = -1;
-          if (nsh < S.t_max - 1) {
-            hs = nsh;
-            hlen = nsh + 1;
-          } else if (ok) {
-            hs = S.t_max - 1;
-            hlen = S.t_max;
-          }
-          if (hs >= 0) {
-            float u[DMAX];
-            candidate<DMAX>(x, v, tp, u);
-            R.hist_l[(size_t)i * S.t_max + hs] = lp;
-            for (int k = 0; k < d; ++k) R.hist_x[((size_t)i * S.t_max + hs) * d + k] = u[k];
-          }
-        }
-        bool advance = ok;
-        if (ok) {
-          float u[DMAX];
-          candidate<DMAX>(x, v, tp, u);
-#pragma unroll
-          for (int k = 0; k < DMAX; ++k) x[k] = u[k];
-          l = lp;
-        } else {
-          if (tp < 0.f) a = tp;
-          else b = tp;
-          if (++nsh >= S.s_max) {
-            flags |= 2;
-            advance = true;
-          }
-        }
-        if (advance) {
-          ++step;
-          if (step < S.n_steps) {
-            load_step(step);
-            st.init(S.k0, S.k1, S.t, (uint32_t)i, (uint32_t)step);
-            st.n = n0 + kPreShrink;
-            phase = 0;
-            nsh = 0;
-            nexp = 0;
-          } else {
-            active = false;
-          }
-        }
-      }
+      __syncthreads();
+      if (moving) decide(in, in ? lbuf[tid] : -CUDART_INF_F, tp);
     }
     if (__syncthreads_or(err)) {
       err = 1;

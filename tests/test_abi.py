@@ -84,7 +84,8 @@ def test_validation_without_gpu(native):
         native.ns_create(q, 100, 5, 10, 1e-3, 1)
     # options out of range
     for k, v in [("depth", 9), ("t_max", 0), ("t_max", 65), ("correction", 7), ("width", -1.0),
-                 ("precision", 2), ("reeval_margin", -1.0), ("reeval_rel", -1e-3), ("reeval_rel", float("inf"))]:
+                 ("precision", 2), ("reeval_margin", -1.0), ("reeval_rel", -1e-3), ("reeval_rel", float("inf")),
+                 ("reeval_defer", -1), ("reeval_defer", 65)]:
         o = native.ns_default_options(**{k: v})
         with pytest.raises(native.NSError):
             native.ns_create(p, 100, 5, 10, 1e-3, 1, opt=o)
@@ -103,4 +104,4 @@ def test_default_options_match_header(native):
     o = native.ns_default_options()
     assert (o.depth, o.correction, o.history_iters, o.t_max, o.e_max, o.s_max) == (0, 2, 1, 64, 64, 128)
     assert o.width == 1.0 and o.vol_frac == 0.5 and o.kmeans_iters == 10
-    assert o.precision == 0 and o.reeval_margin == 2.0 and o.reeval_rel == 4e-3
+    assert o.precision == 0 and o.reeval_margin == 2.0 and o.reeval_rel == 4e-3 and o.reeval_defer == 4

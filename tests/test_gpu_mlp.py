@@ -167,3 +167,23 @@ def test_full_emulator_runs_a_few_iterations(nat):
     # dead points of the two iterations, in ascending order
     nd = 2 * 150
     assert np.all(np.diff(r["dead_l"][:nd]) >= 0)
+
+
+def test_deferred_reevaluation_changes_nothing(nat):
+    """Near-threshold candidates re-evaluated at once (reeval_defer = 0) or
+    batched over up to 4 and 16 rounds: the same runs, bit for bit."""
+    p = _small_emulator(5)
+    runs = [(p, 200, 20, 20, 1e-2, s) for s in (3, 4)]
+    out = {}
+    for defer in (0, 4, 16):
+        o = nat.ns_default_options(precision=1, reeval_margin=5.0, reeval_defer=defer, max_iter=40, chunk_iters=40)
+        h = nat.ns_create_batch(runs, o)
+        nat.ns_run(h, check=False)
+        out[defer] = [nat.ns_result(h, r) for r in range(len(runs))]
+        nat.ns_destroy(h)
+    assert sum(r["n_reeval"] for r in out[0]) > 0
+    for defer in (4, 16):
+        for a, b in zip(out[0], out[defer]):
+            assert a["n_iter"] == b["n_iter"] and a["n_evals"] == b["n_evals"] and a["n_reeval"] == b["n_reeval"]
+            np.testing.assert_array_equal(a["dead_l"], b["dead_l"])
+            np.testing.assert_array_equal(a["dead_x"], b["dead_x"])
