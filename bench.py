@@ -85,6 +85,9 @@ def parse():
     ap.add_argument("--comparison-shapes", type=int, default=0, metavar="SEEDS",
                     help="run the section-4 comparison shapes (Gaussian d = 2..32, Rosenbrock and the 49-Gaussian "
                          "array at N = 100..1000) with SEEDS runs each, print the JSON table and exit")
+    ap.add_argument("--profile-mlp-runs", type=int, default=0, metavar="R",
+                    help="profiling case: R runs of the 27-D emulator workload (BF16 path), one iteration per "
+                         "launch, three launches, small dead buffers; prints no bench line")
     ap.add_argument("--correction-sweep", type=int, default=0, metavar="SEEDS",
                     help="run the batching-error study (correction schemes x m/N) with SEEDS runs per point, "
                          "print its JSON table and exit")
@@ -459,6 +462,21 @@ def main():
                 nat.ns_mlp_loglike(p, img, x, out, precision=prec)
         torch.cuda.synchronize()
         print("profile case done", float(out[:8].sum()))
+        return
+    if args.profile_mlp_runs > 0:
+        import torch
+        from paper_2608_28514_gb300 import _native as nat
+        from paper_2608_28514_gb300 import workloads as W
+        p = W.mlp_emulator(1)
+        opt = nat.ns_default_options(precision=1, max_iter=1, chunk_iters=1, dead_cap=EMU_N + 4 * EMU_M)
+        h = nat.ns_create_batch([(p, EMU_N, EMU_M, EMU_STEPS, 1e-3, s)
+                                 for s in range(1, args.profile_mlp_runs + 1)], opt)
+        for _ in range(3):
+            nat.ns_reset(h)
+            nat.ns_run(h, check=False)
+        torch.cuda.synchronize()
+        print("profile case done", nat.ns_get_stats(h))
+        nat.ns_destroy(h)
         return
     if args.comparison_shapes > 0:
         if int(os.environ.get("RANK", "0")) == 0:

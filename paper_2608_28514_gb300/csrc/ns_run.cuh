@@ -460,28 +460,39 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   };
   for (;;) {
     if (!__syncthreads_or(active ? 1 : 0)) break;
-    const bool moving = active && !pend;  // proposes a candidate this round
     float tp = 0.f;
     bool in = false;
-    if (moving) {
-      tp = (phase == 0) ? a : b;
-      if (phase == 2) {
-        float uu = pre[0];
-        if (nsh < kPreShrink) {
-#pragma unroll
-          for (int j = 1; j < kPreShrink; ++j)
-            if (nsh == j) uu = pre[j];
-        } else {
-          uu = u24(st.next());
-        }
-        tp = fmaf(uu, b - a, a);
-      }
+    if (active && !pend) {
+      // proposals outside the unit cube need no likelihood: settle them here
+      // (a rejection, in the walker's own order of draws) until the walker
+      // holds a candidate to evaluate or has finished its steps
       float u[DMAX];
-      in = candidate<DMAX>(x, v, tp, u);
-      for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = in ? u[k] : 0.5f;
-    } else if (mine && !pend) {
-      for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = 0.5f;
+      for (;;) {
+        tp = (phase == 0) ? a : b;
+        if (phase == 2) {
+          float uu = pre[0];
+          if (nsh < kPreShrink) {
+#pragma unroll
+            for (int j = 1; j < kPreShrink; ++j)
+              if (nsh == j) uu = pre[j];
+          } else {
+            uu = u24(st.next());
+          }
+          tp = fmaf(uu, b - a, a);
+        }
+        in = candidate<DMAX>(x, v, tp, u);
+        if (in) break;
+        decide(false, -CUDART_INF_F, tp);
+        if (!active) break;
+      }
+      if (in)
+        for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = u[k];
     }
+    const bool moving = active && !pend && in;  // holds a candidate to evaluate this round
+    if (mine && !pend && !moving)
+      for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = 0.5f;
+    // every walker finished while settling its proposals: no batch to evaluate
+    if (!__syncthreads_or((moving || pend) ? 1 : 0)) break;
     __syncthreads();
     long long c0 = clock64();
     if (bf16) {
