@@ -383,9 +383,15 @@ ns_status ns_mlp_pack(const ns_likelihood* lik, int d, void* image, void* stream
 
 /* log L of n points x [n][d] (device, unit cube) -> logl [n] (device):
  * precision 1 = BF16 inputs, weights and activations on the tensor cores
- * (tcgen05, FP32 accumulation in tensor memory), 64 points per block;
- * precision 0 = FP32 on the CUDA cores.  A block whose tensor-core pipeline
- * stalls past its wait budget writes NaN for its points. */
+ * (tcgen05, FP32 accumulation in tensor memory), up to 128 points per call;
+ * precision 0 = FP32 on the CUDA cores;
+ * precision 2 = FP32 accuracy on the tensor cores, for networks whose
+ * weights are all BF16 values (NS_ERR_ARG otherwise): inputs and
+ * activations split exactly into three BF16 parts whose products with the
+ * weights are exact in FP32, FP32 accumulation and FP32 epilogues (the MLP
+ * runs re-evaluate near-threshold points this way when the weights allow).
+ * A block whose tensor-core pipeline stalls past its wait budget writes NaN
+ * for its points. */
 ns_status ns_mlp_loglike(const ns_likelihood* lik, const double* lo, const double* hi, int d,
                          const void* image, int n, const float* x, float* logl, int precision,
                          void* stream);

@@ -174,15 +174,27 @@ __device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.f +
 // STAGES weight tiles, the B operand for up to NBMAX candidates, chi^2
 // partials.  The streaming of weight tiles from L2 is throughput-bound, not
 // latency-bound, so a few stages suffice.
-template <int NBMAX, int STAGES>
+// P = 3: the FP32-accurate variant (activations as three BF16 planes).
+template <int NBMAX, int STAGES, int P = 1>
 struct MlpSmem {
   static_assert(NBMAX % 16 == 0 && NBMAX <= kMlpNbMax && STAGES >= 2 && STAGES <= kMlpStagesMax, "");
+  static_assert(P == 1 || P == 3, "");
   static constexpr int kStageOff = 0;
-  static constexpr int kActOff = kStageOff + STAGES * kMlpTileBytes;  // [kpad/64][NBMAX][128 B]
-  static constexpr int kActBytes = (kMlpMaxK / 64) * NBMAX * 128;
+  static constexpr int kActOff = kStageOff + STAGES * kMlpTileBytes;  // [P][kpad/64][NBMAX][128 B]
+  static constexpr int kPlaneBytes = (kMlpMaxK / 64) * NBMAX * 128;
+  static constexpr int kActBytes = P * kPlaneBytes;
   static constexpr int kChiOff = kActOff + kActBytes;                 // [4][NBMAX] floats
   static constexpr int kBytes = kChiOff + 4 * NBMAX * 4;
 };
+
+// a = hi + mid + lo exactly, each a BF16 value (8 significand bits each;
+// the remainders a - hi and (a - hi) - mid are exact in FP32).
+__device__ __forceinline__ void split3_bf16(float a, __nv_bfloat16& hi, __nv_bfloat16& mid, __nv_bfloat16& lo) {
+  hi = __float2bfloat16_rn(a);
+  const float r1 = a - __bfloat162float(hi);
+  mid = __float2bfloat16_rn(r1);
+  lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+}
 
 // Warp roles of the BF16 evaluator: warps 0-7 read the accumulators back
 // (warp w owns tensor-memory lanes 32(w%4)..32(w%4)+31 and every other
@@ -301,15 +313,23 @@ __device__ __forceinline__ int mlp_n_groups(int MT, bool last, int N) {
 
 // Evaluates the batch x [n][d] (unit cube, 1 <= n <= NBMAX) with the BF16
 // tensor-core path into out[n] (log L); the MMAs run with N = n rounded up
-// to 16.  Called by every thread of a block of at least kMlpThreads threads,
+// to 16.  With `rows` non-null, candidate r is row rows[r] of x and its
+// log L goes to out[rows[r]] (a gather/scatter by index list).
+// P = 3 evaluates in FP32 accuracy on the same tensor cores, for networks
+// whose weights are BF16 values: every activation (and the input) is split
+// exactly into three BF16 planes, each weight tile multiplies all three
+// (products of two BF16 values are exact in FP32, the accumulation is FP32),
+// and the epilogues run in FP32 (accurate SiLU; the output residual as
+// (y + bias - data) / sigma).  It differs from the CUDA-core FP32 evaluator
+// only in the order of the FP32 sums.  Called by every thread of a block of at least kMlpThreads threads,
 // with the block's context `ctx` (mlp_ctx_init).  `sm` is 1024-byte aligned
 // and holds MlpSmem<NBMAX, STAGES>::kBytes.  Returns false (for every
 // thread) if a wait gave up, now or before.
-template <int NBMAX, int STAGES>
+template <int NBMAX, int STAGES, int P = 1>
 inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict__ tiles,
                                      const float* __restrict__ f32, const float* x, int x_stride, int n,
-                                     float* out, char* sm, MlpCtx* ctx) {
-  using L = MlpSmem<NBMAX, STAGES>;
+                                     float* out, char* sm, MlpCtx* ctx, const int* rows = nullptr) {
+  using L = MlpSmem<NBMAX, STAGES, P>;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   char* stages = sm + L::kStageOff;
   char* act = sm + L::kActOff;
@@ -327,8 +347,17 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
     const int kb = q / (N * 64), rem = q % (N * 64), r = rem / 64, k = rem % 64;
     const int i = kb * 64 + k;
     float v = 0.f;
-    if (r < n && i < M.d) v = fmaf(M.span[i], x[(size_t)r * x_stride + i], M.lo[i]);
-    *reinterpret_cast<__nv_bfloat16*>(act + kb * NBMAX * 128 + sw128_offset(r, k)) = __float2bfloat16_rn(v);
+    if (r < n && i < M.d) v = fmaf(M.span[i], x[(size_t)(rows ? rows[r] : r) * x_stride + i], M.lo[i]);
+    char* dst = act + kb * NBMAX * 128 + sw128_offset(r, k);
+    if constexpr (P == 1) {
+      *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
+    } else {
+      __nv_bfloat16 h0, h1, h2;
+      split3_bf16(v, h0, h1, h2);
+      *reinterpret_cast<__nv_bfloat16*>(dst) = h0;
+      *reinterpret_cast<__nv_bfloat16*>(dst + L::kPlaneBytes) = h1;
+      *reinterpret_cast<__nv_bfloat16*>(dst + 2 * L::kPlaneBytes) = h2;
+    }
   }
   for (int q = tid; q < 4 * NBMAX; q += blockDim.x) chi[q] = 0.f;
   fence_proxy_async();
@@ -389,11 +418,14 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
               tc_fence_after();
               const unsigned d_tmem = tmem + col0 + (unsigned)((t - G.g0) * N);
               const unsigned a0 = smem_u32(stages + s * kMlpTileBytes);
-              const unsigned b0 = smem_u32(act + kb * NBMAX * 128);
 #pragma unroll
-              for (int k = 0; k < 4; ++k)
-                umma_bf16(d_tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc,
-                          (kb > 0 || k > 0) ? 1u : 0u);
+              for (int pl = 0; pl < P; ++pl) {
+                const unsigned b0 = smem_u32(act + pl * L::kPlaneBytes + kb * NBMAX * 128);
+#pragma unroll
+                for (int k = 0; k < 4; ++k)
+                  umma_bf16(d_tmem, sdesc_sw128(a0 + 32 * k), sdesc_sw128(b0 + 32 * k), idesc,
+                            (kb > 0 || k > 0 || pl > 0) ? 1u : 0u);
+              }
               umma_commit(&ctx->empty[s]);
             }
           }
@@ -446,10 +478,22 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
               const int c0 = i * 16;
               float v[16];
               tmem_ld16(tmem + lane_base + col0 + (unsigned)((t - G.g0) * N + c0), v);
+              if constexpr (P == 1) {
 #pragma unroll
-              for (int c = 0; c < 16; ++c)
-                *reinterpret_cast<__nv_bfloat16*>(dst + sw128_offset(c0 + c, k)) =
-                    __float2bfloat16_rn(silu_fast(v[c] + bias));
+                for (int c = 0; c < 16; ++c)
+                  *reinterpret_cast<__nv_bfloat16*>(dst + sw128_offset(c0 + c, k)) =
+                      __float2bfloat16_rn(silu_fast(v[c] + bias));
+              } else {
+#pragma unroll
+                for (int c = 0; c < 16; ++c) {
+                  __nv_bfloat16 h0, h1, h2;
+                  split3_bf16(silu(v[c] + bias), h0, h1, h2);
+                  char* e = dst + sw128_offset(c0 + c, k);
+                  *reinterpret_cast<__nv_bfloat16*>(e) = h0;
+                  *reinterpret_cast<__nv_bfloat16*>(e + L::kPlaneBytes) = h1;
+                  *reinterpret_cast<__nv_bfloat16*>(e + 2 * L::kPlaneBytes) = h2;
+                }
+              }
             }
           }
           fence_proxy_async();
@@ -463,12 +507,13 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
             for (int t = G.g0; t < G.g1; ++t) {
               const int f = t * 128 + q * 32 + lane;
               const float is = f32[M.isig0 + f];
-              const float cb = (f32[M.bias0[l] + f] - f32[M.data0 + f]) * is;
+              const float bias = f32[M.bias0[l] + f], dk = f32[M.data0 + f];
+              const float cb = (bias - dk) * is;
               float v[16];
               tmem_ld16(tmem + lane_base + col0 + (unsigned)((t - G.g0) * N + c0), v);
 #pragma unroll
               for (int c = 0; c < 16; ++c) {
-                const float r = fmaf(v[c], is, cb);
+                const float r = (P == 1) ? fmaf(v[c], is, cb) : ((v[c] + bias) - dk) * is;
                 sacc[c] = fmaf(r, r, sacc[c]);
               }
             }
@@ -486,7 +531,7 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
     if (err) ctx_set_err(ctx);
     epi_bar_sync();
     for (int r = tid; r < n; r += kMlpEpiWarps * 32)
-      out[r] = -0.5f * (chi[r] + chi[NBMAX + r] + chi[2 * NBMAX + r] + chi[3 * NBMAX + r]);
+      out[rows ? rows[r] : r] = -0.5f * (chi[r] + chi[NBMAX + r] + chi[2 * NBMAX + r] + chi[3 * NBMAX + r]);
   }
   __syncthreads();
   return ctx_err(ctx) == 0u;
@@ -510,7 +555,7 @@ __host__ __device__ constexpr size_t mlp_f32_act_bytes(int nb) {
 
 template <int NB, bool W16>
 __device__ __noinline__ void mlp_eval_f32_w(const MlpDesc& M, const float* __restrict__ f32, const float* x,
-                                            int x_stride, int n, float* out, float* act) {
+                                            int x_stride, int n, float* out, float* act, const int* rows) {
   static_assert(NB % 4 == 0, "NB must be a multiple of 4");
   constexpr int S = mlp_f32_stride(NB);
   constexpr int KU = kMlpF32Ku;
@@ -519,7 +564,7 @@ __device__ __noinline__ void mlp_eval_f32_w(const MlpDesc& M, const float* __res
   float* a1 = act + kMlpMaxK * S;
   for (int q = tid; q < M.d * NB; q += B) {
     const int i = q / NB, r = q - i * NB;
-    a0[i * S + r] = (r < n) ? fmaf(M.span[i], x[(size_t)r * x_stride + i], M.lo[i]) : 0.f;
+    a0[i * S + r] = (r < n) ? fmaf(M.span[i], x[(size_t)(rows ? rows[r] : r) * x_stride + i], M.lo[i]) : 0.f;
   }
   __syncthreads();
   float part[NB];
@@ -586,14 +631,18 @@ __device__ __noinline__ void mlp_eval_f32_w(const MlpDesc& M, const float* __res
           wb[u] = nb[u];
         }
       }
-      if (!last) {
+      if (!last) {  // 16-byte stores: four candidates of one feature each
         if (va) {
 #pragma unroll
-          for (int r = 0; r < NB; ++r) a1[oa * S + r] = silu(acc_a[r]);
+          for (int r = 0; r < NB; r += 4)
+            *reinterpret_cast<float4*>(a1 + oa * S + r) =
+                make_float4(silu(acc_a[r]), silu(acc_a[r + 1]), silu(acc_a[r + 2]), silu(acc_a[r + 3]));
         }
         if (vb) {
 #pragma unroll
-          for (int r = 0; r < NB; ++r) a1[ob * S + r] = silu(acc_b[r]);
+          for (int r = 0; r < NB; r += 4)
+            *reinterpret_cast<float4*>(a1 + ob * S + r) =
+                make_float4(silu(acc_b[r]), silu(acc_b[r + 1]), silu(acc_b[r + 2]), silu(acc_b[r + 3]));
         }
       } else {
         if (va) {
@@ -636,17 +685,20 @@ __device__ __noinline__ void mlp_eval_f32_w(const MlpDesc& M, const float* __res
   for (int r = tid; r < n; r += B) {
     float s = 0.f;
     for (int w = 0; w < nw; ++w) s += red[r * 32 + w];
-    out[r] = -0.5f * s;
+    out[rows ? rows[r] : r] = -0.5f * s;
   }
   __syncthreads();
 }
 
-// The FP32 evaluator for the image's weight storage.
+// The FP32 evaluator for the image's weight storage.  With `rows`
+// non-null, candidate r is row rows[r] of x and its log L goes to
+// out[rows[r]].
 template <int NB>
 __device__ __forceinline__ void mlp_eval_f32(const MlpDesc& M, const float* __restrict__ f32, const float* x,
-                                             int x_stride, int n, float* out, float* act) {
-  if (M.w_bf16) mlp_eval_f32_w<NB, true>(M, f32, x, x_stride, n, out, act);
-  else mlp_eval_f32_w<NB, false>(M, f32, x, x_stride, n, out, act);
+                                             int x_stride, int n, float* out, float* act,
+                                             const int* rows = nullptr) {
+  if (M.w_bf16) mlp_eval_f32_w<NB, true>(M, f32, x, x_stride, n, out, act, rows);
+  else mlp_eval_f32_w<NB, false>(M, f32, x, x_stride, n, out, act, rows);
 }
 
 }  // namespace nsd

@@ -311,22 +311,44 @@ __device__ __noinline__ void walker_phase(const RunDesc& R, const LikParams& P, 
 // re-evaluated in FP32 afterwards, so every log L that is stored (dead
 // points, Algorithm 2) is an FP32 value.
 // Called by every thread of the block.
-inline __device__ bool mlp_batch_f32(const RunDesc& R, const float* xs, int n, float* ls, float* act) {
-  for (int b0 = 0; b0 < n; b0 += kMlpF32NbWide)
-    mlp_eval_f32<kMlpF32NbWide>(*R.mlp_desc, R.mlp_f32, xs + (size_t)b0 * kMaxDim, kMaxDim,
-                                min(kMlpF32NbWide, n - b0), ls + b0, act);
+inline __device__ bool mlp_batch_f32(const RunDesc& R, const float* xs, int n, float* ls, float* act,
+                                     const int* rows = nullptr) {
+  for (int b0 = 0; b0 < n; b0 += kMlpF32NbWide) {
+    if (rows)
+      mlp_eval_f32<kMlpF32NbWide>(*R.mlp_desc, R.mlp_f32, xs, kMaxDim, min(kMlpF32NbWide, n - b0), ls, act,
+                                  rows + b0);
+    else
+      mlp_eval_f32<kMlpF32NbWide>(*R.mlp_desc, R.mlp_f32, xs + (size_t)b0 * kMaxDim, kMaxDim,
+                                  min(kMlpF32NbWide, n - b0), ls + b0, act);
+  }
   return true;
 }
 
+// rows: the n rows of xs (and ls) to evaluate, or null for rows 0..n-1.
 inline __device__ bool mlp_batch_bf16(const RunDesc& R, const float* xs, int n, float* ls, char* tsm,
-                                      MlpCtx* ctx) {
+                                      MlpCtx* ctx, const int* rows = nullptr) {
   // equal calls of at most kMlpNbMax candidates (each call streams every weight tile once)
   const int calls = (n + kMlpNbMax - 1) / kMlpNbMax;
   const int per = (n + calls - 1) / calls;
   bool ok = true;
   for (int b0 = 0; b0 < n && ok; b0 += per)
-    ok = mlp_eval_bf16<kMlpNbMax, kRunMlpStages>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, xs + (size_t)b0 * kMaxDim,
-                                                 kMaxDim, min(per, n - b0), ls + b0, tsm, ctx);
+    ok = rows ? mlp_eval_bf16<kMlpNbMax, kRunMlpStages>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, xs, kMaxDim,
+                                                        min(per, n - b0), ls, tsm, ctx, rows + b0)
+              : mlp_eval_bf16<kMlpNbMax, kRunMlpStages>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32,
+                                                        xs + (size_t)b0 * kMaxDim, kMaxDim, min(per, n - b0),
+                                                        ls + b0, tsm, ctx);
+  return ok;
+}
+
+// FP32-accurate re-evaluation on the tensor cores (three BF16 planes, for
+// networks whose weights are BF16 values) of the listed rows of xs, into ls.
+constexpr int kRunSplitNb = 32;
+inline __device__ bool mlp_reeval_tc(const RunDesc& R, const float* xs, float* ls, const int* list, int n,
+                                     char* tsm, MlpCtx* ctx) {
+  bool ok = true;
+  for (int b0 = 0; b0 < n && ok; b0 += kRunSplitNb)
+    ok = mlp_eval_bf16<kRunSplitNb, kRunMlpStages, 3>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, xs, kMaxDim,
+                                                      min(kRunSplitNb, n - b0), ls, tsm, ctx, list + b0);
   return ok;
 }
 
@@ -348,12 +370,14 @@ inline __device__ void mlp_reeval(const RunDesc& R, float* xbuf, float* lbuf, co
 template <int DMAX>
 __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& S, const float* s_W, const int* s_seed,
                                               const float* s_chol, float* xbuf, float* lbuf, int* rlist, char* msm,
-                                              MlpCtx* ctx, BlockScratch& BS, long long& ev_out, int& fl_out,
-                                              long long& re_out, int& err_out, long long& cyc_eval,
+                                              MlpCtx* ctx, int* mvlist, BlockScratch& BS, long long& ev_out,
+                                              int& fl_out, long long& re_out, int& err_out, long long& cyc_eval,
                                               long long& cyc_reeval) {
   constexpr int RW = dir_row(DMAX);
   const int tid = threadIdx.x, m = R.m, d = S.d;
   const bool bf16 = (R.precision == 1);
+  // FP32 re-evaluations on the tensor cores when the weights are BF16 values
+  const bool tc32 = bf16 && R.mlp_desc->w_bf16;
   char* tsm = align1024_shared(msm);
   float* act = reinterpret_cast<float*>(msm);
   float* xg = xbuf + (size_t)m * kMaxDim;  // kMlpF32Nb staging rows after the m walker rows
@@ -493,10 +517,15 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
       for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = 0.5f;
     // every walker finished while settling its proposals: no batch to evaluate
     if (!__syncthreads_or((moving || pend) ? 1 : 0)) break;
+    // the walkers holding a candidate, in thread order
+    int n_mv;
+    const int mpos = block_exclusive_scan(moving ? 1 : 0, BS, &n_mv);
+    if (moving) mvlist[mpos] = tid;
     __syncthreads();
     long long c0 = clock64();
     if (bf16) {
-      if (!mlp_batch_bf16(R, xbuf, m, lbuf, tsm, ctx)) err = 1;
+      __syncthreads();
+      if (n_mv > 0 && !mlp_batch_bf16(R, xbuf, n_mv, lbuf, tsm, ctx, mvlist)) err = 1;
       long long c1 = clock64();
       ce += c1 - c0;
       c0 = c1;
@@ -516,7 +545,11 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
       if (cnt > 0 && (cnt >= kMlpF32Nb || !still || age > R.reeval_defer)) {
         if (pend) rlist[pos] = tid;
         __syncthreads();
-        mlp_reeval(R, xbuf, lbuf, rlist, cnt, xg, lg, act);
+        if (tc32) {
+          if (!mlp_reeval_tc(R, xbuf, lbuf, rlist, cnt, tsm, ctx)) err = 1;
+        } else {
+          mlp_reeval(R, xbuf, lbuf, rlist, cnt, xg, lg, act);
+        }
         reevals += (tid == 0) ? cnt : 0;
         if (pend) {
           pend = false;
@@ -526,7 +559,8 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
       }
       cr += clock64() - c0;
     } else {
-      mlp_batch_f32(R, xbuf, m, lbuf, act);
+      __syncthreads();
+      if (n_mv > 0) mlp_batch_f32(R, xbuf, n_mv, lbuf, act, mvlist);
       ce += clock64() - c0;
       __syncthreads();
       if (moving) decide(in, in ? lbuf[tid] : -CUDART_INF_F, tp);
@@ -543,32 +577,53 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   if (bf16 && !err) {
     if (mine)
       for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = x[k];
+    if (tid < m) rlist[tid] = tid;
     __syncthreads();
-    mlp_batch_f32(R, xbuf, m, lbuf, act);
+    if (tc32) {
+      if (!mlp_reeval_tc(R, xbuf, lbuf, rlist, m, tsm, ctx)) err = 1;
+    } else {
+      mlp_batch_f32(R, xbuf, m, lbuf, act);
+    }
     if (mine) l = lbuf[tid];
     reevals += (tid == 0) ? m : 0;
-    // history: rows (walker, slot) with an in-box sample
-    int nh = mine ? hlen : 0;
+    // history samples: only Algorithm 2 (the history correction) reads them,
+    // and it takes a sample only above a relaxed threshold, which lies above
+    // W[0]; the samples within the margin of W[0] or above get their FP32
+    // value, the others are never read
+    const float thr0 = s_W[0];
+    const float lim = thr0 - fmaf(R.reeval_rel, fabsf(thr0), R.reeval_margin);
+    uint64_t want = 0ull;
+    int nh = 0;
+    if (mine && R.correction == 2)
+      for (int h = 0; h < hlen; ++h)
+        if (R.hist_l[(size_t)i * S.t_max + h] >= lim) {
+          want |= 1ull << h;
+          ++nh;
+        }
     int tot;
     const int base = block_exclusive_scan(nh, BS, &tot);
     for (int h0 = 0; h0 < tot; h0 += m) {
       // stage up to m history samples per pass in xbuf
       const int nb = min(m, tot - h0);
-      for (int h = 0; h < nh; ++h) {
-        const int gidx = base + h - h0;
+      for (int h = 0, j = 0; h < hlen; ++h) {
+        if (!((want >> h) & 1ull)) continue;
+        const int gidx = base + j++ - h0;
         if (gidx >= 0 && gidx < nb) {
           const float* hx = R.hist_x + ((size_t)i * S.t_max + h) * d;
           for (int k = 0; k < d; ++k) xbuf[(size_t)gidx * kMaxDim + k] = hx[k];
         }
       }
+      for (int q = tid; q < nb; q += blockDim.x) rlist[q] = q;
       __syncthreads();
-      mlp_batch_f32(R, xbuf, nb, lbuf, act);
-      for (int h = 0; h < nh; ++h) {
-        const int gidx = base + h - h0;
-        if (gidx >= 0 && gidx < nb) {
-          float* hl = R.hist_l + (size_t)i * S.t_max + h;
-          if (*hl > -CUDART_INF_F) *hl = lbuf[gidx];
-        }
+      if (tc32) {
+        if (!mlp_reeval_tc(R, xbuf, lbuf, rlist, nb, tsm, ctx)) err = 1;
+      } else {
+        mlp_batch_f32(R, xbuf, nb, lbuf, act);
+      }
+      for (int h = 0, j = 0; h < hlen; ++h) {
+        if (!((want >> h) & 1ull)) continue;
+        const int gidx = base + j++ - h0;
+        if (gidx >= 0 && gidx < nb) R.hist_l[(size_t)i * S.t_max + h] = lbuf[gidx];
       }
       __syncthreads();
       reevals += (tid == 0) ? nb : 0;
@@ -739,8 +794,8 @@ __global__ void NS_RUN_BOUNDS(MLP, DMAX) k_run(const RunDesc* __restrict__ runs,
     int fl = 0, werr = 0;
     SC.t = t;
     if constexpr (MLP) {
-      walker_phase_mlp<DMAX>(R, SC, s_W, s_seed, s_chol, s_xbuf, s_lbuf, s_rlist, s_mlp, &mlp_ctx, S, ev, fl, re, werr,
-                             cyc_eval, cyc_reeval);
+      walker_phase_mlp<DMAX>(R, SC, s_W, s_seed, s_chol, s_xbuf, s_lbuf, s_rlist, s_mlp, &mlp_ctx, s_list, S, ev, fl, re,
+                             werr, cyc_eval, cyc_reeval);
     } else {
       // every walker's rows of the iteration, spread over the whole block
       const long long cd = clock64();

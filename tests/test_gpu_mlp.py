@@ -187,3 +187,21 @@ def test_deferred_reevaluation_changes_nothing(nat):
             assert a["n_iter"] == b["n_iter"] and a["n_evals"] == b["n_evals"] and a["n_reeval"] == b["n_reeval"]
             np.testing.assert_array_equal(a["dead_l"], b["dead_l"])
             np.testing.assert_array_equal(a["dead_x"], b["dead_x"])
+
+
+@pytest.mark.parametrize("widths,n", [((27, 512, 512, 512, 512, 2000), 150), ((5, 128, 200, 300), 64),
+                                      ((3, 64, 100), 1), ((27, 512, 512, 512, 512, 2000), 33)])
+def test_mlp_fp32_accurate_tensor_path(nat, oracle, widths, n):
+    """precision 2 (three BF16 planes on the tensor cores) agrees with the FP64
+    oracle at FP32 accuracy, like the CUDA-core FP32 evaluator."""
+    p = _problem(widths, 3, unit_sigma=False)
+    img = _image(nat, p)
+    rng = np.random.default_rng(n + 11)
+    x = rng.uniform(0, 1, size=(n, p.d)).astype(np.float32)
+    x[0] = p.mlp.theta_star
+    out = torch.zeros(n, device="cuda")
+    nat.ns_mlp_loglike(p, img, torch.tensor(x, device="cuda"), out, precision=2)
+    torch.cuda.synchronize()
+    got = out.cpu().numpy().astype(np.float64)
+    want = oracle.loglike(oracle.Lik(p), x.astype(np.float64))
+    np.testing.assert_allclose(got, want, rtol=2e-5, atol=1e-3)
