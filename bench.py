@@ -295,9 +295,8 @@ def correction_sweep(n_seeds, n_live=1000):
 # the clustering tests of section 2.3 (Table 1)
 # --------------------------------------------------------------------------
 def clustering_tests(n_seeds, m=1, n_live=1000):
-    """Table 1: Test 1 (49 Gaussians, tree depth 6 in the paper, 3 here:
-    the library's deepest tree), Test 2 (two separated 10-D Gaussians, depth
-    1), Test 3 (Gaussian shell, depth 4 in the paper, 3 here), each with (+)
+    """Table 1: Test 1 (49 Gaussians, tree depth 6), Test 2 (two separated
+    10-D Gaussians, depth 1), Test 3 (Gaussian shell, depth 4), each with (+)
     and without (-) the cluster tree, re-clustering every 100 iterations,
     5 d slice steps; all seeds of one configuration in one batch."""
     import numpy as np
@@ -307,8 +306,8 @@ def clustering_tests(n_seeds, m=1, n_live=1000):
     from paper_2608_28514_gb300 import analytic
     from paper_2608_28514_gb300 import workloads as W
 
-    tests = (("test1_array49", W.array49(), 3), ("test2_bimodal10", W.bimodal(10), 1),
-             ("test3_shell", W.shell2d(), 3))
+    tests = (("test1_array49", W.array49(), 6), ("test2_bimodal10", W.bimodal(10), 1),
+             ("test3_shell", W.shell2d(), 4))
     out = {}
     for name, p, depth in tests:
         row = {"log_z_true": analytic.logz(p)}

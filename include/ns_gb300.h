@@ -47,7 +47,7 @@ extern "C" {
 #define NS_MAX_MODES 8         /* MIXTURE components */
 #define NS_MAX_GMM_MODES 64    /* GMM components */
 #define NS_GMM_CAPACITY 512    /* GMM: n_modes x (d rounded up to its register class) */
-#define NS_MAX_DEPTH 3         /* cluster tree depth: up to 8 leaves, 15 nodes */
+#define NS_MAX_DEPTH 6         /* cluster tree depth: up to 64 leaves, 127 nodes */
 #define NS_MAX_BATCH 256       /* m, walkers per run (one thread each) */
 #define NS_MAX_LIVE 65536      /* N_live per run */
 #define NS_MAX_HISTORY 64      /* history slots per walker */
@@ -360,13 +360,16 @@ ns_status ns_evidence_update(int N, int n, const float* dead_l, double* state, d
  * constant dropped), counts [n_nodes], split flags [n_nodes], accepted-leaf
  * mask [n_nodes] and each point's leaf cid [N].  n_nodes = 2^(depth+1) - 1.
  * scratch: ns_cluster_scratch_bytes(N, n_pad, d) bytes of device memory
- * (unused, may be NULL, at depth 0). */
+ * (unused, may be NULL, at depth 0): the whitened points and child bits,
+ * then room for the tree's FP64 node statistics when a deep tree of large
+ * d does not fit in shared memory. */
 ns_status ns_cluster(int N, int n_pad, int d, const float* live_x, const ns_options* opt,
                      uint64_t seed, uint32_t t, float* centres, float* chol, double* chol64,
                      float* logvol, int* count, int* split, int* mask, int* cid, void* scratch,
                      void* stream);
 
-/* Bytes of scratch that ns_cluster needs (0 for bad sizes). */
+/* Bytes of scratch that ns_cluster needs at any depth up to NS_MAX_DEPTH
+ * (0 for bad sizes). */
 size_t ns_cluster_scratch_bytes(int N, int n_pad, int d);
 
 /* a7, MLP likelihood (the emulator of section 5, replaced by a SiLU MLP and

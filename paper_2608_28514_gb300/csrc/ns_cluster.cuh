@@ -18,40 +18,55 @@
 
 namespace nsd {
 
-constexpr int kMaxLeaves = 8;
-constexpr int kRedW = 64;  // values per vector block reduction
+constexpr int kMaxLeaves = 64;  // depth <= 6
+constexpr int kRedW = 64;       // values per vector block reduction
 
+// Scratch of one tree build; L = 2^depth leaves, n_nodes = 2 L - 1.
 struct TreeScratch {
-  float* c;           // [2^D][d]: the two centres of each node of the current level (slot 2q+s)
+  float* c;           // [L][d]: the two centres of each node of the current level (slot 2q+s)
   float* red;         // [nwarps][kRedW] partial sums
   float* out;         // [kRedW] reduced sums
-  unsigned long long* far;  // [kMaxLeaves / 2]
-  int* cnt;           // [kMaxLeaves * 2]
+  unsigned long long* far;  // [L / 2] farthest-member keys of the current level
+  int* cnt;           // [2 L]: members per node of the level, then per (node, side) slot
   int* misc;          // [8]
-  double* leaf_mu;    // [kMaxLeaves][d]
-  double* node_mu;    // [15][d]
-  double* node_M2;    // [15][d*d]   (d*d: full symmetric, for the Cholesky)
-  int* node_n;        // [15]
-  unsigned* node_m2;  // [15] bits of the largest squared Mahalanobis distance
+  double* leaf_mu;    // [L][d]
+  double* node_mu;    // [n_nodes][d]
+  double* node_M2;    // [n_nodes][d*d]   (d*d: full symmetric, for the Cholesky)
+  int* node_n;        // [n_nodes]
+  unsigned* node_m2;  // [n_nodes] bits of the largest squared Mahalanobis distance
+  double* lv;         // [n_nodes] log volumes
+  double* veff;       // [n_nodes] effective (pruned) log volumes
+  int* spl;           // [n_nodes] accepted splits
   double* chol_work;  // per warp: [5 d d + d]
 };
+
+template <class F>
+__host__ __device__ inline size_t tree_layout(int d, int n_nodes, int nwarps, int nw_chol, F&& take) {
+  const int L = (n_nodes + 1) / 2;
+  take(0, sizeof(float) * L * d);
+  take(1, sizeof(float) * nwarps * kRedW);
+  take(2, sizeof(float) * kRedW);
+  take(3, sizeof(unsigned long long) * L);
+  take(4, sizeof(int) * L * 2);
+  take(5, sizeof(int) * 8);
+  take(6, sizeof(double) * L * d);
+  take(7, sizeof(double) * n_nodes * d);
+  take(8, sizeof(double) * (size_t)n_nodes * d * d);
+  take(9, sizeof(int) * n_nodes);
+  take(10, sizeof(unsigned) * n_nodes);
+  take(11, sizeof(double) * n_nodes);
+  take(12, sizeof(double) * n_nodes);
+  take(13, sizeof(int) * n_nodes);
+  return take(14, sizeof(double) * nw_chol * (5 * d * d + d));
+}
 
 __host__ __device__ inline size_t tree_bytes(int d, int n_nodes, int nwarps, int nw_chol) {
   if (n_nodes <= 1) return 0;
   size_t b = 0;
-  auto add = [&](size_t x) { b += (x + 15) & ~(size_t)15; };
-  add(sizeof(float) * kMaxLeaves * d);
-  add(sizeof(float) * nwarps * kRedW);
-  add(sizeof(float) * kRedW);
-  add(sizeof(unsigned long long) * kMaxLeaves);
-  add(sizeof(int) * kMaxLeaves * 2);
-  add(sizeof(int) * 8);
-  add(sizeof(double) * kMaxLeaves * d);
-  add(sizeof(double) * 15 * d);
-  add(sizeof(double) * 15 * d * d);
-  add(sizeof(int) * 15);
-  add(sizeof(unsigned) * 15);
-  add(sizeof(double) * nw_chol * (5 * d * d + d));
+  tree_layout(d, n_nodes, nwarps, nw_chol, [&](int, size_t x) {
+    b += (x + 15) & ~(size_t)15;
+    return b;
+  });
   return b;
 }
 
@@ -64,26 +79,30 @@ __host__ __device__ inline int tree_chol_warps(int d, int nwarps) {
   return w < nwarps ? w : nwarps;
 }
 
-__device__ inline TreeScratch tree_carve(char* base, int d, int nwarps, int nw_chol) {
-  TreeScratch T;
+__device__ inline TreeScratch tree_carve(char* base, int d, int n_nodes, int nwarps, int nw_chol) {
+  char* p[15];
   size_t o = 0;
-  auto take = [&](size_t x) {
-    char* p = base + o;
+  tree_layout(d, n_nodes, nwarps, nw_chol, [&](int k, size_t x) {
+    p[k] = base + o;
     o += (x + 15) & ~(size_t)15;
-    return p;
-  };
-  T.c = reinterpret_cast<float*>(take(sizeof(float) * kMaxLeaves * d));
-  T.red = reinterpret_cast<float*>(take(sizeof(float) * nwarps * kRedW));
-  T.out = reinterpret_cast<float*>(take(sizeof(float) * kRedW));
-  T.far = reinterpret_cast<unsigned long long*>(take(sizeof(unsigned long long) * kMaxLeaves));
-  T.cnt = reinterpret_cast<int*>(take(sizeof(int) * kMaxLeaves * 2));
-  T.misc = reinterpret_cast<int*>(take(sizeof(int) * 8));
-  T.leaf_mu = reinterpret_cast<double*>(take(sizeof(double) * kMaxLeaves * d));
-  T.node_mu = reinterpret_cast<double*>(take(sizeof(double) * 15 * d));
-  T.node_M2 = reinterpret_cast<double*>(take(sizeof(double) * 15 * d * d));
-  T.node_n = reinterpret_cast<int*>(take(sizeof(int) * 15));
-  T.node_m2 = reinterpret_cast<unsigned*>(take(sizeof(unsigned) * 15));
-  T.chol_work = reinterpret_cast<double*>(take(sizeof(double) * nw_chol * (5 * d * d + d)));
+    return o;
+  });
+  TreeScratch T;
+  T.c = reinterpret_cast<float*>(p[0]);
+  T.red = reinterpret_cast<float*>(p[1]);
+  T.out = reinterpret_cast<float*>(p[2]);
+  T.far = reinterpret_cast<unsigned long long*>(p[3]);
+  T.cnt = reinterpret_cast<int*>(p[4]);
+  T.misc = reinterpret_cast<int*>(p[5]);
+  T.leaf_mu = reinterpret_cast<double*>(p[6]);
+  T.node_mu = reinterpret_cast<double*>(p[7]);
+  T.node_M2 = reinterpret_cast<double*>(p[8]);
+  T.node_n = reinterpret_cast<int*>(p[9]);
+  T.node_m2 = reinterpret_cast<unsigned*>(p[10]);
+  T.lv = reinterpret_cast<double*>(p[11]);
+  T.veff = reinterpret_cast<double*>(p[12]);
+  T.spl = reinterpret_cast<int*>(p[13]);
+  T.chol_work = reinterpret_cast<double*>(p[14]);
   return T;
 }
 
@@ -180,7 +199,7 @@ struct TreeIO {
   int* s_mask;      // smem [n_nodes]
 };
 
-inline __device__ void cluster_tree(const TreeIO& io, const TreeScratch& T, BlockScratch& S, int nw_chol) {
+inline __device__ __noinline__ void cluster_tree(const TreeIO& io, const TreeScratch& T, BlockScratch& S, int nw_chol) {
   const int tid = threadIdx.x, B = blockDim.x, lane = tid & 31, wid = tid >> 5;
   const int d = io.d, N = io.N, D = io.depth, n_nodes = (1 << (D + 1)) - 1;
   const int n_leaves = 1 << D;
@@ -200,7 +219,7 @@ inline __device__ void cluster_tree(const TreeIO& io, const TreeScratch& T, Bloc
   for (int lev = 0; lev < D; ++lev) {
     const int first = (1 << lev) - 1, nlev = 1 << lev;
     // members per node of this level
-    for (int q = tid; q < kMaxLeaves * 2; q += B) T.cnt[q] = 0;
+    for (int q = tid; q < 2 * n_leaves; q += B) T.cnt[q] = 0;
     __syncthreads();
     for (int j = tid; j < N; j += B) atomicAdd(&T.cnt[node_at(io.side[j], lev) - first], 1);
     __syncthreads();
@@ -284,8 +303,8 @@ inline __device__ void cluster_tree(const TreeIO& io, const TreeScratch& T, Bloc
       if (!any) break;
       // exact member counts of the (node, side) slots
       const int slots = 2 * nlev;
-      int* scount = T.cnt + kMaxLeaves;
-      if (tid < slots) scount[tid] = 0;
+      int* scount = T.cnt + n_leaves;
+      for (int q = tid; q < slots; q += B) scount[q] = 0;
       __syncthreads();
       for (int j = tid; j < N; j += B) {
         const int bits = io.side[j];
@@ -293,31 +312,35 @@ inline __device__ void cluster_tree(const TreeIO& io, const TreeScratch& T, Bloc
         if (T.cnt[q] >= 2) atomicAdd(&scount[2 * q + ((bits >> lev) & 1)], 1);
       }
       __syncthreads();
-      // centre sums per slot, four dimensions at a time; a slot left empty
-      // keeps its centre
-      for (int c0 = 0; c0 < d; c0 += 4) {
-        float acc[kRedW];
+      // centre sums per slot, 16 slots x four dimensions at a time; a slot
+      // left empty keeps its centre
+      constexpr int kSl = kRedW / 4;
+      for (int s0 = 0; s0 < slots; s0 += kSl) {
+        for (int c0 = 0; c0 < d; c0 += 4) {
+          float acc[kRedW];
 #pragma unroll
-        for (int k = 0; k < kRedW; ++k) acc[k] = 0.f;
-        for (int j = tid; j < N; j += B) {
-          const int bits = io.side[j];
-          const int slot = 2 * (node_at(bits, lev) - first) + ((bits >> lev) & 1);
-          float v4[4];
+          for (int k = 0; k < kRedW; ++k) acc[k] = 0.f;
+          for (int j = tid; j < N; j += B) {
+            const int bits = io.side[j];
+            const int slot = 2 * (node_at(bits, lev) - first) + ((bits >> lev) & 1) - s0;
+            float v4[4];
 #pragma unroll
-          for (int k = 0; k < 4; ++k) v4[k] = (c0 + k < d) ? io.y[(size_t)(c0 + k) * io.n_pad + j] : 0.f;
+            for (int k = 0; k < 4; ++k) v4[k] = (c0 + k < d) ? io.y[(size_t)(c0 + k) * io.n_pad + j] : 0.f;
 #pragma unroll
-          for (int sl = 0; sl < kRedW / 4; ++sl)
-            if (sl == slot) {
+            for (int sl = 0; sl < kSl; ++sl)
+              if (sl == slot) {
 #pragma unroll
-              for (int k = 0; k < 4; ++k) acc[sl * 4 + k] += v4[k];
-            }
+                for (int k = 0; k < 4; ++k) acc[sl * 4 + k] += v4[k];
+              }
+          }
+          block_sum_vec(acc, T);
+          for (int sl = tid; sl < kSl && s0 + sl < slots; sl += B) {
+            const int gs = s0 + sl;
+            if (T.cnt[gs / 2] < 2 || scount[gs] == 0) continue;
+            for (int k = 0; k < 4 && c0 + k < d; ++k) T.c[gs * d + c0 + k] = T.out[sl * 4 + k] / (float)scount[gs];
+          }
+          __syncthreads();
         }
-        block_sum_vec(acc, T);
-        for (int sl = tid; sl < slots; sl += B) {
-          if (T.cnt[sl / 2] < 2 || scount[sl] == 0) continue;
-          for (int k = 0; k < 4 && c0 + k < d; ++k) T.c[sl * d + c0 + k] = T.out[sl * 4 + k] / (float)scount[sl];
-        }
-        __syncthreads();
       }
     }
     // nodes with fewer than two members keep every member in the first child
@@ -327,78 +350,87 @@ inline __device__ void cluster_tree(const TreeIO& io, const TreeScratch& T, Bloc
   const int last_first = n_leaves - 1;
   const int ne = d * (d + 1) / 2;
   // counts per leaf
-  for (int q = tid; q < kMaxLeaves * 2; q += B) T.cnt[q] = 0;
+  for (int q = tid; q < 2 * n_leaves; q += B) T.cnt[q] = 0;
   __syncthreads();
   for (int j = tid; j < N; j += B) atomicAdd(&T.cnt[node_at(io.side[j], D) - last_first], 1);
   __syncthreads();
-  // leaf means (sums relative to the root mean, FP32 per thread, FP64 after)
-  for (int c0 = 0; c0 < d; c0 += 8) {
-    float acc[kRedW];
+  // leaf means (sums relative to the root mean, FP32 per thread, FP64 after),
+  // eight leaves x eight dimensions at a time
+  constexpr int kLf = kRedW / 8;
+  for (int l0 = 0; l0 < n_leaves; l0 += kLf) {
+    for (int c0 = 0; c0 < d; c0 += 8) {
+      float acc[kRedW];
 #pragma unroll
-    for (int k = 0; k < kRedW; ++k) acc[k] = 0.f;
-    for (int j = tid; j < N; j += B) {
-      const int lf = node_at(io.side[j], D) - last_first;
-      float v8[8];
+      for (int k = 0; k < kRedW; ++k) acc[k] = 0.f;
+      for (int j = tid; j < N; j += B) {
+        const int lf = node_at(io.side[j], D) - last_first - l0;
+        float v8[8];
 #pragma unroll
-      for (int k = 0; k < 8; ++k) v8[k] = (c0 + k < d) ? io.x[(size_t)(c0 + k) * io.n_pad + j] - io.s_cent[c0 + k] : 0.f;
+        for (int k = 0; k < 8; ++k)
+          v8[k] = (c0 + k < d) ? io.x[(size_t)(c0 + k) * io.n_pad + j] - io.s_cent[c0 + k] : 0.f;
 #pragma unroll
-      for (int l = 0; l < kMaxLeaves; ++l)
-        if (l == lf) {
+        for (int l = 0; l < kLf; ++l)
+          if (l == lf) {
 #pragma unroll
-          for (int k = 0; k < 8; ++k) acc[l * 8 + k] += v8[k];
-        }
-    }
-    block_sum_vec(acc, T);
-    for (int q = tid; q < n_leaves * 8; q += B) {
-      const int l = q / 8, k = q % 8;
-      if (c0 + k < d) {
-        const int n = T.cnt[l];
-        T.leaf_mu[l * d + c0 + k] = n > 0 ? (double)T.out[l * 8 + k] / n + (double)io.s_cent[c0 + k] : 0.0;
+            for (int k = 0; k < 8; ++k) acc[l * 8 + k] += v8[k];
+          }
       }
+      block_sum_vec(acc, T);
+      for (int q = tid; q < kLf * 8; q += B) {
+        const int l = q / 8, k = q % 8;
+        if (l0 + l < n_leaves && c0 + k < d) {
+          const int n = T.cnt[l0 + l];
+          T.leaf_mu[(l0 + l) * d + c0 + k] =
+              n > 0 ? (double)T.out[l * 8 + k] / n + (double)io.s_cent[c0 + k] : 0.0;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
-  // leaf centred products, eight entries at a time
-  for (int e0 = 0; e0 < ne; e0 += 8) {
-    float acc[kRedW];
+  // leaf centred products, eight leaves x eight entries at a time
+  for (int l0 = 0; l0 < n_leaves; l0 += kLf) {
+    for (int e0 = 0; e0 < ne; e0 += 8) {
+      float acc[kRedW];
 #pragma unroll
-    for (int k = 0; k < kRedW; ++k) acc[k] = 0.f;
-    int ea[8], eb[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) {
-      int e = e0 + k, a = 0;
-      if (e >= ne) e = 0;
-      while ((a + 1) * (a + 2) / 2 <= e) ++a;
-      ea[k] = a;
-      eb[k] = e - a * (a + 1) / 2;
-    }
-    for (int j = tid; j < N; j += B) {
-      const int lf = node_at(io.side[j], D) - last_first;
-      float p8[8];
+      for (int k = 0; k < kRedW; ++k) acc[k] = 0.f;
+      int ea[8], eb[8];
 #pragma unroll
       for (int k = 0; k < 8; ++k) {
-        const float ua = io.x[(size_t)ea[k] * io.n_pad + j] - (float)T.leaf_mu[lf * d + ea[k]];
-        const float ub = io.x[(size_t)eb[k] * io.n_pad + j] - (float)T.leaf_mu[lf * d + eb[k]];
-        p8[k] = (e0 + k < ne) ? ua * ub : 0.f;
+        int e = e0 + k, a = 0;
+        if (e >= ne) e = 0;
+        while ((a + 1) * (a + 2) / 2 <= e) ++a;
+        ea[k] = a;
+        eb[k] = e - a * (a + 1) / 2;
       }
+      for (int j = tid; j < N; j += B) {
+        const int lf = node_at(io.side[j], D) - last_first - l0;
+        if (lf < 0 || lf >= kLf) continue;
+        float p8[8];
 #pragma unroll
-      for (int l = 0; l < kMaxLeaves; ++l)
-        if (l == lf) {
-#pragma unroll
-          for (int k = 0; k < 8; ++k) acc[l * 8 + k] += p8[k];
+        for (int k = 0; k < 8; ++k) {
+          const float ua = io.x[(size_t)ea[k] * io.n_pad + j] - (float)T.leaf_mu[(l0 + lf) * d + ea[k]];
+          const float ub = io.x[(size_t)eb[k] * io.n_pad + j] - (float)T.leaf_mu[(l0 + lf) * d + eb[k]];
+          p8[k] = (e0 + k < ne) ? ua * ub : 0.f;
         }
-    }
-    block_sum_vec(acc, T);
-    for (int q = tid; q < n_leaves * 8; q += B) {
-      const int l = q / 8, k = q % 8;
-      if (e0 + k < ne) {
-        const int nd = last_first + l;
-        const double v = (double)T.out[l * 8 + k];
-        T.node_M2[nd * d * d + ea[k] * d + eb[k]] = v;
-        T.node_M2[nd * d * d + eb[k] * d + ea[k]] = v;
+#pragma unroll
+        for (int l = 0; l < kLf; ++l)
+          if (l == lf) {
+#pragma unroll
+            for (int k = 0; k < 8; ++k) acc[l * 8 + k] += p8[k];
+          }
       }
+      block_sum_vec(acc, T);
+      for (int q = tid; q < kLf * 8; q += B) {
+        const int l = q / 8, k = q % 8;
+        if (l0 + l < n_leaves && e0 + k < ne) {
+          const int nd = last_first + l0 + l;
+          const double v = (double)T.out[l * 8 + k];
+          T.node_M2[(size_t)nd * d * d + ea[k] * d + eb[k]] = v;
+          T.node_M2[(size_t)nd * d * d + eb[k] * d + ea[k]] = v;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
   }
   for (int q = tid; q < n_leaves; q += B) {
     const int nd = last_first + q;
@@ -453,7 +485,7 @@ inline __device__ void cluster_tree(const TreeIO& io, const TreeScratch& T, Bloc
   }
   __syncthreads();
   // ---- bounding ellipsoids: largest squared Mahalanobis distance per node ---
-  for (int q = tid; q < 15; q += B) T.node_m2[q] = 0u;
+  for (int q = tid; q < n_nodes; q += B) T.node_m2[q] = 0u;
   __syncthreads();
   for (int j = tid; j < N; j += B) {
     const int bits = io.side[j];
@@ -473,46 +505,47 @@ inline __device__ void cluster_tree(const TreeIO& io, const TreeScratch& T, Bloc
     }
   }
   __syncthreads();
-  // ---- volumes, pruning bottom-up, accepted leaves (one thread) ------------
+  // ---- volumes, pruning bottom-up, accepted leaves --------------------------
+  for (int nd = tid; nd < n_nodes; nd += B) {
+    const int n = T.node_n[nd];
+    double l = 0.0;
+    for (int i = 0; i < d; ++i) l += log((double)io.s_chol[(size_t)nd * d * d + i * d + i]);
+    const double m2 = (double)__uint_as_float(T.node_m2[nd]);
+    T.lv[nd] = (n > 0) ? l + 0.5 * d * log(m2) : -CUDART_INF;
+  }
+  __syncthreads();
   if (tid == 0) {
-    double lv[15], veff[15];
-    int spl[15], act[15];
-    for (int nd = 0; nd < n_nodes; ++nd) {
-      const int n = T.node_n[nd];
-      double l = 0.0;
-      for (int i = 0; i < d; ++i) l += log((double)io.s_chol[nd * d * d + i * d + i]);
-      const double m2 = (double)__uint_as_float(T.node_m2[nd]);
-      lv[nd] = (n > 0) ? l + 0.5 * d * log(m2) : -CUDART_INF;
-    }
     for (int nd = n_nodes - 1; nd >= 0; --nd) {
       const int c1 = 2 * nd + 1, c2 = 2 * nd + 2;
       if (c1 >= n_nodes) {
-        spl[nd] = 0;
-        veff[nd] = lv[nd];
+        T.spl[nd] = 0;
+        T.veff[nd] = T.lv[nd];
         continue;
       }
-      const double vc = logaddexp_d(veff[c1], veff[c2]);
-      const int ok = T.node_n[c1] > io.n_min && T.node_n[c2] > io.n_min && vc < log(1.0 - (double)io.vol_frac) + lv[nd];
-      spl[nd] = ok;
-      veff[nd] = ok ? vc : lv[nd];
+      const double vc = logaddexp_d(T.veff[c1], T.veff[c2]);
+      const int ok =
+          T.node_n[c1] > io.n_min && T.node_n[c2] > io.n_min && vc < log(1.0 - (double)io.vol_frac) + T.lv[nd];
+      T.spl[nd] = ok;
+      T.veff[nd] = ok ? vc : T.lv[nd];
     }
-    for (int nd = 0; nd < n_nodes; ++nd) {
-      act[nd] = nd == 0 ? 1 : (act[(nd - 1) / 2] && spl[(nd - 1) / 2]);
-      const int mk = act[nd] && !spl[nd];
-      io.s_mask[nd] = mk;
-      io.mask[nd] = mk;
-      io.split[nd] = spl[nd];
-      io.count[nd] = T.node_n[nd];
-      io.logvol[nd] = (float)lv[nd];
-    }
-    for (int nd = 0; nd < n_nodes; ++nd) S.iw[nd] = spl[nd];
+  }
+  __syncthreads();
+  for (int nd = tid; nd < n_nodes; nd += B) {
+    int act = 1;  // every ancestor split
+    for (int k = nd; k > 0; k = (k - 1) / 2) act &= T.spl[(k - 1) / 2];
+    const int mk = act && !T.spl[nd];
+    io.s_mask[nd] = mk;
+    io.mask[nd] = mk;
+    io.split[nd] = T.spl[nd];
+    io.count[nd] = T.node_n[nd];
+    io.logvol[nd] = (float)T.lv[nd];
   }
   __syncthreads();
   // ---- each point's accepted leaf --------------------------------------------
   for (int j = tid; j < N; j += B) {
     const int bits = io.side[j];
     int nd = 0, lev = 0;
-    while (lev < D && S.iw[nd]) {
+    while (lev < D && T.spl[nd]) {
       nd = 2 * nd + 1 + ((bits >> lev) & 1);
       ++lev;
     }

@@ -13,8 +13,8 @@ namespace nsd {
 
 constexpr int kMaxDim = 32;
 constexpr int kMaxModes = 8;
-constexpr int kMaxDepth = 3;
-constexpr int kMaxNodes = 15;
+constexpr int kMaxDepth = 6;
+constexpr int kMaxNodes = 127;
 constexpr int kMaxHistory = 64;
 constexpr uint32_t kPurposeSeed = 0x10000u;
 constexpr uint32_t kPurposeKmeans = 0x20000u;

@@ -110,7 +110,7 @@ __global__ void k_evidence(int N, int n, const float* __restrict__ l, double* st
 __global__ void k_cluster(RunDesc R, uint32_t t) {
   extern __shared__ __align__(16) char sm[];
   __shared__ BlockScratch S;
-  const Carve cv = make_carve(R.d, 1, R.n_nodes, kMaxDim);
+  const Carve cv = make_carve(R.d, 1, R.n_nodes, kMaxDim, false, R.spill != 0);
   cluster_phase(R, t, sm, cv, S);
 }
 
@@ -186,9 +186,13 @@ constexpr size_t kRunSmemBudget = 227 * 1024 - 2048;
 // A run whose cluster tables do not fit in shared memory keeps them in
 // global memory (make_carve's spill).
 bool run_spills(const ns_problem& p, int n_nodes) {
-  if (p.lik->kind == NS_LIK_MLP) return false;
-  return make_carve(p.d, p.m, n_nodes, dmax_class(p.d), false, false).total > kRunSmemBudget;
+  const bool mlp = p.lik->kind == NS_LIK_MLP;
+  return make_carve(p.d, p.m, n_nodes, dmax_class(p.d), mlp, false).total > kRunSmemBudget;
 }
+
+// Global tree scratch of a spilled run, sized for the widest block (the MLP
+// run kernel's warps).
+size_t tree_ws_bytes(int d, int n_nodes) { return tree_bytes(d, n_nodes, kMlpThreads / 32, tree_chol_warps(d, 8)); }
 
 // FNV-1a over the shape of a batch (what fixes the arena layout): a
 // checkpoint restores only into a handle of the same shape.
@@ -613,7 +617,7 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     o.split = take(sizeof(int) * n_nodes);
     o.mask = take(sizeof(int) * n_nodes);
     o.spill = run_spills(p, n_nodes) ? 1 : 0;
-    o.tree_ws = o.spill ? take(tree_bytes(d, n_nodes, 8, tree_chol_warps(d, 8))) : 0;
+    o.tree_ws = o.spill ? take(tree_ws_bytes(d, n_nodes)) : 0;
     HostRun& hr = h->host[r];
     hr.d = d;
     hr.N = N;
@@ -1143,6 +1147,8 @@ ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt_in, fl
                o_chol = take(sizeof(float) * n_nodes * d * d), o_chol64 = take(sizeof(double) * n_nodes * d * d),
                o_logvol = take(sizeof(float) * n_nodes), o_count = take(sizeof(int) * n_nodes),
                o_split = take(sizeof(int) * n_nodes), o_mask = take(sizeof(int) * n_nodes);
+  const bool spill = run_spills(p, n_nodes);
+  const size_t o_tree = take(spill ? tree_ws_bytes(d, n_nodes) : 16);
   if (total > (size_t)NS_NOALLOC_SCRATCH_BYTES) {
     set_err(nullptr, "ns_run_noalloc: this run needs %zu bytes of working memory; the static array holds %u",
             total, (unsigned)NS_NOALLOC_SCRATCH_BYTES);
@@ -1215,6 +1221,8 @@ ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt_in, fl
   R.count = reinterpret_cast<int*>(base + o_count);
   R.split = reinterpret_cast<int*>(base + o_split);
   R.mask = reinterpret_cast<int*>(base + o_mask);
+  R.spill = spill ? 1 : 0;
+  R.tree_ws = spill ? base + o_tree : nullptr;
   R.st = reinterpret_cast<RunState*>(base + o_state);
   const LikParams P = make_lik(*p.lik, p.lo, p.hi, d);
   const int id0 = 0;
@@ -1228,7 +1236,7 @@ ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt_in, fl
   const RunDesc* d_desc = reinterpret_cast<const RunDesc*>(base + o_desc);
   const int* d_ids = reinterpret_cast<const int*>(base + o_ids);
   const int block = block_for_m(m);
-  const size_t smem = make_carve(d, m, n_nodes, dmax_class(d)).total;
+  const size_t smem = make_carve(d, m, n_nodes, dmax_class(d), false, spill).total;
   const int chunk = opt.chunk_iters > 0 ? opt.chunk_iters : 1000;
   const long long max_rounds = opt.max_iter / chunk + 2;
   RunState hs;
@@ -1410,9 +1418,16 @@ ns_status ns_evidence_update(int N, int n, const float* dead_l, double* state, d
   return NS_OK;
 }
 
+// The whitened points and child bits, then (16-byte aligned) the tree
+// scratch of the deepest tree, used when a tree's tables do not fit in
+// shared memory.
+size_t cluster_points_bytes(int N, int n_pad, int d) {
+  return al16(sizeof(float) * (size_t)d * n_pad + sizeof(int) * (size_t)N);
+}
+
 size_t ns_cluster_scratch_bytes(int N, int n_pad, int d) {
   if (N < 2 || n_pad < N || d < 1 || d > NS_MAX_DIM) return 0;
-  return sizeof(float) * (size_t)d * n_pad + sizeof(int) * (size_t)N;
+  return cluster_points_bytes(N, n_pad, d) + tree_ws_bytes(d, (1 << (NS_MAX_DEPTH + 1)) - 1);
 }
 
 ns_status ns_cluster(int N, int n_pad, int d, const float* live_x, const ns_options* opt_in, uint64_t seed,
@@ -1454,7 +1469,11 @@ ns_status ns_cluster(int N, int n_pad, int d, const float* live_x, const ns_opti
     R.wsp = static_cast<float*>(scratch);
     R.side = reinterpret_cast<int*>(static_cast<char*>(scratch) + sizeof(float) * (size_t)d * n_pad);
   }
-  const size_t smem = make_carve(d, 1, R.n_nodes, kMaxDim).total;
+  if (opt.depth > 0 && make_carve(d, 1, R.n_nodes, kMaxDim).total > 227 * 1024) {
+    R.spill = 1;
+    R.tree_ws = static_cast<char*>(scratch) + cluster_points_bytes(N, n_pad, d);
+  }
+  const size_t smem = make_carve(d, 1, R.n_nodes, kMaxDim, false, R.spill != 0).total;
   if (smem > 227 * 1024) {
     set_err(nullptr, "ns_cluster: %zu bytes of shared memory needed (limit 227 KB)", smem);
     return NS_ERR_ARG;

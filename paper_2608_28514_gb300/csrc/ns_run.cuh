@@ -83,8 +83,8 @@ using RunMlpSmem = MlpSmem<kMlpNbMax, kRunMlpStages>;
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
-// spill: the run's cluster tables do not fit next to the rest (large d at
-// depth 3); the Cholesky factors and the tree scratch then stay in global
+// spill: the run's cluster tables do not fit next to the rest (large d or a
+// deep tree); the Cholesky factors and the tree scratch then stay in global
 // memory (only the clustering and the direction draws read them).
 __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax, bool mlp = false,
                                             bool spill = false) {
@@ -97,7 +97,7 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax,
   };
   const size_t cand_bytes = (sizeof(float) * 2 + sizeof(int) * 3) * 2 * m + 64;
   c.chol_global = mlp || spill;
-  c.tree_global = spill && !mlp;
+  c.tree_global = spill;
   c.lik = take(mlp ? 0 : sizeof(LikParams));
   c.scr = take(sizeof(BlockScratch));
   c.sel = take(sizeof(SelectScratch));
@@ -222,7 +222,7 @@ inline __device__ void cluster_phase(const RunDesc& R, uint32_t t, char* sm, con
   }
   const int nw = blockDim.x >> 5;
   const int nw_chol = tree_chol_warps(d, 8) < nw ? tree_chol_warps(d, 8) : nw;
-  const TreeScratch T = tree_carve(cv.tree_global ? R.tree_ws : sm + cv.tree, d, nw, tree_chol_warps(d, 8));
+  const TreeScratch T = tree_carve(cv.tree_global ? R.tree_ws : sm + cv.tree, d, R.n_nodes, nw, tree_chol_warps(d, 8));
   if (threadIdx.x == 0) T.node_n[0] = n;
   __syncthreads();
   TreeIO io;

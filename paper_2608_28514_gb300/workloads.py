@@ -241,3 +241,24 @@ def batched_runs(n_runs, seed=0, d_lo=2, d_hi=30, n_lo=100, n_hi=2000, frac=0.05
             p = mixture(d, rs)
         out.append((p, N, m, rs))
     return out
+
+
+
+def separated_blobs(n_blobs, d, per, seed, sd=0.005, min_sep=0.1, lo=0.2, hi=0.8):
+    """Point sets for the cluster tree (section 2.1): n_blobs equally
+    populated isotropic Gaussian blobs (spread sd) with centres uniform in
+    [lo, hi]^d, redrawn until every pair is at least min_sep apart.  Returns
+    x [n_blobs * per][d] in unit-cube coordinates (shuffled) and the blob
+    label of each point."""
+    rng = np.random.default_rng(seed)
+    for _ in range(10000):
+        c = rng.uniform(lo, hi, size=(n_blobs, d))
+        dist = np.linalg.norm(c[:, None, :] - c[None, :, :], axis=-1)
+        if np.all(dist[np.triu_indices(n_blobs, 1)] >= min_sep):
+            break
+    else:
+        raise RuntimeError("separated_blobs: no layout found")
+    labels = np.repeat(np.arange(n_blobs), per)
+    x = c[labels] + sd * rng.standard_normal((n_blobs * per, d))
+    perm = rng.permutation(len(x))
+    return x[perm], labels[perm]

@@ -62,7 +62,7 @@ def test_loglike_matches_oracle(nat, oracle, maker):
     assert np.all(np.abs(got - want) <= tol), np.max(np.abs(got - want) / tol)
 
 
-CASES = {"array49_d2": (W.array49, 3), "bimodal_d10": (lambda: W.bimodal(10), 1), "shell_d2": (W.shell2d, 3)}
+CASES = {"array49_d2": (W.array49, 6), "bimodal_d10": (lambda: W.bimodal(10), 1), "shell_d2": (W.shell2d, 4)}
 
 
 @pytest.mark.parametrize("name", sorted(CASES))

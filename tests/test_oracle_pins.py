@@ -426,6 +426,60 @@ def test_four_modes_found_at_depth_three(oracle):
     assert out["n_leaves"] == 4
 
 
+def test_deep_tree_top_equals_shallow_tree(oracle):
+    """The tree is built top-down level by level, so a depth-6 tree's first
+    15 nodes (levels 0-3) carry exactly the partition, centres, factors and
+    volumes of the depth-3 tree on the same points and stream; only the
+    pruning, which looks at the deeper levels, may differ."""
+    x, _ = W.separated_blobs(16, 3, 40, 2)
+    deep = oracle.cluster(x, oracle.opts(3, 1, depth=6), 9, 0)
+    shallow = oracle.cluster(x, oracle.opts(3, 1, depth=3), 9, 0)
+    for k in ("count", "centres", "chol", "logvol"):
+        np.testing.assert_array_equal(deep[k][:15], shallow[k][:15], err_msg=k)
+    assert deep["split"][:15].sum() > shallow["split"].sum()
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_deep_tree_finds_twelve_blobs(oracle, seed):
+    """Twelve tight blobs (spread 0.005, centres >= 0.1 apart, 60 points
+    each) in 2-D at depth 6 (64 possible leaves): the pruned tree keeps
+    exactly one leaf per blob -- every split between blobs shrinks the
+    bounding volumes by far more than half, no split of a single Gaussian
+    blob does."""
+    x, lab = W.separated_blobs(12, 2, 60, seed)
+    out = oracle.cluster(x, oracle.opts(2, 1, depth=6), 5 + seed, 0)
+    a = out["assign"]
+    leaves = np.flatnonzero(out["mask"])
+    assert out["n_leaves"] == 12 and len(leaves) == 12
+    assert all(len(set(lab[a == lf])) == 1 for lf in leaves)
+    assert len({lab[a == lf][0] for lf in leaves}) == 12
+
+
+def test_deep_tree_bookkeeping(oracle):
+    """Depth 6: children's counts add up to the parent's, the accepted
+    leaves are the nodes whose ancestors all split and which do not split,
+    every point sits in an accepted leaf, and a split needs more than n_min
+    points on both sides."""
+    x, _ = W.separated_blobs(20, 3, 50, 4)
+    o = oracle.opts(3, 1, depth=6)
+    out = oracle.cluster(x, o, 11, 0)
+    cnt, spl, mask = out["count"], out["split"], out["mask"]
+    n_min = o.n_min if o.n_min > 0 else 3 + 1
+    assert cnt[0] == len(x)
+    for nd in range(63):
+        assert cnt[nd] == cnt[2 * nd + 1] + cnt[2 * nd + 2]
+        if spl[nd]:
+            assert cnt[2 * nd + 1] > n_min and cnt[2 * nd + 2] > n_min
+    for nd in range(127):
+        act, k = 1, nd
+        while k > 0:
+            k = (k - 1) // 2
+            act &= spl[k]
+        assert mask[nd] == (act and not spl[nd])
+    assert np.all(mask[out["assign"]] == 1)
+    assert np.bincount(out["assign"], minlength=127)[mask == 1].tolist() == cnt[mask == 1].tolist()
+
+
 # --------------------------------------------------------------------------
 # whole runs
 # --------------------------------------------------------------------------
