@@ -114,6 +114,9 @@ typedef struct {
     double reeval_rel;    /*   reeval_margin + reeval_rel |threshold| (2.0 and 4e-3) */
     int reeval_defer;     /* MLP only: rounds a near-threshold candidate may wait so that several are
                            * re-evaluated in one FP32 pass, 0..64 (4; 0 = at once); results do not depend on it */
+    int walker_mapping;   /* analytic likelihoods: 0 one walker per thread (default), 1 one walker per warp
+                           * (the lanes share the coordinates); ns_autotune picks per run.  The mappings take
+                           * the same decisions and draws; only the order of the FP32 sums in log L differs */
 } ns_options;
 
 /* One run of a batch. */
@@ -151,6 +154,18 @@ typedef struct {
 } ns_result_t;
 
 /* ---- whole runs ------------------------------------------------------- */
+
+/* Batching (spec: the walker-to-warp mapping is picked by an
+ * autotuner): for every analytic run of a handle that has not run yet (or
+ * was reset), run `iters` iterations (1..1000) with one walker per thread,
+ * then with one walker per warp, each from the run's initial live set;
+ * compare the run's SM cycles per iteration in the slice phase (a4-a7) and
+ * keep the faster mapping for that run; then reset the handle (ns_reset), so
+ * that ns_run starts every run afresh with its chosen mapping.  out_warp
+ * [n_runs] (host, may be NULL) receives each run's choice (1 = per warp; MLP
+ * runs keep their lock-step walkers and report 0).  The choice is not part of
+ * a checkpoint.  NS_ERR_STATE if the handle has run. */
+ns_status ns_autotune(ns_handle* h, int iters, int* out_warp, void* stream);
 
 /* Fill `opt` with the defaults listed above. */
 ns_status ns_default_options(ns_options* opt);

@@ -46,6 +46,7 @@ class NsOptions(C.Structure):
         ("e_max", C.c_int), ("s_max", C.c_int), ("width", C.c_double), ("max_iter", C.c_longlong),
         ("dead_cap", C.c_longlong), ("chunk_iters", C.c_int), ("precision", C.c_int),
         ("reeval_margin", C.c_double), ("reeval_rel", C.c_double), ("reeval_defer", C.c_int),
+        ("walker_mapping", C.c_int),
     ]
 
 
@@ -93,6 +94,7 @@ def lib():
     L.ns_run.argtypes = [_vp, _vp]
     L.ns_reset.argtypes = [_vp, _vp]
     L.ns_step.argtypes = [_vp, C.c_int, _vp]
+    L.ns_autotune.argtypes = [_vp, C.c_int, _vp, _vp]
     L.ns_checkpoint_bytes.argtypes = [_vp]
     L.ns_checkpoint_bytes.restype = C.c_size_t
     L.ns_checkpoint.argtypes = [_vp, _vp, C.c_size_t, _vp]
@@ -136,7 +138,7 @@ def lib():
     L.ns_cluster_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
     L.ns_cluster_scratch_bytes.restype = C.c_size_t
     for name in ("ns_default_options", "ns_create", "ns_create_batch", "ns_run", "ns_reset", "ns_result", "ns_summary",
-                 "ns_phase_cycles", "ns_run_noalloc", "ns_step", "ns_checkpoint", "ns_restore",
+                 "ns_phase_cycles", "ns_run_noalloc", "ns_step", "ns_autotune", "ns_checkpoint", "ns_restore",
                  "ns_last_run_ms", "ns_get_stats", "ns_philox4x32_10", "ns_loglike", "ns_select_worst", "ns_slice_replace",
                  "ns_batch_correct", "ns_evidence_update", "ns_cluster"):
         getattr(L, name).restype = C.c_int
@@ -310,6 +312,15 @@ def ns_restore(h, data, stream=None):
 
 def ns_reset(h, stream=None):
     _check(lib().ns_reset(h.ptr, _stream_ptr(stream)), h.ptr)
+
+
+def ns_autotune(h, iters=3, stream=None):
+    """Pick each run's walker mapping by measurement (ns_autotune); returns
+    the choices, 1 = one walker per warp."""
+    n = int(lib().ns_n_runs(h.ptr))
+    out = (C.c_int * max(1, n))()
+    _check(lib().ns_autotune(h.ptr, int(iters), C.cast(out, _vp), _stream_ptr(stream)), h.ptr)
+    return [int(out[i]) for i in range(n)]
 
 
 def ns_resident_runs_per_sm(d, m, depth=0):

@@ -778,6 +778,219 @@ inline __device__ void slice_walker(const LikParams& P, const SliceCfg& S, int w
 }
 
 // ---------------------------------------------------------------------------
+// a5-a7 with one walker per warp: the 32 lanes of a warp carry one walker,
+// lane i its coordinate i (d <= 32).  The decisions, draws and history are
+// those of slice_walker; only the order of the FP32 sums inside the
+// likelihood differs (warp butterflies).  A butterfly leaves the same sum in
+// every lane (each step adds the same two values, in either order), so every
+// lane holds the same log L and the walker's control flow is warp-uniform.
+// This suits runs with few walkers (m = 1 is the sequential sampler), where a
+// thread per walker leaves most of a block idle.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float warp_sum_all(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(kFull, v, o);
+  return v;
+}
+
+// The likelihood constants of one lane's coordinate; for the correlated
+// Gaussian the lane's column of L (L L^T = inverse covariance): col[k] =
+// L[k][lane] for k >= lane, else 0.
+template <int DMAX>
+struct LaneLik {
+  float span, c, lo, rw;
+  float col[DMAX];
+};
+
+template <int DMAX>
+__device__ __forceinline__ void lane_lik(const LikParams& P, LaneLik<DMAX>& Q) {
+  const int lane = threadIdx.x & 31;
+  Q.span = P.span[lane];
+  Q.c = P.c[lane];
+  Q.lo = P.lo[lane];
+  Q.rw = P.rw[lane];
+#pragma unroll
+  for (int k = 0; k < DMAX; ++k) {
+    float v = 0.f;
+    if (P.kind == kCorr && k >= lane) {
+      const float2 q = P.LpP[(lane >> 1) * kMaxDim + k];
+      v = (lane & 1) ? q.y : q.x;
+    }
+    Q.col[k] = v;
+  }
+}
+
+// log L at the unit-cube point whose coordinate `lane` is u (0 beyond d);
+// the same value in every lane.
+template <int DMAX>
+__device__ __forceinline__ float loglike_lane(const LikParams& P, const LaneLik<DMAX>& Q, float u) {
+  const int lane = threadIdx.x & 31;
+  switch (P.kind) {
+    case kIso: {
+      const float y = fmaf(Q.span, u, Q.c);
+      return -warp_sum_all(y * y) * P.inv2s2;
+    }
+    case kCorr: {
+      // z_lane = sum_{k >= lane} L[k][lane] y_k, then ||z||^2
+      const float y = fmaf(Q.span, u, Q.c);
+      float z = 0.f;
+#pragma unroll
+      for (int k = 0; k < DMAX; ++k) z = fmaf(Q.col[k], __shfl_sync(kFull, y, k), z);
+      return -0.5f * warp_sum_all(z * z);
+    }
+    case kRosen: {
+      const float th = fmaf(Q.span, u, Q.lo);
+      const float nx = __shfl_down_sync(kFull, th, 1);
+      const float p = P.a - th;
+      const float q = fmaf(-th, th, nx);
+      return -warp_sum_all(Q.rw * fmaf(p, p, P.b * q * q));
+    }
+    case kMix: {
+      float e[kMaxModes];
+      float emax = -CUDART_INF_F;
+#pragma unroll
+      for (int k = 0; k < kMaxModes; ++k) {
+        e[k] = -CUDART_INF_F;
+        if (k < P.n_modes) {
+          const float y = fmaf(Q.span, u, P.cm[k * kMaxDim + lane]);
+          e[k] = -warp_sum_all(y * y) * P.inv2s2;
+          emax = fmaxf(emax, e[k]);
+        }
+      }
+      float acc = 0.f;
+#pragma unroll
+      for (int k = 0; k < kMaxModes; ++k)
+        if (k < P.n_modes) acc += expf(e[k] - emax);
+      return emax + logf(acc) - P.log_k;
+    }
+    case kGmm: {
+      float mx = -CUDART_INF_F, acc = 0.f;
+      for (int k = 0; k < P.n_modes; ++k) {
+        float t = 0.f;
+        if (lane < DMAX) {
+          const float y = fmaf(Q.span, u, P.gm[k * DMAX + lane]);
+          t = (y * P.giv[k * DMAX + lane]) * y;
+        }
+        const float e = P.glw[k] - warp_sum_all(t);
+        if (e > mx) {
+          acc = fmaf(acc, expf(mx - e), 1.f);
+          mx = e;
+        } else {
+          acc += expf(e - mx);
+        }
+      }
+      return mx + logf(acc);
+    }
+    case kShell: {
+      const float y = fmaf(Q.span, u, Q.c);
+      const float z = sqrtf(warp_sum_all(y * y)) - P.a;
+      return -z * z * P.inv2s2;
+    }
+    default:
+      return -CUDART_INF_F;
+  }
+}
+
+// One walker on the calling warp (every lane calls, with the same walker).
+// x0: the seed point, coordinate i at x0[i * x0_stride]; dirs: the walker's
+// per-step table [n_steps][dir_row(DMAX)].  Outputs as slice_walker.
+template <int DMAX>
+__device__ void slice_walker_warp(const LikParams& P, const LaneLik<DMAX>& Q, const SliceCfg& S, int walker,
+                                  const float* __restrict__ x0, int x0_stride, float l0,
+                                  const float* __restrict__ dirs, float thr_out, float thr_in, const WalkerOut& O,
+                                  long long& evals_out, int& flags_out) {
+  constexpr int RW = dir_row(DMAX);
+  const int lane = threadIdx.x & 31, d = S.d;
+  const bool mine = lane < d;
+  const uint32_t n0 = shrink_draw0(d);
+  float x = mine ? x0[(size_t)lane * x0_stride] : 0.f;
+  float l = l0;
+  int step = 0, phase = 0, nexp = 0, nsh = 0, hlen = 0, flags = 0;
+  long long evals = 0;
+  float a = 0.f, b = 0.f, v = 0.f, pre0 = 0.f, pre1 = 0.f, pre2 = 0.f;
+  Stream st;
+  auto load_step = [&](int s) {
+    const float* row = dirs + (size_t)s * RW;
+    v = (lane < DMAX) ? row[lane] : 0.f;
+    const float r = row[DMAX];
+    pre0 = row[DMAX + 1];
+    pre1 = row[DMAX + 2];
+    pre2 = row[DMAX + 3];
+    a = -r * S.width;
+    b = (1.f - r) * S.width;
+    st.init(S.k0, S.k1, S.t, (uint32_t)walker, (uint32_t)s);
+    st.n = n0 + kPreShrink;
+  };
+  if (S.n_steps > 0) load_step(0);
+  while (step < S.n_steps) {
+    float tp = (phase == 0) ? a : b;
+    if (phase == 2) {
+      const float uu = nsh == 0 ? pre0 : (nsh == 1 ? pre1 : (nsh == 2 ? pre2 : u24(st.next())));
+      tp = fmaf(uu, b - a, a);
+    }
+    const float u = fmaf(tp, v, x);
+    const bool in = __all_sync(kFull, u >= 0.f && u <= 1.f);
+    float lp = -CUDART_INF_F;
+    if (in) {
+      lp = loglike_lane<DMAX>(P, Q, u);
+      ++evals;
+    }
+    const bool ok = in && (lp > ((phase == 2) ? thr_in : thr_out));
+    if (phase < 2) {
+      const bool expand = ok && (nexp < S.e_max);
+      a = (expand && phase == 0) ? a - S.width : a;
+      b = (expand && phase == 1) ? b + S.width : b;
+      flags |= (ok && !expand) ? 1 : 0;
+      nexp = expand ? nexp + 1 : 0;
+      phase = expand ? phase : phase + 1;
+      continue;
+    }
+    if (step == S.n_steps - 1) {
+      int hs = -1;
+      if (nsh < S.t_max - 1) {
+        hs = nsh;
+        hlen = nsh + 1;
+      } else if (ok) {
+        hs = S.t_max - 1;
+        hlen = S.t_max;
+      }
+      if (hs >= 0) {
+        if (lane == 0) O.hist_l[hs] = lp;
+        if (mine) O.hist_x[(size_t)hs * d + lane] = u;
+      }
+    }
+    bool advance = ok;
+    if (ok) {
+      x = u;
+      l = lp;
+    } else {
+      if (tp < 0.f) a = tp;
+      else b = tp;
+      if (++nsh >= S.s_max) {
+        flags |= 2;
+        advance = true;
+      }
+    }
+    if (advance) {
+      ++step;
+      if (step < S.n_steps) {
+        load_step(step);
+        phase = 0;
+        nsh = 0;
+        nexp = 0;
+      }
+    }
+  }
+  evals_out = evals;
+  flags_out = flags;
+  if (mine) O.new_x[lane] = x;
+  if (lane == 0) {
+    O.new_l[0] = l;
+    O.hist_len[0] = hlen;
+  }
+}
+
+// ---------------------------------------------------------------------------
 // a8-a9: Algorithm 1 (batch sorting) and Algorithm 2 (history correction).
 // Candidates 0..m-1: removed points W; m..2m-1: walkers' new points.
 // ---------------------------------------------------------------------------

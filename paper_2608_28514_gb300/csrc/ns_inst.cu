@@ -36,7 +36,14 @@ cudaError_t NS_CAT(launch_slice_, NS_DMAX)(const LikParams& P, const SliceCfg& S
                                            int correction, const float* live_x, const float* live_l,
                                            const int* seed_slot, const float* W, const float* chol, const int* cid,
                                            float* new_x, float* new_l, float* hist_l, float* hist_x, int* hist_len,
-                                           long long* evals, int* flags, float* dir_scratch, cudaStream_t s) {
+                                           long long* evals, int* flags, float* dir_scratch, int warp,
+                                           cudaStream_t s) {
+  if (warp) {  // four walkers (warps) per block
+    k_slice_warp<NS_DMAX><<<(m + 3) / 4, 128, 0, s>>>(P, SC, m, n_pad, correction, live_x, live_l, seed_slot, W, chol,
+                                                      cid, new_x, new_l, hist_l, hist_x, hist_len, evals, flags,
+                                                      dir_scratch);
+    return cudaGetLastError();
+  }
   k_slice<NS_DMAX><<<(m + 127) / 128, 128, sizeof(float) * 128 * dir_row(NS_DMAX), s>>>(P, SC, m, n_pad, correction, live_x, live_l, seed_slot, W, chol,
                                                    cid, new_x, new_l, hist_l, hist_x, hist_len, evals, flags,
                                                    dir_scratch);

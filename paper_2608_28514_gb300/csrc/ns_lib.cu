@@ -146,7 +146,7 @@ struct ClassFns {
   cudaError_t (*ll)(const LikParams&, int, const float*, float*, cudaStream_t);
   cudaError_t (*sl)(const LikParams&, const SliceCfg&, int, int, int, const float*, const float*, const int*,
                     const float*, const float*, const int*, float*, float*, float*, float*, int*, long long*, int*,
-                    float*, cudaStream_t);
+                    float*, int, cudaStream_t);
   cudaError_t (*occ)(int, size_t, int*);
 };
 #define NS_CLASS_ENTRY(D) {D, launch_run_##D, launch_loglike_##D, launch_slice_##D, occupancy_run_##D},
@@ -342,7 +342,7 @@ ns_status check_opts(const ns_options& o, std::string* err) {
       o.correction < 0 || o.correction > 3 || o.max_iter < 1 || o.dead_cap < 0 || o.chunk_iters < 0 ||
       !(o.vol_frac >= 0 && o.vol_frac < 1) || o.precision < 0 || o.precision > 1 || !(o.reeval_margin >= 0) ||
       !std::isfinite(o.reeval_margin) || !(o.reeval_rel >= 0) || !std::isfinite(o.reeval_rel) ||
-      o.reeval_defer < 0 || o.reeval_defer > 64) {
+      o.reeval_defer < 0 || o.reeval_defer > 64 || o.walker_mapping < 0 || o.walker_mapping > 1) {
     set_err(err, "an option is out of range");
     return NS_ERR_ARG;
   }
@@ -716,6 +716,7 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     R.reeval_margin = (float)opt.reeval_margin;
     R.reeval_rel = (float)opt.reeval_rel;
     R.reeval_defer = opt.reeval_defer;
+    R.walker_warp = (p.lik->kind == NS_LIK_MLP) ? 0 : opt.walker_mapping;
     if (p.lik->kind == NS_LIK_MLP) {
       R.mlp_tiles = reinterpret_cast<const uint8_t*>(base + o.mlp_img);
       R.mlp_desc = reinterpret_cast<const MlpDesc*>(base + o.mlp_desc);
@@ -938,6 +939,48 @@ ns_status ns_run(ns_handle* h, void* stream) {
 ns_status ns_step(ns_handle* h, int n_iters, void* stream) {
   if (!h || n_iters < 1) return NS_ERR_ARG;
   return run_impl(h, stream, n_iters, false);
+}
+
+ns_status ns_autotune(ns_handle* h, int iters, int* out_warp, void* stream) {
+  if (!h || iters < 1 || iters > 1000) return NS_ERR_ARG;
+  if (h->ran) {
+    set_err(&h->err, "ns_autotune needs a handle that has not run (create it, or ns_reset it)");
+    return NS_ERR_STATE;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  const int n = h->n_runs;
+  auto upload = [&]() {
+    return cudaMemcpyAsync(h->d_runs, h->runs.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice, s);
+  };
+  std::vector<double> per_iter[2];
+  for (int mode = 0; mode < 2; ++mode) {
+    for (int r = 0; r < n; ++r)
+      if (h->runs[r].mlp_desc == nullptr) h->runs[r].walker_warp = mode;
+    NS_CUDA(upload(), &h->err);
+    const ns_status st = run_impl(h, stream, iters, false);
+    if (st != NS_OK) {
+      ns_reset(h, stream);
+      return st;
+    }
+    per_iter[mode].resize(n);
+    for (int r = 0; r < n; ++r) {
+      const RunState& S = h->h_states[r];
+      per_iter[mode][r] = (double)S.cycles[kPhSlice] / (double)(S.n_iter > 0 ? S.n_iter : 1);
+    }
+    NS_CUDA(cudaStreamSynchronize(s), &h->err);
+    const ns_status rs = ns_reset(h, stream);
+    if (rs != NS_OK) return rs;
+  }
+  for (int r = 0; r < n; ++r) {
+    const bool analytic = h->runs[r].mlp_desc == nullptr;
+    const int w = (analytic && per_iter[1][r] < per_iter[0][r]) ? 1 : 0;
+    h->runs[r].walker_warp = w;
+    if (out_warp) out_warp[r] = w;
+  }
+  NS_CUDA(upload(), &h->err);
+  NS_CUDA(cudaStreamSynchronize(s), &h->err);
+  h->h2d_bytes += 3LL * (long long)sizeof(RunDesc) * n;
+  return NS_OK;
 }
 
 size_t ns_checkpoint_bytes(const ns_handle* h) { return h ? sizeof(CheckpointHeader) + h->total : 0; }
@@ -1221,6 +1264,7 @@ ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt_in, fl
   R.count = reinterpret_cast<int*>(base + o_count);
   R.split = reinterpret_cast<int*>(base + o_split);
   R.mask = reinterpret_cast<int*>(base + o_mask);
+  R.walker_warp = opt.walker_mapping;
   R.spill = spill ? 1 : 0;
   R.tree_ws = spill ? base + o_tree : nullptr;
   R.st = reinterpret_cast<RunState*>(base + o_state);
@@ -1378,7 +1422,7 @@ ns_status ns_slice_replace(const ns_likelihood* lik, const double* lo, const dou
   cudaStream_t s = (cudaStream_t)stream;
   const cudaError_t e = kClasses[class_index(d)].sl(P, SC, m, n_pad, opt.correction, live_x, live_l, seed_slot, W,
                                                      chol, cid, new_x, new_l, hist_l, hist_x, hist_len, evals, flags,
-                                                     dir_scratch, s);
+                                                     dir_scratch, opt.walker_mapping, s);
   NS_CUDA(e, nullptr);
   return NS_OK;
 }

@@ -65,6 +65,7 @@ struct RunDesc {
   float reeval_margin;    // re-evaluate in FP32 when |logL_bf16 - threshold| <
   float reeval_rel;       //   reeval_margin + reeval_rel |threshold|
   int reeval_defer;       // rounds a near-threshold candidate may wait for a shared FP32 pass
+  int walker_warp;        // analytic runs: 1 = one walker per warp, 0 = one walker per thread
 };
 
 // Shared-memory carve of the run kernel, computed identically on host and
@@ -300,6 +301,39 @@ __device__ __noinline__ void walker_phase(const RunDesc& R, const LikParams& P, 
   fl = act ? f : 0;
   cyc_draw = 0;  // the draws happen before, block-wide (k_run)
   cyc_walk = clock64() - c1;
+}
+
+// a4-a7 with one walker per warp (RunDesc::walker_warp): warp w takes the
+// walkers w, w + n_warps, ... in turn.  On return lane 0 of each warp holds
+// in ev its walkers' likelihood evaluations and in fl how many of them hit a
+// step-out or shrink cap (other lanes 0).  Called by every thread.
+template <int DMAX>
+__device__ __noinline__ void walker_phase_warp(const RunDesc& R, const LikParams& P, const SliceCfg& SC,
+                                               const float* s_W, const int* s_seed, long long& ev, int& fl) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5, m = R.m, d = R.d;
+  LaneLik<DMAX> Q;
+  lane_lik<DMAX>(P, Q);
+  const float thr_out = (R.correction == 3) ? s_W[m - 1] : s_W[0];
+  long long e_sum = 0;
+  int n_cap = 0;
+  for (int i = wid; i < m; i += nw) {
+    const int sd = s_seed[i];
+    const float thr_in = (R.correction == 3) ? s_W[m - 1] : s_W[i];
+    WalkerOut O;
+    O.new_x = R.new_x + (size_t)i * d;
+    O.new_l = R.new_l + i;
+    O.hist_l = R.hist_l + (size_t)i * R.t_max;
+    O.hist_x = R.hist_x + (size_t)i * R.t_max * d;
+    O.hist_len = R.hist_len + i;
+    long long e = 0;
+    int f = 0;
+    slice_walker_warp<DMAX>(P, Q, SC, i, R.live_x + sd, R.n_pad, R.live_l[sd],
+                            R.dirs + (size_t)i * R.n_steps * dir_row(DMAX), thr_out, thr_in, O, e, f);
+    e_sum += e;
+    n_cap += (f != 0) ? 1 : 0;
+  }
+  ev = (lane == 0) ? e_sum : 0;
+  fl = (lane == 0) ? n_cap : 0;
 }
 
 // a4-a7 for MLP runs: the walkers advance in lock step, one round at a time;
@@ -802,7 +836,13 @@ __global__ void NS_RUN_BOUNDS(MLP, DMAX) k_run(const RunDesc* __restrict__ runs,
       draw_directions_block<DMAX>(SC, 0, m, [&](int w) { return s_chol + (size_t)R.live_cid[s_seed[w]] * d * d; },
                                   R.dirs);
       const long long cd1 = clock64();
-      if ((tid & ~31) < m) walker_phase<DMAX>(R, P, SC, s_W, s_seed, s_chol, s_slots, ev, fl, cyc_eval, cyc_reeval);
+      if (R.walker_warp) {
+        walker_phase_warp<DMAX>(R, P, SC, s_W, s_seed, ev, fl);
+        cyc_reeval = clock64() - cd1;
+      } else if ((tid & ~31) < m) {
+        walker_phase<DMAX>(R, P, SC, s_W, s_seed, s_chol, s_slots, ev, fl, cyc_eval, cyc_reeval);
+        fl = fl ? 1 : 0;
+      }
       if (tid == 0) {
         RS.cycles[6] += cd1 - cd;
         RS.cycles[7] += cyc_reeval;
@@ -824,7 +864,7 @@ __global__ void NS_RUN_BOUNDS(MLP, DMAX) k_run(const RunDesc* __restrict__ runs,
       }
     }
     const long long ev_sum = block_sum_ll(ev, S);
-    const long long capped = block_sum_ll(fl ? 1 : 0, S);
+    const long long capped = block_sum_ll(MLP ? (fl ? 1 : 0) : fl, S);  // walkers that hit a cap
     // a8-a9: Algorithms 1 and 2
     const int rel = batch_correct(m, R.K, R.correction, s_W, R.new_l, R.hist_l, R.hist_len, R.t_max, A, Bf, Tm,
                                   s_list, s_vals, s_ctr, S);
@@ -967,6 +1007,43 @@ __global__ void k_slice(const LikParams P, SliceCfg SC, int m, int n_pad, int co
   }
 }
 
+// Step-level slice kernel with one walker per warp (walker w on warp w of
+// the grid); same tables and outputs as k_slice.
+template <int DMAX>
+__global__ void k_slice_warp(const LikParams P, SliceCfg SC, int m, int n_pad, int correction,
+                             const float* __restrict__ live_x, const float* __restrict__ live_l,
+                             const int* __restrict__ seed_slot, const float* __restrict__ W,
+                             const float* __restrict__ chol, const int* __restrict__ cid, float* new_x,
+                             float* new_l, float* hist_l, float* hist_x, int* hist_len, long long* evals,
+                             int* flags, float* dir_scratch) {
+  const int nw = blockDim.x >> 5, lane = threadIdx.x & 31, d = SC.d;
+  const int w0 = blockIdx.x * nw, w1 = min(m, w0 + nw);
+  if (w0 < w1)
+    draw_directions_block<DMAX>(SC, w0, w1, [&](int w) { return chol + (size_t)cid[seed_slot[w]] * d * d; },
+                                dir_scratch);
+  const int i = w0 + (int)(threadIdx.x >> 5);
+  if (i >= m) return;
+  LaneLik<DMAX> Q;
+  lane_lik<DMAX>(P, Q);
+  const int sd = seed_slot[i];
+  const float thr_out = (correction == 3) ? W[m - 1] : W[0];
+  const float thr_in = (correction == 3) ? W[m - 1] : W[i];
+  WalkerOut O;
+  O.new_x = new_x + (size_t)i * d;
+  O.new_l = new_l + i;
+  O.hist_l = hist_l + (size_t)i * SC.t_max;
+  O.hist_x = hist_x + (size_t)i * SC.t_max * d;
+  O.hist_len = hist_len + i;
+  long long ev = 0;
+  int fl = 0;
+  slice_walker_warp<DMAX>(P, Q, SC, i, live_x + sd, n_pad, live_l[sd],
+                          dir_scratch + (size_t)i * SC.n_steps * dir_row(DMAX), thr_out, thr_in, O, ev, fl);
+  if (lane == 0) {
+    evals[i] = ev;
+    flags[i] = fl;
+  }
+}
+
 // Register classes: a run of dimension d uses the smallest class >= d.
 #define NS_FOR_EACH_CLASS(X) X(2) X(4) X(6) X(8) X(10) X(12) X(16) X(20) X(24) X(28) X(32)
 
@@ -979,7 +1056,7 @@ __global__ void k_slice(const LikParams P, SliceCfg SC, int m, int n_pad, int co
                                const float* live_x, const float* live_l, const int* seed_slot,           \
                                const float* W, const float* chol, const int* cid, float* new_x,          \
                                float* new_l, float* hist_l, float* hist_x, int* hist_len, long long* evals, \
-                               int* flags, float* dir_scratch, cudaStream_t s);                            \
+                               int* flags, float* dir_scratch, int warp, cudaStream_t s);                  \
   cudaError_t occupancy_run_##D(int block, size_t smem, int* blocks_per_sm);
 NS_FOR_EACH_CLASS(NS_DECLARE_LAUNCHERS)
 cudaError_t launch_run_mlp(const RunDesc* runs, const int* ids, int n, int block, size_t smem, int chunk,

@@ -166,7 +166,8 @@ def _slice_case(nat, oracle, p, N, m, n_steps, seed, t, opt_kw=None):
     g = {k: v.cpu().numpy() for k, v in out.items()}
     oo = oracle.opts(p.d, m)
     for k, v in (opt_kw or {}).items():
-        setattr(oo, k, v)
+        if k != "walker_mapping":  # how the GPU lays walkers on lanes; not a parameter of the method
+            setattr(oo, k, v)
     lik = oracle.Lik(p)
     corr = (opt_kw or {}).get("correction", 2)
     n_div, n_border = 0, 0
@@ -213,11 +214,30 @@ def test_slice_replace_matches_oracle(nat, oracle, maker, N, m, steps):
     assert n_div <= max(1, m // 20)
 
 
+@pytest.mark.parametrize("maker,N,m,steps", [
+    (lambda: W.gauss2d_sigma05(), 100, 1, 1), (lambda: W.gauss2d_sigma05(), 100, 10, 10),
+    (lambda: W.corr_gauss10(1), 1000, 100, 50), (lambda: W.rosenbrock(10), 1000, 50, 50),
+    (lambda: W.mixture4_d5(1), 2000, 200, 25), (lambda: W.gauss_corr(27, 2), 1500, 150, 135),
+    (lambda: W.gauss_iso(30, 1.0, -7, 7), 2000, 100, 20), (lambda: W.gauss_corr(32, 3), 500, 7, 40),
+    (W.array49, 1000, 10, 10), (lambda: W.bimodal(10), 1000, 5, 50), (W.shell2d, 1000, 1, 10),
+    (lambda: W.shell(7, 2.0, 0.3, -4.0, 4.0), 500, 25, 35),
+])
+def test_slice_replace_warp_matches_oracle(nat, oracle, maker, N, m, steps):
+    """One walker per warp (the lanes share the coordinates): the same
+    decisions, draws and history as the oracle, up to FP32 rounding of the
+    likelihood sums (a divergent walker has a borderline comparison)."""
+    p = maker()
+    n_div = _slice_case(nat, oracle, p, N, m, steps, seed=5 + m, t=3, opt_kw=dict(walker_mapping=1))
+    assert n_div <= max(1, m // 20)
+
+
 def test_slice_history_cap_and_best_of_worst(nat, oracle):
     p = W.corr_gauss10(2)
     _slice_case(nat, oracle, p, 1000, 64, 20, seed=9, t=1, opt_kw=dict(t_max=2))
     _slice_case(nat, oracle, p, 1000, 64, 20, seed=9, t=1, opt_kw=dict(correction=3))
     _slice_case(nat, oracle, p, 1000, 64, 5, seed=9, t=1, opt_kw=dict(width=3.0, e_max=2, s_max=4))
+    for kw in (dict(t_max=2), dict(correction=3), dict(width=3.0, e_max=2, s_max=4)):
+        _slice_case(nat, oracle, p, 1000, 64, 20, seed=9, t=1, opt_kw=dict(walker_mapping=1, **kw))
 
 
 # --------------------------------------------------------------------------

@@ -1,0 +1,77 @@
+"""Walker-to-lane mappings and the autotuner (batching), through the C ABI.
+
+One walker per warp (the lanes share the walker's coordinates) takes the
+same decisions and draws as one walker per thread; the step-level parity
+against the oracle is in test_gpu_parity.py.  Here: whole runs on the warp
+mapping against their closed forms, and ns_autotune -- valid choices, the
+handle left reset, and each run afterwards identical to the same run made
+alone with its chosen mapping.
+"""
+import numpy as np
+import pytest
+
+from paper_2608_28514_gb300 import analytic as A
+from paper_2608_28514_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def nat():
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    from paper_2608_28514_gb300 import _native
+    _native.lib()
+    return _native
+
+
+RUNS = [(W.corr_gauss10(3), 500, 10, 50, 1e-3, 21), (W.gauss2d_sigma05(), 100, 1, 10, 1e-3, 22),
+        (W.mixture4_d5(2), 600, 30, 25, 1e-3, 23), (W.rosenbrock(2), 400, 1, 10, 1e-3, 24),
+        (W.gauss_iso(30, 1.0, -7, 7), 300, 3, 150, 1e-3, 25), (W.shell2d(), 500, 5, 10, 1e-3, 26),
+        (W.gauss_corr(32, 4), 400, 20, 160, 1e-3, 27)]
+
+
+def test_warp_mapping_runs_match_closed_forms(nat):
+    h = nat.ns_create_batch(RUNS, nat.ns_default_options(walker_mapping=1, depth=1))
+    nat.ns_run(h)
+    for r, (p, N, m, ns, sf, seed) in enumerate(RUNS):
+        res = nat.ns_summary(h, r)
+        assert res["status"] == 0
+        truth = A.logz(p)
+        assert abs(res["log_z"] - truth) < 4 * res["log_z_err"] + 0.05, (p.name, res["log_z"], truth)
+    nat.ns_destroy(h)
+
+
+def test_autotune_choices_and_reset(nat):
+    runs = RUNS + [(W.corr_gauss10(5), 1000, 100, 50, 1e-3, 31)]
+    opt = nat.ns_default_options(depth=1)
+    h = nat.ns_create_batch(runs, opt)
+    choice = nat.ns_autotune(h, 3)
+    assert len(choice) == len(runs) and set(choice) <= {0, 1}
+    # a walker per warp runs 100 walkers four at a time: the per-thread mapping must win there
+    assert choice[-1] == 0
+    nat.ns_run(h)
+    got = [nat.ns_result(h, r) for r in range(len(runs))]
+    nat.ns_destroy(h)
+    # each run equals the same run made alone with the chosen mapping, from its initial live set
+    for r, run in enumerate(runs):
+        h1 = nat.ns_create_batch([run], nat.ns_default_options(depth=1, walker_mapping=choice[r]))
+        nat.ns_run(h1)
+        one = nat.ns_result(h1, 0)
+        nat.ns_destroy(h1)
+        assert one["log_z"] == got[r]["log_z"] and one["n_evals"] == got[r]["n_evals"], r
+        np.testing.assert_array_equal(one["dead_l"], got[r]["dead_l"])
+
+
+def test_autotune_needs_a_fresh_handle(nat):
+    h = nat.ns_create_batch(RUNS[:2], nat.ns_default_options())
+    nat.ns_step(h, 2)
+    with pytest.raises(nat.NSError):
+        nat.ns_autotune(h, 2)
+    nat.ns_reset(h)
+    assert len(nat.ns_autotune(h, 2)) == 2
+    with pytest.raises(nat.NSError):
+        nat.ns_autotune(h, 0)
+    nat.ns_destroy(h)
