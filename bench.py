@@ -82,6 +82,8 @@ def parse():
     ap.add_argument("--clustering-tests", type=int, default=0, metavar="SEEDS",
                     help="run the clustering tests of Table 1 with SEEDS runs per configuration (m = 1), print "
                          "the JSON table and exit")
+    ap.add_argument("--mapping-study", type=int, default=0, metavar="RUNS",
+                    help="walker per thread vs per warp vs autotuned, RUNS runs per shape, and the 256-run batch")
     ap.add_argument("--comparison-shapes", type=int, default=0, metavar="SEEDS",
                     help="run the section-4 comparison shapes (Gaussian d = 2..32, Rosenbrock and the 49-Gaussian "
                          "array at N = 100..1000) with SEEDS runs each, print the JSON table and exit")
@@ -399,6 +401,99 @@ def comparison_shapes(n_seeds, m=1):
             "cases": out}
 
 
+def _run_mapping(nat, runs, mapping, warm=0, opt_kw=None):
+    """One batch of runs with walker mapping `mapping` (0 per thread, 1 per
+    warp, "auto" = ns_autotune's per-run choice after `warm` iterations).
+    Returns evaluations per second over the wall time of the whole job
+    (autotuner included, synchronised), the autotuner's share and choices."""
+    import time
+
+    import torch
+
+    opt = nat.ns_default_options(walker_mapping=0 if mapping == "auto" else mapping, **(opt_kw or {}))
+    h = nat.ns_create_batch(runs, opt)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    tune_s, choice, ratio = 0.0, None, None
+    if mapping == "auto":
+        choice, ratio = nat.ns_autotune(h, warm_iters=warm, probe_iters=3)
+        tune_s = time.perf_counter() - t0
+    nat.ns_run(h)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    res = [nat.ns_summary(h, r) for r in range(len(runs))]
+    nat.ns_destroy(h)
+    ev = sum(r["n_evals"] for r in res)
+    return {"evals_per_s": ev / wall, "wall_s": wall, "evals": ev, "autotune_s": tune_s, "choice": choice,
+            "ratio": ratio, "results": res}
+
+
+def batch256(nat, W, analytic, n_runs=256, seed=1):
+    """The heterogeneous batch (d 2..30, N 100..2000, m = floor(0.05 N), four
+    likelihood families) with one walker per thread, one per warp, and the
+    autotuner's per-run choice: aggregate evaluations per second and each
+    run's log Z error against its closed form (Gaussians, and Rosenbrock and
+    mixture runs up to d = 10, where the closed forms are the pins)."""
+    import numpy as np
+
+    runs = W.batched_runs(n_runs, seed=seed)
+    probs = [(p, N, m, 5 * p.d, 1e-3, s) for p, N, m, s in runs]
+    out = {}
+    for mapping in (0, 1, "auto"):
+        r = _run_mapping(nat, probs, mapping, warm=40)  # 2 N / m iterations: X = e^-2
+        z = []
+        for (p, N, m, s), res in zip(runs, r["results"]):
+            if p.kind in (W.GAUSS_ISO, W.GAUSS_CORR) or p.d <= 10:
+                z.append((res["log_z"] - analytic.logz(p)) / res["log_z_err"])
+        z = np.array(z)
+        key = {0: "per_thread", 1: "per_warp", "auto": "autotuned"}[mapping]
+        out[key] = {"evals_per_s": r["evals_per_s"], "wall_s": r["wall_s"],
+                    "mean_abs_dlogz_over_err": float(np.mean(np.abs(z))),
+                    "frac_within_2sigma": float(np.mean(np.abs(z) < 2.0)), "runs_pinned": int(len(z))}
+        if mapping == "auto":
+            out[key]["autotune_s"] = r["autotune_s"]
+            out[key]["runs_per_warp"] = int(sum(r["choice"]))
+    return {"workload": "%d runs: d ~ U{2..30}, N ~ U{100..2000}, m = floor(0.05 N), 5 d slice steps, stop 1e-3, "
+                        "families iso/corr Gaussian, chained Rosenbrock, 4-mode mixture" % n_runs, **out}
+
+
+def mapping_study(n_runs):
+    """Batching: one walker per thread vs one walker per warp vs the
+    autotuner's per-run choice, from the sequential sampler (m = 1) to the
+    headline batch (m = 100), n_runs seeded runs of each shape in one batch,
+    each to its stopping rule; then the heterogeneous 256-run batch."""
+    import numpy as np
+    import torch
+
+    from paper_2608_28514_gb300 import _native as nat
+    from paper_2608_28514_gb300 import analytic
+    from paper_2608_28514_gb300 import workloads as W
+
+    shapes = [("gauss2d_sigma05_N100_m1", W.gauss2d_sigma05(), 100, 1, 10),
+              ("corr10_N1000_m1", W.corr_gauss10(1), 1000, 1, 50),
+              ("gauss_unit_box7_d30_N300_m1", W.gauss_unit_box7(30), 300, 1, 150),
+              ("corr10_N1000_m10", W.corr_gauss10(1), 1000, 10, 50),
+              ("corr10_N1000_m100", W.corr_gauss10(1), 1000, 100, 50)]
+    out = {}
+    for name, p, N, m, ns in shapes:
+        probs = [(p, N, m, ns, 1e-3, 9000 + s) for s in range(n_runs)]
+        row = {}
+        for mapping in (0, 1, "auto"):
+            r = _run_mapping(nat, probs, mapping, warm=2 * N // m)
+            key = {0: "per_thread", 1: "per_warp", "auto": "autotuned"}[mapping]
+            row[key] = {"evals_per_s": r["evals_per_s"], "wall_s": r["wall_s"]}
+            if mapping == "auto":
+                row[key]["autotune_s"] = r["autotune_s"]
+                row[key]["runs_per_warp"] = int(sum(r["choice"]))
+                q = [x for x in r["ratio"] if x == x]
+                row[key]["ratio_warp_over_thread"] = [float(min(q)), float(np.median(q)), float(max(q))]
+        out[name] = row
+    out["batch256"] = batch256(nat, W, analytic)
+    torch.cuda.synchronize()
+    return {"study": "walker mappings and the autotuner: %d runs per shape, evaluations/s over the wall time of the "
+                     "job (autotuner included; warm-up 2 N / m iterations)" % n_runs, "cases": out}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -476,6 +571,10 @@ def main():
         torch.cuda.synchronize()
         print("profile case done", nat.ns_get_stats(h))
         nat.ns_destroy(h)
+        return
+    if args.mapping_study > 0:
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps(mapping_study(args.mapping_study)), flush=True)
         return
     if args.comparison_shapes > 0:
         if int(os.environ.get("RANK", "0")) == 0:

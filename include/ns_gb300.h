@@ -155,17 +155,28 @@ typedef struct {
 
 /* ---- whole runs ------------------------------------------------------- */
 
-/* Batching (spec: the walker-to-warp mapping is picked by an
- * autotuner): for every analytic run of a handle that has not run yet (or
- * was reset), run `iters` iterations (1..1000) with one walker per thread,
- * then with one walker per warp, each from the run's initial live set;
- * compare the run's SM cycles per iteration in the slice phase (a4-a7) and
- * keep the faster mapping for that run; then reset the handle (ns_reset), so
- * that ns_run starts every run afresh with its chosen mapping.  out_warp
- * [n_runs] (host, may be NULL) receives each run's choice (1 = per warp; MLP
- * runs keep their lock-step walkers and report 0).  The choice is not part of
- * a checkpoint.  NS_ERR_STATE if the handle has run. */
-ns_status ns_autotune(ns_handle* h, int iters, int* out_warp, void* stream);
+/* Batching: the walker-to-lane mapping of each analytic run, picked by
+ * measurement.  First warm_iters (>= 0) iterations of every unfinished run
+ * with its current mapping (ordinary iterations of the run: they are kept),
+ * so that the probe sees a live set inside the run rather than the prior;
+ * then a device snapshot of every run's state (live set, cluster tables,
+ * counters), probe_iters (1..1000) iterations with one walker per thread,
+ * the snapshot restored, probe_iters with one walker per warp, the snapshot
+ * restored.  A run keeps the warp mapping where its SM cycles per iteration
+ * in the slice phase (a4-a7) are at least 5 % lower, else the per-thread
+ * one.  On return every run is in its state after the warm-up, bit for bit,
+ * with its chosen mapping.  out_warp [n_runs] (host, may be NULL): the
+ * choices (1 = per warp); out_ratio [n_runs] (host, may be NULL): per-warp
+ * over per-thread cycles per iteration (NaN where not measured: MLP runs,
+ * which keep their lock-step walkers, and runs that had stopped).  The
+ * choices are not part of a checkpoint.  Allocates the snapshot with
+ * cudaMalloc for the duration of the call (NS_ERR_OOM if it cannot). */
+ns_status ns_autotune(ns_handle* h, int warm_iters, int probe_iters, int* out_warp, double* out_ratio,
+                      void* stream);
+
+/* Set run `run`'s walker mapping (0 one walker per thread, 1 one walker per
+ * warp; analytic runs only) for the iterations that follow. */
+ns_status ns_set_walker_mapping(ns_handle* h, int run, int warp);
 
 /* Fill `opt` with the defaults listed above. */
 ns_status ns_default_options(ns_options* opt);

@@ -94,7 +94,8 @@ def lib():
     L.ns_run.argtypes = [_vp, _vp]
     L.ns_reset.argtypes = [_vp, _vp]
     L.ns_step.argtypes = [_vp, C.c_int, _vp]
-    L.ns_autotune.argtypes = [_vp, C.c_int, _vp, _vp]
+    L.ns_autotune.argtypes = [_vp, C.c_int, C.c_int, _vp, _vp, _vp]
+    L.ns_set_walker_mapping.argtypes = [_vp, C.c_int, C.c_int]
     L.ns_checkpoint_bytes.argtypes = [_vp]
     L.ns_checkpoint_bytes.restype = C.c_size_t
     L.ns_checkpoint.argtypes = [_vp, _vp, C.c_size_t, _vp]
@@ -138,7 +139,7 @@ def lib():
     L.ns_cluster_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
     L.ns_cluster_scratch_bytes.restype = C.c_size_t
     for name in ("ns_default_options", "ns_create", "ns_create_batch", "ns_run", "ns_reset", "ns_result", "ns_summary",
-                 "ns_phase_cycles", "ns_run_noalloc", "ns_step", "ns_autotune", "ns_checkpoint", "ns_restore",
+                 "ns_phase_cycles", "ns_run_noalloc", "ns_step", "ns_autotune", "ns_set_walker_mapping", "ns_checkpoint", "ns_restore",
                  "ns_last_run_ms", "ns_get_stats", "ns_philox4x32_10", "ns_loglike", "ns_select_worst", "ns_slice_replace",
                  "ns_batch_correct", "ns_evidence_update", "ns_cluster"):
         getattr(L, name).restype = C.c_int
@@ -314,13 +315,20 @@ def ns_reset(h, stream=None):
     _check(lib().ns_reset(h.ptr, _stream_ptr(stream)), h.ptr)
 
 
-def ns_autotune(h, iters=3, stream=None):
+def ns_autotune(h, warm_iters=0, probe_iters=3, stream=None):
     """Pick each run's walker mapping by measurement (ns_autotune); returns
-    the choices, 1 = one walker per warp."""
+    (choices, ratios): 1 = one walker per warp; per-warp over per-thread
+    slice cycles per iteration (nan where not measured)."""
     n = int(lib().ns_n_runs(h.ptr))
     out = (C.c_int * max(1, n))()
-    _check(lib().ns_autotune(h.ptr, int(iters), C.cast(out, _vp), _stream_ptr(stream)), h.ptr)
-    return [int(out[i]) for i in range(n)]
+    ratio = (C.c_double * max(1, n))()
+    _check(lib().ns_autotune(h.ptr, int(warm_iters), int(probe_iters), C.cast(out, _vp), C.cast(ratio, _vp),
+                             _stream_ptr(stream)), h.ptr)
+    return [int(out[i]) for i in range(n)], [float(ratio[i]) for i in range(n)]
+
+
+def ns_set_walker_mapping(h, run, warp):
+    _check(lib().ns_set_walker_mapping(h.ptr, int(run), int(warp)), h.ptr)
 
 
 def ns_resident_runs_per_sm(d, m, depth=0):

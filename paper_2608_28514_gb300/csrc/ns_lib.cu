@@ -941,45 +941,118 @@ ns_status ns_step(ns_handle* h, int n_iters, void* stream) {
   return run_impl(h, stream, n_iters, false);
 }
 
-ns_status ns_autotune(ns_handle* h, int iters, int* out_warp, void* stream) {
-  if (!h || iters < 1 || iters > 1000) return NS_ERR_ARG;
-  if (h->ran) {
-    set_err(&h->err, "ns_autotune needs a handle that has not run (create it, or ns_reset it)");
-    return NS_ERR_STATE;
+extern "C++" {
+namespace {
+
+// The device buffers of run r that an iteration reads back later: the live
+// set, the cluster tables and the state (the dead buffers are appended at
+// the state's n_dead, the rest is per-iteration scratch).
+template <class F>
+void for_each_run_buffer(const ns_handle* h, int r, F&& f) {
+  const RunDesc& R = h->runs[r];
+  const size_t d = R.d, nn = R.n_nodes;
+  f((void*)R.live_x, sizeof(float) * d * R.n_pad);
+  f((void*)R.live_l, sizeof(float) * R.N);
+  f((void*)R.live_cid, sizeof(int) * R.N);
+  f((void*)R.centres, sizeof(float) * nn * d);
+  f((void*)R.chol, sizeof(float) * nn * d * d);
+  f((void*)R.chol64, sizeof(double) * nn * d * d);
+  f((void*)R.logvol, sizeof(float) * nn);
+  f((void*)R.count, sizeof(int) * nn);
+  f((void*)R.split, sizeof(int) * nn);
+  f((void*)R.mask, sizeof(int) * nn);
+  f((void*)R.st, sizeof(RunState));
+}
+
+}  // namespace
+}  // extern "C++"
+
+ns_status ns_set_walker_mapping(ns_handle* h, int run, int warp) {
+  if (!h || run < 0 || run >= h->n_runs || warp < 0 || warp > 1) return NS_ERR_ARG;
+  if (h->runs[run].mlp_desc != nullptr && warp) {
+    set_err(&h->err, "MLP runs keep their lock-step walkers");
+    return NS_ERR_ARG;
   }
+  h->runs[run].walker_warp = warp;
+  NS_CUDA(cudaMemcpy(h->d_runs + run, &h->runs[run], sizeof(RunDesc), cudaMemcpyHostToDevice), &h->err);
+  return NS_OK;
+}
+
+ns_status ns_autotune(ns_handle* h, int warm_iters, int probe_iters, int* out_warp, double* out_ratio,
+                      void* stream) {
+  if (!h || warm_iters < 0 || probe_iters < 1 || probe_iters > 1000) return NS_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
   const int n = h->n_runs;
-  auto upload = [&]() {
-    return cudaMemcpyAsync(h->d_runs, h->runs.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice, s);
+  if (warm_iters > 0) {
+    const ns_status st = run_impl(h, stream, warm_iters, false);
+    if (st != NS_OK) return st;
+  }
+  // device snapshot of every run's state after the warm-up
+  size_t bytes = 0;
+  for (int r = 0; r < n; ++r) for_each_run_buffer(h, r, [&](void*, size_t b) { bytes += (b + 255) & ~(size_t)255; });
+  char* snap = nullptr;
+  if (cudaMalloc(&snap, bytes) != cudaSuccess) {
+    set_err(&h->err, "ns_autotune: cannot allocate %zu bytes for the state snapshot", bytes);
+    return NS_ERR_OOM;
+  }
+  auto copy_all = [&](bool save) {
+    size_t o = 0;
+    cudaError_t e = cudaSuccess;
+    for (int r = 0; r < n && e == cudaSuccess; ++r)
+      for_each_run_buffer(h, r, [&](void* p, size_t b) {
+        if (e == cudaSuccess)
+          e = save ? cudaMemcpyAsync(snap + o, p, b, cudaMemcpyDeviceToDevice, s)
+                   : cudaMemcpyAsync(p, snap + o, b, cudaMemcpyDeviceToDevice, s);
+        o += (b + 255) & ~(size_t)255;
+      });
+    return e;
   };
+  const std::vector<RunDesc> keep = h->runs;
+  std::vector<RunState> before(n);
   std::vector<double> per_iter[2];
-  for (int mode = 0; mode < 2; ++mode) {
+  ns_status result = NS_OK;
+  cudaError_t e = cudaMemcpyAsync(before.data(), h->d_states, sizeof(RunState) * n, cudaMemcpyDeviceToHost, s);
+  if (e == cudaSuccess) e = copy_all(true);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  for (int mode = 0; mode < 2 && e == cudaSuccess && result == NS_OK; ++mode) {
     for (int r = 0; r < n; ++r)
       if (h->runs[r].mlp_desc == nullptr) h->runs[r].walker_warp = mode;
-    NS_CUDA(upload(), &h->err);
-    const ns_status st = run_impl(h, stream, iters, false);
-    if (st != NS_OK) {
-      ns_reset(h, stream);
-      return st;
-    }
-    per_iter[mode].resize(n);
+    e = cudaMemcpyAsync(h->d_runs, h->runs.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) break;
+    result = run_impl(h, stream, probe_iters, false);
+    per_iter[mode].assign(n, -1.0);
     for (int r = 0; r < n; ++r) {
-      const RunState& S = h->h_states[r];
-      per_iter[mode][r] = (double)S.cycles[kPhSlice] / (double)(S.n_iter > 0 ? S.n_iter : 1);
+      const RunState& A = before[r];
+      const RunState& B = h->h_states[r];
+      const long long it = B.n_iter - A.n_iter;
+      if (it > 0) per_iter[mode][r] = (double)(B.cycles[kPhSlice] - A.cycles[kPhSlice]) / (double)it;
     }
-    NS_CUDA(cudaStreamSynchronize(s), &h->err);
-    const ns_status rs = ns_reset(h, stream);
-    if (rs != NS_OK) return rs;
+    if (e == cudaSuccess) e = copy_all(false);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
+  cudaFree(snap);
+  if (e != cudaSuccess || result != NS_OK) {
+    h->runs = keep;
+    cudaMemcpy(h->d_runs, h->runs.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice);
+    if (e != cudaSuccess) {
+      set_err(&h->err, "ns_autotune: %s", cudaGetErrorString(e));
+      return NS_ERR_CUDA;
+    }
+    return result;
+  }
+  // keep the warp mapping where it saves at least 5 % of the slice phase
+  h->runs = keep;
   for (int r = 0; r < n; ++r) {
-    const bool analytic = h->runs[r].mlp_desc == nullptr;
-    const int w = (analytic && per_iter[1][r] < per_iter[0][r]) ? 1 : 0;
+    const bool measured = h->runs[r].mlp_desc == nullptr && per_iter[0][r] > 0 && per_iter[1][r] > 0;
+    const double ratio = measured ? per_iter[1][r] / per_iter[0][r] : std::nan("");
+    const int w = measured ? (ratio < 0.95 ? 1 : 0) : h->runs[r].walker_warp;
     h->runs[r].walker_warp = w;
     if (out_warp) out_warp[r] = w;
+    if (out_ratio) out_ratio[r] = ratio;
   }
-  NS_CUDA(upload(), &h->err);
+  NS_CUDA(cudaMemcpyAsync(h->d_runs, h->runs.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice, s), &h->err);
+  NS_CUDA(cudaMemcpyAsync(h->h_states, h->d_states, sizeof(RunState) * n, cudaMemcpyDeviceToHost, s), &h->err);
   NS_CUDA(cudaStreamSynchronize(s), &h->err);
-  h->h2d_bytes += 3LL * (long long)sizeof(RunDesc) * n;
   return NS_OK;
 }
 

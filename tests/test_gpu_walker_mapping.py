@@ -4,8 +4,8 @@ One walker per warp (the lanes share the walker's coordinates) takes the
 same decisions and draws as one walker per thread; the step-level parity
 against the oracle is in test_gpu_parity.py.  Here: whole runs on the warp
 mapping against their closed forms, and ns_autotune -- valid choices, the
-handle left reset, and each run afterwards identical to the same run made
-alone with its chosen mapping.
+probe's snapshot restored exactly, and each run afterwards identical to the
+same run made alone with its chosen mapping.
 """
 import numpy as np
 import pytest
@@ -44,34 +44,43 @@ def test_warp_mapping_runs_match_closed_forms(nat):
     nat.ns_destroy(h)
 
 
-def test_autotune_choices_and_reset(nat):
+def test_autotune_choices_and_exact_state(nat):
+    """After a warm-up of 20 iterations the autotuner probes both mappings
+    from one snapshot and restores it: every run then finishes bit for bit
+    like the same run made alone -- 20 iterations one walker per thread, then
+    the chosen mapping."""
     runs = RUNS + [(W.corr_gauss10(5), 1000, 100, 50, 1e-3, 31)]
     opt = nat.ns_default_options(depth=1)
     h = nat.ns_create_batch(runs, opt)
-    choice = nat.ns_autotune(h, 3)
+    choice, ratio = nat.ns_autotune(h, warm_iters=20, probe_iters=3)
     assert len(choice) == len(runs) and set(choice) <= {0, 1}
-    # a walker per warp runs 100 walkers four at a time: the per-thread mapping must win there
-    assert choice[-1] == 0
+    assert all(np.isfinite(ratio))
+    assert all((c == 1) == (q < 0.95) for c, q in zip(choice, ratio))
+    # a walker per warp runs 100 walkers four at a time: the per-thread mapping wins there
+    assert choice[-1] == 0 and ratio[-1] > 2.0
+    assert all(nat.ns_summary(h, r)["n_iter"] == 20 for r in range(len(runs)))
     nat.ns_run(h)
     got = [nat.ns_result(h, r) for r in range(len(runs))]
     nat.ns_destroy(h)
-    # each run equals the same run made alone with the chosen mapping, from its initial live set
     for r, run in enumerate(runs):
-        h1 = nat.ns_create_batch([run], nat.ns_default_options(depth=1, walker_mapping=choice[r]))
+        h1 = nat.ns_create_batch([run], opt)
+        nat.ns_step(h1, 20)
+        nat.ns_set_walker_mapping(h1, 0, choice[r])
         nat.ns_run(h1)
         one = nat.ns_result(h1, 0)
         nat.ns_destroy(h1)
         assert one["log_z"] == got[r]["log_z"] and one["n_evals"] == got[r]["n_evals"], r
         np.testing.assert_array_equal(one["dead_l"], got[r]["dead_l"])
+        np.testing.assert_array_equal(one["dead_x"], got[r]["dead_x"])
 
 
-def test_autotune_needs_a_fresh_handle(nat):
+def test_autotune_arguments(nat):
     h = nat.ns_create_batch(RUNS[:2], nat.ns_default_options())
-    nat.ns_step(h, 2)
+    for warm, probe in ((0, 0), (-1, 3), (0, 1001)):
+        with pytest.raises(nat.NSError):
+            nat.ns_autotune(h, warm, probe)
+    choice, ratio = nat.ns_autotune(h, 0, 2)
+    assert len(choice) == 2
     with pytest.raises(nat.NSError):
-        nat.ns_autotune(h, 2)
-    nat.ns_reset(h)
-    assert len(nat.ns_autotune(h, 2)) == 2
-    with pytest.raises(nat.NSError):
-        nat.ns_autotune(h, 0)
+        nat.ns_set_walker_mapping(h, 2, 1)
     nat.ns_destroy(h)
