@@ -76,6 +76,8 @@ def parse():
                          "status ignored; prints no bench line")
     ap.add_argument("--dead-cap", type=int, default=0)
     ap.add_argument("--no-emulator", action="store_true")
+    ap.add_argument("--no-batch256", action="store_true",
+                    help="skip the 256-run heterogeneous batch (one walker per thread vs autotuned)")
     ap.add_argument("--profile-mlp", type=int, default=0, metavar="N",
                     help="profiling case: the BF16 and FP32 MLP evaluators on N candidates of the 27-D emulator "
                          "network, three launches each; prints no bench line")
@@ -428,7 +430,7 @@ def _run_mapping(nat, runs, mapping, warm=0, opt_kw=None):
             "ratio": ratio, "results": res}
 
 
-def batch256(nat, W, analytic, n_runs=256, seed=1):
+def batch256(nat, W, analytic, n_runs=256, seed=1, mappings=(0, 1, "auto")):
     """The heterogeneous batch (d 2..30, N 100..2000, m = floor(0.05 N), four
     likelihood families) with one walker per thread, one per warp, and the
     autotuner's per-run choice: aggregate evaluations per second and each
@@ -439,7 +441,7 @@ def batch256(nat, W, analytic, n_runs=256, seed=1):
     runs = W.batched_runs(n_runs, seed=seed)
     probs = [(p, N, m, 5 * p.d, 1e-3, s) for p, N, m, s in runs]
     out = {}
-    for mapping in (0, 1, "auto"):
+    for mapping in mappings:
         r = _run_mapping(nat, probs, mapping, warm=40)  # 2 N / m iterations: X = e^-2
         z = []
         for (p, N, m, s), res in zip(runs, r["results"]):
@@ -734,6 +736,9 @@ def main():
     if not args.no_emulator:
         emulator = emulator_compare(nat, W, torch, torch.cuda.get_device_properties(local).multi_processor_count,
                                     measured_peaks())
+    hetero = None
+    if not args.no_batch256 and world == 1:
+        hetero = batch256(nat, W, analytic, mappings=(0, "auto"))
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / args.steps, "higher_is_better": True,
@@ -741,7 +746,7 @@ def main():
                 "config": dict(workload_config(args, R), parallelism=f"replicas x{world} (runs sharded by seed)"),
                 "wall_time_to_logz_s": t_dev / args.steps, "accuracy": acc, "clocks": clocks,
                 "gpu_launches": launches, "roofline": roofline, "e2e": e2e, "cpu_baseline": cpu,
-                "phase_cycle_share": phase_frac, "emulator_bf16_vs_fp32": emulator}
+                "phase_cycle_share": phase_frac, "emulator_bf16_vs_fp32": emulator, "batch256": hetero}
         print(json.dumps(line), flush=True)
     if world > 1:
         dist.barrier()
