@@ -312,3 +312,18 @@ def run(problem, N, m, n_steps, stop_frac, seed, o=None, sequential=False, dead_
     return dict(logz=res.logz, logz_err=res.logz_err, info=res.info, n_dead=n,
                 n_evals=res.n_evals, n_iter=res.n_iter, n_relaxed=res.n_relaxed,
                 status=res.status, dead_x=dx[:n], dead_l=dl[:n], dead_logw=dw[:n])
+
+
+def _run_summary(args):
+    problem, N, m, n_steps, stop_frac, seed = args
+    r = run(problem, N, m, n_steps, stop_frac, seed)
+    return {k: r[k] for k in ("logz", "logz_err", "info", "n_evals", "n_iter", "status")}
+
+
+def run_many(jobs, workers):
+    """Whole oracle runs (problem, N, m, n_steps, stop_frac, seed) in a pool
+    of `workers` processes started with spawn (safe in a process that has
+    already initialised CUDA).  Returns each run's summary, in order."""
+    import multiprocessing as mp
+    with mp.get_context("spawn").Pool(max(1, int(workers))) as pool:
+        return pool.map(_run_summary, list(jobs))
