@@ -117,6 +117,10 @@ typedef struct {
     int walker_mapping;   /* analytic likelihoods: 0 one walker per thread (default), 1 one walker per warp
                            * (the lanes share the coordinates); ns_autotune picks per run.  The mappings take
                            * the same decisions and draws; only the order of the FP32 sums in log L differs */
+    int mlp_batch_cap;    /* MLP precision 1: candidates evaluated per lock-step round, 0..128 (128 = one pass of
+                           * the weights per round; walkers beyond it keep their candidate for the next round and go
+                           * first there; 0 = every candidate of the round, in equal calls).  Decisions do not
+                           * depend on it */
 } ns_options;
 
 /* One run of a batch. */

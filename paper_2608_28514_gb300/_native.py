@@ -46,7 +46,7 @@ class NsOptions(C.Structure):
         ("e_max", C.c_int), ("s_max", C.c_int), ("width", C.c_double), ("max_iter", C.c_longlong),
         ("dead_cap", C.c_longlong), ("chunk_iters", C.c_int), ("precision", C.c_int),
         ("reeval_margin", C.c_double), ("reeval_rel", C.c_double), ("reeval_defer", C.c_int),
-        ("walker_mapping", C.c_int),
+        ("walker_mapping", C.c_int), ("mlp_batch_cap", C.c_int),
     ]
 
 

@@ -342,7 +342,8 @@ ns_status check_opts(const ns_options& o, std::string* err) {
       o.correction < 0 || o.correction > 3 || o.max_iter < 1 || o.dead_cap < 0 || o.chunk_iters < 0 ||
       !(o.vol_frac >= 0 && o.vol_frac < 1) || o.precision < 0 || o.precision > 1 || !(o.reeval_margin >= 0) ||
       !std::isfinite(o.reeval_margin) || !(o.reeval_rel >= 0) || !std::isfinite(o.reeval_rel) ||
-      o.reeval_defer < 0 || o.reeval_defer > 64 || o.walker_mapping < 0 || o.walker_mapping > 1) {
+      o.reeval_defer < 0 || o.reeval_defer > 64 || o.walker_mapping < 0 || o.walker_mapping > 1 ||
+      o.mlp_batch_cap < 0 || o.mlp_batch_cap > kMlpNbMax) {
     set_err(err, "an option is out of range");
     return NS_ERR_ARG;
   }
@@ -518,6 +519,7 @@ ns_status ns_default_options(ns_options* o) {
   o->reeval_margin = 2.0;
   o->reeval_rel = 4e-3;
   o->reeval_defer = 4;
+  o->mlp_batch_cap = kMlpNbMax;
   return NS_OK;
 }
 
@@ -717,6 +719,7 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     R.reeval_rel = (float)opt.reeval_rel;
     R.reeval_defer = opt.reeval_defer;
     R.walker_warp = (p.lik->kind == NS_LIK_MLP) ? 0 : opt.walker_mapping;
+    R.mlp_round_cap = opt.mlp_batch_cap;
     if (p.lik->kind == NS_LIK_MLP) {
       R.mlp_tiles = reinterpret_cast<const uint8_t*>(base + o.mlp_img);
       R.mlp_desc = reinterpret_cast<const MlpDesc*>(base + o.mlp_desc);

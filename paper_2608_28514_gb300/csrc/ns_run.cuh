@@ -66,6 +66,7 @@ struct RunDesc {
   float reeval_rel;       //   reeval_margin + reeval_rel |threshold|
   int reeval_defer;       // rounds a near-threshold candidate may wait for a shared FP32 pass
   int walker_warp;        // analytic runs: 1 = one walker per warp, 0 = one walker per thread
+  int mlp_round_cap;      // BF16 MLP runs: candidates evaluated per round (0 = all, in equal calls)
 };
 
 // Shared-memory carve of the run kernel, computed identically on host and
@@ -458,6 +459,12 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   bool pend = false;
   int age = 0;           // rounds the oldest pending candidate has waited (uniform)
   float ptp = 0.f;       // the pending candidate's position on the line
+  // With a round cap (BF16) at most mlp_round_cap candidates -- one weight
+  // pass -- are evaluated per round; a walker left out holds its candidate
+  // (hold) and goes first in the next round.  Its decisions are unchanged.
+  bool hold = false;
+  float htp = 0.f;       // the held candidate's position on the line
+  const int cap = bf16 ? R.mlp_round_cap : 0;
   // the slice-sampling step on the outcome of this walker's candidate at tp
   auto decide = [&](bool in, float lp, float tp) {
     if (in) ++evals;
@@ -520,7 +527,10 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
     if (!__syncthreads_or(active ? 1 : 0)) break;
     float tp = 0.f;
     bool in = false;
-    if (active && !pend) {
+    if (hold) {  // the candidate in this walker's xbuf row waits for its evaluation
+      tp = htp;
+      in = true;
+    } else if (active && !pend) {
       // proposals outside the unit cube need no likelihood: settle them here
       // (a rejection, in the walker's own order of draws) until the walker
       // holds a candidate to evaluate or has finished its steps
@@ -551,10 +561,24 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
       for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = 0.5f;
     // every walker finished while settling its proposals: no batch to evaluate
     if (!__syncthreads_or((moving || pend) ? 1 : 0)) break;
-    // the walkers holding a candidate, in thread order
+    // the walkers whose candidate is evaluated this round, in thread order
+    // (with a cap: the held ones first, then the new ones, up to the cap)
     int n_mv;
-    const int mpos = block_exclusive_scan(moving ? 1 : 0, BS, &n_mv);
-    if (moving) mvlist[mpos] = tid;
+    bool take = moving;
+    int mpos;
+    if (cap > 0) {
+      int n_old, n_new;
+      const int p_old = block_exclusive_scan((moving && hold) ? 1 : 0, BS, &n_old);
+      const int p_new = block_exclusive_scan((moving && !hold) ? 1 : 0, BS, &n_new);
+      mpos = hold ? p_old : n_old + p_new;
+      n_mv = min(cap, n_old + n_new);
+      take = moving && mpos < cap;
+      hold = moving && !take;
+      if (hold) htp = tp;
+    } else {
+      mpos = block_exclusive_scan(moving ? 1 : 0, BS, &n_mv);
+    }
+    if (take) mvlist[mpos] = tid;
     __syncthreads();
     long long c0 = clock64();
     if (bf16) {
@@ -566,12 +590,12 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
       // candidates close to their threshold wait for their FP32 value
       const float thr = (phase == 2) ? thr_in : thr_out;
       const float margin = fmaf(R.reeval_rel, fabsf(thr), R.reeval_margin);
-      const bool need = moving && in && margin > 0.f && fabsf(lbuf[tid] - thr) < margin;
+      const bool need = take && in && margin > 0.f && fabsf(lbuf[tid] - thr) < margin;
       if (need) {
         pend = true;
         ptp = tp;
       }
-      if (moving && !need) decide(in, in ? lbuf[tid] : -CUDART_INF_F, tp);
+      if (take && !need) decide(in, in ? lbuf[tid] : -CUDART_INF_F, tp);
       int cnt;
       const int pos = block_exclusive_scan(pend ? 1 : 0, BS, &cnt);
       const int still = __syncthreads_or((active && !pend) ? 1 : 0);

@@ -189,6 +189,31 @@ def test_deferred_reevaluation_changes_nothing(nat):
             np.testing.assert_array_equal(a["dead_x"], b["dead_x"])
 
 
+def test_round_cap_changes_nothing(nat):
+    """BF16 rounds capped at 8 or 16 candidates (walkers beyond the cap keep
+    their candidate for the next round) or uncapped, and the 27-D emulator
+    workload (m = 150) at the default cap of 128 or uncapped: the same runs,
+    bit for bit (a candidate's BF16 value does not depend on its batch)."""
+    p = _small_emulator(5)
+    runs = [(p, 200, 20, 20, 1e-2, s) for s in (3, 4)]
+    cases = [(runs, (0, 8, 16), dict(max_iter=40, chunk_iters=40, reeval_margin=5.0)),
+             ([(W.mlp_emulator(1), 1500, 150, 135, 1e-3, s) for s in (1, 2)], (0, 128),
+              dict(max_iter=2, chunk_iters=2, dead_cap=1500 + 600))]
+    for rr, caps, kw in cases:
+        out = {}
+        for cap in caps:
+            o = nat.ns_default_options(precision=1, mlp_batch_cap=cap, **kw)
+            h = nat.ns_create_batch(rr, o)
+            nat.ns_run(h, check=False)
+            out[cap] = [nat.ns_result(h, r) for r in range(len(rr))]
+            nat.ns_destroy(h)
+        for cap in caps[1:]:
+            for a, b in zip(out[0], out[cap]):
+                assert a["n_iter"] == b["n_iter"] and a["n_evals"] == b["n_evals"] and a["n_reeval"] == b["n_reeval"]
+                np.testing.assert_array_equal(a["dead_l"], b["dead_l"])
+                np.testing.assert_array_equal(a["dead_x"], b["dead_x"])
+
+
 @pytest.mark.parametrize("widths,n", [((27, 512, 512, 512, 512, 2000), 150), ((5, 128, 200, 300), 64),
                                       ((3, 64, 100), 1), ((27, 512, 512, 512, 512, 2000), 33)])
 def test_mlp_fp32_accurate_tensor_path(nat, oracle, widths, n):
