@@ -491,6 +491,27 @@ def mapping_study(n_runs):
                 row[key]["ratio_warp_over_thread"] = [float(min(q)), float(np.median(q)), float(max(q))]
         out[name] = row
     out["batch256"] = batch256(nat, W, analytic)
+    # BF16 MLP runs: candidates per weight pass (the tensor-core N), which the
+    # autotuner also picks; the first two iterations of 152 emulator runs
+    p = W.mlp_emulator(1)
+    probs = [(p, EMU_N, EMU_M, EMU_STEPS, 1e-3, s) for s in range(1, 153)]
+    row = {}
+    for cap in (128, 64, 0):
+        opt = nat.ns_default_options(precision=1, mlp_batch_cap=cap, max_iter=EMU_ITERS, chunk_iters=EMU_ITERS,
+                                     dead_cap=EMU_N + 4 * EMU_M)
+        h = nat.ns_create_batch(probs, opt)
+        nat.ns_run(h, check=False)
+        st = nat.ns_get_stats(h)
+        ev = sum(nat.ns_summary(h, r)["n_evals"] for r in range(len(probs)))
+        nat.ns_destroy(h)
+        row["cap_%d" % cap] = {"evals_per_s": ev / (st["run_ms"] * 1e-3), "device_ms": st["run_ms"]}
+    opt = nat.ns_default_options(precision=1, max_iter=10, chunk_iters=10, dead_cap=EMU_N + 20 * EMU_M)
+    h = nat.ns_create_batch(probs, opt)
+    choice, ratio = nat.ns_autotune(h, warm_iters=1, probe_iters=1)
+    nat.ns_destroy(h)
+    row["autotuned_caps"] = {str(c): choice.count(c) for c in sorted(set(choice))}
+    row["ratio_cap64_over_cap128_median"] = float(np.median([x for x in ratio if x == x]))
+    out["emulator27_m150_candidates_per_pass"] = row
     torch.cuda.synchronize()
     return {"study": "walker mappings and the autotuner: %d runs per shape, evaluations/s over the wall time of the "
                      "job (autotuner included; warm-up 2 N / m iterations)" % n_runs, "cases": out}

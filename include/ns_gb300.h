@@ -159,23 +159,29 @@ typedef struct {
 
 /* ---- whole runs ------------------------------------------------------- */
 
-/* Batching: the walker-to-lane mapping of each analytic run, picked by
- * measurement.  First warm_iters (>= 0) iterations of every unfinished run
- * with its current mapping (ordinary iterations of the run: they are kept),
- * so that the probe sees a live set inside the run rather than the prior;
- * then a device snapshot of every run's state (live set, cluster tables,
- * counters), probe_iters (1..1000) iterations with one walker per thread,
- * the snapshot restored, probe_iters with one walker per warp, the snapshot
- * restored.  A run keeps the warp mapping where its SM cycles per iteration
- * in the slice phase (a4-a7) are at least 5 % lower, else the per-thread
- * one.  On return every run is in its state after the warm-up, bit for bit,
- * with its chosen mapping.  out_warp [n_runs] (host, may be NULL): the
- * choices (1 = per warp); out_ratio [n_runs] (host, may be NULL): per-warp
- * over per-thread cycles per iteration (NaN where not measured: MLP runs,
- * which keep their lock-step walkers, and runs that had stopped).  The
- * choices are not part of a checkpoint.  Allocates the snapshot with
- * cudaMalloc for the duration of the call (NS_ERR_OOM if it cannot). */
-ns_status ns_autotune(ns_handle* h, int warm_iters, int probe_iters, int* out_warp, double* out_ratio,
+/* Batching: each run's execution configuration, picked by measurement --
+ * an analytic run's walker-to-lane mapping (one walker per thread, the
+ * default, or one per warp), a BF16 MLP run's candidates per weight pass (the
+ * N of the tensor-core passes: at most 128 per lock-step round, the default;
+ * at most 64; or every candidate of the round in equal calls); FP32 MLP runs
+ * keep theirs.  First warm_iters (>= 0) iterations of every unfinished run
+ * with its current configuration (ordinary iterations of the run: they are
+ * kept), so that the probe sees a live set inside the run rather than the
+ * prior; then a device snapshot of every run's state (live set, cluster
+ * tables, counters) and, for each configuration, probe_iters (1..1000)
+ * iterations followed by the snapshot's restore.  A run leaves its default
+ * only for a configuration with at least 5 % fewer SM cycles per iteration
+ * in the slice phase (a4-a7).  On return every run is in its state after the
+ * warm-up, bit for bit.  The mappings take the same decisions with FP32 sums
+ * in another order; the MLP configurations give identical runs.
+ * out_choice [n_runs] (host, may be NULL): analytic runs 1 = per warp, 0 =
+ * per thread; MLP runs the candidate cap (128, 64, or 0 = equal calls).
+ * out_ratio [n_runs] (host, may be NULL): the second configuration's cycles
+ * per iteration over the default's (warp over thread; 64 over 128), NaN
+ * where not measured (runs that had stopped, FP32 MLP runs).  The choices
+ * are not part of a checkpoint.  Allocates the snapshot with cudaMalloc for
+ * the duration of the call (NS_ERR_OOM if it cannot). */
+ns_status ns_autotune(ns_handle* h, int warm_iters, int probe_iters, int* out_choice, double* out_ratio,
                       void* stream);
 
 /* Set run `run`'s walker mapping (0 one walker per thread, 1 one walker per

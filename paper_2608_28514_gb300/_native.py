@@ -316,9 +316,10 @@ def ns_reset(h, stream=None):
 
 
 def ns_autotune(h, warm_iters=0, probe_iters=3, stream=None):
-    """Pick each run's walker mapping by measurement (ns_autotune); returns
-    (choices, ratios): 1 = one walker per warp; per-warp over per-thread
-    slice cycles per iteration (nan where not measured)."""
+    """Pick each run's configuration by measurement (ns_autotune); returns
+    (choices, ratios): analytic runs 1 = one walker per warp; BF16 MLP runs
+    the candidate cap per round; ratios of the second configuration's slice
+    cycles per iteration over the default's (nan where not measured)."""
     n = int(lib().ns_n_runs(h.ptr))
     out = (C.c_int * max(1, n))()
     ratio = (C.c_double * max(1, n))()

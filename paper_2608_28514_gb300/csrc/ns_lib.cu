@@ -981,7 +981,7 @@ ns_status ns_set_walker_mapping(ns_handle* h, int run, int warp) {
   return NS_OK;
 }
 
-ns_status ns_autotune(ns_handle* h, int warm_iters, int probe_iters, int* out_warp, double* out_ratio,
+ns_status ns_autotune(ns_handle* h, int warm_iters, int probe_iters, int* out_choice, double* out_ratio,
                       void* stream) {
   if (!h || warm_iters < 0 || probe_iters < 1 || probe_iters > 1000) return NS_ERR_ARG;
   cudaStream_t s = (cudaStream_t)stream;
@@ -1011,19 +1011,35 @@ ns_status ns_autotune(ns_handle* h, int warm_iters, int probe_iters, int* out_wa
     return e;
   };
   const std::vector<RunDesc> keep = h->runs;
+  // the configurations a run can take, the first being the default: an
+  // analytic run's walker mapping (per thread, per warp); a BF16 MLP run's
+  // candidates per weight pass (one pass of 128 per round, one of 64, every
+  // candidate of the round in equal calls); FP32 MLP runs have one
+  auto n_cfg = [&](int r) { return keep[r].mlp_desc == nullptr ? 2 : (keep[r].precision == 1 ? 3 : 1); };
+  auto cfg_value = [&](int r, int k) {
+    if (keep[r].mlp_desc == nullptr) return k;
+    return k == 0 ? kMlpNbMax : (k == 1 ? kMlpNbMax / 2 : 0);
+  };
+  auto apply = [&](RunDesc& R, int r, int k) {
+    if (keep[r].mlp_desc == nullptr) R.walker_warp = cfg_value(r, k);
+    else if (keep[r].precision == 1) R.mlp_round_cap = cfg_value(r, k);
+  };
+  int modes = 1;
+  for (int r = 0; r < n; ++r) modes = std::max(modes, n_cfg(r));
   std::vector<RunState> before(n);
-  std::vector<double> per_iter[2];
+  std::vector<std::vector<double>> per_iter(modes, std::vector<double>(n, -1.0));
   ns_status result = NS_OK;
   cudaError_t e = cudaMemcpyAsync(before.data(), h->d_states, sizeof(RunState) * n, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = copy_all(true);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  for (int mode = 0; mode < 2 && e == cudaSuccess && result == NS_OK; ++mode) {
-    for (int r = 0; r < n; ++r)
-      if (h->runs[r].mlp_desc == nullptr) h->runs[r].walker_warp = mode;
+  for (int mode = 0; mode < modes && e == cudaSuccess && result == NS_OK; ++mode) {
+    for (int r = 0; r < n; ++r) {
+      h->runs[r] = keep[r];
+      apply(h->runs[r], r, mode < n_cfg(r) ? mode : 0);
+    }
     e = cudaMemcpyAsync(h->d_runs, h->runs.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice, s);
     if (e != cudaSuccess) break;
     result = run_impl(h, stream, probe_iters, false);
-    per_iter[mode].assign(n, -1.0);
     for (int r = 0; r < n; ++r) {
       const RunState& A = before[r];
       const RunState& B = h->h_states[r];
@@ -1034,8 +1050,8 @@ ns_status ns_autotune(ns_handle* h, int warm_iters, int probe_iters, int* out_wa
     if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   }
   cudaFree(snap);
+  h->runs = keep;
   if (e != cudaSuccess || result != NS_OK) {
-    h->runs = keep;
     cudaMemcpy(h->d_runs, h->runs.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice);
     if (e != cudaSuccess) {
       set_err(&h->err, "ns_autotune: %s", cudaGetErrorString(e));
@@ -1043,15 +1059,20 @@ ns_status ns_autotune(ns_handle* h, int warm_iters, int probe_iters, int* out_wa
     }
     return result;
   }
-  // keep the warp mapping where it saves at least 5 % of the slice phase
-  h->runs = keep;
+  // a run leaves its default only for a configuration at least 5 % faster
+  // in the slice phase
   for (int r = 0; r < n; ++r) {
-    const bool measured = h->runs[r].mlp_desc == nullptr && per_iter[0][r] > 0 && per_iter[1][r] > 0;
-    const double ratio = measured ? per_iter[1][r] / per_iter[0][r] : std::nan("");
-    const int w = measured ? (ratio < 0.95 ? 1 : 0) : h->runs[r].walker_warp;
-    h->runs[r].walker_warp = w;
-    if (out_warp) out_warp[r] = w;
-    if (out_ratio) out_ratio[r] = ratio;
+    int best = 0;
+    const double base = per_iter[0][r];
+    for (int k = 1; k < n_cfg(r); ++k)
+      if (base > 0 && per_iter[k][r] > 0 && per_iter[k][r] < 0.95 * base &&
+          (best == 0 || per_iter[k][r] < per_iter[best][r]))
+        best = k;
+    const bool measured = base > 0 && n_cfg(r) > 1;
+    if (measured) apply(h->runs[r], r, best);
+    if (out_choice)
+      out_choice[r] = keep[r].mlp_desc == nullptr ? h->runs[r].walker_warp : h->runs[r].mlp_round_cap;
+    if (out_ratio) out_ratio[r] = measured && per_iter[1][r] > 0 ? per_iter[1][r] / base : std::nan("");
   }
   NS_CUDA(cudaMemcpyAsync(h->d_runs, h->runs.data(), sizeof(RunDesc) * n, cudaMemcpyHostToDevice, s), &h->err);
   NS_CUDA(cudaMemcpyAsync(h->h_states, h->d_states, sizeof(RunState) * n, cudaMemcpyDeviceToHost, s), &h->err);

@@ -84,3 +84,28 @@ def test_autotune_arguments(nat):
     with pytest.raises(nat.NSError):
         nat.ns_set_walker_mapping(h, 2, 1)
     nat.ns_destroy(h)
+
+
+def test_autotune_mlp_candidate_cap(nat):
+    """BF16 MLP runs: the autotuner picks the candidates per weight pass
+    (128, 64 or every candidate in equal calls); the runs are the same for
+    every choice, so an autotuned run equals the run made without it."""
+    p = W.mlp_emulator(2, widths=(4, 64, 64, 60), sig_lo=1e-2, sig_hi=1e-1)
+    runs = [(p, 300, 150, 12, 1e-2, s) for s in (5, 6)] + [RUNS[0]]
+    opt = nat.ns_default_options(precision=1, max_iter=60, chunk_iters=60)
+    h = nat.ns_create_batch(runs, opt)
+    choice, ratio = nat.ns_autotune(h, warm_iters=5, probe_iters=2)
+    assert choice[0] in (128, 64, 0) and choice[1] in (128, 64, 0) and choice[2] in (0, 1)
+    assert all(np.isfinite(ratio))
+    nat.ns_run(h, check=False)
+    got = [nat.ns_result(h, r) for r in range(2)]
+    nat.ns_destroy(h)
+    h = nat.ns_create_batch(runs, opt)
+    nat.ns_step(h, 5, check=False)
+    nat.ns_run(h, check=False)
+    want = [nat.ns_result(h, r) for r in range(2)]
+    nat.ns_destroy(h)
+    for a, b in zip(got, want):
+        assert a["n_iter"] == b["n_iter"] and a["n_iter"] > 5 and a["n_evals"] == b["n_evals"]
+        np.testing.assert_array_equal(a["dead_l"], b["dead_l"])
+        np.testing.assert_array_equal(a["dead_x"], b["dead_x"])
