@@ -84,6 +84,10 @@ def parse():
     ap.add_argument("--clustering-tests", type=int, default=0, metavar="SEEDS",
                     help="run the clustering tests of Table 1 with SEEDS runs per configuration (m = 1), print "
                          "the JSON table and exit")
+    ap.add_argument("--emulator-convergence", type=int, default=0, metavar="SEEDS",
+                    help="emulator runs to convergence: BF16 vs FP32 (widened data errors), and the emulator "
+                         "configuration on BF16")
+    ap.add_argument("--emulator-cases", default="paired,config", help="cases of --emulator-convergence")
     ap.add_argument("--mapping-study", type=int, default=0, metavar="RUNS",
                     help="walker per thread vs per warp vs autotuned, RUNS runs per shape, and the 256-run batch")
     ap.add_argument("--comparison-shapes", type=int, default=0, metavar="SEEDS",
@@ -517,6 +521,54 @@ def mapping_study(n_runs):
                      "job (autotuner included; warm-up 2 N / m iterations)" % n_runs, "cases": out}
 
 
+def emulator_convergence(n_seeds, cases="paired,config"):
+    """Whole runs of the 27-D emulator likelihood (27-512x4-2000, sigma_k in
+    [1e-3, 1e-1]) to their stopping rule, n_seeds runs of one network per
+    case, all concurrently, 135 slice steps, stop 1e-3.  "paired": the BF16
+    path (FP32 re-evaluation near the threshold) against the plain FP32 path
+    at N = 200, m = 20 (small enough for the FP32 path to finish in minutes);
+    "config": the emulator configuration (N = 1500, m = 150) on the BF16 path.
+    Reported: the device time of ns_run (the wall time to log Z),
+    evaluations, FP32 re-evaluations, and the mean and spread of log Z."""
+    import numpy as np
+    import torch
+
+    from paper_2608_28514_gb300 import _native as nat
+    from paper_2608_28514_gb300 import workloads as W
+
+    def runs_of(p, N, m, precision):
+        opt = nat.ns_default_options(precision=precision)
+        h = nat.ns_create_batch([(p, N, m, 5 * p.d, 1e-3, 500 + s) for s in range(n_seeds)], opt)
+        nat.ns_run(h, check=False)
+        st = nat.ns_get_stats(h)
+        res = [nat.ns_summary(h, r) for r in range(n_seeds)]
+        nat.ns_destroy(h)
+        z = np.array([r["log_z"] for r in res])
+        return {"device_s": st["run_ms"] * 1e-3, "evals_per_run": float(np.mean([r["n_evals"] for r in res])),
+                "evals_per_s": sum(r["n_evals"] for r in res) / (st["run_ms"] * 1e-3),
+                "iterations_per_run": float(np.mean([r["n_iter"] for r in res])),
+                "fp32_reevals_per_run": float(np.mean([r["n_reeval"] for r in res])),
+                "log_z_mean": float(z.mean()), "log_z_std": float(z.std(ddof=1)),
+                "log_z_err_mean": float(np.mean([r["log_z_err"] for r in res])),
+                "info_h_mean": float(np.mean([r["info"] for r in res])),
+                "status": sorted({int(r["status"]) for r in res})}
+
+    out = {}
+    p = W.mlp_emulator(1)
+    if "paired" in cases:
+        a = {"bf16": runs_of(p, 200, 20, 1), "fp32": runs_of(p, 200, 20, 0)}
+        a["dlogz_bf16_minus_fp32"] = a["bf16"]["log_z_mean"] - a["fp32"]["log_z_mean"]
+        a["dlogz_standard_error"] = float(np.sqrt((a["bf16"]["log_z_std"] ** 2 + a["fp32"]["log_z_std"] ** 2)
+                                                  / n_seeds))
+        a["wall_time_ratio_fp32_over_bf16"] = a["fp32"]["device_s"] / a["bf16"]["device_s"]
+        out["paired_N200_m20"] = a
+    if "config" in cases:
+        out["emulator_config_N1500_m150_bf16"] = runs_of(p, 1500, 150, 1)
+    torch.cuda.synchronize()
+    return {"study": "emulator runs to convergence: %d runs per case (one network, seeds 500..), 135 slice steps, "
+                     "stop 1e-3" % n_seeds, "cases": out}
+
+
 def measured_peaks():
     try:
         return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
@@ -594,6 +646,10 @@ def main():
         torch.cuda.synchronize()
         print("profile case done", nat.ns_get_stats(h))
         nat.ns_destroy(h)
+        return
+    if args.emulator_convergence > 0:
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps(emulator_convergence(args.emulator_convergence, args.emulator_cases)), flush=True)
         return
     if args.mapping_study > 0:
         if int(os.environ.get("RANK", "0")) == 0:
