@@ -12,6 +12,7 @@ import zlib
 
 import numpy as np
 import pytest
+from scipy import stats
 
 from paper_2608_28514_gb300 import analytic as A
 from paper_2608_28514_gb300 import workloads as W
@@ -229,6 +230,56 @@ def test_slice_replace_warp_matches_oracle(nat, oracle, maker, N, m, steps):
     p = maker()
     n_div = _slice_case(nat, oracle, p, N, m, steps, seed=5 + m, t=3, opt_kw=dict(walker_mapping=1))
     assert n_div <= max(1, m // 20)
+
+
+@pytest.mark.parametrize("mapping", [0, 1])
+def test_slice_replacement_is_uniform_in_the_constrained_prior(nat, mapping):
+    """Exactness of the slice step (section 2.2): a live set of N points iid
+    uniform in a disc of the 2-D Gaussian's box (sigma 0.5, log L = -2 |theta|^2);
+    given the m-th worst, the survivors are iid uniform in the disc of that
+    radius, so a walker seeded from them keeps that distribution, and with
+    the best-of-worst threshold W[m-1] for every walker each new point is
+    uniform in {log L > W[m-1]}: X(new) / X(W[m-1]) = |theta_new|^2 / rho^2 is
+    U(0, 1) (disc areas).  40 live sets x 50 walkers, 5 steps, both walker
+    mappings; KS test and the mean."""
+    p = W.gauss2d_sigma05()
+    N, m, steps = 2000, 50, 5
+    n_pad = ((N + 31) // 32) * 32
+    ratios = []
+    rng = np.random.default_rng(4321 + mapping)
+    opt = nat.ns_default_options(correction=3, walker_mapping=mapping)
+    for rep in range(40):
+        r = 1.5 * np.sqrt(rng.uniform(size=N))
+        ang = rng.uniform(0.0, 2.0 * np.pi, size=N)
+        x = ((np.stack([r * np.cos(ang), r * np.sin(ang)], 1) + 5.0) / 10.0).astype(np.float32)
+        th = -5.0 + 10.0 * x.astype(np.float64)
+        l = (-2.0 * np.sum(th * th, 1)).astype(np.float32)
+        order = np.lexsort((np.arange(N), l))
+        worst = order[:m]
+        Wv = l[worst]
+        seeds = rng.choice(np.sort(order[m:]), size=m, replace=True).astype(np.int32)
+        cov = np.cov(x.T.astype(np.float64), bias=True)
+        chol = np.linalg.cholesky(cov + 1e-10 * np.trace(cov) / 2 * np.eye(2)).astype(np.float32)
+        live_x = np.zeros((2, n_pad), dtype=np.float32)
+        live_x[:, :N] = x.T
+        T = opt.t_max
+        out = dict(new_x=torch.zeros(m, 2, device=DEV), new_l=torch.zeros(m, device=DEV),
+                   hist_l=torch.zeros((m, T), device=DEV), hist_x=torch.zeros(m, T, 2, device=DEV),
+                   hist_len=torch.zeros(m, dtype=torch.int32, device=DEV),
+                   evals=torch.zeros(m, dtype=torch.int64, device=DEV),
+                   flags=torch.zeros(m, dtype=torch.int32, device=DEV))
+        nat.ns_slice_replace(p, N, n_pad, m, steps, opt, 77 + rep, rep, _t(live_x), _t(l), _t(seeds, torch.int32),
+                             _t(Wv), _t(chol), torch.zeros(N, dtype=torch.int32, device=DEV), **out)
+        torch.cuda.synchronize()
+        nx = out["new_x"].cpu().numpy().astype(np.float64)
+        tn = -5.0 + 10.0 * nx
+        rho2 = -float(Wv[m - 1]) / 2.0
+        ratios.append(np.sum(tn * tn, 1) / rho2)
+        assert np.all(out["flags"].cpu().numpy() == 0)
+    u = np.concatenate(ratios)
+    assert np.all(u < 1.0 + 1e-5)
+    assert stats.kstest(u, "uniform").pvalue > 1e-4
+    assert abs(u.mean() - 0.5) < 5.0 * math.sqrt(1.0 / 12.0 / len(u))
 
 
 def test_slice_history_cap_and_best_of_worst(nat, oracle):
