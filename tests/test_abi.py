@@ -85,7 +85,8 @@ def test_validation_without_gpu(native):
     # options out of range
     for k, v in [("depth", 9), ("t_max", 0), ("t_max", 65), ("correction", 7), ("width", -1.0),
                  ("precision", 2), ("reeval_margin", -1.0), ("reeval_rel", -1e-3), ("reeval_rel", float("inf")),
-                 ("reeval_defer", -1), ("reeval_defer", 65)]:
+                 ("reeval_defer", -1), ("reeval_defer", 65), ("walker_mapping", 2), ("walker_mapping", -1),
+                 ("mlp_batch_cap", -1), ("mlp_batch_cap", 129)]:
         o = native.ns_default_options(**{k: v})
         with pytest.raises(native.NSError):
             native.ns_create(p, 100, 5, 10, 1e-3, 1, opt=o)
@@ -105,3 +106,13 @@ def test_default_options_match_header(native):
     assert (o.depth, o.correction, o.history_iters, o.t_max, o.e_max, o.s_max) == (0, 2, 1, 64, 64, 128)
     assert o.width == 1.0 and o.vol_frac == 0.5 and o.kmeans_iters == 10
     assert o.precision == 0 and o.reeval_margin == 2.0 and o.reeval_rel == 4e-3 and o.reeval_defer == 4
+    assert o.walker_mapping == 0 and o.mlp_batch_cap == 128
+
+
+def test_autotune_and_mapping_arguments_without_gpu(native):
+    lib = native.lib()
+    assert lib.ns_autotune(None, 0, 3, None, None, None) == native.NS_ERR_ARG
+    assert lib.ns_set_walker_mapping(None, 0, 1) == native.NS_ERR_ARG
+    # a depth-6 tree's scratch: the points, then the deepest tree's FP64 node statistics
+    assert native.ns_cluster_scratch_bytes(1000, 1024, 10) > 4 * 10 * 1024 + 4 * 1000 + 8 * 127 * 100
+    assert native.ns_cluster_scratch_bytes(1, 32, 2) == 0
