@@ -208,6 +208,8 @@ def _slice_case(nat, oracle, p, N, m, n_steps, seed, t, opt_kw=None):
     (lambda: W.rosenbrock(2), 1000, 50, 10), (lambda: W.rosenbrock(10), 1000, 50, 50),
     (lambda: W.mixture4_d5(1), 2000, 200, 25), (lambda: W.gauss_corr(27, 2), 1500, 150, 135),
     (lambda: W.gauss_iso(30, 1.0, -7, 7), 2000, 100, 20), (lambda: W.gauss_iso(3, 1.0, -7, 7), 64, 32, 15),
+    (W.array49, 1000, 10, 10), (lambda: W.bimodal(10), 1000, 5, 50), (W.shell2d, 1000, 1, 10),
+    (lambda: W.shell(7, 2.0, 0.3, -4.0, 4.0), 500, 25, 35),
 ])
 def test_slice_replace_matches_oracle(nat, oracle, maker, N, m, steps):
     p = maker()
@@ -278,6 +280,52 @@ def test_slice_replacement_is_uniform_in_the_constrained_prior(nat, mapping):
         assert np.all(out["flags"].cpu().numpy() == 0)
     u = np.concatenate(ratios)
     assert np.all(u < 1.0 + 1e-5)
+    assert stats.kstest(u, "uniform").pvalue > 1e-4
+    assert abs(u.mean() - 0.5) < 5.0 * math.sqrt(1.0 / 12.0 / len(u))
+
+
+@pytest.mark.parametrize("mapping", [0, 1])
+def test_slice_replacement_is_uniform_in_a_10d_ellipsoid(nat, oracle, mapping):
+    """The same exactness in 10 dimensions: a live set iid uniform in the
+    ellipsoid {(theta - mu)^T Sigma^-1 (theta - mu) <= 9} of the correlated
+    Gaussian (inside the box), the best-of-worst threshold W[m-1] for every
+    walker; the prior mass of {log L > c} grows as (-c)^(d/2), so
+    (log L_new / W[m-1])^(d/2) is U(0, 1).  20 live sets x 50 walkers, 20
+    steps, both walker mappings."""
+    p = W.corr_gauss10(1)
+    d, N, m, steps = p.d, 2000, 50, 20
+    n_pad = ((N + 31) // 32) * 32
+    lik = oracle.Lik(p)
+    A_ = np.linalg.cholesky(p.cov)
+    rng = np.random.default_rng(987 + mapping)
+    opt = nat.ns_default_options(correction=3, walker_mapping=mapping)
+    ratios = []
+    for rep in range(20):
+        g = rng.standard_normal((N, d))
+        u = g / np.linalg.norm(g, axis=1, keepdims=True) * rng.uniform(size=(N, 1)) ** (1.0 / d)
+        x = ((p.mean + 3.0 * u @ A_.T - p.lo) / (p.hi - p.lo)).astype(np.float32)
+        l = oracle.loglike(lik, x.astype(np.float64)).astype(np.float32)
+        order = np.lexsort((np.arange(N), l))
+        Wv = l[order[:m]]
+        seeds = rng.choice(np.sort(order[m:]), size=m, replace=True).astype(np.int32)
+        cov = np.cov(x.T.astype(np.float64), bias=True)
+        chol = np.linalg.cholesky(cov + 1e-10 * np.trace(cov) / d * np.eye(d)).astype(np.float32)
+        live_x = np.zeros((d, n_pad), dtype=np.float32)
+        live_x[:, :N] = x.T
+        T = opt.t_max
+        out = dict(new_x=torch.zeros(m, d, device=DEV), new_l=torch.zeros(m, device=DEV),
+                   hist_l=torch.zeros((m, T), device=DEV), hist_x=torch.zeros(m, T, d, device=DEV),
+                   hist_len=torch.zeros(m, dtype=torch.int32, device=DEV),
+                   evals=torch.zeros(m, dtype=torch.int64, device=DEV),
+                   flags=torch.zeros(m, dtype=torch.int32, device=DEV))
+        nat.ns_slice_replace(p, N, n_pad, m, steps, opt, 77 + rep, rep, _t(live_x), _t(l), _t(seeds, torch.int32),
+                             _t(Wv), _t(chol), torch.zeros(N, dtype=torch.int32, device=DEV), **out)
+        torch.cuda.synchronize()
+        ln = oracle.loglike(lik, out["new_x"].cpu().numpy().astype(np.float64))
+        ratios.append((ln / float(Wv[m - 1])) ** (d / 2))
+        assert np.all(out["flags"].cpu().numpy() == 0)
+    u = np.concatenate(ratios)
+    assert np.all(u < 1.0 + 1e-4)
     assert stats.kstest(u, "uniform").pvalue > 1e-4
     assert abs(u.mean() - 0.5) < 5.0 * math.sqrt(1.0 / 12.0 / len(u))
 
