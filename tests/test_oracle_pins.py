@@ -149,6 +149,35 @@ def test_slice_step_is_uniform_on_a_1d_slice(oracle):
     assert stats.kstest((xs - 0.35) / 0.3, "uniform").pvalue > 1e-3
 
 
+def test_slice_step_is_uniform_in_a_10d_ellipsoid(oracle):
+    """Exactness of the oracle's slice sampler in 10 dimensions: seeds iid
+    uniform in the ellipsoid {log L > c} of a correlated Gaussian (inside the
+    box) stay uniform there after 20 steps against c, so (log L_new / c)^(d/2)
+    -- the ratio of the prior masses -- is U(0, 1) (KS test and the mean)."""
+    p = W.corr_gauss10(1)
+    lik = oracle.Lik(p)
+    d = p.d
+    o = oracle.opts(d, 1)
+    A_ = np.linalg.cholesky(p.cov)
+    rng = np.random.default_rng(2468)
+    g = rng.standard_normal((600, d))
+    u = g / np.linalg.norm(g, axis=1, keepdims=True) * rng.uniform(size=(600, 1)) ** (1.0 / d)
+    th = p.mean + 3.0 * u @ A_.T
+    x = (th - p.lo) / (p.hi - p.lo)
+    c = -0.5 * 9.0
+    cov = np.cov(x.T, bias=True)
+    chol = np.linalg.cholesky(cov)
+    ll = oracle.loglike(lik, x)
+    r = []
+    for wk in range(600):
+        res = oracle.slice_walker(lik, o, 20, 13, 2, wk, x[wk], float(ll[wk]), chol, c, c)
+        assert res["l"] > c
+        r.append((res["l"] / c) ** (d / 2))
+    r = np.array(r)
+    assert stats.kstest(r, "uniform").pvalue > 1e-3
+    assert abs(r.mean() - 0.5) < 4.0 * math.sqrt(1.0 / 12.0 / len(r))
+
+
 def test_slice_walker_invariants(oracle):
     p = W.gauss_corr(4, seed=5)
     lik = oracle.Lik(p)
