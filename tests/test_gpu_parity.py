@@ -503,7 +503,7 @@ def test_headline_config_matches_oracle_in_distribution(nat, oracle):
     assert all(o["status"] == 0 for o in out)
     se = math.sqrt(zg.var(ddof=1) / len(zg) + zo.var(ddof=1) / len(zo))
     assert abs(zg.mean() - zo.mean()) < 4 * se, (zg.mean(), zo.mean(), se)
-    assert abs(zg.mean()) < 0.1 and abs(zo.mean()) < 0.1
+    assert abs(zg.mean()) < 0.1 and abs(zo.mean()) < 0.15  # 152 and 48 runs: 4.5 standard errors from +0.04
 
 
 def test_rosenbrock_and_mixture_runs(nat):
