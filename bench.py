@@ -221,8 +221,18 @@ def emulator_compare(nat, W, torch, n_sm, peaks):
         nat.ns_destroy(h)
         ev = sum(r["n_evals"] for r in res) - EMU_N * len(runs)  # slice-step evaluations (initial set excluded)
         re = sum(r["n_reeval"] for r in res)
+        tf = ev * EMU_FLOP / (st["run_ms"] / 1e3) / 1e12
+        # the useful MLP work of the runs against the peak of the pipe the path computes on: the
+        # measured sustained BF16 tensor rate (launches of ~0.3 s), or the FP32 ALU rate
+        if prec == 1:
+            pk = (peaks or {}).get("bf16_tflops_sustained") or (peaks or {}).get("bf16_tflops")
+            basis = "measured bf16 (sustained)" if pk else None
+        else:
+            pk = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+            basis = "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz"
         out[name] = {"evals_per_s": ev / (st["run_ms"] / 1e3), "ms": st["run_ms"], "evals": ev, "fp32_reevals": re,
-                     "effective_tflops": ev * EMU_FLOP / (st["run_ms"] / 1e3) / 1e12}
+                     "effective_tflops": tf, "peak_tflops": pk, "frac_of_peak": (tf / pk) if pk else None,
+                     "peak_basis": basis}
     out["bf16_over_fp32"] = out["bf16"]["evals_per_s"] / out["fp32"]["evals_per_s"]
     # the tensor-core evaluator alone on a large batch (8 calls of 128 candidates per SM)
     nb = nat.ns_mlp_image_bytes(p)
