@@ -569,3 +569,24 @@ def test_rosenbrock_quadratures_agree():
     assert abs(a - b) < 1e-7
     c = A.logz_rosenbrock_chain(2, 1.0, 100.0, -5.0, 5.0, h=0.002)
     assert abs(a - c) < 1e-7
+
+
+def test_laplace_evidence_is_exact_for_a_linear_network():
+    """oracle/laplace.py (the approximate route to the emulator's evidence)
+    against the closed form of a linear network, where the posterior is a
+    Gaussian truncated by the box: log Z = sum_k log(s_k sqrt(2 pi) [Phi((1 -
+    mu_k)/s_k) - Phi(-mu_k/s_k)]), mu = data/a, s = sigma/a, with modes close to
+    two faces so that the truncation matters."""
+    pytest.importorskip("torch")
+    from oracle import laplace
+    a = np.array([2.0, 0.5, 1.25])
+    mu = np.array([0.03, 0.5, 0.97])
+    sg = np.array([0.05, 0.1, 0.08])
+    spec = W.MLPSpec([3, 3], [np.diag(a)], [np.zeros(3)], a * mu, sg, mu + 0.01)
+    p = W.Problem(W.MLP, 3, np.zeros(3), np.ones(3), mlp=spec, name="linear3")
+    out = laplace.laplace_logz(p, n_mc=400000, seed=1)
+    s = sg / a
+    want = np.sum(np.log(s * math.sqrt(2 * math.pi) * (special.ndtr((1 - mu) / s) - special.ndtr(-mu / s))))
+    assert abs(out["log_z"] - want) < 0.01, (out["log_z"], want)
+    np.testing.assert_allclose(out["theta_hat"], mu, atol=1e-12)
+    assert abs(out["logl_hat"]) < 1e-20
