@@ -124,6 +124,36 @@ def _oracle_one(seed_m):
     return r["n_evals"], time.perf_counter() - t0, r["logz"]
 
 
+def _oracle_mlp_one(seed_n):
+    """FP64 oracle evaluations of the emulator likelihood at n seeded points."""
+    seed, n = seed_n
+    sys.path.insert(0, ROOT)
+    import numpy as np
+    from oracle import oracle as O
+    from paper_2608_28514_gb300 import workloads as W
+    p = W.mlp_emulator(1)
+    lik = O.Lik(p)
+    x = np.random.default_rng(seed).uniform(size=(n, p.d))
+    t0 = time.perf_counter()
+    O.loglike(lik, x)
+    return n, time.perf_counter() - t0
+
+
+def emulator_cpu_baseline(n_proc, per_proc=1000):
+    """The emulator likelihood on the host cores: the FP64 oracle's MLP, one
+    process per core, per_proc evaluations each (a sample of the likelihood
+    work; whole oracle runs of this workload take hours)."""
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(n_proc) as pool:
+        out = pool.map(_oracle_mlp_one, [(100 + k, per_proc) for k in range(n_proc)])
+    wall = time.perf_counter() - t0
+    n = sum(o[0] for o in out)
+    return {"value": n / wall, "unit": UNIT, "cores": n_proc, "kind": "oracle",
+            "sample": f"{n} FP64 evaluations of the 27-512x4-2000 MLP likelihood at seeded points, {per_proc} per "
+                      f"process, {wall:.1f} s wall (pool start-up included)"}
+
+
 def oracle_sample(n_proc, seeds, m):
     ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
@@ -201,7 +231,7 @@ class ClockSampler:
 # --------------------------------------------------------------------------
 # the emulator likelihood: BF16 vs FP32 path
 # --------------------------------------------------------------------------
-def emulator_compare(nat, W, torch, n_sm, peaks):
+def emulator_compare(nat, W, torch, n_sm, peaks, cpu_cores=0):
     p = W.mlp_emulator(1)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     runs = [(p, EMU_N, EMU_M, EMU_STEPS, 1e-3, s) for s in range(1, n_sm + 1)]
@@ -234,6 +264,7 @@ def emulator_compare(nat, W, torch, n_sm, peaks):
                      "effective_tflops": tf, "peak_tflops": pk, "frac_of_peak": (tf / pk) if pk else None,
                      "peak_basis": basis}
     out["bf16_over_fp32"] = out["bf16"]["evals_per_s"] / out["fp32"]["evals_per_s"]
+    out["cpu_baseline"] = emulator_cpu_baseline(cpu_cores) if cpu_cores > 0 else None
     # the tensor-core evaluator alone on a large batch (8 calls of 128 candidates per SM)
     nb = nat.ns_mlp_image_bytes(p)
     img = torch.empty(nb + 1024, dtype=torch.uint8, device="cuda")
@@ -822,7 +853,7 @@ def main():
     emulator = None
     if not args.no_emulator:
         emulator = emulator_compare(nat, W, torch, torch.cuda.get_device_properties(local).multi_processor_count,
-                                    measured_peaks())
+                                    measured_peaks(), cpu_cores=0 if args.no_cpu else min(16, host_cores()))
     hetero = None
     if not args.no_batch256 and world == 1:
         hetero = batch256(nat, W, analytic, mappings=(0, "auto"))
