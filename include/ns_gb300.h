@@ -48,7 +48,7 @@ extern "C" {
 #define NS_MAX_GMM_MODES 64    /* GMM components */
 #define NS_GMM_CAPACITY 512    /* GMM: n_modes x (d rounded up to its register class) */
 #define NS_MAX_DEPTH 6         /* cluster tree depth: up to 64 leaves, 127 nodes */
-#define NS_MAX_BATCH 256       /* m, walkers per run (one thread each) */
+#define NS_MAX_BATCH 256       /* m, walkers per run (one thread, or one warp, each) */
 #define NS_MAX_LIVE 65536      /* N_live per run */
 #define NS_MAX_HISTORY 64      /* history slots per walker */
 #define NS_PURPOSE_SEED 0x10000u
