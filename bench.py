@@ -143,10 +143,8 @@ def emulator_cpu_baseline(n_proc, per_proc=1000):
     """The emulator likelihood on the host cores: the FP64 oracle's MLP, one
     process per core, per_proc evaluations each (a sample of the likelihood
     work; whole oracle runs of this workload take hours)."""
-    ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
-    with ctx.Pool(n_proc) as pool:
-        out = pool.map(_oracle_mlp_one, [(100 + k, per_proc) for k in range(n_proc)])
+    out = _spawn_map(_oracle_mlp_one, [(100 + k, per_proc) for k in range(n_proc)], n_proc)
     wall = time.perf_counter() - t0
     n = sum(o[0] for o in out)
     return {"value": n / wall, "unit": UNIT, "cores": n_proc, "kind": "oracle",
@@ -154,11 +152,18 @@ def emulator_cpu_baseline(n_proc, per_proc=1000):
                       f"process, {wall:.1f} s wall (pool start-up included)"}
 
 
+def _spawn_map(fn, items, n_proc):
+    """fn over items in n_proc spawned processes (safe after CUDA has been
+    initialised); a worker that dies raises BrokenProcessPool instead of
+    leaving the caller waiting."""
+    import concurrent.futures as cf
+    with cf.ProcessPoolExecutor(max_workers=max(1, n_proc), mp_context=mp.get_context("spawn")) as ex:
+        return list(ex.map(fn, items))
+
+
 def oracle_sample(n_proc, seeds, m):
-    ctx = mp.get_context("spawn")
     t0 = time.perf_counter()
-    with ctx.Pool(n_proc) as pool:
-        out = pool.map(_oracle_one, [(s, m) for s in seeds])
+    out = _spawn_map(_oracle_one, [(s, m) for s in seeds], n_proc)
     wall = time.perf_counter() - t0
     evals = sum(o[0] for o in out)
     return evals, wall, out

@@ -320,10 +320,34 @@ def _run_summary(args):
     return {k: r[k] for k in ("logz", "logz_err", "info", "n_evals", "n_iter", "status")}
 
 
-def run_many(jobs, workers):
+def run_many(jobs, workers, fn=None):
     """Whole oracle runs (problem, N, m, n_steps, stop_frac, seed) in a pool
     of `workers` processes started with spawn (safe in a process that has
-    already initialised CUDA).  Returns each run's summary, in order."""
+    already initialised CUDA).  Returns each run's summary, in order.  A
+    worker that dies (a crash, a kill) is detected: the call raises
+    RuntimeError naming the lost jobs instead of waiting for them."""
+    import concurrent.futures as cf
     import multiprocessing as mp
-    with mp.get_context("spawn").Pool(max(1, int(workers))) as pool:
-        return pool.map(_run_summary, list(jobs))
+    from concurrent.futures.process import BrokenProcessPool
+    jobs = list(jobs)
+    fn = fn or _run_summary
+    with cf.ProcessPoolExecutor(max_workers=max(1, int(workers)), mp_context=mp.get_context("spawn")) as ex:
+        futs = [ex.submit(fn, j) for j in jobs]
+        out, lost = [], []
+        for k, f in enumerate(futs):
+            try:
+                out.append(f.result())
+            except BrokenProcessPool:
+                lost.append(k)
+                out.append(None)
+    if lost:
+        raise RuntimeError(f"oracle worker died: {len(lost)} of {len(jobs)} runs lost (jobs {lost[:8]})")
+    return out
+
+
+def _exit_worker(job):
+    """A job that ends its worker process abruptly (for the failure-detection test)."""
+    import os
+    if job == "die":
+        os._exit(3)
+    return job

@@ -590,3 +590,12 @@ def test_laplace_evidence_is_exact_for_a_linear_network():
     assert abs(out["log_z"] - want) < 0.01, (out["log_z"], want)
     np.testing.assert_allclose(out["theta_hat"], mu, atol=1e-12)
     assert abs(out["logl_hat"]) < 1e-20
+
+
+def test_oracle_pool_detects_a_dead_worker(oracle):
+    """Host-side failure detection: a pool worker that exits abruptly is
+    reported (RuntimeError) instead of hanging the caller; healthy pools
+    return every result in order."""
+    assert oracle.run_many(["a", "b", "c"], 2, fn=oracle._exit_worker) == ["a", "b", "c"]
+    with pytest.raises(RuntimeError, match="worker died"):
+        oracle.run_many(["a", "die", "c"], 2, fn=oracle._exit_worker)
