@@ -43,12 +43,15 @@ sys.path.insert(0, ROOT)
 METRIC = "likelihood evals/s and wall-time to log Z at |ΔlogZ|<0.1; BF16 vs FP32 path"
 UNIT = "evals/s"
 D, N_LIVE, M, N_STEPS, STOP = 10, 1000, 100, 50, 1e-3
-# algorithmic FP32 work of one correlated-Gaussian evaluation at d = 10:
-# candidate x + t v (d FMA), y = theta - mean (d FMA), z = L^T y
-# (d(d+1)/2 FMA), |z|^2 (d FMA)
-FLOP_PER_EVAL = 2 * (3 * D + D * (D + 1) // 2)
-# FP32 peak: 152 SMs x 128 FP32 lanes x 2 FLOP x 2070 MHz (maximum SM clock)
-SMS, FP32_LANES, SM_MAX_MHZ = 152, 128, 2070.0
+# algorithmic FP32 work of one correlated-Gaussian likelihood at d = 10:
+# the triangular product z = L^T y with the Cholesky factor of the
+# precision (d(d+1)/2 FMA = d(d+1) FLOP) plus y = theta - mean and |z|^2
+# (2d FLOP): 130 FLOP; the slice arithmetic around the likelihood (the
+# candidate x + t v, the unit-cube map) is not counted
+FLOP_PER_EVAL = D * (D + 1) + 2 * D
+# FP32 peak: SMs (from the device) x 128 FP32 lanes x 2 FLOP x 2070 MHz
+# (the maximum SM clock)
+FP32_LANES, SM_MAX_MHZ = 128, 2070.0
 
 
 # the 27-D emulator-style likelihood (MLP 27 -> 512 x 4 -> 2000, SiLU),
@@ -263,8 +266,8 @@ def emulator_compare(nat, W, torch, n_sm, peaks, cpu_cores=0):
             pk = (peaks or {}).get("bf16_tflops_sustained") or (peaks or {}).get("bf16_tflops")
             basis = "measured bf16 (sustained)" if pk else None
         else:
-            pk = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
-            basis = "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz"
+            pk = n_sm * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+            basis = f"FP32 FMA: {n_sm} SMs x 128 lanes x 2 FLOP x 2070 MHz"
         out[name] = {"evals_per_s": ev / (st["run_ms"] / 1e3), "ms": st["run_ms"], "evals": ev, "fp32_reevals": re,
                      "effective_tflops": tf, "peak_tflops": pk, "frac_of_peak": (tf / pk) if pk else None,
                      "peak_basis": basis}
@@ -317,7 +320,7 @@ def correction_sweep(n_seeds, n_live=1000):
     import torch
 
     from paper_2608_28514_gb300 import _native as nat
-    from paper_2608_28514_gb300 import analytic
+    from tests import analytic
     from paper_2608_28514_gb300 import workloads as W
 
     p = W.gauss2d_unit_box7()
@@ -357,7 +360,7 @@ def clustering_tests(n_seeds, m=1, n_live=1000):
     import torch
 
     from paper_2608_28514_gb300 import _native as nat
-    from paper_2608_28514_gb300 import analytic
+    from tests import analytic
     from paper_2608_28514_gb300 import workloads as W
 
     tests = (("test1_array49", W.array49(), 6), ("test2_bimodal10", W.bimodal(10), 1),
@@ -429,7 +432,7 @@ def comparison_shapes(n_seeds, m=1):
     import torch
 
     from paper_2608_28514_gb300 import _native as nat
-    from paper_2608_28514_gb300 import analytic
+    from tests import analytic
     from paper_2608_28514_gb300 import workloads as W
 
     cases = [(f"gauss_d{d}", W.gauss_unit_box7(d), 1000) for d in (2, 4, 8, 16, 32)]
@@ -518,7 +521,7 @@ def mapping_study(n_runs):
     import torch
 
     from paper_2608_28514_gb300 import _native as nat
-    from paper_2608_28514_gb300 import analytic
+    from tests import analytic
     from paper_2608_28514_gb300 import workloads as W
 
     shapes = [("gauss2d_sigma05_N100_m1", W.gauss2d_sigma05(), 100, 1, 10),
@@ -732,7 +735,7 @@ def main():
     import torch.distributed as dist
 
     from paper_2608_28514_gb300 import _native as nat
-    from paper_2608_28514_gb300 import analytic
+    from tests import analytic
     from paper_2608_28514_gb300 import workloads as W
 
     torch.cuda.set_device(local)
@@ -815,7 +818,8 @@ def main():
     avg_launch_s = (ker_ms / 1e3) / max(1, launches)
     flops_per_launch = FLOP_PER_EVAL * evals / max(1, launches)
     achieved = flops_per_launch / avg_launch_s / 1e12
-    peak = SMS * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
+    n_sm = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = n_sm * FP32_LANES * 2 * SM_MAX_MHZ * 1e6 / 1e12
     # DRAM bytes per launch from the ncu record of this kernel, scaled by the
     # run-iterations of a launch; null once the kernel sources have changed
     traffic = None
@@ -830,7 +834,7 @@ def main():
             traffic = None
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
                 "traffic": traffic, "kernel": "nsd::k_run<10>",
-                "peak_basis": "FP32 FMA: 152 SMs x 128 lanes x 2 FLOP x 2070 MHz (recipe unit counts, max clock)",
+                "peak_basis": f"FP32 FMA: {n_sm} SMs (device) x 128 lanes x 2 FLOP x 2070 MHz (max clock)",
                 "flop_per_eval": FLOP_PER_EVAL}
 
     # end to end through the C ABI from host buffers

@@ -174,6 +174,13 @@ typedef struct {
  * in the slice phase (a4-a7).  On return every run is in its state after the
  * warm-up, bit for bit.  The mappings take the same decisions with FP32 sums
  * in another order; the MLP configurations give identical runs.
+ * A probe is never allowed to dominate the job it tunes: after the warm-up
+ * the iterations left are estimated from each run's stopping rule (with its
+ * current lmax and log Z, (N/m)(lmax - k/N - log Z - log stop_frac), at
+ * most max_iter minus the iterations done); if the probe's iterations
+ * (configurations x probe_iters) exceed a quarter of the longest run's
+ * estimate, nothing is probed and every run keeps its configuration
+ * (out_ratio NaN).
  * out_choice [n_runs] (host, may be NULL): analytic runs 1 = per warp, 0 =
  * per thread; MLP runs the candidate cap (128, 64, or 0 = equal calls).
  * out_ratio [n_runs] (host, may be NULL): the second configuration's cycles
@@ -306,16 +313,27 @@ void ns_destroy(ns_handle* h);
  * structs as for ns_create_batch (opt NULL = defaults; opt->dead_cap is
  * ignored, dead_cap sizes the caller's arrays).
  *
- * Limits and errors: a run whose working set does not fit the array
- * (roughly d <= 32, N <= 4096, m <= 256 with the default history) is
- * rejected with NS_ERR_ARG and a message giving the bytes it needs; so is
- * dead_cap < N + m.  Every call shares the one array: it is re-initialised
- * at the start of each call, and calls whose GPU work overlaps (two host
- * threads, or two streams) race on it and give wrong results -- serialise
- * them.  The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress) with that device current; make that first call
- * before any stream capture begins.  The call waits for the run to finish
- * on `stream`. */
+ * Limits and errors: the run's working set is, to within a few KB of
+ * descriptors and 256-byte rounding,
+ *   4 m (n_slice_steps r + t_max (d + 1) + 2 d + 2)        walkers
+ *   + 4 n_pad (d + 2) [+ 4 n_pad (d + 1) if depth > 0]      live set
+ *   + 12 n_nodes d^2 (+ the tree scratch of a spilled run)  cluster tables
+ * bytes, with r = c + 4 rounded up to a multiple of 4 (the per-step
+ * direction row; c = d rounded up to its register class 2,4,6,8,10,12,16,
+ * 20,24,28,32), n_pad = N rounded up to 32, n_nodes = 2^(depth+1) - 1.  The slice steps usually dominate: d = 32,
+ * N = 4096, m = 128, 160 slice steps, depth 0 needs about 4.6 MB and fits;
+ * the same run with m = 256 needs about 8.7 MB and does not.  A run that
+ * does not fit is rejected with NS_ERR_ARG and a message giving the bytes
+ * it needs; so is dead_cap < N + m.  Every call shares the one array: it is
+ * re-initialised at the start of each call, and calls whose GPU work
+ * overlaps (two host threads, or two streams) race on it and give wrong
+ * results -- serialise them.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress) with that device current
+ * and keeps it for the life of the process; make that first call before
+ * any stream capture begins.  The kept address belongs to the device's
+ * primary context: after cudaDeviceReset it is stale, so a program that
+ * resets a device must not call ns_run_noalloc on it again.  The call waits
+ * for the run to finish on `stream`. */
 #define NS_NOALLOC_SCRATCH_BYTES (8u << 20)
 ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt, float* dead_x, float* dead_logl,
                          double* dead_logw, long long dead_cap, ns_result_t* out, void* stream);

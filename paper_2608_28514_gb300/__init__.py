@@ -2,8 +2,8 @@
 
 The sampler runs in the CUDA library ``libns_gb300.so`` behind the C ABI of
 ``include/ns_gb300.h``; :mod:`._native` is its ctypes binding.  The
-workload generators (:mod:`.workloads`) and the closed-form evidences
-(:mod:`.analytic`) are host-side helpers for tests and benchmarks.
+workload generators (:mod:`.workloads`) are host-side helpers that describe
+the seeded synthetic problems.
 """
 from . import workloads  # noqa: F401
 

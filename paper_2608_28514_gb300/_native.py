@@ -398,6 +398,42 @@ def ns_destroy(h):
         h.ptr = _vp()
 
 
+def noalloc_capacity(d, dead_x, dead_logl, dead_logw):
+    """The dead-point capacity that ns_run_noalloc may write into the
+    caller's tensors, after checking them: the C entry point gets bare
+    device pointers and cannot see a buffer's size, so every tensor must be
+    contiguous, of its dtype (float32, float32, float64), on one CUDA device,
+    and dead_x must hold cap * d floats and dead_logw cap doubles, where cap
+    = dead_logl.numel().  Raises NSError(NS_ERR_ARG) otherwise, before any
+    device work."""
+    import torch
+    bufs = (("dead_x", dead_x, torch.float32), ("dead_logl", dead_logl, torch.float32),
+            ("dead_logw", dead_logw, torch.float64))
+    for name, t, dt in bufs:
+        if not isinstance(t, torch.Tensor):
+            raise NSError(NS_ERR_ARG, f"ns_run_noalloc: {name} must be a torch tensor")
+        if t.dtype != dt:
+            raise NSError(NS_ERR_ARG, f"ns_run_noalloc: {name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise NSError(NS_ERR_ARG, f"ns_run_noalloc: {name} must be contiguous")
+    cap = int(dead_logl.numel())
+    if int(dead_x.numel()) < cap * int(d):
+        raise NSError(NS_ERR_ARG, f"ns_run_noalloc: dead_x holds {dead_x.numel()} floats, "
+                                  f"fewer than cap * d = {cap} * {d}")
+    if int(dead_logw.numel()) < cap:
+        raise NSError(NS_ERR_ARG, f"ns_run_noalloc: dead_logw holds {dead_logw.numel()} values, "
+                                  f"fewer than cap = {cap}")
+    devs = {t.device for _, t, _ in bufs}
+    if any(dv.type != "cuda" for dv in devs) or len(devs) != 1:
+        raise NSError(NS_ERR_ARG, "ns_run_noalloc: dead_x, dead_logl and dead_logw must be on one CUDA "
+                                  f"device, got {sorted(str(dv) for dv in devs)}")
+    dev = next(iter(devs))
+    if dev.index is not None and dev.index != torch.cuda.current_device():
+        raise NSError(NS_ERR_ARG, f"ns_run_noalloc: the buffers are on {dev}, the current device is "
+                                  f"cuda:{torch.cuda.current_device()}")
+    return cap
+
+
 def ns_run_noalloc(problem, n_live, m, n_slice_steps, stop_frac, seed, dead_x, dead_logl, dead_logw,
                    opt=None, stream=None, check=True):
     """One whole run that allocates no device memory: the library works in
@@ -406,6 +442,7 @@ def ns_run_noalloc(problem, n_live, m, n_slice_steps, stop_frac, seed, dead_x, d
     (float32, float32, float64).  For callers that cannot allocate device
     memory themselves (see ns_run_noalloc in include/ns_gb300.h).  Returns
     the scalar results; samples stay in the caller's tensors."""
+    cap = noalloc_capacity(int(problem.d), dead_x, dead_logl, dead_logw)
     keep = _Keep()
     lik = likelihood_struct(problem, keep)
     pr = NsProblem()
@@ -419,7 +456,6 @@ def ns_run_noalloc(problem, n_live, m, n_slice_steps, stop_frac, seed, dead_x, d
     pr.stop_frac = float(stop_frac)
     pr.seed = int(seed) & (2**64 - 1)
     r = NsResult()
-    cap = int(dead_logl.numel())
     st = lib().ns_run_noalloc(C.byref(pr), C.byref(opt) if opt is not None else None, _ptr(dead_x),
                               _ptr(dead_logl), _ptr(dead_logw), cap, C.byref(r), _stream_ptr(stream))
     if check:

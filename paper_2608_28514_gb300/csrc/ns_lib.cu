@@ -981,6 +981,39 @@ ns_status ns_set_walker_mapping(ns_handle* h, int run, int warp) {
   return NS_OK;
 }
 
+extern "C++" {
+namespace {
+
+// A list of device-to-device copies done by one launch: block b copies
+// segment b (sizes are multiples of 4 bytes; 16-byte words where the
+// addresses and size allow).
+struct CopySeg {
+  const char* src;
+  char* dst;
+  long long bytes;
+};
+__global__ void k_copy_segments(const CopySeg* __restrict__ seg) {
+  const CopySeg S = seg[blockIdx.x];
+  const bool v16 = ((reinterpret_cast<uintptr_t>(S.src) | reinterpret_cast<uintptr_t>(S.dst) | (uintptr_t)S.bytes) &
+                    15u) == 0;
+  if (v16) {
+    const int4* a = reinterpret_cast<const int4*>(S.src);
+    int4* b = reinterpret_cast<int4*>(S.dst);
+    for (long long i = threadIdx.x; i < S.bytes / 16; i += blockDim.x) b[i] = a[i];
+  } else {
+    const int* a = reinterpret_cast<const int*>(S.src);
+    int* b = reinterpret_cast<int*>(S.dst);
+    for (long long i = threadIdx.x; i < S.bytes / 4; i += blockDim.x) b[i] = a[i];
+  }
+}
+
+// ns_autotune's minimum-job guard: the largest share of the remaining job
+// (in iterations) a probe may take.
+constexpr double kAutotuneMaxProbeFrac = 0.25;
+
+}  // namespace
+}  // extern "C++"
+
 ns_status ns_autotune(ns_handle* h, int warm_iters, int probe_iters, int* out_choice, double* out_ratio,
                       void* stream) {
   if (!h || warm_iters < 0 || probe_iters < 1 || probe_iters > 1000) return NS_ERR_ARG;
@@ -990,25 +1023,82 @@ ns_status ns_autotune(ns_handle* h, int warm_iters, int probe_iters, int* out_ch
     const ns_status st = run_impl(h, stream, warm_iters, false);
     if (st != NS_OK) return st;
   }
+  // Minimum-job guard: a probe costs modes x probe_iters iterations (the
+  // snapshot and its restores are three copy launches); it is skipped, and
+  // every run keeps its current configuration, when those iterations exceed
+  // a quarter of the job that is left.  The iterations left of run r are
+  // estimated from its stopping rule, lmax - k/N - log Z < log(stop_frac):
+  // with lmax and log Z frozen at their values now, (N/m) (lmax - k/N -
+  // log Z - log stop_frac), at most max_iter - n_iter; the job is its
+  // longest run.
+  {
+    std::vector<RunState> now(n);
+    std::vector<std::vector<float>> ll(n);
+    NS_CUDA(cudaMemcpyAsync(now.data(), h->d_states, sizeof(RunState) * n, cudaMemcpyDeviceToHost, s), &h->err);
+    for (int r = 0; r < n; ++r) {
+      ll[r].resize(h->runs[r].N);
+      NS_CUDA(cudaMemcpyAsync(ll[r].data(), h->runs[r].live_l, sizeof(float) * h->runs[r].N, cudaMemcpyDeviceToHost,
+                              s),
+              &h->err);
+    }
+    NS_CUDA(cudaStreamSynchronize(s), &h->err);
+    double left_iters = 0.0;
+    int modes_est = 1;
+    for (int r = 0; r < n; ++r) {
+      const RunState& S = now[r];
+      const RunDesc& R = h->runs[r];
+      modes_est = std::max(modes_est, R.mlp_desc == nullptr ? 2 : (R.precision == 1 ? 3 : 1));
+      if (S.stopped || S.status != 0) continue;
+      double left = (double)(R.max_iter - S.n_iter);
+      if (S.initialized && std::isfinite(S.logz)) {
+        float lmax = -INFINITY;
+        for (float v : ll[r]) lmax = std::max(lmax, v);
+        const double gap = (double)lmax - (double)S.k / R.N - S.logz - R.log_stop;
+        left = std::min(left, std::max(0.0, gap) * (double)R.N / R.m);
+      }
+      left_iters = std::max(left_iters, left);
+    }
+    if ((double)modes_est * probe_iters > kAutotuneMaxProbeFrac * left_iters) {
+      for (int r = 0; r < n; ++r) {
+        if (out_choice)
+          out_choice[r] = h->runs[r].mlp_desc == nullptr ? h->runs[r].walker_warp : h->runs[r].mlp_round_cap;
+        if (out_ratio) out_ratio[r] = std::nan("");
+      }
+      return NS_OK;
+    }
+  }
   // device snapshot of every run's state after the warm-up
   size_t bytes = 0;
   for (int r = 0; r < n; ++r) for_each_run_buffer(h, r, [&](void*, size_t b) { bytes += (b + 255) & ~(size_t)255; });
   char* snap = nullptr;
-  if (cudaMalloc(&snap, bytes) != cudaSuccess) {
+  size_t n_seg_max = 0;
+  for (int r = 0; r < n; ++r) for_each_run_buffer(h, r, [&](void*, size_t) { ++n_seg_max; });
+  if (cudaMalloc(&snap, bytes + 2 * sizeof(CopySeg) * n_seg_max) != cudaSuccess) {
     set_err(&h->err, "ns_autotune: cannot allocate %zu bytes for the state snapshot", bytes);
     return NS_ERR_OOM;
   }
-  auto copy_all = [&](bool save) {
+  // the snapshot and each restore are one launch of a segment-list copy (a
+  // few hundred small buffers per batch of runs: one cudaMemcpyAsync each
+  // cost more than the probe itself on short jobs)
+  std::vector<CopySeg> seg_save, seg_load;
+  {
     size_t o = 0;
-    cudaError_t e = cudaSuccess;
-    for (int r = 0; r < n && e == cudaSuccess; ++r)
+    for (int r = 0; r < n; ++r)
       for_each_run_buffer(h, r, [&](void* p, size_t b) {
-        if (e == cudaSuccess)
-          e = save ? cudaMemcpyAsync(snap + o, p, b, cudaMemcpyDeviceToDevice, s)
-                   : cudaMemcpyAsync(p, snap + o, b, cudaMemcpyDeviceToDevice, s);
+        seg_save.push_back({static_cast<const char*>(p), snap + o, (long long)b});
+        seg_load.push_back({snap + o, static_cast<char*>(p), (long long)b});
         o += (b + 255) & ~(size_t)255;
       });
-    return e;
+  }
+  const int n_seg = (int)seg_save.size();
+  CopySeg* d_seg = reinterpret_cast<CopySeg*>(snap + bytes);
+  cudaError_t e0 = cudaMemcpyAsync(d_seg, seg_save.data(), sizeof(CopySeg) * n_seg, cudaMemcpyHostToDevice, s);
+  if (e0 == cudaSuccess)
+    e0 = cudaMemcpyAsync(d_seg + n_seg, seg_load.data(), sizeof(CopySeg) * n_seg, cudaMemcpyHostToDevice, s);
+  auto copy_all = [&](bool save) {
+    if (e0 != cudaSuccess) return e0;
+    k_copy_segments<<<n_seg, 256, 0, s>>>(d_seg + (save ? 0 : n_seg));
+    return cudaGetLastError();
   };
   const std::vector<RunDesc> keep = h->runs;
   // the configurations a run can take, the first being the default: an

@@ -11,7 +11,7 @@ import math
 import numpy as np
 from scipy import integrate, special
 
-from . import workloads as W
+from paper_2608_28514_gb300 import workloads as W
 
 _SQ2 = math.sqrt(2.0)
 

@@ -116,3 +116,26 @@ def test_autotune_and_mapping_arguments_without_gpu(native):
     # a depth-6 tree's scratch: the points, then the deepest tree's FP64 node statistics
     assert native.ns_cluster_scratch_bytes(1000, 1024, 10) > 4 * 10 * 1024 + 4 * 1000 + 8 * 127 * 100
     assert native.ns_cluster_scratch_bytes(1, 32, 2) == 0
+
+
+def test_noalloc_buffers_are_checked_before_any_launch():
+    """ns_run_noalloc hands bare pointers to the library, which cannot see
+    a buffer's size: the binding rejects a wrong dtype, a short or
+    non-contiguous buffer, or host memory with NS_ERR_ARG before anything
+    reaches the device (so this runs without a GPU)."""
+    torch = pytest.importorskip("torch")
+    from paper_2608_28514_gb300 import _native as nat
+    cap, d = 100, 3
+    ok = dict(dead_x=torch.empty(cap, d), dead_logl=torch.empty(cap), dead_logw=torch.empty(cap, dtype=torch.float64))
+    bad = [
+        (dict(ok, dead_logw=torch.empty(cap)), "float64"),
+        (dict(ok, dead_x=torch.empty(cap, d, dtype=torch.float64)), "float32"),
+        (dict(ok, dead_x=torch.empty(cap, d - 1)), "cap * d"),
+        (dict(ok, dead_logw=torch.empty(cap - 1, dtype=torch.float64)), "cap ="),
+        (dict(ok, dead_x=torch.empty(d, cap).t()), "contiguous"),
+        (ok, "CUDA"),
+    ]
+    for kw, what in bad:
+        with pytest.raises(nat.NSError) as ei:
+            nat.noalloc_capacity(d, kw["dead_x"], kw["dead_logl"], kw["dead_logw"])
+        assert ei.value.status == nat.NS_ERR_ARG and what in str(ei.value), (what, str(ei.value))

@@ -15,7 +15,7 @@ import os
 import numpy as np
 import pytest
 
-from paper_2608_28514_gb300 import analytic as A
+from tests import analytic as A
 from paper_2608_28514_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu

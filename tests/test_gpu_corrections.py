@@ -10,7 +10,7 @@ best-of-worst threshold inflates Z more and more as m/N grows.
 import numpy as np
 import pytest
 
-from paper_2608_28514_gb300 import analytic as A
+from tests import analytic as A
 from paper_2608_28514_gb300 import workloads as W
 
 pytestmark = pytest.mark.gpu

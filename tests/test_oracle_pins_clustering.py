@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 from scipy import special, stats
 
-from paper_2608_28514_gb300 import analytic as A
+from tests import analytic as A
 from paper_2608_28514_gb300 import workloads as W
 
 GOLDEN = os.path.join(os.path.dirname(__file__), "golden")
