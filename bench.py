@@ -99,6 +99,8 @@ def parse():
     ap.add_argument("--profile-mlp-runs", type=int, default=0, metavar="R",
                     help="profiling case: R runs of the 27-D emulator workload (BF16 path), one iteration per "
                          "launch, three launches, small dead buffers; prints no bench line")
+    ap.add_argument("--depth-sweep", type=int, default=0, metavar="SEEDS",
+                    help="the tree-depth study of section 2.3 (Test 2 truncated to d = 2..10, depth 0..6) and exit")
     ap.add_argument("--correction-sweep", type=int, default=0, metavar="SEEDS",
                     help="run the batching-error study (correction schemes x m/N) with SEEDS runs per point, "
                          "print its JSON table and exit")
@@ -307,15 +309,18 @@ def emulator_compare(nat, W, torch, n_sm, peaks, cpu_cores=0):
 # --------------------------------------------------------------------------
 CORRECTION_SCHEMES = (("naive", 0, 1), ("sorting", 1, 1), ("history_K1", 2, 1), ("history_K2", 2, 2),
                       ("history_K10", 2, 10), ("best_of_worst", 3, 1))
-SWEEP_M = (1, 2, 5, 10, 20, 50, 100, 200)
+# (m, N_live): m/N = 0.001 .. 0.2 at N = 1000, and m/N = 0.5 at N = 512
+# (m = 256, the library's largest batch)
+SWEEP_MN = tuple((m, 1000) for m in (1, 2, 5, 10, 20, 50, 100, 200)) + ((256, 512),)
 
 
-def correction_sweep(n_seeds, n_live=1000):
-    """The 2-D unit Gaussian on [-7, 7]^2, N_live = 1000, 5 d = 10 slice steps:
-    for every correction scheme and m/N in {0.001 .. 0.2}, the mean and
-    standard deviation of log Z - log Z_true over n_seeds runs, all runs of a
-    scheme in one batch.  m/N = 0.5 and 1 lie outside the library's limits
-    (m <= 256 walkers per run; m = N leaves no survivor to seed a walker)."""
+def correction_sweep(n_seeds):
+    """The 2-D unit Gaussian on [-7, 7]^2, 5 d = 10 slice steps: for every
+    correction scheme and m/N in {0.001 .. 0.2} (N_live = 1000) and 0.5
+    (N_live = 512, m = 256), the mean and standard deviation of
+    log Z - log Z_true over n_seeds runs, all runs of a scheme in one batch.
+    m/N = 1 lies outside the method as read here (m = N leaves no survivor
+    to seed a walker)."""
     import numpy as np
     import torch
 
@@ -329,22 +334,23 @@ def correction_sweep(n_seeds, n_live=1000):
     t_all = 0.0
     for name, corr, K in CORRECTION_SCHEMES:
         opt = nat.ns_default_options(correction=corr, history_iters=K)
-        runs = [(p, n_live, m, 10, 1e-3, 1000 * m + s) for m in SWEEP_M for s in range(1, n_seeds + 1)]
+        runs = [(p, n_live, m, 10, 1e-3, 1000 * m + s) for m, n_live in SWEEP_MN for s in range(1, n_seeds + 1)]
         h = nat.ns_create_batch(runs, opt)
         nat.ns_run(h)
         t_all += nat.ns_get_stats(h)["run_ms"]
         res = [nat.ns_summary(h, r) for r in range(len(runs))]
         nat.ns_destroy(h)
         rows = {}
-        for i, m in enumerate(SWEEP_M):
+        for i, (m, n_live) in enumerate(SWEEP_MN):
             z = np.array([r["log_z"] for r in res[i * n_seeds:(i + 1) * n_seeds]]) - truth
             rel = sum(r["n_relaxed"] for r in res[i * n_seeds:(i + 1) * n_seeds])
-            rows[f"{m / n_live:g}"] = {"m": m, "mean_dlogz": float(z.mean()), "std": float(z.std(ddof=1)),
-                                       "sem": float(z.std(ddof=1) / np.sqrt(n_seeds)), "relaxed_points": int(rel)}
+            rows[f"{m / n_live:g}"] = {"m": m, "n_live": n_live, "mean_dlogz": float(z.mean()),
+                                       "std": float(z.std(ddof=1)), "sem": float(z.std(ddof=1) / np.sqrt(n_seeds)),
+                                       "relaxed_points": int(rel)}
         table[name] = rows
     torch.cuda.synchronize()
-    return {"study": "batching error vs m/N (section 3.2): 2-D unit Gaussian, prior [-7,7]^2, N_live=%d, "
-                     "10 slice steps, %d seeds per point" % (n_live, n_seeds),
+    return {"study": "batching error vs m/N (section 3.2): 2-D unit Gaussian, prior [-7,7]^2, N_live=1000 "
+                     "(512 at m/N=0.5), 10 slice steps, %d seeds per point" % n_seeds,
             "log_z_true": truth, "device_ms": t_all, "schemes": table}
 
 
@@ -383,6 +389,49 @@ def clustering_tests(n_seeds, m=1, n_live=1000):
     torch.cuda.synchronize()
     return {"study": "clustering tests (section 2.3, Table 1): N_live=%d, m=%d, %d runs per configuration"
                      % (n_live, m, n_seeds), "tests": out}
+
+
+def depth_sweep(n_seeds, m=1, n_live=1000, dims=(2, 4, 6, 8, 10), depths=(0, 1, 2, 3, 4, 5, 6)):
+    """The depth study of section 2.3 (Fig. 1): Test 2 (two Gaussians of
+    weights 1/10 and 1 at -10 and +10 in every coordinate, variances
+    alternating 0.1 / 1, prior [-20, 20]^d) truncated to d = 2..10, with the
+    cluster tree at depth 0..6, re-clustering every 100 iterations, 5 d
+    slice steps, N_live = 1000, m = 1: mean likelihood evaluations per run
+    and log Z over n_seeds runs; all dimensions of one depth in one batch."""
+    import numpy as np
+    import torch
+
+    from paper_2608_28514_gb300 import _native as nat
+    from tests import analytic
+    from paper_2608_28514_gb300 import workloads as W
+
+    probs = {d: W.bimodal(d) for d in dims}
+    truth = {d: analytic.logz(p) for d, p in probs.items()}
+    table = {str(d): {"log_z_true": truth[d]} for d in dims}
+    t_all = 0.0
+    for dep in depths:
+        runs = [(probs[d], n_live, m, 5 * d, 1e-3, 9000 + s) for d in dims for s in range(n_seeds)]
+        h = nat.ns_create_batch(runs, nat.ns_default_options(depth=dep, recluster_every=100,
+                                                             walker_mapping=1 if m == 1 else 0))
+        nat.ns_run(h)
+        t_all += nat.ns_get_stats(h)["run_ms"]
+        res = [nat.ns_summary(h, r) for r in range(len(runs))]
+        nat.ns_destroy(h)
+        for i, d in enumerate(dims):
+            rr = res[i * n_seeds:(i + 1) * n_seeds]
+            z = np.array([r["log_z"] for r in rr])
+            ev = np.array([r["n_evals"] for r in rr], dtype=np.float64)
+            table[str(d)][str(dep)] = {"evaluations_mean": float(ev.mean()), "evaluations_sem": float(
+                ev.std(ddof=1) / np.sqrt(n_seeds)), "log_z_mean": float(z.mean()), "log_z_std": float(z.std(ddof=1))}
+    for d in dims:
+        e0 = table[str(d)]["0"]["evaluations_mean"]
+        for dep in depths:
+            row = table[str(d)][str(dep)]
+            row["evaluations_vs_depth0"] = row["evaluations_mean"] / e0
+    torch.cuda.synchronize()
+    return {"study": "tree depth sweep (section 2.3, Fig. 1): Test 2 truncated to d, N_live=%d, m=%d, 5 d slice steps, "
+                     "re-clustering every 100 iterations, %d runs per point" % (n_live, m, n_seeds),
+            "device_ms": t_all, "dims": table}
 
 
 # --------------------------------------------------------------------------
@@ -711,6 +760,10 @@ def main():
     if args.clustering_tests > 0:
         if int(os.environ.get("RANK", "0")) == 0:
             print(json.dumps(clustering_tests(args.clustering_tests)), flush=True)
+        return
+    if args.depth_sweep > 0:
+        if int(os.environ.get("RANK", "0")) == 0:
+            print(json.dumps(depth_sweep(args.depth_sweep)), flush=True)
         return
     if args.correction_sweep > 0:
         if int(os.environ.get("RANK", "0")) == 0:

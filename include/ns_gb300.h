@@ -260,6 +260,35 @@ ns_status ns_summary(const ns_handle* h, int run, ns_result_t* out);
  * Valid after ns_run. */
 ns_status ns_phase_cycles(const ns_handle* h, int run, long long* out);
 
+/* Tracing: a copy of one of run `run`'s device buffers, as the last
+ * iteration left it (call between ns_step / ns_run calls; asynchronous on
+ * `stream`, which this call synchronises).  `which` names the buffer; its
+ * size in bytes is ns_run_buffer_bytes(h, run, which) and `bytes` must equal
+ * it (NS_ERR_ARG otherwise):
+ *   NS_BUF_LIVE_X       float [d][n_pad]      live points, unit cube, n_pad = N rounded up to 32
+ *   NS_BUF_LIVE_L       float [N]             their log L
+ *   NS_BUF_LIVE_CID     int   [N]             their cluster-tree leaf
+ *   NS_BUF_NEW_X        float [m][d]          the last iteration's walker outputs (a4-a6): new points
+ *   NS_BUF_NEW_L        float [m]             their log L
+ *   NS_BUF_HIST_L       float [m][t_max]      shrink history of each walker's last slice step
+ *   NS_BUF_HIST_X       float [m][t_max][d]   its points
+ *   NS_BUF_HIST_LEN     int   [m]             entries used
+ *   NS_BUF_WALKER_EVALS int   [m]             likelihood evaluations of each walker (in-box candidates)
+ *   NS_BUF_WALKER_FLAGS int   [m]             bit 0: a step-out cap was hit, bit 1: a shrink cap
+ *   NS_BUF_CHOL         float [n_nodes][d][d] the cluster tree's Cholesky factors (row-major, lower)
+ *   NS_BUF_CENTRES      float [n_nodes][d]    its centres
+ *   NS_BUF_MASK         int   [n_nodes]       its accepted leaves
+ * The walker buffers are the step level's (ns_slice_replace) for the
+ * iteration's selection; together with the live set read before that
+ * iteration they let a caller replay each walker on the CPU. */
+typedef enum {
+    NS_BUF_LIVE_X = 0, NS_BUF_LIVE_L, NS_BUF_LIVE_CID, NS_BUF_NEW_X, NS_BUF_NEW_L, NS_BUF_HIST_L,
+    NS_BUF_HIST_X, NS_BUF_HIST_LEN, NS_BUF_WALKER_EVALS, NS_BUF_WALKER_FLAGS, NS_BUF_CHOL,
+    NS_BUF_CENTRES, NS_BUF_MASK, NS_BUF_COUNT_
+} ns_buffer;
+size_t ns_run_buffer_bytes(const ns_handle* h, int run, int which);
+ns_status ns_copy_run_buffer(ns_handle* h, int run, int which, void* host, size_t bytes, void* stream);
+
 /* How many runs of dimension d, batch m and tree depth one SM of the
  * current device holds at once (one thread block each); -1 on error.
  * ns_create_batch with (this) x (SM count) runs of that shape fills the

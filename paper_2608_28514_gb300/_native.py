@@ -103,6 +103,9 @@ def lib():
     L.ns_result.argtypes = [_vp, C.c_int, C.POINTER(NsResult)]
     L.ns_summary.argtypes = [_vp, C.c_int, C.POINTER(NsResult)]
     L.ns_phase_cycles.argtypes = [_vp, C.c_int, C.POINTER(C.c_longlong)]
+    L.ns_run_buffer_bytes.argtypes = [_vp, C.c_int, C.c_int]
+    L.ns_run_buffer_bytes.restype = C.c_size_t
+    L.ns_copy_run_buffer.argtypes = [_vp, C.c_int, C.c_int, _vp, C.c_size_t, _vp]
     L.ns_run_noalloc.argtypes = [C.POINTER(NsProblem), C.POINTER(NsOptions), _vp, _vp, _vp, C.c_longlong,
                                  C.POINTER(NsResult), _vp]
     L.ns_resident_runs_per_sm.argtypes = [C.c_int, C.c_int, C.c_int]
@@ -141,7 +144,7 @@ def lib():
     for name in ("ns_default_options", "ns_create", "ns_create_batch", "ns_run", "ns_reset", "ns_result", "ns_summary",
                  "ns_phase_cycles", "ns_run_noalloc", "ns_step", "ns_autotune", "ns_set_walker_mapping", "ns_checkpoint", "ns_restore",
                  "ns_last_run_ms", "ns_get_stats", "ns_philox4x32_10", "ns_loglike", "ns_select_worst", "ns_slice_replace",
-                 "ns_batch_correct", "ns_evidence_update", "ns_cluster"):
+                 "ns_batch_correct", "ns_evidence_update", "ns_cluster", "ns_copy_run_buffer"):
         getattr(L, name).restype = C.c_int
     _lib = L
     return L
@@ -297,6 +300,11 @@ def ns_step(h, n_iters, stream=None, check=True):
     return st
 
 
+def ns_checkpoint_bytes(h):
+    """Size in bytes of the handle's checkpoint."""
+    return int(lib().ns_checkpoint_bytes(h.ptr))
+
+
 def ns_checkpoint(h, stream=None):
     """The handle's whole state as bytes (see ns_restore)."""
     n = int(lib().ns_checkpoint_bytes(h.ptr))
@@ -352,6 +360,30 @@ def ns_get_stats(h):
 PHASES = ("cluster", "select", "slice", "correct", "update", "evidence")
 MLP_PHASES = ("mlp_eval", "mlp_reeval")  # inside the slice phase of MLP runs
 WALK_PHASES = ("draw", "walk")           # inside the slice phase of other runs (first warp)
+
+
+# ns_buffer: name -> (enum value, numpy dtype)
+RUN_BUFFERS = {"live_x": (0, np.float32), "live_l": (1, np.float32), "live_cid": (2, np.int32),
+               "new_x": (3, np.float32), "new_l": (4, np.float32), "hist_l": (5, np.float32),
+               "hist_x": (6, np.float32), "hist_len": (7, np.int32), "walker_evals": (8, np.int32),
+               "walker_flags": (9, np.int32), "chol": (10, np.float32), "centres": (11, np.float32),
+               "mask": (12, np.int32)}
+
+
+def ns_run_buffer_bytes(h, run, name):
+    """Size in bytes of one of a run's device buffers (0 for a bad run)."""
+    return int(lib().ns_run_buffer_bytes(h.ptr, int(run), RUN_BUFFERS[name][0]))
+
+
+def ns_copy_run_buffer(h, run, name, stream=None):
+    """A host copy (flat numpy array) of one of a run's device buffers as the
+    last iteration left it; see ns_copy_run_buffer in include/ns_gb300.h for
+    the names, layouts and shapes."""
+    which, dt = RUN_BUFFERS[name]
+    nb = ns_run_buffer_bytes(h, run, name)
+    out = np.empty(nb // np.dtype(dt).itemsize, dtype=dt)
+    _check(lib().ns_copy_run_buffer(h.ptr, int(run), which, out.ctypes.data_as(_vp), nb, _stream_ptr(stream)), h.ptr)
+    return out
 
 
 def ns_phase_cycles(h, run=0, mlp=False, walk=False):

@@ -18,6 +18,7 @@
 #include <cstring>
 #include <mutex>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/ns_gb300.h"
@@ -566,8 +567,9 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     int mlp_owner;  // the run whose MLP image this run reads (itself if it owns one)
     int spill;      // cluster tables in global memory
     size_t tree_ws;
-    size_t lik, mlp_img, mlp_desc, live_x, live_l, live_cid, new_x, new_l, hist_l, hist_x, hist_len, stage_x, dirs, wsp, side, dead_x,
-        dead_l, dead_logw, centres, chol, chol64, logvol, count, split, mask;
+    size_t lik, mlp_img, mlp_desc, live_x, live_l, live_cid, new_x, new_l, hist_l, hist_x, hist_len, wk_evals,
+        wk_flags, stage_x, dirs, wsp, side, dead_x, dead_l, dead_logw, centres, chol, chol64, logvol, count, split,
+        mask;
   };
   std::vector<Off> off(n_runs);
   h->host.resize(n_runs);
@@ -603,6 +605,8 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     o.hist_l = take(sizeof(float) * (size_t)m * opt.t_max);
     o.hist_x = take(sizeof(float) * (size_t)m * opt.t_max * d);
     o.hist_len = take(sizeof(int) * m);
+    o.wk_evals = take(sizeof(int) * m);
+    o.wk_flags = take(sizeof(int) * m);
     o.stage_x = take(sizeof(float) * (size_t)m * d);
     o.dirs = take(sizeof(float) * (size_t)m * p.n_slice_steps *
                   dir_row(p.lik->kind == NS_LIK_MLP ? kMaxDim : dmax_class(d)));
@@ -697,6 +701,8 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     R.hist_l = reinterpret_cast<float*>(base + o.hist_l);
     R.hist_x = reinterpret_cast<float*>(base + o.hist_x);
     R.hist_len = reinterpret_cast<int*>(base + o.hist_len);
+    R.wk_evals = reinterpret_cast<int*>(base + o.wk_evals);
+    R.wk_flags = reinterpret_cast<int*>(base + o.wk_flags);
     R.stage_x = reinterpret_cast<float*>(base + o.stage_x);
     R.dirs = reinterpret_cast<float*>(base + o.dirs);
     R.wsp = reinterpret_cast<float*>(base + o.wsp);
@@ -1296,6 +1302,52 @@ ns_status ns_phase_cycles(const ns_handle* h, int run, long long* out) {
   if (!h || !out || run < 0 || run >= h->n_runs) return NS_ERR_ARG;
   if (!h->ran) return NS_ERR_STATE;
   for (int i = 0; i < 8; ++i) out[i] = h->h_states[run].cycles[i];
+  return NS_OK;
+}
+
+extern "C++" {
+namespace {
+// (device address, bytes) of one of run r's buffers (ns_buffer), or {null, 0}.
+std::pair<const void*, size_t> run_buffer(const ns_handle* h, int r, int which) {
+  const RunDesc& R = h->runs[r];
+  const size_t d = R.d, N = R.N, m = R.m, nn = R.n_nodes, T = R.t_max;
+  switch (which) {
+    case NS_BUF_LIVE_X: return {R.live_x, sizeof(float) * d * R.n_pad};
+    case NS_BUF_LIVE_L: return {R.live_l, sizeof(float) * N};
+    case NS_BUF_LIVE_CID: return {R.live_cid, sizeof(int) * N};
+    case NS_BUF_NEW_X: return {R.new_x, sizeof(float) * m * d};
+    case NS_BUF_NEW_L: return {R.new_l, sizeof(float) * m};
+    case NS_BUF_HIST_L: return {R.hist_l, sizeof(float) * m * T};
+    case NS_BUF_HIST_X: return {R.hist_x, sizeof(float) * m * T * d};
+    case NS_BUF_HIST_LEN: return {R.hist_len, sizeof(int) * m};
+    case NS_BUF_WALKER_EVALS: return {R.wk_evals, sizeof(int) * m};
+    case NS_BUF_WALKER_FLAGS: return {R.wk_flags, sizeof(int) * m};
+    case NS_BUF_CHOL: return {R.chol, sizeof(float) * nn * d * d};
+    case NS_BUF_CENTRES: return {R.centres, sizeof(float) * nn * d};
+    case NS_BUF_MASK: return {R.mask, sizeof(int) * nn};
+    default: return {nullptr, 0};
+  }
+}
+}  // namespace
+}  // extern "C++"
+
+size_t ns_run_buffer_bytes(const ns_handle* h, int run, int which) {
+  if (!h || run < 0 || run >= h->n_runs) return 0;
+  return run_buffer(h, run, which).second;
+}
+
+ns_status ns_copy_run_buffer(ns_handle* h, int run, int which, void* host, size_t bytes, void* stream) {
+  if (!h || !host || run < 0 || run >= h->n_runs) return NS_ERR_ARG;
+  const auto b = run_buffer(h, run, which);
+  if (!b.first || b.second != bytes) {
+    set_err(&h->err, "ns_copy_run_buffer: buffer %d of run %d has %zu bytes, %zu requested", which, run, b.second,
+            bytes);
+    return NS_ERR_ARG;
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  NS_CUDA(cudaMemcpyAsync(host, b.first, bytes, cudaMemcpyDeviceToHost, s), &h->err);
+  NS_CUDA(cudaStreamSynchronize(s), &h->err);
+  h->d2h_bytes += (long long)bytes;
   return NS_OK;
 }
 

@@ -40,6 +40,8 @@ struct RunDesc {
   float* hist_l;
   float* hist_x;
   int* hist_len;
+  int* wk_evals;   // [m] likelihood evaluations of each walker in the last iteration (may be null)
+  int* wk_flags;   // [m] its cap flags (bit 0 step-out, bit 1 shrink)
   float* stage_x;
   float* dirs;     // [m][n_steps][dir_row(DMAX of the run's class)] per-step directions and draws
   float* wsp;      // [d][n_pad] whitened live points (cluster tree, depth >= 1)
@@ -330,6 +332,10 @@ __device__ __noinline__ void walker_phase_warp(const RunDesc& R, const LikParams
     int f = 0;
     slice_walker_warp<DMAX>(P, Q, SC, i, R.live_x + sd, R.n_pad, R.live_l[sd],
                             R.dirs + (size_t)i * R.n_steps * dir_row(DMAX), thr_out, thr_in, O, e, f);
+    if (lane == 0 && R.wk_evals) {
+      R.wk_evals[i] = (int)e;
+      R.wk_flags[i] = f;
+    }
     e_sum += e;
     n_cap += (f != 0) ? 1 : 0;
   }
@@ -691,6 +697,10 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
     for (int k = 0; k < d; ++k) R.new_x[(size_t)i * d + k] = x[k];
     R.new_l[i] = l;
     R.hist_len[i] = hlen;
+    if (R.wk_evals) {
+      R.wk_evals[i] = (int)evals;
+      R.wk_flags[i] = flags;
+    }
   }
   cr += clock64() - c_end;
   ev_out = mine ? evals : 0;
@@ -865,6 +875,10 @@ __global__ void NS_RUN_BOUNDS(MLP, DMAX) k_run(const RunDesc* __restrict__ runs,
         cyc_reeval = clock64() - cd1;
       } else if ((tid & ~31) < m) {
         walker_phase<DMAX>(R, P, SC, s_W, s_seed, s_chol, s_slots, ev, fl, cyc_eval, cyc_reeval);
+        if (R.wk_evals && tid < m) {
+          R.wk_evals[tid] = (int)ev;
+          R.wk_flags[tid] = fl;
+        }
         fl = fl ? 1 : 0;
       }
       if (tid == 0) {

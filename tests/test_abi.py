@@ -25,7 +25,7 @@ def native():
 def _declared_functions():
     text = open(HEADER).read()
     text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-    names = re.findall(r"\b(?:ns_status|void|int|const char\*)\s+(ns_\w+)\s*\(", text)
+    names = re.findall(r"\b(?:ns_status|void|int|size_t|const char\*)\s+(ns_\w+)\s*\(", text)
     return sorted(set(names))
 
 

@@ -230,3 +230,88 @@ def test_mlp_fp32_accurate_tensor_path(nat, oracle, widths, n):
     got = out.cpu().numpy().astype(np.float64)
     want = oracle.loglike(oracle.Lik(p), x.astype(np.float64))
     np.testing.assert_allclose(got, want, rtol=2e-5, atol=1e-3)
+
+
+# --------------------------------------------------------------------------
+# the lock-step MLP walkers of the run kernel on fixed streams
+# --------------------------------------------------------------------------
+def _mlp_walkers_vs_oracle(nat, oracle, p, N, m, ns, T, precision, seed):
+    """Runs T iterations, reads the live set and cluster factor the next
+    iteration starts from (ns_copy_run_buffer), runs iteration T, and replays
+    each of its walkers with the oracle's slice walker on the same Philox
+    streams, seed point and thresholds.  Returns (walkers compared, walkers
+    that diverged at a borderline comparison)."""
+    opt = nat.ns_default_options(precision=precision)
+    assert (T % max(1, 100 // m)) != 0  # no re-clustering at iteration T: the factor read is the one used
+    h = nat.ns_create_batch([(p, N, m, ns, 1e-3, seed)], opt)
+    nat.ns_step(h, T)
+    assert nat.ns_summary(h, 0)["n_iter"] == T
+    d = p.d
+    lx = nat.ns_copy_run_buffer(h, 0, "live_x").reshape(d, -1)[:, :N].T.copy()
+    ll = nat.ns_copy_run_buffer(h, 0, "live_l")
+    chol = nat.ns_copy_run_buffer(h, 0, "chol")[: d * d].reshape(d, d).astype(np.float64)
+    assert np.all(nat.ns_copy_run_buffer(h, 0, "live_cid") == 0)
+    nat.ns_step(h, 1)
+    g = {k: nat.ns_copy_run_buffer(h, 0, k) for k in
+         ("new_x", "new_l", "hist_l", "hist_x", "hist_len", "walker_evals", "walker_flags")}
+    nat.ns_destroy(h)
+    t_max = opt.t_max
+    g["new_x"] = g["new_x"].reshape(m, d)
+    g["hist_l"] = g["hist_l"].reshape(m, t_max)
+    g["hist_x"] = g["hist_x"].reshape(m, t_max, d)
+    worst, seeds = oracle.select(ll.astype(np.float64), m, seed, T)
+    Wv = ll[worst]
+    lik = oracle.Lik(p)
+    oo = oracle.opts(d, m)
+    tol = lambda l64: 2e-5 * np.abs(l64) + 1e-3  # FP32 evaluation of the MLP (test_mlp_fp32_matches_oracle)
+    # BF16 runs: history samples below this never get their FP32 value (Algorithm 2 cannot take them)
+    lim = Wv[0] - (opt.reeval_margin + opt.reeval_rel * abs(Wv[0]))
+    n_div = 0
+    for i in range(m):
+        r = oracle.slice_walker(lik, oo, ns, seed, T, i, lx[seeds[i]].astype(np.float64), float(ll[seeds[i]]),
+                                chol, float(Wv[0]), float(Wv[i]))
+        if np.max(np.abs(r["x"] - g["new_x"][i])) <= 1e-5:
+            l64 = oracle.loglike(lik, g["new_x"][i].astype(np.float64))[0]
+            assert abs(l64 - g["new_l"][i]) <= tol(l64), (i, l64, g["new_l"][i])
+            assert g["walker_evals"][i] == r["n_evals"], (i, g["walker_evals"][i], r["n_evals"])
+            assert g["walker_flags"][i] == r["flags"]
+            hl = g["hist_len"][i]
+            assert hl == r["hist_len"], (i, hl, r["hist_len"])
+            np.testing.assert_allclose(g["hist_x"][i, :hl], r["hist_x"], atol=1e-5)
+            hx = g["hist_x"][i, :hl].astype(np.float64)
+            fin = np.isfinite(r["hist_l"])
+            np.testing.assert_array_equal(np.isfinite(g["hist_l"][i, :hl]), fin)
+            h64 = oracle.loglike(lik, hx[fin]) if fin.any() else np.zeros(0)
+            hg = g["hist_l"][i, :hl][fin]
+            fp32 = np.ones(len(hg), dtype=bool) if precision == 0 else hg >= lim
+            assert np.all(np.abs(hg[fp32] - h64[fp32]) <= tol(h64[fp32])), i
+            # the others keep their BF16 value
+            assert np.all(np.abs(hg[~fp32] - h64[~fp32]) <= 1e-2 * np.abs(h64[~fp32]) + 1.0), i
+        else:
+            n_div += 1
+            assert r["min_l_margin"] < 4e-5 or r["min_box_margin"] < 1e-5, (i, r["min_l_margin"],
+                                                                             r["min_box_margin"])
+        assert g["new_l"][i] > Wv[i]
+        assert np.all((g["new_x"][i] >= 0) & (g["new_x"][i] <= 1))
+    return m, n_div
+
+
+@pytest.mark.parametrize("precision", [0, 1])
+@pytest.mark.parametrize("net", ["emulator27", "small4"])
+def test_mlp_run_walkers_match_oracle_on_fixed_streams(nat, oracle, precision, net):
+    """The run kernel's lock-step MLP walkers (out-of-box proposals settled
+    locally, rounds batched onto the evaluator, and in BF16 mode FP32
+    re-evaluation near the threshold with deferred passes and the round
+    cap) take the sequential slice sampler's decisions: each walker's new
+    point, log L, history, evaluation count and cap flags equal the FP64
+    oracle walker's on the same streams, except where a comparison was
+    borderline at FP32 accuracy.  On the 27-D emulator network (27 -> 512 x
+    4 -> 2000) at iteration 100 (N = 300, m = 16, 8 slice steps) and on a
+    4-D network (4 -> 64 -> 64 -> 60) at iteration 31 (N = 200, m = 20, 20
+    steps)."""
+    if net == "emulator27":
+        p, N, m, ns, T = W.mlp_emulator(1), 300, 16, 8, 100
+    else:
+        p, N, m, ns, T = _small_emulator(3), 200, 20, 20, 31
+    n, n_div = _mlp_walkers_vs_oracle(nat, oracle, p, N, m, ns, T, precision, seed=9)
+    assert n_div <= max(1, n // 10), n_div
