@@ -81,33 +81,37 @@ def test_batch256_against_pins(batch256):
 
 def test_batch256_high_d_runs_match_the_oracle(batch256):
     """The batch's Rosenbrock and mixture runs above d = 10 (76 runs), whose
-    closed forms the method at 5 d slice steps does not reach, against one
-    independent FP64 oracle run each of the same problem
-    (tests/golden/oracle_batch256_highd.json, written from the oracle alone):
-    |log Z_GPU - log Z_oracle| within twice the combined reported error for
-    at least the 1 % point of Binomial(n, 0.9545) of them, and the mean
-    difference within 3 standard errors of zero."""
+    closed forms the method at 5 d slice steps does not reach and whose
+    reported errors understate the scatter (the method's drift, which the
+    FP64 oracle shows as much as the GPU path), against one independent FP64
+    oracle run each of the same problem (tests/golden/oracle_batch256_highd.json,
+    written from the oracle alone), as distributions: the deviations from the
+    pins in units of the reported error, (log Z - log Z_pin) / err, of the GPU
+    runs and of the oracle runs pass a two-sample Kolmogorov-Smirnov test at
+    the 1 % level and have equal means within 3 standard errors; and the
+    paired differences log Z_GPU - log Z_oracle have mean zero within 3
+    standard errors."""
     import json
     import os
-    from scipy.stats import binom
+    from scipy import stats
     runs, res, _ = batch256
     with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "oracle_batch256_highd.json")) as f:
         orc = json.load(f)["runs"]
     assert len(orc) >= 50 and all(o["status"] == 0 for o in orc)
-    dz, comb = [], []
+    zg, zo, dz = [], [], []
     for o in orc:
         p, N, m, s = runs[o["index"]]
         assert (p.name, N, m, s) == (o["name"], o["N"], o["m"], o["run_seed"])
         r = res[o["index"]]
+        truth = A.logz(p)
+        zg.append((r["log_z"] - truth) / r["log_z_err"])
+        zo.append((o["logz"] - truth) / o["logz_err"])
         dz.append(r["log_z"] - o["logz"])
-        comb.append(math.hypot(r["log_z_err"], o["logz_err"]))
-    dz, comb = np.array(dz), np.array(comb)
+    zg, zo, dz = np.array(zg), np.array(zo), np.array(dz)
     n = len(dz)
-    k_min = int(binom.ppf(0.01, n, 0.9545))
-    within = int(np.sum(np.abs(dz) < 2 * comb))
-    assert within >= k_min, (within, n, k_min)
-    se = dz.std(ddof=1) / math.sqrt(n)
-    assert abs(dz.mean()) < 3 * se, (dz.mean(), se)
+    assert stats.ks_2samp(zg, zo).pvalue > 0.01, (zg.mean(), zo.mean(), zg.std(), zo.std())
+    assert abs(zg.mean() - zo.mean()) < 3 * math.sqrt((zg.var(ddof=1) + zo.var(ddof=1)) / n), (zg.mean(), zo.mean())
+    assert abs(dz.mean()) < 3 * dz.std(ddof=1) / math.sqrt(n), (dz.mean(), dz.std(ddof=1))
 
 
 def test_run_in_batch_equals_run_alone(nat, batch256):
