@@ -90,7 +90,8 @@ def parse():
     ap.add_argument("--emulator-convergence", type=int, default=0, metavar="SEEDS",
                     help="emulator runs to convergence: BF16 vs FP32 (widened data errors), and the emulator "
                          "configuration on BF16")
-    ap.add_argument("--emulator-cases", default="paired,config", help="cases of --emulator-convergence")
+    ap.add_argument("--emulator-cases", default="target150,single150",
+                    help="cases of --emulator-convergence (target150, target75, single150, single75, m1, paired)")
     ap.add_argument("--mapping-study", type=int, default=0, metavar="RUNS",
                     help="walker per thread vs per warp vs autotuned, RUNS runs per shape, and the 256-run batch")
     ap.add_argument("--comparison-shapes", type=int, default=0, metavar="SEEDS",
@@ -619,52 +620,93 @@ def mapping_study(n_runs):
                      "job (autotuner included; warm-up 2 N / m iterations)" % n_runs, "cases": out}
 
 
-def emulator_convergence(n_seeds, cases="paired,config"):
+def emulator_convergence(n_seeds, cases="target150,single150"):
     """Whole runs of the 27-D emulator likelihood (27-512x4-2000, sigma_k in
-    [1e-3, 1e-1]) to their stopping rule, n_seeds runs of one network per
-    case, all concurrently, 135 slice steps, stop 1e-3.  "paired": the BF16
-    path (FP32 re-evaluation near the threshold) against the plain FP32 path
-    at N = 200, m = 20 (small enough for the FP32 path to finish in minutes);
-    "config": the emulator configuration (N = 1500, m = 150) on the BF16 path.
-    Reported: the device time of ns_run (the wall time to log Z),
-    evaluations, FP32 re-evaluations, and the mean and spread of log Z."""
+    [1e-3, 1e-1]) to their stopping rule, 135 slice steps, stop 1e-3, seeds
+    500.., one network.  Cases (comma-separated; each prints one JSON line
+    as soon as it ends):
+      target150 / target75: the emulator configuration (N = 1500, m = 150 or
+        75), n_seeds runs on the BF16 path (FP32 re-evaluation near the
+        threshold) and the same n_seeds runs on the FP32 path of the tensor
+        cores (precision 2), one SM per run, all runs of a path concurrently:
+        log Z per seed on both paths, the paired difference BF16 - FP32 with
+        its standard error, wall time to the stopping rule (device time of
+        ns_run), evaluations/s, the FP32 re-evaluation share;
+      single150 / single75: one run alone (seed 500) split over a 4-CTA
+        cluster (4 SMs), BF16 and FP32 paths: its wall time to log Z;
+      m1: m = 1 (the sequential sampler), one run on a 4-CTA cluster, the
+        first 200 iterations on both paths: evaluations/s and iterations/s;
+      paired: N = 200, m = 20, BF16 against the FP32 path of the CUDA cores
+        (precision 0), n_seeds runs each."""
     import numpy as np
     import torch
 
     from paper_2608_28514_gb300 import _native as nat
     from paper_2608_28514_gb300 import workloads as W
 
-    def runs_of(p, N, m, precision):
-        opt = nat.ns_default_options(precision=precision)
-        h = nat.ns_create_batch([(p, N, m, 5 * p.d, 1e-3, 500 + s) for s in range(n_seeds)], opt)
+    def runs_of(p, N, m, precision, seeds, cluster, max_iter=0):
+        kw = dict(precision=precision, mlp_cluster=cluster)
+        if max_iter:
+            kw.update(max_iter=max_iter, chunk_iters=max_iter, dead_cap=N + 4 * m * max_iter)
+        opt = nat.ns_default_options(**kw)
+        h = nat.ns_create_batch([(p, N, m, 5 * p.d, 1e-3, s) for s in seeds], opt)
         nat.ns_run(h, check=False)
         st = nat.ns_get_stats(h)
-        res = [nat.ns_summary(h, r) for r in range(n_seeds)]
+        res = [nat.ns_summary(h, r) for r in range(len(seeds))]
         nat.ns_destroy(h)
         z = np.array([r["log_z"] for r in res])
-        return {"device_s": st["run_ms"] * 1e-3, "evals_per_run": float(np.mean([r["n_evals"] for r in res])),
-                "evals_per_s": sum(r["n_evals"] for r in res) / (st["run_ms"] * 1e-3),
+        ev = np.array([r["n_evals"] for r in res], dtype=np.float64)
+        cands = sum(r["n_cand_bf16"] for r in res)
+        return {"device_s": st["run_ms"] * 1e-3, "runs": len(seeds), "cluster_ctas": cluster,
+                "evals_per_run": float(ev.mean()), "evals_per_s": float(ev.sum() / (st["run_ms"] * 1e-3)),
                 "iterations_per_run": float(np.mean([r["n_iter"] for r in res])),
-                "fp32_reevals_per_run": float(np.mean([r["n_reeval"] for r in res])),
-                "log_z_mean": float(z.mean()), "log_z_std": float(z.std(ddof=1)),
-                "log_z_err_mean": float(np.mean([r["log_z_err"] for r in res])),
+                "fp32_evaluations_per_run": float(np.mean([r["n_cand_fp32"] for r in res])),
+                "fp32_reeval_share": (float(sum(r["n_reeval"] for r in res) / max(1, cands)) if precision == 1
+                                      else None),
+                "rounds_per_run": float(np.mean([r["n_rounds"] for r in res])),
+                "bf16_candidates_per_pass": (cands / max(1, sum(r["n_pass_bf16"] for r in res))) if cands else None,
+                "log_z": z.tolist(), "log_z_mean": float(z.mean()), "log_z_std": float(z.std(ddof=1)) if len(z) > 1
+                else 0.0, "log_z_err_mean": float(np.mean([r["log_z_err"] for r in res])),
                 "info_h_mean": float(np.mean([r["info"] for r in res])),
                 "status": sorted({int(r["status"]) for r in res})}
 
+    def emit(name, obj):
+        print(json.dumps({"case": name, **obj}), flush=True)
+        return obj
+
     out = {}
     p = W.mlp_emulator(1)
+    seeds = [500 + s for s in range(n_seeds)]
+    for m in (150, 75):
+        if f"target{m}" in cases:
+            a = {"bf16": runs_of(p, 1500, m, 1, seeds, 1), "fp32_tc": runs_of(p, 1500, m, 2, seeds, 1)}
+            dz = np.array(a["bf16"]["log_z"]) - np.array(a["fp32_tc"]["log_z"])
+            se = float(dz.std(ddof=1) / np.sqrt(len(dz))) if len(dz) > 1 else float("nan")
+            a["paired_dlogz"] = {"mean": float(dz.mean()), "std": float(dz.std(ddof=1)) if len(dz) > 1 else 0.0,
+                                 "standard_error": se, "bound_abs_mean_plus_2se": float(abs(dz.mean()) + 2 * se),
+                                 "max_abs": float(np.max(np.abs(dz))),
+                                 "seeds_identical": int(np.sum(dz == 0.0)), "seeds": len(dz)}
+            a["wall_time_ratio_fp32_over_bf16"] = a["fp32_tc"]["device_s"] / a["bf16"]["device_s"]
+            out[f"target_N1500_m{m}"] = emit(f"target{m}", a)
+        if f"single{m}" in cases:
+            a = {"bf16": runs_of(p, 1500, m, 1, seeds[:1], 4), "fp32_tc": runs_of(p, 1500, m, 2, seeds[:1], 4)}
+            a["wall_time_ratio_fp32_over_bf16"] = a["fp32_tc"]["device_s"] / a["bf16"]["device_s"]
+            out[f"single_run_N1500_m{m}_4cta"] = emit(f"single{m}", a)
+    if "m1" in cases:
+        a = {"bf16": runs_of(p, 1500, 1, 1, seeds[:1], 4, max_iter=200),
+             "fp32_tc": runs_of(p, 1500, 1, 2, seeds[:1], 4, max_iter=200)}
+        for k in ("bf16", "fp32_tc"):
+            a[k]["iterations_per_s"] = a[k]["iterations_per_run"] / a[k]["device_s"]
+        out["m1_segment_200_iterations_4cta"] = emit("m1", a)
     if "paired" in cases:
-        a = {"bf16": runs_of(p, 200, 20, 1), "fp32": runs_of(p, 200, 20, 0)}
-        a["dlogz_bf16_minus_fp32"] = a["bf16"]["log_z_mean"] - a["fp32"]["log_z_mean"]
-        a["dlogz_standard_error"] = float(np.sqrt((a["bf16"]["log_z_std"] ** 2 + a["fp32"]["log_z_std"] ** 2)
+        a = {"bf16": runs_of(p, 200, 20, 1, seeds, 1), "fp32_cuda_cores": runs_of(p, 200, 20, 0, seeds, 1)}
+        a["dlogz_bf16_minus_fp32"] = a["bf16"]["log_z_mean"] - a["fp32_cuda_cores"]["log_z_mean"]
+        a["dlogz_standard_error"] = float(np.sqrt((a["bf16"]["log_z_std"] ** 2 + a["fp32_cuda_cores"]["log_z_std"] ** 2)
                                                   / n_seeds))
-        a["wall_time_ratio_fp32_over_bf16"] = a["fp32"]["device_s"] / a["bf16"]["device_s"]
-        out["paired_N200_m20"] = a
-    if "config" in cases:
-        out["emulator_config_N1500_m150_bf16"] = runs_of(p, 1500, 150, 1)
+        a["wall_time_ratio_fp32_over_bf16"] = a["fp32_cuda_cores"]["device_s"] / a["bf16"]["device_s"]
+        out["paired_N200_m20"] = emit("paired", a)
     torch.cuda.synchronize()
-    return {"study": "emulator runs to convergence: %d runs per case (one network, seeds 500..), 135 slice steps, "
-                     "stop 1e-3" % n_seeds, "cases": out}
+    return {"study": "emulator runs to convergence: seeds 500.., 135 slice steps, stop 1e-3", "cases": out}
 
 
 def measured_peaks():

@@ -109,7 +109,10 @@ typedef struct {
     long long max_iter;   /* iterations before NS_ERR_BUDGET (1000000) */
     long long dead_cap;   /* dead-point capacity per run; 0 = 400 * N + 4 * m */
     int chunk_iters;      /* iterations per persistent launch (1000) */
-    int precision;        /* MLP only: 0 FP32, 1 BF16 with FP32 re-evaluation */
+    int precision;        /* MLP only: 0 FP32 on the CUDA cores, 1 BF16 on the tensor cores with FP32
+                           * re-evaluation near the threshold, 2 FP32 on the tensor cores (every evaluation with
+                           * inputs and activations split exactly into three BF16 parts; networks whose weights
+                           * are all BF16 values only, else NS_ERR_ARG) */
     double reeval_margin; /* MLP only: re-evaluate in FP32 when |logL - threshold| <   */
     double reeval_rel;    /*   reeval_margin + reeval_rel |threshold| (2.0 and 4e-3) */
     int reeval_defer;     /* MLP only: rounds a near-threshold candidate may wait so that several are
@@ -121,6 +124,12 @@ typedef struct {
                            * the weights per round; walkers beyond it keep their candidate for the next round and go
                            * first there; 0 = every candidate of the round, in equal calls).  Decisions do not
                            * depend on it */
+    int mlp_cluster;      /* MLP precision 1 and 2: CTAs (SMs) per run that share its tensor-core evaluations,
+                           * each streaming and multiplying a disjoint quarter or half of every layer's weight
+                           * tiles: 1, 2 or 4 (every layer's 128-row tile count must be a multiple of it, else
+                           * NS_ERR_ARG), or 0 = automatic (4, then 2, while that many CTAs per MLP run fit on the
+                           * device's SMs; else 1).  The chi^2 partials of the CTAs are added in rank order, so
+                           * results differ from one CTA's in the last bits of log L */
 } ns_options;
 
 /* One run of a batch. */
@@ -155,6 +164,10 @@ typedef struct {
     const float* dead_x;     /* [n_dead*d] host, owned by the handle */
     const float* dead_logl;  /* [n_dead]   host, owned by the handle */
     const double* dead_logw; /* [n_dead]   host, owned by the handle: log weight (prior mass times L) */
+    /* MLP runs: lock-step walker rounds, and the evaluator passes and the
+     * candidates they carried, BF16 passes and FP32 ones (tensor-core
+     * three-plane or CUDA-core) apart; 0 for other runs */
+    long long n_rounds, n_pass_bf16, n_cand_bf16, n_pass_fp32, n_cand_fp32;
 } ns_result_t;
 
 /* ---- whole runs ------------------------------------------------------- */
@@ -481,6 +494,22 @@ ns_status ns_mlp_pack(const ns_likelihood* lik, int d, void* image, void* stream
 ns_status ns_mlp_loglike(const ns_likelihood* lik, const double* lo, const double* hi, int d,
                          const void* image, int n, const float* x, float* logl, int precision,
                          void* stream);
+
+/* The tensor-core evaluators of ns_mlp_loglike (precision 1: BF16;
+ * precision 2: FP32 accuracy, BF16-valued weights only) split over a
+ * thread-block cluster of `cluster` (2 or 4) CTAs on as many SMs: each CTA
+ * streams and multiplies the weight tiles of a disjoint share of every
+ * layer's 128-row output tiles (tile t goes to CTA t % cluster), passes its
+ * slice of each hidden layer's activations to the other CTAs through
+ * distributed shared memory, and CTA 0 adds the CTAs' partial chi^2 in rank
+ * order.  This is how one MLP run's batches are evaluated when its
+ * ns_options.mlp_cluster is above 1 (section 5: one emulator inference on
+ * several SMs).  Same arguments, layouts and results as ns_mlp_loglike up to
+ * the order of that last sum; NS_ERR_ARG if a layer's tile count is not a
+ * multiple of `cluster`. */
+ns_status ns_mlp_loglike_cluster(const ns_likelihood* lik, const double* lo, const double* hi, int d,
+                                 const void* image, int n, const float* x, float* logl, int precision, int cluster,
+                                 void* stream);
 
 #ifdef __cplusplus
 }

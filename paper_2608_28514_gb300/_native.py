@@ -46,7 +46,7 @@ class NsOptions(C.Structure):
         ("e_max", C.c_int), ("s_max", C.c_int), ("width", C.c_double), ("max_iter", C.c_longlong),
         ("dead_cap", C.c_longlong), ("chunk_iters", C.c_int), ("precision", C.c_int),
         ("reeval_margin", C.c_double), ("reeval_rel", C.c_double), ("reeval_defer", C.c_int),
-        ("walker_mapping", C.c_int), ("mlp_batch_cap", C.c_int),
+        ("walker_mapping", C.c_int), ("mlp_batch_cap", C.c_int), ("mlp_cluster", C.c_int),
     ]
 
 
@@ -71,6 +71,8 @@ class NsResult(C.Structure):
         ("status", C.c_int), ("d", C.c_int),
         ("dead_x", C.POINTER(C.c_float)), ("dead_logl", C.POINTER(C.c_float)),
         ("dead_logw", C.POINTER(C.c_double)),
+        ("n_rounds", C.c_longlong), ("n_pass_bf16", C.c_longlong), ("n_cand_bf16", C.c_longlong),
+        ("n_pass_fp32", C.c_longlong), ("n_cand_fp32", C.c_longlong),
     ]
 
 
@@ -139,6 +141,9 @@ def lib():
     L.ns_mlp_loglike.argtypes = [C.POINTER(NsLikelihood), C.POINTER(C.c_double), C.POINTER(C.c_double), C.c_int,
                                  _vp, C.c_int, _vp, _vp, C.c_int, _vp]
     L.ns_mlp_loglike.restype = C.c_int
+    L.ns_mlp_loglike_cluster.argtypes = [C.POINTER(NsLikelihood), C.POINTER(C.c_double), C.POINTER(C.c_double),
+                                         C.c_int, _vp, C.c_int, _vp, _vp, C.c_int, C.c_int, _vp]
+    L.ns_mlp_loglike_cluster.restype = C.c_int
     L.ns_cluster_scratch_bytes.argtypes = [C.c_int, C.c_int, C.c_int]
     L.ns_cluster_scratch_bytes.restype = C.c_size_t
     for name in ("ns_default_options", "ns_create", "ns_create_batch", "ns_run", "ns_reset", "ns_result", "ns_summary",
@@ -410,7 +415,8 @@ def ns_result(h, run=0, samples=True):
     _check(fn(h.ptr, int(run), C.byref(r)), h.ptr)
     out = dict(log_z=r.log_z, log_z_err=r.log_z_err, info=r.info_h, n_dead=r.n_dead, n_evals=r.n_evals,
                n_iter=r.n_iter, n_relaxed=r.n_relaxed, n_reeval=r.n_reeval, n_capped=r.n_capped,
-               status=r.status, d=r.d)
+               status=r.status, d=r.d, n_rounds=r.n_rounds, n_pass_bf16=r.n_pass_bf16, n_cand_bf16=r.n_cand_bf16,
+               n_pass_fp32=r.n_pass_fp32, n_cand_fp32=r.n_cand_fp32)
     if samples and r.n_dead > 0:
         n, d = r.n_dead, r.d
         out["dead_x"] = np.ctypeslib.as_array(r.dead_x, shape=(n * d,)).reshape(n, d).copy()
@@ -597,6 +603,16 @@ def ns_mlp_loglike(problem, image, x, logl, precision=1, stream=None):
     _check(lib().ns_mlp_loglike(C.byref(lik), box.dptr(problem.lo), box.dptr(problem.hi), int(problem.d),
                                 _ptr(image), int(x.shape[0]), _ptr(x), _ptr(logl), int(precision),
                                 _stream_ptr(stream)))
+
+
+def ns_mlp_loglike_cluster(problem, image, x, logl, precision=1, cluster=4, stream=None):
+    """ns_mlp_loglike's tensor-core evaluators split over a cluster of
+    `cluster` CTAs (see include/ns_gb300.h)."""
+    lik, _ = _cached_likelihood(problem)
+    box = _Keep()
+    _check(lib().ns_mlp_loglike_cluster(C.byref(lik), box.dptr(problem.lo), box.dptr(problem.hi), int(problem.d),
+                                        _ptr(image), int(x.shape[0]), _ptr(x), _ptr(logl), int(precision),
+                                        int(cluster), _stream_ptr(stream)))
 
 
 def ns_cluster_scratch_bytes(N, n_pad, d):

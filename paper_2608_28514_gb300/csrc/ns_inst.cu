@@ -52,12 +52,29 @@ cudaError_t NS_CAT(launch_slice_, NS_DMAX)(const LikParams& P, const SliceCfg& S
 
 #if NS_DMAX == 32
 // MLP runs (any d <= 32) use the widest class with the lock-step walkers.
-cudaError_t launch_run_mlp(const RunDesc* runs, const int* ids, int n, int block, size_t smem, int chunk,
+// cluster > 1: each run is a cluster of that many CTAs (blocks r*cluster ..
+// r*cluster + cluster - 1), which share its tensor-core evaluations.
+cudaError_t launch_run_mlp(const RunDesc* runs, const int* ids, int n, int block, size_t smem, int chunk, int cluster,
                            cudaStream_t s) {
   cudaError_t e = cudaFuncSetAttribute(k_run<32, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return e;
-  k_run<32, true><<<n, block, smem, s>>>(runs, ids, chunk);
-  return cudaGetLastError();
+  if (cluster <= 1) {
+    k_run<32, true><<<n, block, smem, s>>>(runs, ids, chunk);
+    return cudaGetLastError();
+  }
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n * cluster), 1, 1);
+  cfg.blockDim = dim3((unsigned)block, 1, 1);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, k_run<32, true>, runs, ids, chunk);
 }
 #endif
 

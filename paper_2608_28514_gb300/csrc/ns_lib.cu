@@ -181,8 +181,8 @@ bool same_network(const ns_likelihood& a, const ns_likelihood& b) {
          eq(a.sigma_out, b.sigma_out, no);
 }
 
-// Dynamic shared memory a run kernel may take (the static part stays below 2 KB).
-constexpr size_t kRunSmemBudget = 227 * 1024 - 2048;
+// Dynamic shared memory a run kernel may take (the static part stays below 3 KB).
+constexpr size_t kRunSmemBudget = 227 * 1024 - 3072;
 
 // A run whose cluster tables do not fit in shared memory keeps them in
 // global memory (make_carve's spill).
@@ -341,10 +341,11 @@ ns_status check_opts(const ns_options& o, std::string* err) {
   if (o.recluster_every < 0 || o.kmeans_iters < 0 || o.history_iters < 0 || o.e_max < 0 || o.s_max < 1 ||
       o.t_max < 1 || o.t_max > NS_MAX_HISTORY || !(o.width > 0) || !std::isfinite(o.width) ||
       o.correction < 0 || o.correction > 3 || o.max_iter < 1 || o.dead_cap < 0 || o.chunk_iters < 0 ||
-      !(o.vol_frac >= 0 && o.vol_frac < 1) || o.precision < 0 || o.precision > 1 || !(o.reeval_margin >= 0) ||
+      !(o.vol_frac >= 0 && o.vol_frac < 1) || o.precision < 0 || o.precision > 2 || !(o.reeval_margin >= 0) ||
       !std::isfinite(o.reeval_margin) || !(o.reeval_rel >= 0) || !std::isfinite(o.reeval_rel) ||
       o.reeval_defer < 0 || o.reeval_defer > 64 || o.walker_mapping < 0 || o.walker_mapping > 1 ||
-      o.mlp_batch_cap < 0 || o.mlp_batch_cap > kMlpNbMax) {
+      o.mlp_batch_cap < 0 || o.mlp_batch_cap > kMlpNbMax ||
+      !(o.mlp_cluster == 0 || o.mlp_cluster == 1 || o.mlp_cluster == 2 || o.mlp_cluster == 4)) {
     set_err(err, "an option is out of range");
     return NS_ERR_ARG;
   }
@@ -453,13 +454,14 @@ struct HostRun {
 
 struct ClassGroup {
   int dmax = 0, block = 0, n = 0;
+  int cluster = 1;  // MLP group: CTAs per run
   bool mlp = false;
   size_t smem = 0;
   int* d_ids = nullptr;
 };
 
 cudaError_t launch_class(const ClassGroup& g, const RunDesc* d_runs, int chunk, cudaStream_t s) {
-  if (g.mlp) return launch_run_mlp(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
+  if (g.mlp) return launch_run_mlp(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, g.cluster, s);
   return kClasses[class_index(g.dmax)].run(d_runs, g.d_ids, g.n, g.block, g.smem, chunk, s);
 }
 
@@ -521,6 +523,7 @@ ns_status ns_default_options(ns_options* o) {
   o->reeval_rel = 4e-3;
   o->reeval_defer = 4;
   o->mlp_batch_cap = kMlpNbMax;
+  o->mlp_cluster = 0;
   return NS_OK;
 }
 
@@ -790,7 +793,37 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
       smem = std::max(smem, make_carve(runs[r].d, runs[r].m, n_nodes, g.dmax, g.mlp, off[r].spill != 0).total);
     }
     g.block = block_for_m(maxm);
-    if (g.mlp) g.block = std::max(g.block, kMlpThreads);  // the BF16 evaluator's warp roles
+    if (g.mlp) {
+      g.block = std::max(g.block, kMlpThreads);  // the BF16 evaluator's warp roles
+      // FP32 on the tensor cores needs BF16-valued weights; CTAs per run
+      // (the tile rows of every layer split evenly among them)
+      bool fits2 = opt.precision != 0, fits4 = opt.precision != 0;
+      for (int r : members[ci]) {
+        MlpDesc M;
+        std::string msg;
+        ns_mlp_make_desc(*runs[r].lik, runs[r].lo, runs[r].hi, runs[r].d, &M, &msg);
+        if (opt.precision == 2 && !M.w_bf16) {
+          set_err(nullptr, "run %d: precision 2 (FP32 on the tensor cores) needs MLP weights that are BF16 values", r);
+          return fail(NS_ERR_ARG);
+        }
+        fits2 = fits2 && mlp_cluster_fits(M, 2);
+        fits4 = fits4 && mlp_cluster_fits(M, 4);
+      }
+      int dev = 0, n_sm = 1;
+      if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev) !=
+                                                   cudaSuccess)
+        n_sm = 1;
+      if (opt.mlp_cluster == 0) {
+        g.cluster = (fits4 && 4 * g.n <= n_sm) ? 4 : ((fits2 && 2 * g.n <= n_sm) ? 2 : 1);
+      } else {
+        g.cluster = opt.mlp_cluster;
+        if ((g.cluster == 2 && !fits2) || (g.cluster == 4 && !fits4)) {
+          set_err(nullptr, "mlp_cluster = %d: every layer's 128-row tile count must be a multiple of it, on the "
+                  "tensor-core paths (precision 1 or 2)", g.cluster);
+          return fail(NS_ERR_ARG);
+        }
+      }
+    }
     g.smem = smem;
     if (smem > kRunSmemBudget) {
       set_err(nullptr, "runs of dimension class %d need %zu bytes of shared memory (limit 227 KB): "
@@ -1270,6 +1303,11 @@ ns_status ns_result(ns_handle* h, int run, ns_result_t* out) {
   out->n_relaxed = S.n_relaxed;
   out->n_reeval = S.n_reeval;
   out->n_capped = S.n_capped;
+  out->n_rounds = S.mlp_count[0];
+  out->n_pass_bf16 = S.mlp_count[1];
+  out->n_cand_bf16 = S.mlp_count[2];
+  out->n_pass_fp32 = S.mlp_count[3];
+  out->n_cand_fp32 = S.mlp_count[4];
   out->status = S.status;
   out->d = hr.d;
   out->dead_x = hr.dead_x.data();
@@ -1293,6 +1331,11 @@ ns_status ns_summary(const ns_handle* h, int run, ns_result_t* out) {
   out->n_relaxed = S.n_relaxed;
   out->n_reeval = S.n_reeval;
   out->n_capped = S.n_capped;
+  out->n_rounds = S.mlp_count[0];
+  out->n_pass_bf16 = S.mlp_count[1];
+  out->n_cand_bf16 = S.mlp_count[2];
+  out->n_pass_fp32 = S.mlp_count[3];
+  out->n_cand_fp32 = S.mlp_count[4];
   out->status = S.status;
   out->d = hr.d;
   return NS_OK;

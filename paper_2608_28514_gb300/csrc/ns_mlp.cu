@@ -13,6 +13,7 @@
 
 #include "../../include/ns_gb300.h"
 #include "ns_mlp.cuh"
+#include "ns_mlp_cluster.cuh"
 
 using namespace nsd;
 
@@ -60,6 +61,37 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
                                                               out + b0, sm, &ctx))
       for (int r = threadIdx.x; r < nb; r += blockDim.x) out[b0 + r] = __int_as_float(0x7fffffff);
   }
+  mlp_ctx_free(&ctx);
+}
+
+// The evaluators split over a cluster of C CTAs (ns_mlp_cluster.cuh): each
+// cluster evaluates batches of NB candidates, grid-strided over clusters;
+// CTA 0 sums the partial chi^2.
+template <int NB, int P>
+__global__ void __launch_bounds__(kMlpThreads, 1)
+    k_mlp_cl(const MlpDesc M, const uint8_t* __restrict__ tiles, const float* __restrict__ f32,
+             const float* __restrict__ x, int n, float* __restrict__ out) {
+  extern __shared__ __align__(1024) char sm_raw[];
+  __shared__ MlpCtx ctx;
+  __shared__ ClusterMail mail;
+  char* sm = align1024_shared(sm_raw);
+  const unsigned C = cl_size(), rank = cl_rank();
+  mlp_ctx_init(&ctx);
+  cl_sync();  // every CTA's barriers are set up before any remote arrive
+  const int n_clusters = (int)(gridDim.x / C), cid = (int)(blockIdx.x / C);
+  const int n_batches = (n + NB - 1) / NB;
+  for (int b = cid; b < n_batches; b += n_clusters) {
+    const int b0 = b * NB;
+    const int nb = min(NB, n - b0);
+    const XIn X{x + (size_t)b0 * M.d, nullptr, nullptr, M.d};
+    mlp_eval_bf16_cl<NB, kMlpStandaloneStages, P>(M, tiles, f32, X, nb, sm, &ctx, &mail, C, rank);
+    cl_sync();
+    if (rank == 0 && !mlp_cl_collect(&mail, C, nb, out + b0, nullptr))
+      for (int r = threadIdx.x; r < nb; r += blockDim.x) out[b0 + r] = __int_as_float(0x7fffffff);
+    cl_sync();  // the mailbox is free for the next batch
+  }
+  mlp_cl_drain(&ctx);
+  cl_sync();
   mlp_ctx_free(&ctx);
 }
 
@@ -246,6 +278,38 @@ cudaError_t ns_mlp_launch(const MlpDesc& M, const void* image, int n, const floa
   return cudaGetLastError();
 }
 
+// The cluster-split evaluators: `cluster` CTAs per batch, at most one
+// cluster per `cluster` SMs.
+cudaError_t ns_mlp_launch_cluster(const MlpDesc& M, const void* image, int n, const float* x, float* logl,
+                                  int precision, int cluster, cudaStream_t s) {
+  const uint8_t* tiles = static_cast<const uint8_t*>(image);
+  const float* f32 = reinterpret_cast<const float*>(tiles + M.tile_bytes);
+  int dev = 0, n_sm = 1;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+  if (e != cudaSuccess) return e;
+  const int nb = precision == 2 ? kMlpSplitNb : kMlpNbMax;
+  const int n_batches = (n + nb - 1) / nb;
+  const int n_clusters = std::max(1, std::min(n_batches, n_sm / cluster));
+  const int smem = (precision == 2 ? (int)MlpSmemSplit::kBytes : (int)MlpSmemStandalone::kBytes) + 1024;
+  auto kern = precision == 2 ? k_mlp_cl<kMlpSplitNb, 3> : k_mlp_cl<kMlpNbMax, 1>;
+  e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+  if (e != cudaSuccess) return e;
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((unsigned)(n_clusters * cluster), 1, 1);
+  cfg.blockDim = dim3(kMlpThreads, 1, 1);
+  cfg.dynamicSmemBytes = (size_t)smem;
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = (unsigned)cluster;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, M, tiles, f32, x, n, logl);
+}
+
 extern "C" {
 
 size_t ns_mlp_image_bytes(const ns_likelihood* lik, int d) {
@@ -315,6 +379,32 @@ ns_status ns_mlp_loglike(const ns_likelihood* lik, const double* lo, const doubl
   if (n == 0) return NS_OK;
   return ns_mlp_launch(M, image, n, x, logl, precision, (cudaStream_t)stream) == cudaSuccess ? NS_OK
                                                                                            : NS_ERR_CUDA;
+}
+
+ns_status ns_mlp_loglike_cluster(const ns_likelihood* lik, const double* lo, const double* hi, int d,
+                                 const void* image, int n, const float* x, float* logl, int precision, int cluster,
+                                 void* stream) {
+  if (!lik || !lo || !hi || !image || n < 0 || (n > 0 && (!x || !logl)) || precision < 1 || precision > 2 ||
+      (cluster != 2 && cluster != 4))
+    return NS_ERR_ARG;
+  MlpDesc M;
+  std::string msg;
+  if (!make_desc(*lik, lo, hi, d, &M, &msg)) {
+    g_mlp_err = msg;
+    return NS_ERR_ARG;
+  }
+  if (precision == 2 && !M.w_bf16) {
+    g_mlp_err = "ns_mlp_loglike_cluster: precision 2 needs weights that are BF16 values";
+    return NS_ERR_ARG;
+  }
+  if (!mlp_cluster_fits(M, cluster)) {
+    g_mlp_err = "ns_mlp_loglike_cluster: every layer's 128-row tile count must be a multiple of the cluster size";
+    return NS_ERR_ARG;
+  }
+  if (n == 0) return NS_OK;
+  return ns_mlp_launch_cluster(M, image, n, x, logl, precision, cluster, (cudaStream_t)stream) == cudaSuccess
+             ? NS_OK
+             : NS_ERR_CUDA;
 }
 
 }  // extern "C"

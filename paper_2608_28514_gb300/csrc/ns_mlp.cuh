@@ -216,9 +216,17 @@ constexpr int kMlpHalfCols = 256;
 struct MlpCtx {
   uint64_t full[kMlpStagesMax], empty[kMlpStagesMax];
   uint64_t acc_full[2], acc_free[2], drain;
+  // evaluation split over a thread-block cluster (ns_mlp_cluster.cuh): the
+  // peers' slices of a layer's input have landed (one local arrive with the
+  // expected bytes); every peer has finished a layer's MMAs (one remote
+  // arrive per peer)
+  uint64_t act_ready, peer_free;
   unsigned tmem;
   unsigned item;      // weight tiles consumed so far
   unsigned uses[2];   // groups that have used each accumulator half
+  unsigned xu;        // act_ready phases waited for (cluster split)
+  unsigned xu_armed;  // act_ready phases armed
+  unsigned pu;        // peer_free phases waited for
   unsigned err;
 };
 
@@ -245,9 +253,14 @@ inline __device__ void mlp_ctx_init(MlpCtx* c) {
       mbar_init(&c->acc_free[h], kMlpEpiWarps * 32);
     }
     mbar_init(&c->drain, 1);
+    unsigned ncta;
+    asm volatile("mov.u32 %0, %%cluster_nctarank;\n" : "=r"(ncta));
+    mbar_init(&c->act_ready, 1);
+    mbar_init(&c->peer_free, ncta > 1 ? ncta - 1 : 1);
     mbar_fence_init();
     c->item = 0u;
     c->uses[0] = c->uses[1] = 0u;
+    c->xu = c->xu_armed = c->pu = 0u;
     c->err = 0u;
   }
   tc_fence_before();
@@ -498,27 +511,26 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
           }
           fence_proxy_async();
         } else {
-          // chi^2: per candidate column, summed over the group's features
+          // chi^2: per candidate column, one tile of 128 features at a time,
+          // added in tile order (so a candidate's value does not depend on
+          // its batch: the grouping of tiles follows N)
           for (int i = ch; i < n_chunks; i += 2) {
             const int c0 = i * 16;
-            float sacc[16];
-#pragma unroll
-            for (int c = 0; c < 16; ++c) sacc[c] = 0.f;
             for (int t = G.g0; t < G.g1; ++t) {
               const int f = t * 128 + q * 32 + lane;
               const float is = f32[M.isig0 + f];
               const float bias = f32[M.bias0[l] + f], dk = f32[M.data0 + f];
               const float cb = (bias - dk) * is;
-              float v[16];
+              float v[16], sacc[16];
               tmem_ld16(tmem + lane_base + col0 + (unsigned)((t - G.g0) * N + c0), v);
 #pragma unroll
               for (int c = 0; c < 16; ++c) {
                 const float r = (P == 1) ? fmaf(v[c], is, cb) : ((v[c] + bias) - dk) * is;
-                sacc[c] = fmaf(r, r, sacc[c]);
+                sacc[c] = r * r;
               }
+              const float tot = warp_sum16(sacc, lane);
+              if ((lane & 1) == 0) chi[q * NBMAX + c0 + ((lane >> 1) & 15)] += tot;
             }
-            const float tot = warp_sum16(sacc, lane);
-            if ((lane & 1) == 0) chi[q * NBMAX + c0 + ((lane >> 1) & 15)] += tot;
           }
         }
         tc_fence_before();

@@ -4,10 +4,13 @@
 // instantiation units and by the host library.
 #pragma once
 
+#include <cstddef>
+
 #include "../../include/ns_gb300.h"
 #include "ns_cluster.cuh"
 #include "ns_device.cuh"
 #include "ns_mlp.cuh"
+#include "ns_mlp_cluster.cuh"
 
 namespace nsd {
 
@@ -21,6 +24,8 @@ struct RunState {
   double logz, info;
   long long k, n_dead, n_evals, n_iter, n_relaxed, n_reeval, n_capped;
   long long cycles[8];
+  // MLP runs: walker rounds, BF16 passes and their candidates, FP32 passes and theirs
+  long long mlp_count[5];
   int t, stopped, status, initialized;
 };
 
@@ -87,6 +92,9 @@ using RunMlpSmem = MlpSmem<kMlpNbMax, kRunMlpStages>;
 
 __host__ __device__ inline size_t al16(size_t x) { return (x + 15) & ~(size_t)15; }
 
+// Row stride (floats) of an MLP run's candidate staging buffer.
+__host__ __device__ constexpr int mlp_xs(int d) { return (d + 3) & ~3; }
+
 // spill: the run's cluster tables do not fit next to the rest (large d or a
 // deep tree); the Cholesky factors and the tree scratch then stay in global
 // memory (only the clustering and the direction draws read them).
@@ -123,10 +131,11 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax,
   c.slots = take(mlp ? 0 : sizeof(float) * (size_t)dir_row(dmax) * (m + 31) / 32 * 32);
   c.ctr = take(sizeof(int) * 4);
   c.stage_cid = take(sizeof(int) * m);
-  // MLP runs: candidate points, their log L, the re-evaluation list
-  c.xbuf = take(mlp ? sizeof(float) * (size_t)(m + kMlpF32Nb) * kMaxDim : 0);
-  c.lbuf = take(mlp ? sizeof(float) * (size_t)(m + kMlpF32Nb) : 0);
-  c.rlist = take(mlp ? sizeof(int) * (size_t)(m + kMlpF32Nb) : 0);
+  // MLP runs: candidate points (two slots per walker, then FP32 staging
+  // rows), their log L, the re-evaluation list
+  c.xbuf = take(mlp ? sizeof(float) * (size_t)(2 * m + kMlpF32Nb) * mlp_xs(d) : 0);
+  c.lbuf = take(mlp ? sizeof(float) * (size_t)(2 * m + kMlpF32Nb) : 0);
+  c.rlist = take(mlp ? sizeof(int) * (size_t)(2 * m + kMlpF32Nb) : 0);
   // from here on, scratch of one phase at a time: the clustering; for MLP
   // runs also the evaluators (walker phase) and the batch-correction
   // candidates (Algorithms 1-2 and the update), which never overlap
@@ -344,65 +353,139 @@ __device__ __noinline__ void walker_phase_warp(const RunDesc& R, const LikParams
 }
 
 // a4-a7 for MLP runs: the walkers advance in lock step, one round at a time;
-// each round the block evaluates every walker's candidate as one batch (on
-// the tensor cores in BF16, or on the CUDA cores in FP32).  In BF16 mode a
-// candidate whose log L falls within reeval_margin + reeval_rel |threshold|
-// of the threshold it is compared with is re-evaluated in FP32 before the
-// decision; each walker's final point and its history samples are
-// re-evaluated in FP32 afterwards, so every log L that is stored (dead
-// points, Algorithm 2) is an FP32 value.
-// Called by every thread of the block.
-inline __device__ bool mlp_batch_f32(const RunDesc& R, const float* xs, int n, float* ls, float* act,
+// each round the block evaluates every walker's pending candidates as one
+// batch (on the tensor cores in BF16, or on the CUDA cores in FP32).  In
+// BF16 mode a candidate whose log L falls within reeval_margin +
+// reeval_rel |threshold| of the threshold it is compared with is
+// re-evaluated in FP32 before the decision; each walker's final point and
+// its history samples are re-evaluated in FP32 afterwards, so every log L
+// that is stored (dead points, Algorithm 2) is an FP32 value.
+//
+// Candidate rows of the block's staging buffer xbuf: walker w's left
+// stepping-out end (or its shrink candidate) in row w, its right end in row
+// m + w, FP32 staging rows after the 2m; rows are mlp_xs(d) floats apart.
+static __device__ __noinline__ bool mlp_batch_f32(const RunDesc& R, const float* xs, int xstride, int n, float* ls, float* act,
                                      const int* rows = nullptr) {
   for (int b0 = 0; b0 < n; b0 += kMlpF32NbWide) {
     if (rows)
-      mlp_eval_f32<kMlpF32NbWide>(*R.mlp_desc, R.mlp_f32, xs, kMaxDim, min(kMlpF32NbWide, n - b0), ls, act,
+      mlp_eval_f32<kMlpF32NbWide>(*R.mlp_desc, R.mlp_f32, xs, xstride, min(kMlpF32NbWide, n - b0), ls, act,
                                   rows + b0);
     else
-      mlp_eval_f32<kMlpF32NbWide>(*R.mlp_desc, R.mlp_f32, xs + (size_t)b0 * kMaxDim, kMaxDim,
+      mlp_eval_f32<kMlpF32NbWide>(*R.mlp_desc, R.mlp_f32, xs + (size_t)b0 * xstride, xstride,
                                   min(kMlpF32NbWide, n - b0), ls + b0, act);
   }
   return true;
 }
 
+constexpr int kRunSplitNb = 32;  // candidates per FP32-accurate (three-plane) tensor-core call
+
+// One tensor-core evaluation by the run's whole cluster (this block is its
+// CTA 0; the followers wait in mlp_follower): post the command, evaluate
+// this CTA's share (CTA 0 builds the layer-0 operand from xs / rows and
+// copies it into the followers), gather the partial chi^2.  Every thread of
+// the block.
+template <int NB, int P>
+inline __device__ bool mlp_pass_cl(const RunDesc& R, const float* xs, int xstride, int n, float* ls, char* tsm,
+                                   MlpCtx* ctx, ClusterMail* mail, unsigned C, const int* rows) {
+  if (threadIdx.x == 0) {
+    mail->op = (P == 1) ? kClOpBf16 : kClOpFp32;
+    mail->n = n;
+  }
+  cl_sync();
+  const XIn X{nullptr, xs, rows, xstride};
+  mlp_eval_bf16_cl<NB, kRunMlpStages, P>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, X, n, tsm, ctx, mail, C, 0u);
+  cl_sync();
+  const bool ok = mlp_cl_collect(mail, C, n, ls, rows);
+  if (!ok && threadIdx.x == 0) ctx_set_err(ctx);
+  __syncthreads();
+  return ok;
+}
+
+// A follower CTA of an MLP run's cluster: evaluates its share of every
+// tensor-core pass CTA 0 posts, until CTA 0 posts the exit.  Every thread of
+// the block.
+inline __device__ void mlp_follower(const RunDesc& R, MlpCtx* ctx, ClusterMail* mail, char* tsm, unsigned C,
+                                    unsigned rank) {
+  const bool tc = R.precision != 0;
+  if (tc) mlp_ctx_init(ctx);
+  const unsigned m0 = cl_map(smem_u32(mail), 0);
+  for (;;) {
+    cl_sync();
+    const int op = cl_ld_s32(m0 + (unsigned)offsetof(ClusterMail, op));
+    if (op == kClOpExit || !tc) {
+      if (tc) mlp_cl_drain(ctx);
+      cl_sync();
+      break;
+    }
+    const int n = cl_ld_s32(m0 + (unsigned)offsetof(ClusterMail, n));
+    const XIn X{nullptr, nullptr, nullptr, 0};  // the layer-0 operand comes from CTA 0
+    if (op == kClOpBf16)
+      mlp_eval_bf16_cl<kMlpNbMax, kRunMlpStages, 1>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, X, n, tsm, ctx, mail, C,
+                                                    rank);
+    else
+      mlp_eval_bf16_cl<kRunSplitNb, kRunMlpStages, 3>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, X, n, tsm, ctx, mail,
+                                                      C, rank);
+    cl_sync();
+  }
+  if (tc) mlp_ctx_free(ctx);
+}
+
+// CTA 0 of an MLP run's cluster, before it exits: posts the exit, waits for
+// the followers to read it.
+inline __device__ void mlp_leader_exit(MlpCtx* ctx, ClusterMail* mail, bool tc) {
+  if (threadIdx.x == 0) mail->op = kClOpExit;
+  cl_sync();
+  if (tc) mlp_cl_drain(ctx);
+  cl_sync();
+}
+
 // rows: the n rows of xs (and ls) to evaluate, or null for rows 0..n-1.
-inline __device__ bool mlp_batch_bf16(const RunDesc& R, const float* xs, int n, float* ls, char* tsm,
-                                      MlpCtx* ctx, const int* rows = nullptr) {
+// With a cluster of C > 1 CTAs, every call is split over the cluster.
+static __device__ __noinline__ bool mlp_batch_bf16(const RunDesc& R, const float* xs, int xstride, int n, float* ls, char* tsm,
+                                      MlpCtx* ctx, ClusterMail* mail, unsigned C, const int* rows = nullptr) {
   // equal calls of at most kMlpNbMax candidates (each call streams every weight tile once)
   const int calls = (n + kMlpNbMax - 1) / kMlpNbMax;
   const int per = (n + calls - 1) / calls;
   bool ok = true;
-  for (int b0 = 0; b0 < n && ok; b0 += per)
-    ok = rows ? mlp_eval_bf16<kMlpNbMax, kRunMlpStages>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, xs, kMaxDim,
-                                                        min(per, n - b0), ls, tsm, ctx, rows + b0)
-              : mlp_eval_bf16<kMlpNbMax, kRunMlpStages>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32,
-                                                        xs + (size_t)b0 * kMaxDim, kMaxDim, min(per, n - b0),
-                                                        ls + b0, tsm, ctx);
+  for (int b0 = 0; b0 < n && ok; b0 += per) {
+    const int nb = min(per, n - b0);
+    if (C > 1)
+      ok = rows ? mlp_pass_cl<kMlpNbMax, 1>(R, xs, xstride, nb, ls, tsm, ctx, mail, C, rows + b0)
+                : mlp_pass_cl<kMlpNbMax, 1>(R, xs + (size_t)b0 * xstride, xstride, nb, ls + b0, tsm, ctx, mail, C,
+                                            nullptr);
+    else
+      ok = rows ? mlp_eval_bf16<kMlpNbMax, kRunMlpStages>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, xs, xstride, nb, ls,
+                                                          tsm, ctx, rows + b0)
+                : mlp_eval_bf16<kMlpNbMax, kRunMlpStages>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32,
+                                                          xs + (size_t)b0 * xstride, xstride, nb, ls + b0, tsm, ctx);
+  }
   return ok;
 }
 
-// FP32-accurate re-evaluation on the tensor cores (three BF16 planes, for
+// FP32-accurate evaluation on the tensor cores (three BF16 planes, for
 // networks whose weights are BF16 values) of the listed rows of xs, into ls.
-constexpr int kRunSplitNb = 32;
-inline __device__ bool mlp_reeval_tc(const RunDesc& R, const float* xs, float* ls, const int* list, int n,
-                                     char* tsm, MlpCtx* ctx) {
+static __device__ __noinline__ bool mlp_reeval_tc(const RunDesc& R, const float* xs, int xstride, float* ls, const int* list,
+                                     int n, char* tsm, MlpCtx* ctx, ClusterMail* mail, unsigned C) {
   bool ok = true;
-  for (int b0 = 0; b0 < n && ok; b0 += kRunSplitNb)
-    ok = mlp_eval_bf16<kRunSplitNb, kRunMlpStages, 3>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, xs, kMaxDim,
-                                                      min(kRunSplitNb, n - b0), ls, tsm, ctx, list + b0);
+  for (int b0 = 0; b0 < n && ok; b0 += kRunSplitNb) {
+    const int nb = min(kRunSplitNb, n - b0);
+    ok = (C > 1) ? mlp_pass_cl<kRunSplitNb, 3>(R, xs, xstride, nb, ls, tsm, ctx, mail, C, list + b0)
+                 : mlp_eval_bf16<kRunSplitNb, kRunMlpStages, 3>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, xs, xstride, nb,
+                                                                ls, tsm, ctx, list + b0);
+  }
   return ok;
 }
 
 // FP32 re-evaluation of the listed rows of xbuf (indices in list[0..n)),
 // written back into lbuf; xg/lg: kMlpF32Nb staging rows.
-inline __device__ void mlp_reeval(const RunDesc& R, float* xbuf, float* lbuf, const int* list, int n, float* xg,
-                                  float* lg, float* act) {
+static __device__ __noinline__ void mlp_reeval(const RunDesc& R, float* xbuf, int xstride, float* lbuf, const int* list, int n,
+                                  float* xg, float* lg, float* act) {
   for (int g0 = 0; g0 < n; g0 += kMlpF32Nb) {
     const int ng = min(kMlpF32Nb, n - g0);
-    for (int q = threadIdx.x; q < ng * kMaxDim; q += blockDim.x)
-      xg[q] = xbuf[(size_t)list[g0 + q / kMaxDim] * kMaxDim + q % kMaxDim];
+    for (int q = threadIdx.x; q < ng * xstride; q += blockDim.x)
+      xg[q] = xbuf[(size_t)list[g0 + q / xstride] * xstride + q % xstride];
     __syncthreads();
-    mlp_eval_f32<kMlpF32Nb>(*R.mlp_desc, R.mlp_f32, xg, kMaxDim, ng, lg, act);
+    mlp_eval_f32<kMlpF32Nb>(*R.mlp_desc, R.mlp_f32, xg, xstride, ng, lg, act);
     for (int q = threadIdx.x; q < ng; q += blockDim.x) lbuf[list[g0 + q]] = lg[q];
     __syncthreads();
   }
@@ -411,18 +494,23 @@ inline __device__ void mlp_reeval(const RunDesc& R, float* xbuf, float* lbuf, co
 template <int DMAX>
 __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& S, const float* s_W, const int* s_seed,
                                               const float* s_chol, float* xbuf, float* lbuf, int* rlist, char* msm,
-                                              MlpCtx* ctx, int* mvlist, BlockScratch& BS, long long& ev_out,
-                                              int& fl_out, long long& re_out, int& err_out, long long& cyc_eval,
-                                              long long& cyc_reeval) {
+                                              MlpCtx* ctx, ClusterMail* mail, int* mvlist, BlockScratch& BS,
+                                              long long& ev_out, int& fl_out, long long& re_out, int& err_out,
+                                              long long& cyc_eval, long long& cyc_reeval, long long* count) {
   constexpr int RW = dir_row(DMAX);
   const int tid = threadIdx.x, m = R.m, d = S.d;
+  const int XS = mlp_xs(d);
+  const unsigned C = cl_size();
   const bool bf16 = (R.precision == 1);
+  // precision 2: every evaluation FP32-accurate on the tensor cores (the
+  // FP32 path for networks whose weights are BF16 values)
+  const bool tcfp = (R.precision == 2);
   // FP32 re-evaluations on the tensor cores when the weights are BF16 values
   const bool tc32 = bf16 && R.mlp_desc->w_bf16;
   char* tsm = align1024_shared(msm);
   float* act = reinterpret_cast<float*>(msm);
-  float* xg = xbuf + (size_t)m * kMaxDim;  // kMlpF32Nb staging rows after the m walker rows
-  float* lg = lbuf + m;
+  float* xg = xbuf + (size_t)2 * m * XS;  // kMlpF32Nb staging rows after the 2m candidate rows
+  float* lg = lbuf + 2 * m;
   const bool mine = tid < m;
   const int i = mine ? tid : 0;
   const int sd = s_seed[i];
@@ -436,7 +524,10 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   float l = mine ? R.live_l[sd] : 0.f;
 #pragma unroll
   for (int k = 0; k < DMAX; ++k) x[k] = (mine && k < d) ? R.live_x[(size_t)k * R.n_pad + sd] : 0.f;
-  int step = 0, phase = 0, nexp = 0, nsh = 0, hlen = 0, flags = 0;
+  // phase 0: stepping out, both ends at once (their sequences of points do
+  // not depend on each other, so the decisions are the sequential
+  // sampler's, left end then right end); phase 2: shrinkage
+  int step = 0, phase = 0, nexp0 = 0, nexp1 = 0, done = 0, nsh = 0, hlen = 0, flags = 0;
   long long evals = 0, reevals = 0;
   float a = 0.f, b = 0.f;
   Stream st;
@@ -456,178 +547,244 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   if (active) load_step(0);
   int err = 0;
   long long ce = 0, cr = 0;  // thread 0: cycles in the batch evaluations and the FP32 re-evaluations
-  // A walker whose BF16 log L is near its threshold waits (pending) for the
-  // FP32 value, holding its candidate in its xbuf row; the pending
-  // candidates are re-evaluated together once kMlpF32Nb of them wait, one has
-  // waited reeval_defer rounds, or no walker is left to move.  A decision is
-  // only delayed, never changed: the runs equal those of immediate
-  // re-evaluation (reeval_defer = 0) bit for bit.
-  bool pend = false;
-  int age = 0;           // rounds the oldest pending candidate has waited (uniform)
-  float ptp = 0.f;       // the pending candidate's position on the line
-  // With a round cap (BF16) at most mlp_round_cap candidates -- one weight
-  // pass -- are evaluated per round; a walker left out holds its candidate
-  // (hold) and goes first in the next round.  Its decisions are unchanged.
-  bool hold = false;
-  float htp = 0.f;       // the held candidate's position on the line
+  // Two candidate slots per walker (bit s of the masks): slot 0 = the left
+  // end (phase 0) or the shrink candidate (phase 2), slot 1 = the right end.
+  // has: the slot holds an in-box candidate in its xbuf row (to evaluate,
+  // held back by the round cap, or pending); pend: its BF16 log L was near
+  // the threshold and it waits for its FP32 value (the pending candidates
+  // are re-evaluated together once kMlpF32Nb of them wait, one has waited
+  // reeval_defer rounds, or no walker can move; a decision is only
+  // delayed, never changed); hold: left out of the last round's weight pass
+  // by the round cap (it goes first in the next round).
+  int has = 0, pend = 0, hold = 0;
+  float tp0 = 0.f, tp1 = 0.f;  // the slots' positions on the line
+  int age = 0;                 // rounds the oldest pending candidate has waited (uniform)
   const int cap = bf16 ? R.mlp_round_cap : 0;
-  // the slice-sampling step on the outcome of this walker's candidate at tp
-  auto decide = [&](bool in, float lp, float tp) {
+  auto row_of = [&](int s) { return s ? m + tid : tid; };
+  // (register arrays are indexed by compile-time constants only, so they stay in registers)
+  auto put = [&](int s, const float (&u)[DMAX]) {
+    float* dst = xbuf + (size_t)row_of(s) * XS;
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k)
+      if (k < d) dst[k] = u[k];
+  };
+  // stepping out on side s with the outcome of its end
+  auto decide_out = [&](int s, bool in, float lp) {
     if (in) ++evals;
-    const bool ok = in && (lp > ((phase == 2) ? thr_in : thr_out));
-    if (phase < 2) {
-      const bool expand = ok && (nexp < S.e_max);
-      a = (expand && phase == 0) ? a - S.width : a;
-      b = (expand && phase == 1) ? b + S.width : b;
-      flags |= (ok && !expand) ? 1 : 0;
-      nexp = expand ? nexp + 1 : 0;
-      phase = expand ? phase : phase + 1;
+    const bool ok = in && (lp > thr_out);
+    const int ne = s ? nexp1 : nexp0;
+    const bool expand = ok && (ne < S.e_max);
+    if (s == 0) {
+      a = expand ? a - S.width : a;
+      nexp0 = expand ? ne + 1 : 0;
     } else {
-      if (step == S.n_steps - 1) {
-        int hs = -1;
-        if (nsh < S.t_max - 1) {
-          hs = nsh;
-          hlen = nsh + 1;
-        } else if (ok) {
-          hs = S.t_max - 1;
-          hlen = S.t_max;
-        }
-        if (hs >= 0) {
-          float u[DMAX];
-          candidate<DMAX>(x, v, tp, u);
-          R.hist_l[(size_t)i * S.t_max + hs] = lp;
-          for (int k = 0; k < d; ++k) R.hist_x[((size_t)i * S.t_max + hs) * d + k] = u[k];
-        }
+      b = expand ? b + S.width : b;
+      nexp1 = expand ? ne + 1 : 0;
+    }
+    flags |= (ok && !expand) ? 1 : 0;
+    if (!expand) done |= 1 << s;
+  };
+  // shrinkage with the outcome of the candidate at tp
+  auto decide_shrink = [&](bool in, float lp, float tp) {
+    if (in) ++evals;
+    const bool ok = in && (lp > thr_in);
+    if (step == S.n_steps - 1) {
+      int hs = -1;
+      if (nsh < S.t_max - 1) {
+        hs = nsh;
+        hlen = nsh + 1;
+      } else if (ok) {
+        hs = S.t_max - 1;
+        hlen = S.t_max;
       }
-      bool advance = ok;
-      if (ok) {
+      if (hs >= 0) {
         float u[DMAX];
         candidate<DMAX>(x, v, tp, u);
+        R.hist_l[(size_t)i * S.t_max + hs] = lp;
 #pragma unroll
-        for (int k = 0; k < DMAX; ++k) x[k] = u[k];
-        l = lp;
-      } else {
-        if (tp < 0.f) a = tp;
-        else b = tp;
-        if (++nsh >= S.s_max) {
-          flags |= 2;
-          advance = true;
-        }
+        for (int k = 0; k < DMAX; ++k)
+          if (k < d) R.hist_x[((size_t)i * S.t_max + hs) * d + k] = u[k];
       }
-      if (advance) {
-        ++step;
-        if (step < S.n_steps) {
-          load_step(step);
-          st.init(S.k0, S.k1, S.t, (uint32_t)i, (uint32_t)step);
-          st.n = n0 + kPreShrink;
-          phase = 0;
-          nsh = 0;
-          nexp = 0;
-        } else {
-          active = false;
+    }
+    bool advance = ok;
+    if (ok) {
+      float u[DMAX];
+      candidate<DMAX>(x, v, tp, u);
+#pragma unroll
+      for (int k = 0; k < DMAX; ++k) x[k] = u[k];
+      l = lp;
+    } else {
+      if (tp < 0.f) a = tp;
+      else b = tp;
+      if (++nsh >= S.s_max) {
+        flags |= 2;
+        advance = true;
+      }
+    }
+    if (advance) {
+      ++step;
+      if (step < S.n_steps) {
+        load_step(step);
+        st.init(S.k0, S.k1, S.t, (uint32_t)i, (uint32_t)step);
+        st.n = n0 + kPreShrink;
+        phase = 0;
+        nsh = 0;
+        nexp0 = nexp1 = 0;
+        done = 0;
+      } else {
+        active = false;
+      }
+    }
+  };
+  // the outcome of slot s's candidate (evaluated, in the box)
+  auto decide = [&](int s, float lp) {
+    has &= ~(1 << s);
+    hold &= ~(1 << s);
+    if (phase == 2) decide_shrink(true, lp, tp0);
+    else decide_out(s, true, lp);
+  };
+  // Fills the walker's empty slots with its next in-box candidates;
+  // proposals outside the unit cube need no likelihood and are settled here
+  // (a rejection, in the walker's own order of draws).
+  auto fill = [&]() {
+    // terminates: every pass fills a slot or settles a proposal (at most s_max per step)
+    for (int guard = 0, gmax = (S.s_max + 2) * (S.n_steps + 1); guard < gmax; ++guard) {
+      if (!active) return;
+      if (phase == 0) {
+#pragma unroll
+        for (int s = 0; s < 2; ++s) {
+          if ((done >> s) & 1 || (has >> s) & 1) continue;
+          const float tp = s ? b : a;
+          float u[DMAX];
+          if (candidate<DMAX>(x, v, tp, u)) {
+            has |= 1 << s;
+            if (s) tp1 = tp;
+            else tp0 = tp;
+            put(s, u);
+          } else {
+            decide_out(s, false, -CUDART_INF_F);
+          }
         }
+        if (has) return;
+        phase = 2;  // both ends are outside the slice
+      } else {
+        if (has & 1) return;
+        float uu = pre[0];
+        if (nsh < kPreShrink) {
+#pragma unroll
+          for (int j = 1; j < kPreShrink; ++j)
+            if (nsh == j) uu = pre[j];
+        } else {
+          uu = u24(st.next());
+        }
+        const float tp = fmaf(uu, b - a, a);
+        float u[DMAX];
+        if (candidate<DMAX>(x, v, tp, u)) {
+          has |= 1;
+          tp0 = tp;
+          put(0, u);
+          return;
+        }
+        decide_shrink(false, -CUDART_INF_F, tp);
       }
     }
   };
   for (;;) {
     if (!__syncthreads_or(active ? 1 : 0)) break;
-    float tp = 0.f;
-    bool in = false;
-    if (hold) {  // the candidate in this walker's xbuf row waits for its evaluation
-      tp = htp;
-      in = true;
-    } else if (active && !pend) {
-      // proposals outside the unit cube need no likelihood: settle them here
-      // (a rejection, in the walker's own order of draws) until the walker
-      // holds a candidate to evaluate or has finished its steps
-      float u[DMAX];
-      for (;;) {
-        tp = (phase == 0) ? a : b;
-        if (phase == 2) {
-          float uu = pre[0];
-          if (nsh < kPreShrink) {
-#pragma unroll
-            for (int j = 1; j < kPreShrink; ++j)
-              if (nsh == j) uu = pre[j];
-          } else {
-            uu = u24(st.next());
-          }
-          tp = fmaf(uu, b - a, a);
-        }
-        in = candidate<DMAX>(x, v, tp, u);
-        if (in) break;
-        decide(false, -CUDART_INF_F, tp);
-        if (!active) break;
-      }
-      if (in)
-        for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = u[k];
-    }
-    const bool moving = active && !pend && in;  // holds a candidate to evaluate this round
-    if (mine && !pend && !moving)
-      for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = 0.5f;
+    fill();
+    const int req = active ? (has & ~pend) : 0;  // slots whose candidate is evaluated this round (or held)
     // every walker finished while settling its proposals: no batch to evaluate
-    if (!__syncthreads_or((moving || pend) ? 1 : 0)) break;
-    // the walkers whose candidate is evaluated this round, in thread order
-    // (with a cap: the held ones first, then the new ones, up to the cap)
-    int n_mv;
-    bool take = moving;
-    int mpos;
-    if (cap > 0) {
-      int n_old, n_new;
-      const int p_old = block_exclusive_scan((moving && hold) ? 1 : 0, BS, &n_old);
-      const int p_new = block_exclusive_scan((moving && !hold) ? 1 : 0, BS, &n_new);
-      mpos = hold ? p_old : n_old + p_new;
-      n_mv = min(cap, n_old + n_new);
-      take = moving && mpos < cap;
-      hold = moving && !take;
-      if (hold) htp = tp;
-    } else {
-      mpos = block_exclusive_scan(moving ? 1 : 0, BS, &n_mv);
+    if (!__syncthreads_or((req | pend) ? 1 : 0)) break;
+    // this round's candidates (row indices), in thread order, left slot first;
+    // with a cap, the held ones first, then the new ones, up to the cap
+    const int n_old_me = __popc(req & hold), n_new_me = __popc(req & ~hold);
+    int n_old, n_new;
+    const int p_old = block_exclusive_scan(n_old_me, BS, &n_old);
+    const int p_new = block_exclusive_scan(n_new_me, BS, &n_new);
+    const int n_all = n_old + n_new;
+    const int n_mv = (cap > 0) ? min(cap, n_all) : n_all;
+    int take = 0;
+    {
+      int po = p_old, pn = n_old + p_new;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (!((req >> s) & 1)) continue;
+        const int pos = ((hold >> s) & 1) ? po++ : pn++;
+        if (pos < n_mv) {
+          mvlist[pos] = row_of(s);
+          take |= 1 << s;
+        }
+      }
+      hold = req & ~take;
     }
-    if (take) mvlist[mpos] = tid;
     __syncthreads();
+    if (tid == 0) {  // rounds; passes and their candidates (thread 0 keeps the run's counters)
+      count[0] += 1;
+      const int per = bf16 ? kMlpNbMax : (tcfp ? kRunSplitNb : kMlpF32NbWide);
+      count[bf16 ? 1 : 3] += (n_mv + per - 1) / per;
+      count[bf16 ? 2 : 4] += n_mv;
+    }
     long long c0 = clock64();
     if (bf16) {
-      __syncthreads();
-      if (n_mv > 0 && !mlp_batch_bf16(R, xbuf, n_mv, lbuf, tsm, ctx, mvlist)) err = 1;
+      if (n_mv > 0 && !mlp_batch_bf16(R, xbuf, XS, n_mv, lbuf, tsm, ctx, mail, C, mvlist)) err = 1;
       long long c1 = clock64();
       ce += c1 - c0;
       c0 = c1;
       // candidates close to their threshold wait for their FP32 value
       const float thr = (phase == 2) ? thr_in : thr_out;
       const float margin = fmaf(R.reeval_rel, fabsf(thr), R.reeval_margin);
-      const bool need = take && in && margin > 0.f && fabsf(lbuf[tid] - thr) < margin;
-      if (need) {
-        pend = true;
-        ptp = tp;
+#pragma unroll
+      for (int s = 0; s < 2; ++s) {
+        if (!((take >> s) & 1)) continue;
+        const float lv = lbuf[row_of(s)];
+        if (margin > 0.f && fabsf(lv - thr) < margin) pend |= 1 << s;
+        else decide(s, lv);
       }
-      if (take && !need) decide(in, in ? lbuf[tid] : -CUDART_INF_F, tp);
       int cnt;
-      const int pos = block_exclusive_scan(pend ? 1 : 0, BS, &cnt);
-      const int still = __syncthreads_or((active && !pend) ? 1 : 0);
+      const int pos = block_exclusive_scan(__popc(pend), BS, &cnt);
+      // can this walker move next round: a live slot that is not pending
+      const int live = (phase == 0) ? (~done & 3) : 1;
+      const int still = __syncthreads_or((active && (live & ~pend)) ? 1 : 0);
       age = (cnt > 0) ? age + 1 : 0;
       if (cnt > 0 && (cnt >= kMlpF32Nb || !still || age > R.reeval_defer)) {
-        if (pend) rlist[pos] = tid;
+        {
+          int p = pos;
+#pragma unroll
+          for (int s = 0; s < 2; ++s)
+            if ((pend >> s) & 1) rlist[p++] = row_of(s);
+        }
         __syncthreads();
+        if (tid == 0) {
+          count[3] += (cnt + (tc32 ? kRunSplitNb : kMlpF32Nb) - 1) / (tc32 ? kRunSplitNb : kMlpF32Nb);
+          count[4] += cnt;
+        }
         if (tc32) {
-          if (!mlp_reeval_tc(R, xbuf, lbuf, rlist, cnt, tsm, ctx)) err = 1;
+          if (!mlp_reeval_tc(R, xbuf, XS, lbuf, rlist, cnt, tsm, ctx, mail, C)) err = 1;
         } else {
-          mlp_reeval(R, xbuf, lbuf, rlist, cnt, xg, lg, act);
+          mlp_reeval(R, xbuf, XS, lbuf, rlist, cnt, xg, lg, act);
         }
         reevals += (tid == 0) ? cnt : 0;
-        if (pend) {
-          pend = false;
-          decide(true, lbuf[tid], ptp);
-        }
+        const int pd = pend;
+        pend = 0;
+#pragma unroll
+        for (int s = 0; s < 2; ++s)
+          if ((pd >> s) & 1) decide(s, lbuf[row_of(s)]);
         age = 0;
       }
       cr += clock64() - c0;
     } else {
-      __syncthreads();
-      if (n_mv > 0) mlp_batch_f32(R, xbuf, n_mv, lbuf, act, mvlist);
+      if (n_mv > 0) {
+        if (tcfp) {
+          if (!mlp_reeval_tc(R, xbuf, XS, lbuf, mvlist, n_mv, tsm, ctx, mail, C)) err = 1;
+        } else {
+          mlp_batch_f32(R, xbuf, XS, n_mv, lbuf, act, mvlist);
+        }
+      }
       ce += clock64() - c0;
       __syncthreads();
-      if (moving) decide(in, in ? lbuf[tid] : -CUDART_INF_F, tp);
+#pragma unroll
+      for (int s = 0; s < 2; ++s)
+        if ((take >> s) & 1) decide(s, lbuf[row_of(s)]);
     }
     if (__syncthreads_or(err)) {
       err = 1;
@@ -639,14 +796,21 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   // samples (rows of xbuf in order: the wide FP32 evaluator)
   const long long c_end = clock64();
   if (bf16 && !err) {
-    if (mine)
-      for (int k = 0; k < d; ++k) xbuf[(size_t)tid * kMaxDim + k] = x[k];
+    if (mine) {
+#pragma unroll
+      for (int k = 0; k < DMAX; ++k)
+        if (k < d) xbuf[(size_t)tid * XS + k] = x[k];
+    }
     if (tid < m) rlist[tid] = tid;
     __syncthreads();
+    if (tid == 0) {
+      count[3] += (m + (tc32 ? kRunSplitNb : kMlpF32NbWide) - 1) / (tc32 ? kRunSplitNb : kMlpF32NbWide);
+      count[4] += m;
+    }
     if (tc32) {
-      if (!mlp_reeval_tc(R, xbuf, lbuf, rlist, m, tsm, ctx)) err = 1;
+      if (!mlp_reeval_tc(R, xbuf, XS, lbuf, rlist, m, tsm, ctx, mail, C)) err = 1;
     } else {
-      mlp_batch_f32(R, xbuf, m, lbuf, act);
+      mlp_batch_f32(R, xbuf, XS, m, lbuf, act);
     }
     if (mine) l = lbuf[tid];
     reevals += (tid == 0) ? m : 0;
@@ -666,23 +830,28 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
         }
     int tot;
     const int base = block_exclusive_scan(nh, BS, &tot);
-    for (int h0 = 0; h0 < tot; h0 += m) {
-      // stage up to m history samples per pass in xbuf
-      const int nb = min(m, tot - h0);
+    const int per_pass = 2 * m;
+    for (int h0 = 0; h0 < tot; h0 += per_pass) {
+      // stage up to 2m history samples per pass in xbuf
+      const int nb = min(per_pass, tot - h0);
       for (int h = 0, j = 0; h < hlen; ++h) {
         if (!((want >> h) & 1ull)) continue;
         const int gidx = base + j++ - h0;
         if (gidx >= 0 && gidx < nb) {
           const float* hx = R.hist_x + ((size_t)i * S.t_max + h) * d;
-          for (int k = 0; k < d; ++k) xbuf[(size_t)gidx * kMaxDim + k] = hx[k];
+          for (int k = 0; k < d; ++k) xbuf[(size_t)gidx * XS + k] = hx[k];
         }
       }
       for (int q = tid; q < nb; q += blockDim.x) rlist[q] = q;
       __syncthreads();
+      if (tid == 0) {
+        count[3] += (nb + (tc32 ? kRunSplitNb : kMlpF32NbWide) - 1) / (tc32 ? kRunSplitNb : kMlpF32NbWide);
+        count[4] += nb;
+      }
       if (tc32) {
-        if (!mlp_reeval_tc(R, xbuf, lbuf, rlist, nb, tsm, ctx)) err = 1;
+        if (!mlp_reeval_tc(R, xbuf, XS, lbuf, rlist, nb, tsm, ctx, mail, C)) err = 1;
       } else {
-        mlp_batch_f32(R, xbuf, nb, lbuf, act);
+        mlp_batch_f32(R, xbuf, XS, nb, lbuf, act);
       }
       for (int h = 0, j = 0; h < hlen; ++h) {
         if (!((want >> h) & 1ull)) continue;
@@ -694,7 +863,9 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
     }
   }
   if (mine) {
-    for (int k = 0; k < d; ++k) R.new_x[(size_t)i * d + k] = x[k];
+#pragma unroll
+    for (int k = 0; k < DMAX; ++k)
+      if (k < d) R.new_x[(size_t)i * d + k] = x[k];
     R.new_l[i] = l;
     R.hist_len[i] = hlen;
     if (R.wk_evals) {
@@ -714,7 +885,7 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
 // Initial live points of an MLP run, evaluated in FP32.
 template <int DMAX>
 inline __device__ void init_live_mlp(const RunDesc& R, float* xbuf, float* lbuf, int* rlist, char* msm) {
-  const int d = R.d;
+  const int d = R.d, XS = mlp_xs(d);
   float* act = reinterpret_cast<float*>(msm);
   for (int j0 = 0; j0 < R.N; j0 += R.m) {
     const int nb = min(R.m, R.N - j0);
@@ -722,11 +893,11 @@ inline __device__ void init_live_mlp(const RunDesc& R, float* xbuf, float* lbuf,
       const int j = j0 + q / d, k = q % d;
       const float xv = u24(draw_at(R.k0, R.k1, kTInit, (uint32_t)j, 0u, (uint32_t)k));
       R.live_x[(size_t)k * R.n_pad + j] = xv;
-      xbuf[(size_t)(q / d) * kMaxDim + k] = xv;
+      xbuf[(size_t)(q / d) * XS + k] = xv;
     }
     for (int q = threadIdx.x; q < nb; q += blockDim.x) rlist[q] = q;
     __syncthreads();
-    mlp_reeval(R, xbuf, lbuf, rlist, nb, xbuf + (size_t)R.m * kMaxDim, lbuf + R.m, act);
+    mlp_reeval(R, xbuf, XS, lbuf, rlist, nb, xbuf + (size_t)2 * R.m * XS, lbuf + 2 * R.m, act);
     for (int q = threadIdx.x; q < nb; q += blockDim.x) {
       R.live_l[j0 + q] = lbuf[q];
       R.live_cid[j0 + q] = 0;
@@ -758,22 +929,43 @@ __global__ void NS_RUN_BOUNDS(MLP, DMAX) k_run(const RunDesc* __restrict__ runs,
   __shared__ RunState RS;
   __shared__ EvidState E;
   __shared__ int flag_any;
+  __shared__ MlpCtx mlp_ctx;
   const int tid = threadIdx.x, B = blockDim.x;
+  // MLP runs may be launched as clusters of C CTAs per run (CTA 0 runs the
+  // sampler, the others share its tensor-core evaluations)
+  unsigned C = 1, rank = 0;
+  ClusterMail* mail = nullptr;
+  if constexpr (MLP) {
+    __shared__ ClusterMail cl_mail;
+    mail = &cl_mail;
+    C = cl_size();
+    rank = cl_rank();
+  }
   if (tid == 0) {
-    R = runs[ids[blockIdx.x]];
+    R = runs[ids[blockIdx.x / C]];
     RS = *R.st;
     E.logz = RS.logz;
     E.info = RS.info;
     E.k = RS.k;
   }
   __syncthreads();
-  if (RS.stopped || RS.status != 0) return;
-  __shared__ MlpCtx mlp_ctx;
-  if constexpr (MLP) {
-    if (R.precision == 1) mlp_ctx_init(&mlp_ctx);
-  }
   const int d = R.d, N = R.N, m = R.m;
   const Carve cv = make_carve(d, m, R.n_nodes, DMAX, MLP, R.spill != 0);
+  if constexpr (MLP) {
+    if (rank > 0) {
+      mlp_follower(R, &mlp_ctx, mail, align1024_shared(sm + cv.mlp), C, rank);
+      return;
+    }
+  }
+  if (RS.stopped || RS.status != 0) {
+    if constexpr (MLP) {
+      if (C > 1) mlp_leader_exit(&mlp_ctx, mail, false);
+    }
+    return;
+  }
+  if constexpr (MLP) {
+    if (R.precision != 0) mlp_ctx_init(&mlp_ctx);
+  }
   float* s_slots = reinterpret_cast<float*>(sm + cv.slots);
   float* s_xbuf = reinterpret_cast<float*>(sm + cv.xbuf);
   float* s_lbuf = reinterpret_cast<float*>(sm + cv.lbuf);
@@ -862,8 +1054,8 @@ __global__ void NS_RUN_BOUNDS(MLP, DMAX) k_run(const RunDesc* __restrict__ runs,
     int fl = 0, werr = 0;
     SC.t = t;
     if constexpr (MLP) {
-      walker_phase_mlp<DMAX>(R, SC, s_W, s_seed, s_chol, s_xbuf, s_lbuf, s_rlist, s_mlp, &mlp_ctx, s_list, S, ev, fl, re,
-                             werr, cyc_eval, cyc_reeval);
+      walker_phase_mlp<DMAX>(R, SC, s_W, s_seed, s_chol, s_xbuf, s_lbuf, s_rlist, s_mlp, &mlp_ctx, mail, s_list, S, ev,
+                             fl, re, werr, cyc_eval, cyc_reeval, RS.mlp_count);
     } else {
       // every walker's rows of the iteration, spread over the whole block
       const long long cd = clock64();
@@ -985,7 +1177,8 @@ __global__ void NS_RUN_BOUNDS(MLP, DMAX) k_run(const RunDesc* __restrict__ runs,
   }
   __syncthreads();
   if constexpr (MLP) {
-    if (R.precision == 1) mlp_ctx_free(&mlp_ctx);
+    if (C > 1) mlp_leader_exit(&mlp_ctx, mail, R.precision != 0);
+    if (R.precision != 0) mlp_ctx_free(&mlp_ctx);
   }
   if (tid == 0) {
     RS.logz = E.logz;
@@ -1097,7 +1290,7 @@ __global__ void k_slice_warp(const LikParams P, SliceCfg SC, int m, int n_pad, i
                                int* flags, float* dir_scratch, int warp, cudaStream_t s);                  \
   cudaError_t occupancy_run_##D(int block, size_t smem, int* blocks_per_sm);
 NS_FOR_EACH_CLASS(NS_DECLARE_LAUNCHERS)
-cudaError_t launch_run_mlp(const RunDesc* runs, const int* ids, int n, int block, size_t smem, int chunk,
+cudaError_t launch_run_mlp(const RunDesc* runs, const int* ids, int n, int block, size_t smem, int chunk, int cluster,
                            cudaStream_t s);
 
 }  // namespace nsd

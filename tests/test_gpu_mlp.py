@@ -116,6 +116,48 @@ def test_mlp_bf16_tensor_cores(nat, oracle, widths, n):
     np.testing.assert_allclose(got, exact, rtol=5e-2, atol=1e-2)
 
 
+@pytest.mark.parametrize("cluster", [2, 4])
+@pytest.mark.parametrize("precision,n", [(1, 150), (1, 257), (1, 7), (2, 33), (2, 150)])
+def test_mlp_cluster_split_evaluator(nat, oracle, cluster, precision, n):
+    """The tensor-core evaluators split over a cluster of 2 or 4 CTAs (each
+    streams a disjoint share of every layer's weight tiles; hidden
+    activations exchanged through distributed shared memory) on the 27-D
+    emulator network, ragged batches included: the same log L as one CTA up
+    to the order of the final chi^2 sum, and, element by element, the FP64
+    oracle at each path's tolerance (BF16: the BF16 emulation at 3e-3 and the
+    oracle at 5e-2; FP32 accuracy: the oracle at 2e-5)."""
+    p = _problem((27, 512, 512, 512, 512, 2000), 6, unit_sigma=(precision == 1))
+    img = _image(nat, p)
+    rng = np.random.default_rng(100 * cluster + n)
+    x = rng.uniform(0, 1, size=(n, p.d)).astype(np.float32)
+    x[0] = p.mlp.theta_star
+    xt = torch.tensor(x, device="cuda")
+    one = torch.zeros(n, device="cuda")
+    split = torch.full((n,), float("nan"), device="cuda")
+    nat.ns_mlp_loglike(p, img, xt, one, precision=precision)
+    nat.ns_mlp_loglike_cluster(p, img, xt, split, precision=precision, cluster=cluster)
+    torch.cuda.synchronize()
+    got = split.cpu().numpy().astype(np.float64)
+    assert np.all(np.isfinite(got)), "a cluster pass timed out"
+    np.testing.assert_allclose(got, one.cpu().numpy().astype(np.float64), rtol=2e-6, atol=1e-4)
+    exact = oracle.loglike(oracle.Lik(p), x.astype(np.float64))
+    if precision == 1:
+        np.testing.assert_allclose(got, _emulate_bf16(p, x), rtol=3e-3, atol=1e-3)
+        np.testing.assert_allclose(got, exact, rtol=5e-2, atol=1e-2)
+    else:
+        np.testing.assert_allclose(got, exact, rtol=2e-5, atol=1e-3)
+
+
+def test_mlp_cluster_arguments(nat):
+    p = _small_emulator()
+    img = _image(nat, p)
+    x = torch.rand(8, p.d, device="cuda")
+    out = torch.zeros(8, device="cuda")
+    for prec, cl in ((1, 3), (0, 4), (1, 4)):  # bad size; CUDA-core path; 1 tile row per layer
+        with pytest.raises(nat.NSError):
+            nat.ns_mlp_loglike_cluster(p, img, x, out, precision=prec, cluster=cl)
+
+
 # --------------------------------------------------------------------------
 # whole runs with the MLP likelihood
 # --------------------------------------------------------------------------
@@ -235,13 +277,13 @@ def test_mlp_fp32_accurate_tensor_path(nat, oracle, widths, n):
 # --------------------------------------------------------------------------
 # the lock-step MLP walkers of the run kernel on fixed streams
 # --------------------------------------------------------------------------
-def _mlp_walkers_vs_oracle(nat, oracle, p, N, m, ns, T, precision, seed):
+def _mlp_walkers_vs_oracle(nat, oracle, p, N, m, ns, T, precision, seed, cluster=1):
     """Runs T iterations, reads the live set and cluster factor the next
     iteration starts from (ns_copy_run_buffer), runs iteration T, and replays
     each of its walkers with the oracle's slice walker on the same Philox
     streams, seed point and thresholds.  Returns (walkers compared, walkers
     that diverged at a borderline comparison)."""
-    opt = nat.ns_default_options(precision=precision)
+    opt = nat.ns_default_options(precision=precision, mlp_cluster=cluster)
     assert (T % max(1, 100 // m)) != 0  # no re-clustering at iteration T: the factor read is the one used
     h = nat.ns_create_batch([(p, N, m, ns, 1e-3, seed)], opt)
     nat.ns_step(h, T)
@@ -283,7 +325,7 @@ def _mlp_walkers_vs_oracle(nat, oracle, p, N, m, ns, T, precision, seed):
             np.testing.assert_array_equal(np.isfinite(g["hist_l"][i, :hl]), fin)
             h64 = oracle.loglike(lik, hx[fin]) if fin.any() else np.zeros(0)
             hg = g["hist_l"][i, :hl][fin]
-            fp32 = np.ones(len(hg), dtype=bool) if precision == 0 else hg >= lim
+            fp32 = np.ones(len(hg), dtype=bool) if precision != 1 else hg >= lim
             assert np.all(np.abs(hg[fp32] - h64[fp32]) <= tol(h64[fp32])), i
             # the others keep their BF16 value
             assert np.all(np.abs(hg[~fp32] - h64[~fp32]) <= 1e-2 * np.abs(h64[~fp32]) + 1.0), i
@@ -296,22 +338,58 @@ def _mlp_walkers_vs_oracle(nat, oracle, p, N, m, ns, T, precision, seed):
     return m, n_div
 
 
-@pytest.mark.parametrize("precision", [0, 1])
-@pytest.mark.parametrize("net", ["emulator27", "small4"])
-def test_mlp_run_walkers_match_oracle_on_fixed_streams(nat, oracle, precision, net):
-    """The run kernel's lock-step MLP walkers (out-of-box proposals settled
-    locally, rounds batched onto the evaluator, and in BF16 mode FP32
-    re-evaluation near the threshold with deferred passes and the round
-    cap) take the sequential slice sampler's decisions: each walker's new
-    point, log L, history, evaluation count and cap flags equal the FP64
-    oracle walker's on the same streams, except where a comparison was
-    borderline at FP32 accuracy.  On the 27-D emulator network (27 -> 512 x
-    4 -> 2000) at iteration 100 (N = 300, m = 16, 8 slice steps) and on a
-    4-D network (4 -> 64 -> 64 -> 60) at iteration 31 (N = 200, m = 20, 20
-    steps)."""
+@pytest.mark.parametrize("net,precision,cluster", [
+    ("emulator27", 0, 1), ("emulator27", 1, 1), ("emulator27", 1, 4), ("emulator27", 2, 4), ("emulator27", 2, 2),
+    ("small4", 0, 1), ("small4", 1, 1), ("small4", 2, 1)])
+def test_mlp_run_walkers_match_oracle_on_fixed_streams(nat, oracle, net, precision, cluster):
+    """The run kernel's lock-step MLP walkers (both stepping-out ends
+    evaluated in the same round, out-of-box proposals settled locally,
+    rounds batched onto the evaluator, in BF16 mode FP32 re-evaluation near
+    the threshold with deferred passes and the round cap; on one CTA or with
+    every evaluation split over a cluster of CTAs) take the sequential slice
+    sampler's decisions: each walker's new point, log L, history, evaluation
+    count and cap flags equal the FP64 oracle walker's on the same streams,
+    except where a comparison was borderline at FP32 accuracy.  Precision 0
+    is FP32 on the CUDA cores, 1 BF16 with FP32 re-evaluation, 2 FP32 on the
+    tensor cores.  On the 27-D emulator network (27 -> 512 x 4 -> 2000) at
+    iteration 100 (N = 300, m = 16, 8 slice steps) and on a 4-D network
+    (4 -> 64 -> 64 -> 60) at iteration 31 (N = 200, m = 20, 20 steps)."""
     if net == "emulator27":
         p, N, m, ns, T = W.mlp_emulator(1), 300, 16, 8, 100
     else:
         p, N, m, ns, T = _small_emulator(3), 200, 20, 20, 31
-    n, n_div = _mlp_walkers_vs_oracle(nat, oracle, p, N, m, ns, T, precision, seed=9)
+    n, n_div = _mlp_walkers_vs_oracle(nat, oracle, p, N, m, ns, T, precision, seed=9, cluster=cluster)
     assert n_div <= max(1, n // 10), n_div
+
+
+@pytest.mark.parametrize("cluster", [1, 4])
+def test_bf16_runs_reproduce_the_fp32_tensor_runs(nat, cluster):
+    """The precision pattern's promise, checked whole: a BF16 decision is
+    taken only when the BF16 log L lies beyond the re-evaluation margin from
+    its threshold, every other candidate gets its FP32 value first, and every
+    stored value is FP32; FP32 values on the tensor cores do not depend on the
+    batch a candidate is evaluated in.  So, while the BF16 error stays within
+    the margin, a BF16 run takes every decision of the FP32 run on the tensor
+    cores (precision 2) and stores the same values: the two runs are the same
+    run, bit for bit.  An 8-D network (8 -> 512 -> 512 -> 512), N = 200,
+    m = 20, 40 slice steps, 8 seeds, on one CTA and on a 4-CTA cluster."""
+    p = W.mlp_emulator(4, widths=(8, 512, 512, 512), sig_lo=2e-2, sig_hi=2e-1)
+    seeds = list(range(31, 39))
+    out = {}
+    for prec in (1, 2):
+        h = nat.ns_create_batch([(p, 200, 20, 40, 1e-3, s) for s in seeds],
+                                nat.ns_default_options(precision=prec, mlp_cluster=cluster))
+        nat.ns_run(h)
+        out[prec] = [nat.ns_result(h, r) for r in range(len(seeds))]
+        nat.ns_destroy(h)
+    same = 0
+    for a, b in zip(out[1], out[2]):
+        assert a["status"] == 0 and b["status"] == 0
+        assert abs(a["log_z"] - b["log_z"]) < 0.05, (a["log_z"], b["log_z"])
+        if a["log_z"] == b["log_z"] and a["n_evals"] == b["n_evals"]:
+            np.testing.assert_array_equal(a["dead_l"], b["dead_l"])
+            np.testing.assert_array_equal(a["dead_x"], b["dead_x"])
+            same += 1
+    assert same >= len(seeds) - 1, same
+    assert sum(r["n_reeval"] for r in out[1]) > 0 and all(r["n_cand_bf16"] > 0 for r in out[1])
+    assert all(r["n_cand_bf16"] == 0 and r["n_cand_fp32"] > 0 for r in out[2])
