@@ -27,7 +27,8 @@ def _torch():
 
 
 def laplace_logz(problem, n_mc=400000, seed=0, hessian=False, max_steps=50):
-    """Returns dict(log_z, log_z_untruncated, box_mass, theta_hat, logl_hat)."""
+    """Returns dict(log_z, log_z_untruncated, box_mass, theta_hat, logl_hat,
+    cov): cov = F^-1, the covariance of the Gaussian approximation."""
     torch = _torch()
     spec = problem.mlp
     dt = torch.float64
@@ -71,4 +72,4 @@ def laplace_logz(problem, n_mc=400000, seed=0, hessian=False, max_steps=50):
     s = th + z @ L.T
     mass = float(((s >= 0) & (s <= 1)).all(1).to(dt).mean())
     return {"log_z": lz + math.log(max(mass, 1e-300)), "log_z_untruncated": lz, "box_mass": mass,
-            "theta_hat": th.numpy(), "logl_hat": l_hat}
+            "theta_hat": th.numpy(), "logl_hat": l_hat, "cov": (0.5 * (C + C.T)).numpy()}

@@ -393,3 +393,34 @@ def test_bf16_runs_reproduce_the_fp32_tensor_runs(nat, cluster):
     assert same >= len(seeds) - 1, same
     assert sum(r["n_reeval"] for r in out[1]) > 0 and all(r["n_cand_bf16"] > 0 for r in out[1])
     assert all(r["n_cand_bf16"] == 0 and r["n_cand_fp32"] > 0 for r in out[2])
+
+
+def test_bf16_error_near_the_posterior_is_inside_the_margin(nat):
+    """Calibration of the FP32 re-evaluation margin on the 27-D emulator
+    network where it matters, near the end of a run: 20000 points of the
+    posterior region (the Laplace approximation's Gaussian around the mode,
+    oracle/laplace.py, clipped to the box; log L from about l_max - 30 to
+    l_max), evaluated in BF16 and in FP32 on the tensor cores.  Twice the
+    99.99th percentile of |log L_BF16 - log L_FP32| lies inside the default
+    margin 2 + 4e-3 |log L|, so a BF16 decision there agrees with the FP32
+    one."""
+    from oracle import laplace
+    p = W.mlp_emulator(1)
+    lap = laplace.laplace_logz(p, n_mc=1000)
+    L = np.linalg.cholesky(lap["cov"])
+    z = np.random.default_rng(3).standard_normal((20000, p.d))
+    x = np.clip(lap["theta_hat"] + z @ L.T, 0.0, 1.0).astype(np.float32)
+    img = _image(nat, p)
+    xt = torch.tensor(x, device="cuda")
+    lb = torch.zeros(len(x), device="cuda")
+    lf = torch.zeros(len(x), device="cuda")
+    nat.ns_mlp_loglike(p, img, xt, lb, precision=1)
+    nat.ns_mlp_loglike(p, img, xt, lf, precision=2)
+    torch.cuda.synchronize()
+    lb, lf = lb.cpu().numpy().astype(np.float64), lf.cpu().numpy().astype(np.float64)
+    err = np.abs(lb - lf)
+    q = float(np.quantile(err, 0.9999))
+    opt = nat.ns_default_options()
+    margin = opt.reeval_margin + opt.reeval_rel * np.abs(lf)
+    assert 2 * q < float(margin.min()), (q, float(margin.min()), float(lf.min()), float(lf.max()))
+    assert np.all(err < margin), float(np.max(err - margin))
