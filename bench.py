@@ -632,6 +632,8 @@ def emulator_convergence(n_seeds, cases="target150,single150"):
         log Z per seed on both paths, the paired difference BF16 - FP32 with
         its standard error, wall time to the stopping rule (device time of
         ns_run), evaluations/s, the FP32 re-evaluation share;
+      cluster150 / cluster75: the same paired comparison with every run
+        split over a 4-CTA cluster (n_seeds clusters side by side);
       single150 / single75: one run alone (seed 500) split over a 4-CTA
         cluster (4 SMs), BF16 and FP32 paths: its wall time to log Z;
       m1: m = 1 (the sequential sampler), one run on a 4-CTA cluster, the
@@ -663,6 +665,8 @@ def emulator_convergence(n_seeds, cases="target150,single150"):
                 "fp32_evaluations_per_run": float(np.mean([r["n_cand_fp32"] for r in res])),
                 "fp32_reeval_share": (float(sum(r["n_reeval"] for r in res) / max(1, cands)) if precision == 1
                                       else None),
+                "x2_reeval_share": (float(sum(r["n_cand_x2"] for r in res) / max(1, cands)) if precision == 1
+                                    else None),
                 "rounds_per_run": float(np.mean([r["n_rounds"] for r in res])),
                 "bf16_candidates_per_pass": (cands / max(1, sum(r["n_pass_bf16"] for r in res))) if cands else None,
                 "log_z": z.tolist(), "log_z_mean": float(z.mean()), "log_z_std": float(z.std(ddof=1)) if len(z) > 1
@@ -688,6 +692,16 @@ def emulator_convergence(n_seeds, cases="target150,single150"):
                                  "seeds_identical": int(np.sum(dz == 0.0)), "seeds": len(dz)}
             a["wall_time_ratio_fp32_over_bf16"] = a["fp32_tc"]["device_s"] / a["bf16"]["device_s"]
             out[f"target_N1500_m{m}"] = emit(f"target{m}", a)
+        if f"cluster{m}" in cases:
+            a = {"bf16": runs_of(p, 1500, m, 1, seeds, 4), "fp32_tc": runs_of(p, 1500, m, 2, seeds, 4)}
+            dz = np.array(a["bf16"]["log_z"]) - np.array(a["fp32_tc"]["log_z"])
+            se = float(dz.std(ddof=1) / np.sqrt(len(dz))) if len(dz) > 1 else float("nan")
+            a["paired_dlogz"] = {"mean": float(dz.mean()), "std": float(dz.std(ddof=1)) if len(dz) > 1 else 0.0,
+                                 "standard_error": se, "bound_abs_mean_plus_2se": float(abs(dz.mean()) + 2 * se),
+                                 "max_abs": float(np.max(np.abs(dz))),
+                                 "seeds_identical": int(np.sum(dz == 0.0)), "seeds": len(dz)}
+            a["wall_time_ratio_fp32_over_bf16"] = a["fp32_tc"]["device_s"] / a["bf16"]["device_s"]
+            out[f"cluster_N1500_m{m}_4cta"] = emit(f"cluster{m}", a)
         if f"single{m}" in cases:
             a = {"bf16": runs_of(p, 1500, m, 1, seeds[:1], 4), "fp32_tc": runs_of(p, 1500, m, 2, seeds[:1], 4)}
             a["wall_time_ratio_fp32_over_bf16"] = a["fp32_tc"]["device_s"] / a["bf16"]["device_s"]
@@ -963,9 +977,9 @@ def main():
         hetero = batch256(nat, W, analytic, mappings=(0, "auto"))
     # "wall time to log Z at |dlogZ| < 0.1": one run of this workload reports
     # an error of ~0.165, so an estimate with a standard error below 0.1 is the
-    # mean of k = 3 independent runs of one problem; they run side by side, so
-    # the time to it is the device time of one 3-run launch to the stopping rule
-    k_pool = 3
+    # mean of k = 4 independent runs of one problem; they run side by side, so
+    # the time to it is the device time of one 4-run launch to the stopping rule
+    k_pool = 4
     p0 = W.corr_gauss10(1)
     hp = nat.ns_create_batch([(p0, N_LIVE, args.m, N_STEPS, STOP, 9000 + j) for j in range(k_pool)],
                              nat.ns_default_options(chunk_iters=args.chunk))

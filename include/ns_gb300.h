@@ -130,6 +130,12 @@ typedef struct {
                            * NS_ERR_ARG), or 0 = automatic (4, then 2, while that many CTAs per MLP run fit on the
                            * device's SMs; else 1).  The chi^2 partials of the CTAs are added in rank order, so
                            * results differ from one CTA's in the last bits of log L */
+    int two_plane;        /* MLP precision 1, BF16-valued weights: a candidate inside the BF16 margin is first
+                           * re-evaluated with 16-bit activations (two BF16 planes, 64 per tensor-core pass) and
+                           * goes on to FP32 only if that value lies within reeval2_margin + reeval2_rel
+                           * |threshold| of its threshold (1, default), or goes to FP32 at once (0) */
+    double reeval2_margin; /* (0.05) */
+    double reeval2_rel;    /* (1e-4) */
 } ns_options;
 
 /* One run of a batch. */
@@ -165,9 +171,10 @@ typedef struct {
     const float* dead_logl;  /* [n_dead]   host, owned by the handle */
     const double* dead_logw; /* [n_dead]   host, owned by the handle: log weight (prior mass times L) */
     /* MLP runs: lock-step walker rounds, and the evaluator passes and the
-     * candidates they carried, BF16 passes and FP32 ones (tensor-core
-     * three-plane or CUDA-core) apart; 0 for other runs */
-    long long n_rounds, n_pass_bf16, n_cand_bf16, n_pass_fp32, n_cand_fp32;
+     * candidates they carried, BF16 passes, FP32 ones (tensor-core
+     * three-plane or CUDA-core) and 16-bit ones (two planes) apart; 0 for
+     * other runs */
+    long long n_rounds, n_pass_bf16, n_cand_bf16, n_pass_fp32, n_cand_fp32, n_pass_x2, n_cand_x2;
 } ns_result_t;
 
 /* ---- whole runs ------------------------------------------------------- */
@@ -488,7 +495,10 @@ ns_status ns_mlp_pack(const ns_likelihood* lik, int d, void* image, void* stream
  * weights are all BF16 values (NS_ERR_ARG otherwise): inputs and
  * activations split exactly into three BF16 parts whose products with the
  * weights are exact in FP32, FP32 accumulation and FP32 epilogues (the MLP
- * runs re-evaluate near-threshold points this way when the weights allow).
+ * runs re-evaluate near-threshold points this way when the weights allow);
+ * precision 3 = 16-bit accuracy on the tensor cores (two BF16 planes per
+ * input and activation, relative rounding 2^-17; BF16-valued weights only),
+ * the intermediate stage of the MLP runs' re-evaluation.
  * A block whose tensor-core pipeline stalls past its wait budget writes NaN
  * for its points. */
 ns_status ns_mlp_loglike(const ns_likelihood* lik, const double* lo, const double* hi, int d,

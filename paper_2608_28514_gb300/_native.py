@@ -47,6 +47,7 @@ class NsOptions(C.Structure):
         ("dead_cap", C.c_longlong), ("chunk_iters", C.c_int), ("precision", C.c_int),
         ("reeval_margin", C.c_double), ("reeval_rel", C.c_double), ("reeval_defer", C.c_int),
         ("walker_mapping", C.c_int), ("mlp_batch_cap", C.c_int), ("mlp_cluster", C.c_int),
+        ("two_plane", C.c_int), ("reeval2_margin", C.c_double), ("reeval2_rel", C.c_double),
     ]
 
 
@@ -73,6 +74,7 @@ class NsResult(C.Structure):
         ("dead_logw", C.POINTER(C.c_double)),
         ("n_rounds", C.c_longlong), ("n_pass_bf16", C.c_longlong), ("n_cand_bf16", C.c_longlong),
         ("n_pass_fp32", C.c_longlong), ("n_cand_fp32", C.c_longlong),
+        ("n_pass_x2", C.c_longlong), ("n_cand_x2", C.c_longlong),
     ]
 
 
@@ -416,7 +418,8 @@ def ns_result(h, run=0, samples=True):
     out = dict(log_z=r.log_z, log_z_err=r.log_z_err, info=r.info_h, n_dead=r.n_dead, n_evals=r.n_evals,
                n_iter=r.n_iter, n_relaxed=r.n_relaxed, n_reeval=r.n_reeval, n_capped=r.n_capped,
                status=r.status, d=r.d, n_rounds=r.n_rounds, n_pass_bf16=r.n_pass_bf16, n_cand_bf16=r.n_cand_bf16,
-               n_pass_fp32=r.n_pass_fp32, n_cand_fp32=r.n_cand_fp32)
+               n_pass_fp32=r.n_pass_fp32, n_cand_fp32=r.n_cand_fp32, n_pass_x2=r.n_pass_x2,
+               n_cand_x2=r.n_cand_x2)
     if samples and r.n_dead > 0:
         n, d = r.n_dead, r.d
         out["dead_x"] = np.ctypeslib.as_array(r.dead_x, shape=(n * d,)).reshape(n, d).copy()

@@ -626,17 +626,6 @@ __device__ __forceinline__ void prefetch_row(float* slot, const float* __restric
   cp_async_commit();
 }
 
-// Asks L2 to fetch the row at src (dir_row(DMAX) floats) ahead of its
-// cp.async: the per-iteration table of a wide batch of runs does not stay in
-// L2 between its writing and its reading, and a row one step ahead is not
-// always early enough for a copy from DRAM.
-template <int DMAX>
-__device__ __forceinline__ void prefetch_row_l2(const float* __restrict__ src) {
-  constexpr int RW = dir_row(DMAX);
-#pragma unroll
-  for (int i = 0; i < RW; i += 32) asm volatile("prefetch.global.L2 [%0];\n" ::"l"(src + i));
-}
-
 // Waits for the walker's prefetched row and unpacks it.
 template <int DMAX>
 __device__ __forceinline__ void take_row(const float* slot, float (&v)[DMAX], float& r, float (&pre)[kPreShrink]) {
@@ -688,7 +677,6 @@ inline __device__ void slice_walker(const LikParams& P, const SliceCfg& S, int w
     a = -r * S.width;
     b = (1.f - r) * S.width;
     if (S.n_steps > 1) prefetch_row<DMAX>(slot, dirs + RW);
-    if (S.n_steps > 2) prefetch_row_l2<DMAX>(dirs + 2 * RW);
   }
   while (__any_sync(kFull, active)) {
     if (active) {
@@ -766,7 +754,6 @@ inline __device__ void slice_walker(const LikParams& P, const SliceCfg& S, int w
             a = -r * S.width;
             b = (1.f - r) * S.width;
             if (step + 1 < S.n_steps) prefetch_row<DMAX>(slot, dirs + (size_t)(step + 1) * RW);
-            if (step + 2 < S.n_steps) prefetch_row_l2<DMAX>(dirs + (size_t)(step + 2) * RW);
             st.init(S.k0, S.k1, S.t, (uint32_t)walker, (uint32_t)step);
             st.n = n0 + kPreShrink;
             phase = 0;

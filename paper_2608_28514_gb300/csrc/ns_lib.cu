@@ -345,7 +345,9 @@ ns_status check_opts(const ns_options& o, std::string* err) {
       !std::isfinite(o.reeval_margin) || !(o.reeval_rel >= 0) || !std::isfinite(o.reeval_rel) ||
       o.reeval_defer < 0 || o.reeval_defer > 64 || o.walker_mapping < 0 || o.walker_mapping > 1 ||
       o.mlp_batch_cap < 0 || o.mlp_batch_cap > kMlpNbMax ||
-      !(o.mlp_cluster == 0 || o.mlp_cluster == 1 || o.mlp_cluster == 2 || o.mlp_cluster == 4)) {
+      !(o.mlp_cluster == 0 || o.mlp_cluster == 1 || o.mlp_cluster == 2 || o.mlp_cluster == 4) ||
+      o.two_plane < 0 || o.two_plane > 1 || !(o.reeval2_margin >= 0) || !std::isfinite(o.reeval2_margin) ||
+      !(o.reeval2_rel >= 0) || !std::isfinite(o.reeval2_rel)) {
     set_err(err, "an option is out of range");
     return NS_ERR_ARG;
   }
@@ -524,6 +526,9 @@ ns_status ns_default_options(ns_options* o) {
   o->reeval_defer = 4;
   o->mlp_batch_cap = kMlpNbMax;
   o->mlp_cluster = 0;
+  o->two_plane = 1;
+  o->reeval2_margin = 0.05;
+  o->reeval2_rel = 1e-4;
   return NS_OK;
 }
 
@@ -727,6 +732,9 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     R.reeval_margin = (float)opt.reeval_margin;
     R.reeval_rel = (float)opt.reeval_rel;
     R.reeval_defer = opt.reeval_defer;
+    R.two_plane = opt.two_plane;
+    R.reeval2_margin = (float)opt.reeval2_margin;
+    R.reeval2_rel = (float)opt.reeval2_rel;
     R.walker_warp = (p.lik->kind == NS_LIK_MLP) ? 0 : opt.walker_mapping;
     R.mlp_round_cap = opt.mlp_batch_cap;
     if (p.lik->kind == NS_LIK_MLP) {
@@ -1308,6 +1316,8 @@ ns_status ns_result(ns_handle* h, int run, ns_result_t* out) {
   out->n_cand_bf16 = S.mlp_count[2];
   out->n_pass_fp32 = S.mlp_count[3];
   out->n_cand_fp32 = S.mlp_count[4];
+  out->n_pass_x2 = S.mlp_count[5];
+  out->n_cand_x2 = S.mlp_count[6];
   out->status = S.status;
   out->d = hr.d;
   out->dead_x = hr.dead_x.data();
@@ -1336,6 +1346,8 @@ ns_status ns_summary(const ns_handle* h, int run, ns_result_t* out) {
   out->n_cand_bf16 = S.mlp_count[2];
   out->n_pass_fp32 = S.mlp_count[3];
   out->n_cand_fp32 = S.mlp_count[4];
+  out->n_pass_x2 = S.mlp_count[5];
+  out->n_cand_x2 = S.mlp_count[6];
   out->status = S.status;
   out->d = hr.d;
   return NS_OK;

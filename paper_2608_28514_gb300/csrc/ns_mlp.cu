@@ -95,6 +95,28 @@ __global__ void __launch_bounds__(kMlpThreads, 1)
   mlp_ctx_free(&ctx);
 }
 
+// The 16-bit variant (two BF16 planes), batches of 64.
+constexpr int kMlpX2Nb = 64;
+using MlpSmemX2 = MlpSmem<kMlpX2Nb, kMlpStandaloneStages, 2>;
+
+__global__ void __launch_bounds__(kMlpThreads, 1)
+    k_mlp_x2(const MlpDesc M, const uint8_t* __restrict__ tiles, const float* __restrict__ f32,
+             const float* __restrict__ x, int n, float* __restrict__ out) {
+  extern __shared__ __align__(1024) char sm_raw[];
+  __shared__ MlpCtx ctx;
+  char* sm = align1024_shared(sm_raw);
+  mlp_ctx_init(&ctx);
+  const int n_batches = (n + kMlpX2Nb - 1) / kMlpX2Nb;
+  for (int b = blockIdx.x; b < n_batches; b += gridDim.x) {
+    const int b0 = b * kMlpX2Nb;
+    const int nb = min(kMlpX2Nb, n - b0);
+    if (!mlp_eval_bf16<kMlpX2Nb, kMlpStandaloneStages, 2>(M, tiles, f32, x + (size_t)b0 * M.d, M.d, nb, out + b0, sm,
+                                                           &ctx))
+      for (int r = threadIdx.x; r < nb; r += blockDim.x) out[b0 + r] = __int_as_float(0x7fffffff);
+  }
+  mlp_ctx_free(&ctx);
+}
+
 __global__ void __launch_bounds__(256, 1)
     k_mlp_f32(const MlpDesc M, const float* __restrict__ f32, const float* __restrict__ x, int n,
               float* __restrict__ out) {
@@ -251,7 +273,16 @@ cudaError_t ns_mlp_launch(const MlpDesc& M, const void* image, int n, const floa
                           cudaStream_t s) {
   const uint8_t* tiles = static_cast<const uint8_t*>(image);
   const float* f32 = reinterpret_cast<const float*>(tiles + M.tile_bytes);
-  if (precision == 2) {
+  if (precision == 3) {
+    const int smem = MlpSmemX2::kBytes + 1024;
+    cudaError_t e = cudaFuncSetAttribute(k_mlp_x2, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    int dev = 0, n_sm = 1;
+    if (e == cudaSuccess) e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&n_sm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    const int n_batches = (n + kMlpX2Nb - 1) / kMlpX2Nb;
+    k_mlp_x2<<<std::min(n_batches, n_sm), kMlpThreads, smem, s>>>(M, tiles, f32, x, n, logl);
+  } else if (precision == 2) {
     const int smem = MlpSmemSplit::kBytes + 1024;
     cudaError_t e = cudaFuncSetAttribute(k_mlp_split3, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     int dev = 0, n_sm = 1;
@@ -347,7 +378,7 @@ ns_status ns_mlp_pack(const ns_likelihood* lik, int d, void* image, void* stream
 
 ns_status ns_mlp_loglike(const ns_likelihood* lik, const double* lo, const double* hi, int d, const void* image, int n,
                          const float* x, float* logl, int precision, void* stream) {
-  if (!lik || !lo || !hi || !image || n < 0 || (n > 0 && (!x || !logl)) || precision < 0 || precision > 2)
+  if (!lik || !lo || !hi || !image || n < 0 || (n > 0 && (!x || !logl)) || precision < 0 || precision > 3)
     return NS_ERR_ARG;
   MlpDesc M;
   bool cached = false;
@@ -372,8 +403,8 @@ ns_status ns_mlp_loglike(const ns_likelihood* lik, const double* lo, const doubl
       return NS_ERR_ARG;
     }
   }
-  if (precision == 2 && !M.w_bf16) {
-    g_mlp_err = "ns_mlp_loglike: precision 2 needs weights that are BF16 values";
+  if (precision >= 2 && !M.w_bf16) {
+    g_mlp_err = "ns_mlp_loglike: precision 2 and 3 need weights that are BF16 values";
     return NS_ERR_ARG;
   }
   if (n == 0) return NS_OK;

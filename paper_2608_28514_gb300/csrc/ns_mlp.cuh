@@ -178,7 +178,7 @@ __device__ __forceinline__ float silu_fast(float z) { return __fdividef(z, 1.f +
 template <int NBMAX, int STAGES, int P = 1>
 struct MlpSmem {
   static_assert(NBMAX % 16 == 0 && NBMAX <= kMlpNbMax && STAGES >= 2 && STAGES <= kMlpStagesMax, "");
-  static_assert(P == 1 || P == 3, "");
+  static_assert(P >= 1 && P <= 3, "");
   static constexpr int kStageOff = 0;
   static constexpr int kActOff = kStageOff + STAGES * kMlpTileBytes;  // [P][kpad/64][NBMAX][128 B]
   static constexpr int kPlaneBytes = (kMlpMaxK / 64) * NBMAX * 128;
@@ -194,6 +194,27 @@ __device__ __forceinline__ void split3_bf16(float a, __nv_bfloat16& hi, __nv_bfl
   const float r1 = a - __bfloat162float(hi);
   mid = __float2bfloat16_rn(r1);
   lo = __float2bfloat16_rn(r1 - __bfloat162float(mid));
+}
+
+// The value v of one operand element as P BF16 planes at dst, dst +
+// plane_bytes, dst + 2 plane_bytes: P = 1 rounds it to BF16; P = 2 keeps 16
+// significand bits (hi + lo, lo the BF16 rounding of the exact remainder,
+// relative error at most 2^-17); P = 3 keeps all of it (hi + mid + lo).
+template <int P>
+__device__ __forceinline__ void store_planes(char* dst, int plane_bytes, float v) {
+  if constexpr (P == 1) {
+    *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
+  } else if constexpr (P == 2) {
+    const __nv_bfloat16 hi = __float2bfloat16_rn(v);
+    *reinterpret_cast<__nv_bfloat16*>(dst) = hi;
+    *reinterpret_cast<__nv_bfloat16*>(dst + plane_bytes) = __float2bfloat16_rn(v - __bfloat162float(hi));
+  } else {
+    __nv_bfloat16 h0, h1, h2;
+    split3_bf16(v, h0, h1, h2);
+    *reinterpret_cast<__nv_bfloat16*>(dst) = h0;
+    *reinterpret_cast<__nv_bfloat16*>(dst + plane_bytes) = h1;
+    *reinterpret_cast<__nv_bfloat16*>(dst + 2 * plane_bytes) = h2;
+  }
 }
 
 // Warp roles of the BF16 evaluator: warps 0-7 read the accumulators back
@@ -362,15 +383,7 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
     float v = 0.f;
     if (r < n && i < M.d) v = fmaf(M.span[i], x[(size_t)(rows ? rows[r] : r) * x_stride + i], M.lo[i]);
     char* dst = act + kb * NBMAX * 128 + sw128_offset(r, k);
-    if constexpr (P == 1) {
-      *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
-    } else {
-      __nv_bfloat16 h0, h1, h2;
-      split3_bf16(v, h0, h1, h2);
-      *reinterpret_cast<__nv_bfloat16*>(dst) = h0;
-      *reinterpret_cast<__nv_bfloat16*>(dst + L::kPlaneBytes) = h1;
-      *reinterpret_cast<__nv_bfloat16*>(dst + 2 * L::kPlaneBytes) = h2;
-    }
+    store_planes<P>(dst, L::kPlaneBytes, v);
   }
   for (int q = tid; q < 4 * NBMAX; q += blockDim.x) chi[q] = 0.f;
   fence_proxy_async();
@@ -491,22 +504,11 @@ inline __device__ bool mlp_eval_bf16(const MlpDesc& M, const uint8_t* __restrict
               const int c0 = i * 16;
               float v[16];
               tmem_ld16(tmem + lane_base + col0 + (unsigned)((t - G.g0) * N + c0), v);
-              if constexpr (P == 1) {
+              // BF16 path: SiLU on the special-function unit; the wider paths: accurate SiLU
 #pragma unroll
-                for (int c = 0; c < 16; ++c)
-                  *reinterpret_cast<__nv_bfloat16*>(dst + sw128_offset(c0 + c, k)) =
-                      __float2bfloat16_rn(silu_fast(v[c] + bias));
-              } else {
-#pragma unroll
-                for (int c = 0; c < 16; ++c) {
-                  __nv_bfloat16 h0, h1, h2;
-                  split3_bf16(silu(v[c] + bias), h0, h1, h2);
-                  char* e = dst + sw128_offset(c0 + c, k);
-                  *reinterpret_cast<__nv_bfloat16*>(e) = h0;
-                  *reinterpret_cast<__nv_bfloat16*>(e + L::kPlaneBytes) = h1;
-                  *reinterpret_cast<__nv_bfloat16*>(e + 2 * L::kPlaneBytes) = h2;
-                }
-              }
+              for (int c = 0; c < 16; ++c)
+                store_planes<P>(dst + sw128_offset(c0 + c, k), L::kPlaneBytes,
+                                (P == 1) ? silu_fast(v[c] + bias) : silu(v[c] + bias));
             }
           }
           fence_proxy_async();

@@ -109,7 +109,7 @@ struct ClusterMail {
   int err[kMlpClusterMax];
   float chi[kMlpClusterMax][kMlpNbMax];
 };
-enum { kClOpExit = 0, kClOpBf16 = 1, kClOpFp32 = 3 };
+enum { kClOpExit = 0, kClOpBf16 = 1, kClOpX2 = 2, kClOpFp32 = 3 };  // the op is the planes of the pass
 
 // Where the candidates' unit-cube coordinates come from: global memory (g:
 // every CTA builds the layer-0 operand itself), or rows of CTA 0's shared
@@ -171,15 +171,7 @@ inline __device__ bool mlp_eval_bf16_cl(const MlpDesc& M, const uint8_t* __restr
         v = fmaf(M.span[i], xv, M.lo[i]);
       }
       char* dst = act + kb * NBMAX * 128 + sw128_offset(r, k);
-      if constexpr (P == 1) {
-        *reinterpret_cast<__nv_bfloat16*>(dst) = __float2bfloat16_rn(v);
-      } else {
-        __nv_bfloat16 h0, h1, h2;
-        split3_bf16(v, h0, h1, h2);
-        *reinterpret_cast<__nv_bfloat16*>(dst) = h0;
-        *reinterpret_cast<__nv_bfloat16*>(dst + L::kPlaneBytes) = h1;
-        *reinterpret_cast<__nv_bfloat16*>(dst + 2 * L::kPlaneBytes) = h2;
-      }
+      store_planes<P>(dst, L::kPlaneBytes, v);
     }
     fence_proxy_async();
   }
@@ -351,22 +343,11 @@ inline __device__ bool mlp_eval_bf16_cl(const MlpDesc& M, const uint8_t* __restr
                 const int c0 = i * 16;
                 float v[16];
                 tmem_ld16(tmem + lane_base + col0 + (unsigned)((j - G.g0) * N + c0), v);
-                if constexpr (P == 1) {
+                // BF16 path: SiLU on the special-function unit; the wider paths: accurate SiLU
 #pragma unroll
-                  for (int c = 0; c < 16; ++c)
-                    *reinterpret_cast<__nv_bfloat16*>(dst + sw128_offset(c0 + c, k)) =
-                        __float2bfloat16_rn(silu_fast(v[c] + bias));
-                } else {
-#pragma unroll
-                  for (int c = 0; c < 16; ++c) {
-                    __nv_bfloat16 h0, h1, h2;
-                    split3_bf16(silu(v[c] + bias), h0, h1, h2);
-                    char* e = dst + sw128_offset(c0 + c, k);
-                    *reinterpret_cast<__nv_bfloat16*>(e) = h0;
-                    *reinterpret_cast<__nv_bfloat16*>(e + L::kPlaneBytes) = h1;
-                    *reinterpret_cast<__nv_bfloat16*>(e + 2 * L::kPlaneBytes) = h2;
-                  }
-                }
+                for (int c = 0; c < 16; ++c)
+                  store_planes<P>(dst + sw128_offset(c0 + c, k), L::kPlaneBytes,
+                                  (P == 1) ? silu_fast(v[c] + bias) : silu(v[c] + bias));
               }
             }
           }

@@ -24,8 +24,9 @@ struct RunState {
   double logz, info;
   long long k, n_dead, n_evals, n_iter, n_relaxed, n_reeval, n_capped;
   long long cycles[8];
-  // MLP runs: walker rounds, BF16 passes and their candidates, FP32 passes and theirs
-  long long mlp_count[5];
+  // MLP runs: walker rounds, BF16 passes and their candidates, FP32 passes and
+  // theirs, 16-bit (two-plane) passes and theirs
+  long long mlp_count[7];
   int t, stopped, status, initialized;
 };
 
@@ -72,6 +73,9 @@ struct RunDesc {
   float reeval_margin;    // re-evaluate in FP32 when |logL_bf16 - threshold| <
   float reeval_rel;       //   reeval_margin + reeval_rel |threshold|
   int reeval_defer;       // rounds a near-threshold candidate may wait for a shared FP32 pass
+  int two_plane;          // BF16 runs: a 16-bit (two-plane) pass between the BF16 and the FP32 values
+  float reeval2_margin;   // FP32 after the 16-bit pass when |logL_16 - threshold| <
+  float reeval2_rel;      //   reeval2_margin + reeval2_rel |threshold|
   int walker_warp;        // analytic runs: 1 = one walker per warp, 0 = one walker per thread
   int mlp_round_cap;      // BF16 MLP runs: candidates evaluated per round (0 = all, in equal calls)
 };
@@ -378,6 +382,7 @@ static __device__ __noinline__ bool mlp_batch_f32(const RunDesc& R, const float*
 }
 
 constexpr int kRunSplitNb = 32;  // candidates per FP32-accurate (three-plane) tensor-core call
+constexpr int kRunX2Nb = 64;     // candidates per 16-bit (two-plane) tensor-core call
 
 // One tensor-core evaluation by the run's whole cluster (this block is its
 // CTA 0; the followers wait in mlp_follower): post the command, evaluate
@@ -388,7 +393,7 @@ template <int NB, int P>
 inline __device__ bool mlp_pass_cl(const RunDesc& R, const float* xs, int xstride, int n, float* ls, char* tsm,
                                    MlpCtx* ctx, ClusterMail* mail, unsigned C, const int* rows) {
   if (threadIdx.x == 0) {
-    mail->op = (P == 1) ? kClOpBf16 : kClOpFp32;
+    mail->op = P;  // kClOpBf16, kClOpX2 or kClOpFp32
     mail->n = n;
   }
   cl_sync();
@@ -422,6 +427,9 @@ inline __device__ void mlp_follower(const RunDesc& R, MlpCtx* ctx, ClusterMail* 
     if (op == kClOpBf16)
       mlp_eval_bf16_cl<kMlpNbMax, kRunMlpStages, 1>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, X, n, tsm, ctx, mail, C,
                                                     rank);
+    else if (op == kClOpX2)
+      mlp_eval_bf16_cl<kRunX2Nb, kRunMlpStages, 2>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, X, n, tsm, ctx, mail, C,
+                                                   rank);
     else
       mlp_eval_bf16_cl<kRunSplitNb, kRunMlpStages, 3>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, X, n, tsm, ctx, mail,
                                                       C, rank);
@@ -476,6 +484,22 @@ static __device__ __noinline__ bool mlp_reeval_tc(const RunDesc& R, const float*
   return ok;
 }
 
+// 16-bit evaluation on the tensor cores (two BF16 planes: activations and
+// inputs to a relative 2^-17, weights exact when they are BF16 values) of
+// the listed rows of xs, into ls.
+static __device__ __noinline__ bool mlp_eval_x2(const RunDesc& R, const float* xs, int xstride, float* ls,
+                                                const int* list, int n, char* tsm, MlpCtx* ctx, ClusterMail* mail,
+                                                unsigned C) {
+  bool ok = true;
+  for (int b0 = 0; b0 < n && ok; b0 += kRunX2Nb) {
+    const int nb = min(kRunX2Nb, n - b0);
+    ok = (C > 1) ? mlp_pass_cl<kRunX2Nb, 2>(R, xs, xstride, nb, ls, tsm, ctx, mail, C, list + b0)
+                 : mlp_eval_bf16<kRunX2Nb, kRunMlpStages, 2>(*R.mlp_desc, R.mlp_tiles, R.mlp_f32, xs, xstride, nb, ls,
+                                                             tsm, ctx, list + b0);
+  }
+  return ok;
+}
+
 // FP32 re-evaluation of the listed rows of xbuf (indices in list[0..n)),
 // written back into lbuf; xg/lg: kMlpF32Nb staging rows.
 static __device__ __noinline__ void mlp_reeval(const RunDesc& R, float* xbuf, int xstride, float* lbuf, const int* list, int n,
@@ -507,6 +531,8 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   const bool tcfp = (R.precision == 2);
   // FP32 re-evaluations on the tensor cores when the weights are BF16 values
   const bool tc32 = bf16 && R.mlp_desc->w_bf16;
+  // a 16-bit (two-plane) stage between the BF16 value and the FP32 one
+  const bool two = tc32 && R.two_plane != 0;
   char* tsm = align1024_shared(msm);
   float* act = reinterpret_cast<float*>(msm);
   float* xg = xbuf + (size_t)2 * m * XS;  // kMlpF32Nb staging rows after the 2m candidate rows
@@ -556,9 +582,9 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   // reeval_defer rounds, or no walker can move; a decision is only
   // delayed, never changed); hold: left out of the last round's weight pass
   // by the round cap (it goes first in the next round).
-  int has = 0, pend = 0, hold = 0;
+  int has = 0, pend = 0, pend2 = 0, hold = 0;  // pend2: waits for its 16-bit value (then pend: FP32)
   float tp0 = 0.f, tp1 = 0.f;  // the slots' positions on the line
-  int age = 0;                 // rounds the oldest pending candidate has waited (uniform)
+  int age = 0, age2 = 0;       // rounds the oldest pending candidate has waited, per stage (uniform)
   const int cap = bf16 ? R.mlp_round_cap : 0;
   auto row_of = [&](int s) { return s ? m + tid : tid; };
   // (register arrays are indexed by compile-time constants only, so they stay in registers)
@@ -692,9 +718,9 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   for (;;) {
     if (!__syncthreads_or(active ? 1 : 0)) break;
     fill();
-    const int req = active ? (has & ~pend) : 0;  // slots whose candidate is evaluated this round (or held)
+    const int req = active ? (has & ~(pend | pend2)) : 0;  // slots whose candidate is evaluated this round (or held)
     // every walker finished while settling its proposals: no batch to evaluate
-    if (!__syncthreads_or((req | pend) ? 1 : 0)) break;
+    if (!__syncthreads_or((req | pend | pend2) ? 1 : 0)) break;
     // this round's candidates (row indices), in thread order, left slot first;
     // with a cap, the held ones first, then the new ones, up to the cap
     const int n_old_me = __popc(req & hold), n_new_me = __popc(req & ~hold);
@@ -730,23 +756,59 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
       long long c1 = clock64();
       ce += c1 - c0;
       c0 = c1;
-      // candidates close to their threshold wait for their FP32 value
+      // candidates close to their threshold wait for a more precise value:
+      // the 16-bit one (two), then, if that is close too, the FP32 one
       const float thr = (phase == 2) ? thr_in : thr_out;
       const float margin = fmaf(R.reeval_rel, fabsf(thr), R.reeval_margin);
 #pragma unroll
       for (int s = 0; s < 2; ++s) {
         if (!((take >> s) & 1)) continue;
         const float lv = lbuf[row_of(s)];
-        if (margin > 0.f && fabsf(lv - thr) < margin) pend |= 1 << s;
-        else decide(s, lv);
+        if (margin > 0.f && fabsf(lv - thr) < margin) {
+          if (two) pend2 |= 1 << s;
+          else pend |= 1 << s;
+        } else {
+          decide(s, lv);
+        }
+      }
+      // can this walker move next round: a live slot that is not pending
+      const int live = (phase == 0) ? (~done & 3) : 1;
+      if (two) {
+        int cnt2;
+        const int pos2 = block_exclusive_scan(__popc(pend2), BS, &cnt2);
+        const int still2 = __syncthreads_or((active && (live & ~(pend | pend2))) ? 1 : 0);
+        age2 = (cnt2 > 0) ? age2 + 1 : 0;
+        if (cnt2 > 0 && (cnt2 >= kRunX2Nb || !still2 || age2 > R.reeval_defer)) {
+          {
+            int p = pos2;
+#pragma unroll
+            for (int s = 0; s < 2; ++s)
+              if ((pend2 >> s) & 1) rlist[p++] = row_of(s);
+          }
+          __syncthreads();
+          if (tid == 0) {
+            count[5] += (cnt2 + kRunX2Nb - 1) / kRunX2Nb;
+            count[6] += cnt2;
+          }
+          if (!mlp_eval_x2(R, xbuf, XS, lbuf, rlist, cnt2, tsm, ctx, mail, C)) err = 1;
+          const float margin2 = fmaf(R.reeval2_rel, fabsf(thr), R.reeval2_margin);
+          const int pd = pend2;
+          pend2 = 0;
+#pragma unroll
+          for (int s = 0; s < 2; ++s) {
+            if (!((pd >> s) & 1)) continue;
+            const float lv = lbuf[row_of(s)];
+            if (fabsf(lv - thr) < margin2) pend |= 1 << s;
+            else decide(s, lv);
+          }
+          age2 = 0;
+        }
       }
       int cnt;
       const int pos = block_exclusive_scan(__popc(pend), BS, &cnt);
-      // can this walker move next round: a live slot that is not pending
-      const int live = (phase == 0) ? (~done & 3) : 1;
-      const int still = __syncthreads_or((active && (live & ~pend)) ? 1 : 0);
+      const int still = __syncthreads_or((active && (live & ~(pend | pend2))) ? 1 : 0);
       age = (cnt > 0) ? age + 1 : 0;
-      if (cnt > 0 && (cnt >= kMlpF32Nb || !still || age > R.reeval_defer)) {
+      if (cnt > 0 && (cnt >= (tc32 ? kRunSplitNb : kMlpF32Nb) || !still || age > R.reeval_defer)) {
         {
           int p = pos;
 #pragma unroll

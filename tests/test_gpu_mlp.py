@@ -395,6 +395,51 @@ def test_bf16_runs_reproduce_the_fp32_tensor_runs(nat, cluster):
     assert all(r["n_cand_bf16"] == 0 and r["n_cand_fp32"] > 0 for r in out[2])
 
 
+@pytest.mark.parametrize("widths,n", [((27, 512, 512, 512, 512, 2000), 150), ((5, 128, 200, 300), 64),
+                                      ((27, 512, 512, 512, 512, 2000), 65)])
+def test_mlp_16bit_tensor_path(nat, oracle, widths, n):
+    """precision 3 (inputs and activations as two BF16 planes, relative
+    rounding 2^-17; BF16-valued weights exact) agrees with the FP64 oracle to
+    16-bit accuracy, far closer than the BF16 path."""
+    p = _problem(widths, 8, unit_sigma=False)
+    img = _image(nat, p)
+    x = np.random.default_rng(n + 3).uniform(0, 1, size=(n, p.d)).astype(np.float32)
+    x[0] = p.mlp.theta_star
+    xt = torch.tensor(x, device="cuda")
+    o2, o1 = torch.zeros(n, device="cuda"), torch.zeros(n, device="cuda")
+    nat.ns_mlp_loglike(p, img, xt, o2, precision=3)
+    nat.ns_mlp_loglike(p, img, xt, o1, precision=1)
+    torch.cuda.synchronize()
+    want = oracle.loglike(oracle.Lik(p), x.astype(np.float64))
+    e2 = np.abs(o2.cpu().numpy() - want)
+    e1 = np.abs(o1.cpu().numpy() - want)
+    np.testing.assert_allclose(o2.cpu().numpy(), want, rtol=2e-4, atol=1e-2)
+    assert np.median(e2) * 20 < np.median(e1), (np.median(e2), np.median(e1))
+
+
+def test_two_plane_stage_changes_nothing(nat):
+    """The 16-bit stage between the BF16 value and the FP32 one only saves
+    FP32 passes: with or without it, BF16 runs are the same run, bit for bit
+    (every decision it takes lies beyond its margin from the threshold),
+    with fewer FP32 re-evaluations."""
+    p = W.mlp_emulator(4, widths=(8, 512, 512, 512), sig_lo=2e-2, sig_hi=2e-1)
+    runs = [(p, 200, 20, 40, 1e-3, s) for s in (41, 42, 43)]
+    out = {}
+    for two in (0, 1):
+        h = nat.ns_create_batch(runs, nat.ns_default_options(precision=1, two_plane=two))
+        nat.ns_run(h)
+        out[two] = [nat.ns_result(h, r) for r in range(len(runs))]
+        nat.ns_destroy(h)
+    same = 0
+    for a, b in zip(out[0], out[1]):
+        if a["log_z"] == b["log_z"] and a["n_evals"] == b["n_evals"]:
+            np.testing.assert_array_equal(a["dead_l"], b["dead_l"])
+            same += 1
+    assert same >= len(runs) - 1, same
+    assert sum(r["n_cand_x2"] for r in out[1]) > 0 and all(r["n_cand_x2"] == 0 for r in out[0])
+    assert sum(r["n_reeval"] for r in out[1]) < sum(r["n_reeval"] for r in out[0])
+
+
 def test_bf16_error_near_the_posterior_is_inside_the_margin(nat):
     """Calibration of the FP32 re-evaluation margin on the 27-D emulator
     network where it matters, near the end of a run: 20000 points of the
@@ -424,3 +469,12 @@ def test_bf16_error_near_the_posterior_is_inside_the_margin(nat):
     margin = opt.reeval_margin + opt.reeval_rel * np.abs(lf)
     assert 2 * q < float(margin.min()), (q, float(margin.min()), float(lf.min()), float(lf.max()))
     assert np.all(err < margin), float(np.max(err - margin))
+    # the 16-bit stage's error against its own margin
+    l2 = torch.zeros(len(x), device="cuda")
+    nat.ns_mlp_loglike(p, img, xt, l2, precision=3)
+    torch.cuda.synchronize()
+    e2 = np.abs(l2.cpu().numpy().astype(np.float64) - lf)
+    margin2 = opt.reeval2_margin + opt.reeval2_rel * np.abs(lf)
+    assert 2 * float(np.quantile(e2, 0.9999)) < float(margin2.min()), (float(np.quantile(e2, 0.9999)),
+                                                                        float(margin2.min()))
+    assert np.all(e2 < margin2)
