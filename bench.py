@@ -247,9 +247,11 @@ def emulator_compare(nat, W, torch, n_sm, peaks, cpu_cores=0):
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     runs = [(p, EMU_N, EMU_M, EMU_STEPS, 1e-3, s) for s in range(1, n_sm + 1)]
     out = {"workload": f"27-D emulator MLP 27-512x4-2000 (SiLU, BF16-exact weights), N_live={EMU_N}, m={EMU_M}, "
-                       f"{EMU_STEPS} slice steps, {n_sm} runs (one per SM), first {EMU_ITERS} iterations of each",
-           "reeval": "FP32 re-evaluation when |logL - threshold| < 2 + 4e-3 |threshold| (library defaults)"}
-    for name, prec in (("bf16", 1), ("fp32", 0)):
+                       f"{EMU_STEPS} slice steps, {n_sm} runs (one per SM), first {EMU_ITERS} iterations of each "
+                       "(early iterations: few candidates near the threshold; whole runs in whole_run_record)",
+           "reeval": "16-bit stage when |logL - threshold| < 2 + 4e-3 |threshold|, FP32 when the 16-bit value is "
+                     "within 0.05 + 1e-4 |threshold| (library defaults)"}
+    for name, prec in (("bf16", 1), ("fp32_tc", 2), ("fp32", 0)):
         opt = nat.ns_default_options(precision=prec, max_iter=EMU_ITERS, chunk_iters=EMU_ITERS)
         h = nat.ns_create_batch(runs, opt)
         nat.ns_run(h, check=False)  # warm-up
@@ -265,7 +267,7 @@ def emulator_compare(nat, W, torch, n_sm, peaks, cpu_cores=0):
         tf = ev * EMU_FLOP / (st["run_ms"] / 1e3) / 1e12
         # the useful MLP work of the runs against the peak of the pipe the path computes on: the
         # measured sustained BF16 tensor rate (launches of ~0.3 s), or the FP32 ALU rate
-        if prec == 1:
+        if prec in (1, 2):
             pk = (peaks or {}).get("bf16_tflops_sustained") or (peaks or {}).get("bf16_tflops")
             basis = "measured bf16 (sustained)" if pk else None
         else:
@@ -275,6 +277,19 @@ def emulator_compare(nat, W, torch, n_sm, peaks, cpu_cores=0):
                      "effective_tflops": tf, "peak_tflops": pk, "frac_of_peak": (tf / pk) if pk else None,
                      "peak_basis": basis}
     out["bf16_over_fp32"] = out["bf16"]["evals_per_s"] / out["fp32"]["evals_per_s"]
+    out["bf16_over_fp32_tc"] = out["bf16"]["evals_per_s"] / out["fp32_tc"]["evals_per_s"]
+    # whole runs to the stopping rule take minutes per path: their numbers come
+    # from the study record (bench.py --emulator-convergence), while the kernel
+    # sources still match the build that wrote it
+    rec = os.path.join(ROOT, "profiles", "emulator_runs_N1500.json")
+    out["whole_run_record"] = None
+    if os.path.exists(rec):
+        try:
+            rj = json.load(open(rec))
+            if rj.get("csrc_sha256_16") == csrc_hash():
+                out["whole_run_record"] = rj.get("summary")
+        except (ValueError, KeyError):
+            pass
     out["cpu_baseline"] = emulator_cpu_baseline(cpu_cores) if cpu_cores > 0 else None
     # the tensor-core evaluator alone on a large batch (8 calls of 128 candidates per SM)
     nb = nat.ns_mlp_image_bytes(p)
