@@ -478,3 +478,30 @@ def test_bf16_error_near_the_posterior_is_inside_the_margin(nat):
     assert 2 * float(np.quantile(e2, 0.9999)) < float(margin2.min()), (float(np.quantile(e2, 0.9999)),
                                                                         float(margin2.min()))
     assert np.all(e2 < margin2)
+
+
+def test_cluster_option_validation(nat):
+    """mlp_cluster must divide every layer's 128-row tile count and needs a
+    tensor-core path; the automatic choice takes 4 CTAs per run while they fit
+    the SMs and falls back to one CTA per run."""
+    small = _small_emulator()          # one tile row per layer: no split
+    big = W.mlp_emulator(1)            # 4 / 4 / 4 / 4 / 16 tile rows
+    bad = [(small, dict(precision=1, mlp_cluster=2)), (big, dict(precision=0, mlp_cluster=4)),
+           (big, dict(precision=1, mlp_cluster=3))]
+    for p, kw in bad:
+        with pytest.raises(nat.NSError) as ei:
+            nat.ns_create_batch([(p, 200, 20, 10, 1e-2, 1)], nat.ns_default_options(**kw))
+        assert ei.value.status == nat.NS_ERR_ARG
+    # precision 2 needs BF16-valued weights
+    q = _small_emulator()
+    q.mlp.weights = [w * np.float32(1.0 + 1e-3) for w in q.mlp.weights]
+    with pytest.raises(nat.NSError):
+        nat.ns_create_batch([(q, 200, 20, 10, 1e-2, 1)], nat.ns_default_options(precision=2))
+    # automatic: a small batch runs, one CTA per run for a network that cannot split
+    for p in (small, big):
+        h = nat.ns_create_batch([(p, 200, 20, 10, 1e-2, 1)],
+                                nat.ns_default_options(precision=1, max_iter=2, chunk_iters=2))
+        nat.ns_run(h, check=False)
+        r = nat.ns_summary(h, 0)
+        nat.ns_destroy(h)
+        assert r["n_iter"] == 2 and r["n_cand_bf16"] > 0
