@@ -136,8 +136,6 @@ typedef struct {
                            * |threshold| of its threshold (1, default), or goes to FP32 at once (0) */
     double reeval2_margin; /* (0.05) */
     double reeval2_rel;    /* (1e-4) */
-    int reeval2_defer;     /* rounds a candidate may wait for its 16-bit value so that several share a pass,
-                            * 0..64 (0, default: the round that needs it runs the pass); results do not depend on it */
 } ns_options;
 
 /* One run of a batch. */

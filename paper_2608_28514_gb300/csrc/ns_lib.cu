@@ -347,7 +347,7 @@ ns_status check_opts(const ns_options& o, std::string* err) {
       o.mlp_batch_cap < 0 || o.mlp_batch_cap > kMlpNbMax ||
       !(o.mlp_cluster == 0 || o.mlp_cluster == 1 || o.mlp_cluster == 2 || o.mlp_cluster == 4) ||
       o.two_plane < 0 || o.two_plane > 1 || !(o.reeval2_margin >= 0) || !std::isfinite(o.reeval2_margin) ||
-      !(o.reeval2_rel >= 0) || !std::isfinite(o.reeval2_rel) || o.reeval2_defer < 0 || o.reeval2_defer > 64) {
+      !(o.reeval2_rel >= 0) || !std::isfinite(o.reeval2_rel)) {
     set_err(err, "an option is out of range");
     return NS_ERR_ARG;
   }
@@ -529,7 +529,6 @@ ns_status ns_default_options(ns_options* o) {
   o->two_plane = 1;
   o->reeval2_margin = 0.05;
   o->reeval2_rel = 1e-4;
-  o->reeval2_defer = 0;
   return NS_OK;
 }
 
@@ -736,7 +735,6 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     R.two_plane = opt.two_plane;
     R.reeval2_margin = (float)opt.reeval2_margin;
     R.reeval2_rel = (float)opt.reeval2_rel;
-    R.reeval2_defer = opt.reeval2_defer;
     R.walker_warp = (p.lik->kind == NS_LIK_MLP) ? 0 : opt.walker_mapping;
     R.mlp_round_cap = opt.mlp_batch_cap;
     if (p.lik->kind == NS_LIK_MLP) {

@@ -76,7 +76,6 @@ struct RunDesc {
   int two_plane;          // BF16 runs: a 16-bit (two-plane) pass between the BF16 and the FP32 values
   float reeval2_margin;   // FP32 after the 16-bit pass when |logL_16 - threshold| <
   float reeval2_rel;      //   reeval2_margin + reeval2_rel |threshold|
-  int reeval2_defer;      // rounds a candidate may wait for a shared 16-bit pass
   int walker_warp;        // analytic runs: 1 = one walker per warp, 0 = one walker per thread
   int mlp_round_cap;      // BF16 MLP runs: candidates evaluated per round (0 = all, in equal calls)
 };
@@ -779,7 +778,7 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
         const int pos2 = block_exclusive_scan(__popc(pend2), BS, &cnt2);
         const int still2 = __syncthreads_or((active && (live & ~(pend | pend2))) ? 1 : 0);
         age2 = (cnt2 > 0) ? age2 + 1 : 0;
-        if (cnt2 > 0 && (cnt2 >= kRunX2Nb || !still2 || age2 > R.reeval2_defer)) {
+        if (cnt2 > 0 && (cnt2 >= kRunX2Nb || !still2 || age2 > R.reeval_defer)) {
           {
             int p = pos2;
 #pragma unroll

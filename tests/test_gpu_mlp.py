@@ -213,14 +213,12 @@ def test_full_emulator_runs_a_few_iterations(nat):
 
 def test_deferred_reevaluation_changes_nothing(nat):
     """Near-threshold candidates re-evaluated at once (reeval_defer = 0) or
-    batched over up to 4 and 16 rounds (and their 16-bit stage over up to 0,
-    2 and 8): the same runs, bit for bit."""
+    batched over up to 4 and 16 rounds: the same runs, bit for bit."""
     p = _small_emulator(5)
     runs = [(p, 200, 20, 20, 1e-2, s) for s in (3, 4)]
     out = {}
     for defer in (0, 4, 16):
-        o = nat.ns_default_options(precision=1, reeval_margin=5.0, reeval_defer=defer, reeval2_defer=defer // 2,
-                                   max_iter=40, chunk_iters=40)
+        o = nat.ns_default_options(precision=1, reeval_margin=5.0, reeval_defer=defer, max_iter=40, chunk_iters=40)
         h = nat.ns_create_batch(runs, o)
         nat.ns_run(h, check=False)
         out[defer] = [nat.ns_result(h, r) for r in range(len(runs))]
