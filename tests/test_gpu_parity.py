@@ -462,8 +462,9 @@ def test_gauss2d_whole_runs_50_seeds(nat):
 @pytest.mark.parametrize("m", [1, 10, 50, 100])
 def test_corr_gauss10_batched_runs(nat, m):
     """The 10-D correlated Gaussian (N = 1000, 50 slice steps) at every batch
-    size of the workload: each run within 4 sigma of the closed form, the
-    dead sequence non-decreasing."""
+    size of the workload: each run within 4 of its reported errors of the
+    closed form, the dead sequence non-decreasing (the 50-seed statistic is
+    in test_gpu_whole_run_parity.py)."""
     n_seeds = 8 if m > 1 else 2
     probs = [W.corr_gauss10(s) for s in range(1, n_seeds + 1)]
     h = nat.ns_create_batch([(p, 1000, m, 50, 1e-3, 100 + s) for s, p in enumerate(probs)])
@@ -474,7 +475,7 @@ def test_corr_gauss10_batched_runs(nat, m):
         assert res["status"] == 0
         truth = A.logz(p)
         dz.append((res["log_z"] - truth) / res["log_z_err"])
-        assert abs(res["log_z"] - truth) < 4 * res["log_z_err"] + 0.05, (r, res["log_z"], truth)
+        assert abs(res["log_z"] - truth) < 4 * res["log_z_err"], (r, res["log_z"], truth)
         nd = res["n_iter"] * m
         assert np.all(np.diff(res["dead_l"][:nd]) >= 0)
     nat.ns_destroy(h)
@@ -507,15 +508,21 @@ def test_headline_config_matches_oracle_in_distribution(nat, oracle):
 
 
 def test_rosenbrock_and_mixture_runs(nat):
+    """Single runs of the configuration-3 shapes: their invariants (status,
+    dead sequence non-decreasing, weights summing to Z).  Their accuracy is
+    tested in distribution, 50 seeds against the FP64 oracle, in
+    test_gpu_whole_run_parity.py (the 10-D Rosenbrock's reported error
+    understates its scatter, so a single-run bound would be arbitrary)."""
     cases = [(W.rosenbrock(2), 1000, 50, 10), (W.rosenbrock(10), 1000, 50, 50), (W.mixture4_d5(1), 2000, 200, 25)]
     h = nat.ns_create_batch([(p, N, m, ns, 1e-3, 7) for p, N, m, ns in cases])
     nat.ns_run(h)
     for r, (p, N, m, ns) in enumerate(cases):
         res = nat.ns_result(h, r)
-        truth = A.logz(p)
-        assert res["status"] == 0
-        # single clusters on multimodal / curved targets: loose bound
-        assert abs(res["log_z"] - truth) < 6 * res["log_z_err"] + 0.3, (p.name, res["log_z"], truth)
+        assert res["status"] == 0 and np.isfinite(res["log_z"]) and res["log_z_err"] > 0
+        nd = res["n_iter"] * m
+        assert np.all(np.diff(res["dead_l"][:nd]) >= 0)
+        w = res["dead_logw"]
+        assert abs(np.log(np.sum(np.exp(w - w.max()))) + w.max() - res["log_z"]) < 1e-9
     nat.ns_destroy(h)
 
 
