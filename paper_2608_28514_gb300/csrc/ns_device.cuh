@@ -588,9 +588,10 @@ __device__ __forceinline__ void draw_row(const SliceCfg& S, int walker, int s, c
 // chol_of(i): walker i's cluster factor.  Called by every thread; ends with a
 // block barrier.
 template <int DMAX, typename CholOf>
-__device__ __forceinline__ void draw_directions_block(const SliceCfg& S, int w0, int w1, CholOf chol_of,
+__device__ __forceinline__ void draw_directions_block(const SliceCfg& S_ref, int w0, int w1, CholOf chol_of,
                                                       float* __restrict__ dirs) {
   constexpr int RW = dir_row(DMAX);
+  const SliceCfg S = S_ref;  // in registers across the rows' stores
   const int rows = (w1 - w0) * S.n_steps;
   for (int q = threadIdx.x; q < rows; q += blockDim.x) {
     const int i = w0 + q / S.n_steps, s = q - (i - w0) * S.n_steps;
@@ -644,13 +645,18 @@ __device__ __forceinline__ void take_row(const float* slot, float (&v)[DMAX], fl
 // All lanes of a warp must call it.  dirs: this walker's table from
 // draw_directions_block; slot: dir_row(DMAX) floats of shared memory (16-byte
 // aligned) private to this walker, used to prefetch the next step's row.
+// The step configuration is copied into registers first: read through the
+// reference, every field would be loaded again after each store the loop
+// makes (the history), which cost 14 % of the 10-D run kernel's time.
 template <int DMAX>
 inline __device__ void slice_walker(const LikParams& P, const SliceCfg& S, int walker, bool active,
                                     const float* __restrict__ x0, int x0_stride, float l0,
                                     const float* __restrict__ dirs, float* slot, float thr_out, float thr_in,
                                     const WalkerOut& O, long long& evals_out, int& flags_out) {
   constexpr int RW = dir_row(DMAX);
-  const int d = S.d;
+  const int d = S.d, n_steps = S.n_steps, e_max = S.e_max, s_max = S.s_max, t_max = S.t_max;
+  const float width = S.width;
+  const uint32_t k0 = S.k0, k1 = S.k1, t = S.t;
   const uint32_t n0 = shrink_draw0(d);
   float x[DMAX], v[DMAX];
   float pre[kPreShrink];
@@ -666,17 +672,14 @@ inline __device__ void slice_walker(const LikParams& P, const SliceCfg& S, int w
   int step = 0, phase = 0, nexp = 0, nsh = 0, hlen = 0, flags = 0;
   long long evals = 0;
   float a = 0.f, b = 0.f;
-  Stream st;
-  st.init(S.k0, S.k1, S.t, (uint32_t)walker, 0u);
-  st.n = n0 + kPreShrink;
-  if (S.n_steps <= 0) active = false;
+  if (n_steps <= 0) active = false;
   if (active) {
     prefetch_row<DMAX>(slot, dirs);
     float r;
     take_row<DMAX>(slot, v, r, pre);
-    a = -r * S.width;
-    b = (1.f - r) * S.width;
-    if (S.n_steps > 1) prefetch_row<DMAX>(slot, dirs + RW);
+    a = -r * width;
+    b = (1.f - r) * width;
+    if (n_steps > 1) prefetch_row<DMAX>(slot, dirs + RW);
   }
   while (__any_sync(kFull, active)) {
     if (active) {
@@ -688,8 +691,8 @@ inline __device__ void slice_walker(const LikParams& P, const SliceCfg& S, int w
 #pragma unroll
           for (int j = 1; j < kPreShrink; ++j)
             if (nsh == j) uu = pre[j];
-        } else {
-          uu = u24(st.next());
+        } else {  // later shrinks (rare): straight from the step's stream
+          uu = u24(draw_at(k0, k1, t, (uint32_t)walker, (uint32_t)step, n0 + (uint32_t)nsh));
         }
         tp = fmaf(uu, b - a, a);
       }
@@ -706,21 +709,21 @@ inline __device__ void slice_walker(const LikParams& P, const SliceCfg& S, int w
       const bool ok = in && (lp > ((phase == 2) ? thr_in : thr_out));
       if (phase < 2) {
         // expansion: predicated updates, no branches
-        const bool expand = ok && (nexp < S.e_max);
-        a = (expand && phase == 0) ? a - S.width : a;
-        b = (expand && phase == 1) ? b + S.width : b;
+        const bool expand = ok && (nexp < e_max);
+        a = (expand && phase == 0) ? a - width : a;
+        b = (expand && phase == 1) ? b + width : b;
         flags |= (ok && !expand) ? 1 : 0;
         nexp = expand ? nexp + 1 : 0;
         phase = expand ? phase : phase + 1;
       } else {
-        if (step == S.n_steps - 1) {
+        if (step == n_steps - 1) {
           int hs = -1;
-          if (nsh < S.t_max - 1) {
+          if (nsh < t_max - 1) {
             hs = nsh;
             hlen = nsh + 1;
           } else if (ok) {
-            hs = S.t_max - 1;
-            hlen = S.t_max;
+            hs = t_max - 1;
+            hlen = t_max;
           }
           if (hs >= 0) {
             float u[DMAX];
@@ -741,21 +744,19 @@ inline __device__ void slice_walker(const LikParams& P, const SliceCfg& S, int w
         } else {
           if (tp < 0.f) a = tp;
           else b = tp;
-          if (++nsh >= S.s_max) {
+          if (++nsh >= s_max) {
             flags |= 2;
             advance = true;
           }
         }
         if (advance) {
           ++step;
-          if (step < S.n_steps) {
+          if (step < n_steps) {
             float r;
             take_row<DMAX>(slot, v, r, pre);
-            a = -r * S.width;
-            b = (1.f - r) * S.width;
-            if (step + 1 < S.n_steps) prefetch_row<DMAX>(slot, dirs + (size_t)(step + 1) * RW);
-            st.init(S.k0, S.k1, S.t, (uint32_t)walker, (uint32_t)step);
-            st.n = n0 + kPreShrink;
+            a = -r * width;
+            b = (1.f - r) * width;
+            if (step + 1 < n_steps) prefetch_row<DMAX>(slot, dirs + (size_t)(step + 1) * RW);
             phase = 0;
             nsh = 0;
             nexp = 0;
@@ -901,6 +902,9 @@ __device__ void slice_walker_warp(const LikParams& P, const LaneLik<DMAX>& Q, co
                                   long long& evals_out, int& flags_out) {
   constexpr int RW = dir_row(DMAX);
   const int lane = threadIdx.x & 31, d = S.d;
+  const int n_steps = S.n_steps, e_max = S.e_max, s_max = S.s_max, t_max = S.t_max;  // in registers
+  const float width = S.width;
+  const uint32_t k0 = S.k0, k1 = S.k1, t = S.t;
   const bool mine = lane < d;
   const uint32_t n0 = shrink_draw0(d);
   float x = mine ? x0[(size_t)lane * x0_stride] : 0.f;
@@ -908,7 +912,6 @@ __device__ void slice_walker_warp(const LikParams& P, const LaneLik<DMAX>& Q, co
   int step = 0, phase = 0, nexp = 0, nsh = 0, hlen = 0, flags = 0;
   long long evals = 0;
   float a = 0.f, b = 0.f, v = 0.f, pre0 = 0.f, pre1 = 0.f, pre2 = 0.f;
-  Stream st;
   auto load_step = [&](int s) {
     const float* row = dirs + (size_t)s * RW;
     v = (lane < DMAX) ? row[lane] : 0.f;
@@ -916,16 +919,18 @@ __device__ void slice_walker_warp(const LikParams& P, const LaneLik<DMAX>& Q, co
     pre0 = row[DMAX + 1];
     pre1 = row[DMAX + 2];
     pre2 = row[DMAX + 3];
-    a = -r * S.width;
-    b = (1.f - r) * S.width;
-    st.init(S.k0, S.k1, S.t, (uint32_t)walker, (uint32_t)s);
-    st.n = n0 + kPreShrink;
+    a = -r * width;
+    b = (1.f - r) * width;
   };
-  if (S.n_steps > 0) load_step(0);
-  while (step < S.n_steps) {
+  if (n_steps > 0) load_step(0);
+  while (step < n_steps) {
     float tp = (phase == 0) ? a : b;
     if (phase == 2) {
-      const float uu = nsh == 0 ? pre0 : (nsh == 1 ? pre1 : (nsh == 2 ? pre2 : u24(st.next())));
+      const float uu =
+          nsh == 0 ? pre0
+                   : (nsh == 1 ? pre1
+                               : (nsh == 2 ? pre2 : u24(draw_at(k0, k1, t, (uint32_t)walker, (uint32_t)step,
+                                                                n0 + (uint32_t)nsh))));
       tp = fmaf(uu, b - a, a);
     }
     const float u = fmaf(tp, v, x);
@@ -937,22 +942,22 @@ __device__ void slice_walker_warp(const LikParams& P, const LaneLik<DMAX>& Q, co
     }
     const bool ok = in && (lp > ((phase == 2) ? thr_in : thr_out));
     if (phase < 2) {
-      const bool expand = ok && (nexp < S.e_max);
-      a = (expand && phase == 0) ? a - S.width : a;
-      b = (expand && phase == 1) ? b + S.width : b;
+      const bool expand = ok && (nexp < e_max);
+      a = (expand && phase == 0) ? a - width : a;
+      b = (expand && phase == 1) ? b + width : b;
       flags |= (ok && !expand) ? 1 : 0;
       nexp = expand ? nexp + 1 : 0;
       phase = expand ? phase : phase + 1;
       continue;
     }
-    if (step == S.n_steps - 1) {
+    if (step == n_steps - 1) {
       int hs = -1;
-      if (nsh < S.t_max - 1) {
+      if (nsh < t_max - 1) {
         hs = nsh;
         hlen = nsh + 1;
       } else if (ok) {
-        hs = S.t_max - 1;
-        hlen = S.t_max;
+        hs = t_max - 1;
+        hlen = t_max;
       }
       if (hs >= 0) {
         if (lane == 0) O.hist_l[hs] = lp;
@@ -966,14 +971,14 @@ __device__ void slice_walker_warp(const LikParams& P, const LaneLik<DMAX>& Q, co
     } else {
       if (tp < 0.f) a = tp;
       else b = tp;
-      if (++nsh >= S.s_max) {
+      if (++nsh >= s_max) {
         flags |= 2;
         advance = true;
       }
     }
     if (advance) {
       ++step;
-      if (step < S.n_steps) {
+      if (step < n_steps) {
         load_step(step);
         phase = 0;
         nsh = 0;

@@ -516,12 +516,13 @@ static __device__ __noinline__ void mlp_reeval(const RunDesc& R, float* xbuf, in
 }
 
 template <int DMAX>
-__device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& S, const float* s_W, const int* s_seed,
+__device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& S_ref, const float* s_W, const int* s_seed,
                                               const float* s_chol, float* xbuf, float* lbuf, int* rlist, char* msm,
                                               MlpCtx* ctx, ClusterMail* mail, int* mvlist, BlockScratch& BS,
                                               long long& ev_out, int& fl_out, long long& re_out, int& err_out,
                                               long long& cyc_eval, long long& cyc_reeval, long long* count) {
   constexpr int RW = dir_row(DMAX);
+  const SliceCfg S = S_ref;  // in registers: the loop's stores would make every read a reload
   const int tid = threadIdx.x, m = R.m, d = S.d;
   const int XS = mlp_xs(d);
   const unsigned C = cl_size();
@@ -556,9 +557,6 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
   int step = 0, phase = 0, nexp0 = 0, nexp1 = 0, done = 0, nsh = 0, hlen = 0, flags = 0;
   long long evals = 0, reevals = 0;
   float a = 0.f, b = 0.f;
-  Stream st;
-  st.init(S.k0, S.k1, S.t, (uint32_t)i, 0u);
-  st.n = n0 + kPreShrink;
   auto load_step = [&](int s_) {
     const float* row = dirs + (size_t)s_ * RW;
 #pragma unroll
@@ -651,8 +649,6 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
       ++step;
       if (step < S.n_steps) {
         load_step(step);
-        st.init(S.k0, S.k1, S.t, (uint32_t)i, (uint32_t)step);
-        st.n = n0 + kPreShrink;
         phase = 0;
         nsh = 0;
         nexp0 = nexp1 = 0;
@@ -700,8 +696,8 @@ __device__ __noinline__ void walker_phase_mlp(const RunDesc& R, const SliceCfg& 
 #pragma unroll
           for (int j = 1; j < kPreShrink; ++j)
             if (nsh == j) uu = pre[j];
-        } else {
-          uu = u24(st.next());
+        } else {  // later shrinks (rare): straight from the step's stream
+          uu = u24(draw_at(S.k0, S.k1, S.t, (uint32_t)i, (uint32_t)step, n0 + (uint32_t)nsh));
         }
         const float tp = fmaf(uu, b - a, a);
         float u[DMAX];
