@@ -532,16 +532,28 @@ __device__ __forceinline__ void draw_row(const SliceCfg& S, int walker, int s, c
                                          float* __restrict__ out) {
   constexpr int RW = dir_row(DMAX);
   const int d = S.d;
-  Stream st;
-  st.init(S.k0, S.k1, S.t, (uint32_t)walker, (uint32_t)s);
+  // every Philox block the row needs, computed up front: the blocks are
+  // independent, so their rounds overlap (drawn one after another, each
+  // waited for the last).  Words 0 .. 2 ceil(d/2) - 1 feed the normals, then
+  // come r and the shrink draws.
+  constexpr int NP = (DMAX + 1) / 2, NB = (2 * NP + 1 + kPreShrink + 3) / 4;
+  uint32_t w[4 * NB];
+#pragma unroll
+  for (int b = 0; b < NB; ++b) {
+    const U4 q = philox((uint32_t)b, (uint32_t)s, (uint32_t)walker, S.t, S.k0, S.k1);
+    w[4 * b] = q.x;
+    w[4 * b + 1] = q.y;
+    w[4 * b + 2] = q.z;
+    w[4 * b + 3] = q.w;
+  }
   float z[DMAX];
 #pragma unroll
   for (int i = 0; i < DMAX; ++i) z[i] = 0.f;
 #pragma unroll
-  for (int p = 0; p < (DMAX + 1) / 2; ++p)
+  for (int p = 0; p < NP; ++p)
     if (2 * p < d) {
-      const float u1 = u24_open0(st.next());
-      const float u2 = u24(st.next());
+      const float u1 = u24_open0(w[2 * p]);
+      const float u2 = u24(w[2 * p + 1]);
       // Box-Muller; the angle on the special-function unit: 2 pi u2 - pi
       // stays in [-pi, pi), where the intrinsics are accurate to ~1e-6
       // absolute, and (cos, sin)(2 pi u2) = -(cos, sin)(2 pi u2 - pi).  The
@@ -574,9 +586,16 @@ __device__ __forceinline__ void draw_row(const SliceCfg& S, int walker, int s, c
     }
     row[i] = acc;
   }
-  row[DMAX] = u24(st.next());
+  {
+    const int nr = 2 * ((d + 1) / 2);  // the word of r (a select chain keeps w in registers)
 #pragma unroll
-  for (int j = 0; j < kPreShrink; ++j) row[DMAX + 1 + j] = u24(st.next());
+    for (int k = 0; k <= 2 * NP; k += 2)
+      if (k == nr) {
+        row[DMAX] = u24(w[k]);
+#pragma unroll
+        for (int j = 0; j < kPreShrink; ++j) row[DMAX + 1 + j] = u24(w[k + 1 + j]);
+      }
+  }
 #pragma unroll
   for (int i = 0; i < RW; i += 4)
     *reinterpret_cast<float4*>(out + i) = make_float4(row[i], row[i + 1], row[i + 2], row[i + 3]);
@@ -1215,26 +1234,32 @@ inline __device__ void evidence_add(EvidState& E, int N, int n, const float* __r
 constexpr int kTile = 128;
 constexpr int kTileS = kTile + 2;  // row stride of a moments tile: rows start on different banks
 
-// One warp: L = chol(A) for a d x d FP64 matrix (smem, row-major).  Returns
-// false (uniformly) if a pivot is not positive.
+// One warp: L = chol(A) for a d x d FP64 matrix (smem, row-major; A is not
+// changed).  Right-looking, in place in L: per column one reciprocal square
+// root of the pivot, the column scaled by it, then the trailing lower
+// triangle updated, one row per lane (d <= 32).  The chain of dependent FP64
+// operations per column is the rsqrt and two more (FP64 latency bounds this
+// on a part with few FP64 units; the left-looking form added a shuffle
+// reduction, a square root, a dot-product chain and a divide per column).
+// Returns false (uniformly) if a pivot is not positive.
 inline __device__ bool warp_cholesky(int d, const double* A, double* L) {
   const int lane = threadIdx.x & 31;
-  for (int i = lane; i < d * d; i += 32) L[i] = 0.0;
+  for (int q = lane; q < d * d; q += 32) L[q] = ((q % d) <= (q / d)) ? A[q] : 0.0;
   __syncwarp();
   for (int j = 0; j < d; ++j) {
-    double part = 0.0;
-    for (int k = lane; k < j; k += 32) part += L[j * d + k] * L[j * d + k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
-    const double s = A[j * d + j] - part;
+    const double s = L[j * d + j];
     if (!(s > 0.0) || !isfinite(s)) return false;
-    const double ljj = sqrt(s);
-    if (lane > j && lane < d) {
-      double u = A[lane * d + j];
-      for (int k = 0; k < j; ++k) u -= L[lane * d + k] * L[j * d + k];
-      L[lane * d + j] = u / ljj;
+    const double r = rsqrt(s);
+    const int i = j + 1 + lane;
+    double lij = 0.0;
+    if (i < d) {
+      lij = L[i * d + j] * r;
+      L[i * d + j] = lij;
     }
-    if (lane == j) L[j * d + j] = ljj;
+    __syncwarp();
+    if (lane == 0) L[j * d + j] = s * r;
+    if (i < d)
+      for (int k = j + 1; k <= i; ++k) L[i * d + k] -= lij * L[k * d + j];
     __syncwarp();
   }
   return true;
@@ -1322,10 +1347,12 @@ inline __device__ void warp_eigen_clip(int d, const double* C, double delta, dou
 inline __device__ void reg_cholesky(int d, double* C, double* L, double* work, BlockScratch& S) {
   const int tid = threadIdx.x;
   double* A = work;
-  if (tid == 0) {
-    double tr = 0.0;
-    for (int i = 0; i < d; ++i) tr += C[i * d + i];
-    S.dw[0] = tr;
+  if (tid < 32) {  // the trace: a shuffle tree instead of a chain of d FP64 adds
+    double part = 0.0;
+    for (int i = tid; i < d; i += 32) part += C[i * d + i];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(kFull, part, o);
+    if (tid == 0) S.dw[0] = part;
   }
   __syncthreads();
   const double tr = S.dw[0];
@@ -1385,9 +1412,21 @@ inline __device__ int node_moments(const float* __restrict__ live_x, int n_pad, 
   __syncthreads();
   int cnt = 0;
   for (int j0 = 0; j0 < N; j0 += kTile) {
-    for (int q = tid; q < d * kTile; q += B) {
-      const int i = q / kTile, jj = q % kTile, j = j0 + jj;
-      tile[i * kTileS + jj] = (j < N && member(j)) ? live_x[(size_t)i * n_pad + j] - ref[i] : 0.f;
+    // eight loads in flight per thread before the first store (one at a
+    // time, the tile's loads were most of the clustering phase)
+    for (int q0 = tid; q0 < d * kTile; q0 += 8 * B) {
+      float v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * B;
+        const int i = q / kTile, jj = q % kTile, j = j0 + jj;
+        v[u] = (q < d * kTile && j < N && member(j)) ? live_x[(size_t)i * n_pad + j] - ref[i] : 0.f;
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int q = q0 + u * B;
+        if (q < d * kTile) tile[(q / kTile) * kTileS + q % kTile] = v[u];
+      }
     }
     if (tid < kTile) cnt += (j0 + tid < N && member(j0 + tid)) ? 1 : 0;
     __syncthreads();
