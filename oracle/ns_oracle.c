@@ -238,6 +238,7 @@ void orc_default_opts(orc_opts* o, int d, int m)
     o->max_iter = 1000000;
     o->dead_cap = 0;
     o->correction = 2;
+    o->bracket = 0;
 }
 
 /* ======================================================================= */
@@ -684,7 +685,7 @@ static void lower_solve(int d, const double* Lo, const double* r, double* y)
  * enclose every member (the unit-ball constant is dropped; it cancels in
  * the pruning comparison). */
 static void node_stats(int d, const double* x, const int* members, int n,
-                       double* centre, double* chol, double* logvol)
+                       double* centre, double* chol, double* logvol, double* m2_out)
 {
     double* cov = (double*)calloc((size_t)d * d, sizeof(double));
     for (int i = 0; i < d; ++i) centre[i] = 0.0;
@@ -710,6 +711,7 @@ static void node_stats(int d, const double* x, const int* members, int n,
     double lv = 0.0;
     for (int i = 0; i < d; ++i) lv += log(chol[i * d + i]);
     *logvol = n > 0 ? lv + 0.5 * d * log(m2) : -INFINITY;
+    *m2_out = m2;
     free(cov);
 }
 
@@ -775,7 +777,7 @@ static void kmeans_split(int d, const double* x, const int* members, int n,
 int orc_cluster(int N, int d, const double* x, const orc_opts* o,
                 const uint32_t key[2], uint32_t t,
                 double* centres, double* chol, double* logvol, int* count,
-                int* split, int* mask, int* assign)
+                int* split, int* mask, int* assign, double* radius)
 {
     const int D = o->depth;
     const int n_nodes = (1 << (D + 1)) - 1;
@@ -797,7 +799,9 @@ int orc_cluster(int N, int d, const double* x, const orc_opts* o,
         for (int j = 0; j < N; ++j)
             if (path[(size_t)j * (D + 1) + depth_nd] == nd) members[n++] = j;
         count[nd] = n;
-        node_stats(d, x, members, n, centres + (size_t)nd * d, chol + (size_t)nd * d * d, &logvol[nd]);
+        double m2 = 0.0;
+        node_stats(d, x, members, n, centres + (size_t)nd * d, chol + (size_t)nd * d * d, &logvol[nd], &m2);
+        if (radius) radius[nd] = n > 0 ? sqrt(m2) : 0.0;
         if (depth_nd < D) {
             if (n >= 2) {
                 kmeans_split(d, x, members, n, centres, chol, o->kmeans_iters, key, t, nd, side);
@@ -871,7 +875,7 @@ typedef struct {
     int d, N, n_nodes;
     double *x, *l;  /* live set [N][d], [N] */
     int* cid;
-    double *centres, *chol, *logvol;
+    double *centres, *chol, *logvol, *radius;
     int *count, *split, *mask, *assign;
 } orc_live;
 
@@ -886,6 +890,7 @@ static void live_alloc(orc_live* s, int N, int d, int depth)
     s->centres = (double*)calloc((size_t)s->n_nodes * d, sizeof(double));
     s->chol = (double*)calloc((size_t)s->n_nodes * d * d, sizeof(double));
     s->logvol = (double*)calloc((size_t)s->n_nodes, sizeof(double));
+    s->radius = (double*)calloc((size_t)s->n_nodes, sizeof(double));
     s->count = (int*)calloc((size_t)s->n_nodes, sizeof(int));
     s->split = (int*)calloc((size_t)s->n_nodes, sizeof(int));
     s->mask = (int*)calloc((size_t)s->n_nodes, sizeof(int));
@@ -894,7 +899,7 @@ static void live_alloc(orc_live* s, int N, int d, int depth)
 
 static void live_free(orc_live* s)
 {
-    free(s->x); free(s->l); free(s->cid); free(s->centres); free(s->chol); free(s->logvol);
+    free(s->x); free(s->l); free(s->cid); free(s->centres); free(s->chol); free(s->logvol); free(s->radius);
     free(s->count); free(s->split); free(s->mask); free(s->assign);
 }
 
@@ -911,11 +916,23 @@ static void live_init(orc_live* s, const orc_lik* L, const uint32_t key[2], long
     *n_evals += s->N;
 }
 
+/* Reading c12 (bracket = 1): the slice bracket's width is counted in units
+ * of the walker's cluster's bounding radius, i.e. the direction factor is the
+ * cluster's Cholesky factor times its radius (a node with no positive finite
+ * radius keeps its factor).  The unscaled factors stay in the tree itself. */
 static void live_recluster(orc_live* s, const orc_opts* o, const uint32_t key[2], uint32_t t)
 {
     orc_cluster(s->N, s->d, s->x, o, key, t, s->centres, s->chol, s->logvol, s->count,
-                s->split, s->mask, s->assign);
+                s->split, s->mask, s->assign, s->radius);
     memcpy(s->cid, s->assign, sizeof(int) * (size_t)s->N);
+    if (o->bracket == 1) {
+        const int dd = s->d * s->d;
+        for (int nd = 0; nd < s->n_nodes; ++nd) {
+            const double r = s->radius[nd];
+            if (!(r > 0.0) || !isfinite(r)) continue;
+            for (int q = 0; q < dd; ++q) s->chol[(size_t)nd * dd + q] *= r;
+        }
+    }
 }
 
 static double live_max(const orc_live* s)

@@ -74,6 +74,10 @@ typedef struct {
     long long max_iter;  /* safety cap on iterations */
     long long dead_cap;  /* capacity of the caller's dead arrays */
     int correction;      /* 0 naive, 1 sorting (Alg. 1), 2 sorting + history (Alg. 2) */
+    int bracket;         /* initial slice bracket: 0 = width in units of the cluster's
+                            Cholesky factor (reading c3); 1 = width in units of the
+                            cluster's bounding radius, the factor scaled by the largest
+                            Mahalanobis distance of a member from the centre (reading c12) */
 } orc_opts;
 
 void orc_default_opts(orc_opts* o, int d, int m);
@@ -116,11 +120,13 @@ int orc_evid_should_stop(const orc_evid* e, double lmax, double stop_frac);
 
 /* ---- a3: clustering ----------------------------------------------------- */
 /* Nodes in heap order (root 0, children 2n+1, 2n+2); 2^(depth+1)-1 nodes.
- * x is [N][d] row-major. */
+ * x is [N][d] row-major.  radius (may be NULL): per node the largest
+ * Mahalanobis distance of a member from the node's centre, in the node's
+ * own Cholesky units (0 for an empty node). */
 int orc_cluster(int N, int d, const double* x, const orc_opts* o,
                 const uint32_t key[2], uint32_t t,
                 double* centres, double* chol, double* logvol, int* count,
-                int* split, int* mask, int* assign);
+                int* split, int* mask, int* assign, double* radius);
 int orc_nearest_leaf(int d, int n_nodes, const double* centres, const int* mask,
                      const double* x);
 /* Regularised Cholesky of a covariance (section 2.1): returns 1 if the

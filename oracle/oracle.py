@@ -45,6 +45,7 @@ class OrcOpts(C.Structure):
         ("vol_frac", C.c_double), ("kmeans_iters", C.c_int), ("history_iters", C.c_int),
         ("t_max", C.c_int), ("e_max", C.c_int), ("s_max", C.c_int), ("width", C.c_double),
         ("max_iter", C.c_longlong), ("dead_cap", C.c_longlong), ("correction", C.c_int),
+        ("bracket", C.c_int),
     ]
 
 
@@ -92,7 +93,7 @@ def lib():
         L.orc_evid_should_stop.argtypes = [C.POINTER(OrcEvid), C.c_double, C.c_double]
         L.orc_evid_should_stop.restype = C.c_int
         L.orc_cluster.argtypes = [C.c_int, C.c_int, _dp, C.POINTER(OrcOpts), _up, C.c_uint32,
-                                  _dp, _dp, _dp, _ip, _ip, _ip, _ip]
+                                  _dp, _dp, _dp, _ip, _ip, _ip, _ip, _dp]
         L.orc_cluster.restype = C.c_int
         L.orc_nearest_leaf.argtypes = [C.c_int, C.c_int, _dp, _ip, _dp]
         L.orc_reg_cholesky.argtypes = [C.c_int, _dp, _dp]
@@ -277,10 +278,11 @@ def cluster(x, o, seed, t):
     split = np.zeros(nn, dtype=np.int32)
     mask = np.zeros(nn, dtype=np.int32)
     assign = np.zeros(N, dtype=np.int32)
+    radius = np.zeros(nn)
     nl = lib().orc_cluster(N, d, x.reshape(-1), C.byref(o), _key(seed), t, centres.reshape(-1),
-                           chol.reshape(-1), logvol, count, split, mask, assign)
+                           chol.reshape(-1), logvol, count, split, mask, assign, radius)
     return dict(centres=centres, chol=chol, logvol=logvol, count=count, split=split, mask=mask,
-                assign=assign, n_leaves=nl)
+                assign=assign, n_leaves=nl, radius=radius)
 
 
 def nearest_leaf(centres, mask, x):

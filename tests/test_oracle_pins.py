@@ -509,16 +509,69 @@ def test_deep_tree_bookkeeping(oracle):
     assert np.bincount(out["assign"], minlength=127)[mask == 1].tolist() == cnt[mask == 1].tolist()
 
 
+def _max_mahalanobis(x):
+    """Largest Mahalanobis distance of the rows of x from their mean, under
+    the regularised covariance of section 2.1 (1/n normalisation, jitter
+    1e-10 tr/d), by linear solves."""
+    mu = x.mean(0)
+    cov = np.cov(x.T, bias=True)
+    cov = cov + 1e-10 * np.trace(cov) / x.shape[1] * np.eye(x.shape[1])
+    r = x - mu
+    return math.sqrt(np.max(np.einsum("ij,ij->i", r, np.linalg.solve(cov, r.T).T)))
+
+
+def test_node_radius_is_the_largest_mahalanobis_distance(oracle):
+    """The bounding radius of every node (the second bracket reading's unit
+    and the volume rule's enlargement), against linear solves: the root over
+    all points, each accepted leaf over its members."""
+    rng = np.random.default_rng(19)
+    x = np.vstack([rng.normal([0.25, 0.3, 0.3], 0.03, size=(150, 3)) @ np.diag([1.0, 0.5, 1.5]),
+                   rng.normal([0.75, 0.7, 0.6], 0.05, size=(120, 3))])
+    out = oracle.cluster(x, oracle.opts(3, 1, depth=1), 3, 0)
+    assert out["split"][0] == 1
+    assert out["radius"][0] == pytest.approx(_max_mahalanobis(x), rel=1e-10)
+    for nd in (1, 2):
+        members = x[out["assign"] == nd]
+        assert out["radius"][nd] == pytest.approx(_max_mahalanobis(members), rel=1e-10)
+
+
+def test_radius_bracket_is_the_unit_bracket_times_the_radius(oracle):
+    """Reading c12 against its definition: with one cluster, clustered once
+    (at t = 0), a run whose bracket is counted in units of the bounding
+    radius r0 takes the same walk as a run with the unit bracket of width r0
+    (the direction r0 L z/|z| with bracket [-r, 1 - r] against L z/|z| with
+    [-r r0, (1 - r) r0]): the same dead points up to FP64 rounding.  r0 is
+    recomputed here from the initial live set (24-bit Philox uniforms)."""
+    p = W.corr_gauss10(3)
+    N, m, K = 200, 10, 30
+    x0 = np.array([(oracle.stream_draws(5, oracle.T_INIT, j, 0, 0, p.d) >> 8) * 2.0 ** -24 for j in range(N)])
+    r0 = _max_mahalanobis(x0)
+    assert 2.0 < r0 < 10.0
+    oa = oracle.opts(p.d, m, bracket=1, recluster_every=10 ** 6, max_iter=K)
+    ob = oracle.opts(p.d, m, bracket=0, recluster_every=10 ** 6, max_iter=K, width=r0)
+    a = oracle.run(p, N, m, 20, 1e-3, 5, o=oa)
+    b = oracle.run(p, N, m, 20, 1e-3, 5, o=ob)
+    assert a["n_iter"] == b["n_iter"] == K and a["n_dead"] == b["n_dead"]
+    np.testing.assert_allclose(a["dead_l"], b["dead_l"], rtol=1e-9, atol=1e-9)
+    np.testing.assert_allclose(a["dead_x"], b["dead_x"], rtol=0, atol=1e-9)
+    assert abs(a["n_evals"] - b["n_evals"]) <= 2
+    # and it is not the unit bracket of width 1
+    c = oracle.run(p, N, m, 20, 1e-3, 5, o=oracle.opts(p.d, m, recluster_every=10 ** 6, max_iter=K))
+    assert not np.allclose(a["dead_l"], c["dead_l"])
+
+
 # --------------------------------------------------------------------------
 # whole runs
 # --------------------------------------------------------------------------
-def test_batched_m1_equals_sequential(oracle):
+@pytest.mark.parametrize("bracket", [0, 1])
+def test_batched_m1_equals_sequential(oracle, bracket):
     """At m = 1 Algorithm 1 keeps the new point (logL > W[0]) and Algorithm
     2 finds no faulty point (P = W[0] < logL), so the batched sampler is the
-    textbook sequential one, bit for bit (section 3.2)."""
+    textbook sequential one, bit for bit (section 3.2), under either bracket
+    reading."""
     for p, N in [(W.gauss2d_sigma05(), 100), (W.mixture4_d5(2), 150)]:
-        o1 = oracle.opts(p.d, 1, depth=1 if p.kind == W.MIXTURE else 0)
-        o2 = oracle.opts(p.d, 1, depth=1 if p.kind == W.MIXTURE else 0)
+        o1 = oracle.opts(p.d, 1, depth=1 if p.kind == W.MIXTURE else 0, bracket=bracket)
+        o2 = oracle.opts(p.d, 1, depth=1 if p.kind == W.MIXTURE else 0, bracket=bracket)
         a = oracle.run(p, N, 1, 2 * p.d, 1e-2, 17, o=o1)
         b = oracle.run(p, N, 1, 2 * p.d, 1e-2, 17, o=o2, sequential=True)
         assert a["n_dead"] == b["n_dead"]

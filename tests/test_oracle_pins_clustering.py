@@ -73,13 +73,15 @@ def test_shell_values():
             assert abs(O.loglike(lik, x[None, :])[0] + 0.5 * k * k) < 1e-12
 
 
-@pytest.mark.parametrize("name,depth", [("array49_d2", 3), ("shell_d2", 3)])
-def test_oracle_runs_recover_table1(oracle, name, depth):
+@pytest.mark.parametrize("name,depth,bracket", [("array49_d2", 3, 0), ("shell_d2", 3, 0), ("array49_d2", 3, 1),
+                                                ("shell_d2", 3, 1)])
+def test_oracle_runs_recover_table1(oracle, name, depth, bracket):
     """Sequential (m = 1) oracle runs of the 2-D tests with N = 300 live
-    points and the cluster tree: the mean over 6 seeds within 4 standard
-    errors (of the runs' own error estimates) of the closed form."""
+    points and the cluster tree, under either bracket reading: the mean over
+    6 seeds within 4 standard errors (of the runs' own error estimates) of
+    the closed form."""
     p = MAKERS[name]()
-    o = oracle.opts(p.d, 1, depth=depth, recluster_every=100)
+    o = oracle.opts(p.d, 1, depth=depth, recluster_every=100, bracket=bracket)
     z, err = [], []
     for s in range(1, 7):
         r = oracle.run(p, 300, 1, 10, 1e-3, 500 + s, o=o)
