@@ -102,6 +102,9 @@ def parse():
                          "launch, three launches, small dead buffers; prints no bench line")
     ap.add_argument("--depth-sweep", type=int, default=0, metavar="SEEDS",
                     help="the tree-depth study of section 2.3 (Test 2 truncated to d = 2..10, depth 0..6) and exit")
+    ap.add_argument("--bracket", type=int, default=0, choices=[0, 1],
+                    help="--depth-sweep and --clustering-tests: the slice bracket's unit (0 the cluster's Cholesky "
+                         "factor, 1 that factor times the cluster's bounding radius)")
     ap.add_argument("--correction-sweep", type=int, default=0, metavar="SEEDS",
                     help="run the batching-error study (correction schemes x m/N) with SEEDS runs per point, "
                          "print its JSON table and exit")
@@ -373,11 +376,13 @@ def correction_sweep(n_seeds):
 # --------------------------------------------------------------------------
 # the clustering tests of section 2.3 (Table 1)
 # --------------------------------------------------------------------------
-def clustering_tests(n_seeds, m=1, n_live=1000):
+def clustering_tests(n_seeds, m=1, n_live=1000, bracket=0):
     """Table 1: Test 1 (49 Gaussians, tree depth 6), Test 2 (two separated
     10-D Gaussians, depth 1), Test 3 (Gaussian shell, depth 4), each with (+)
     and without (-) the cluster tree, re-clustering every 100 iterations,
-    5 d slice steps; all seeds of one configuration in one batch."""
+    5 d slice steps; all seeds of one configuration in one batch.  bracket:
+    the slice bracket's unit (0 the cluster's Cholesky factor, 1 that factor
+    times the cluster's bounding radius)."""
     import numpy as np
     import torch
 
@@ -392,7 +397,7 @@ def clustering_tests(n_seeds, m=1, n_live=1000):
         row = {"log_z_true": analytic.logz(p)}
         for tag, dep in (("+", depth), ("-", 0)):
             h = nat.ns_create_batch([(p, n_live, m, 5 * p.d, 1e-3, 7000 + s) for s in range(n_seeds)],
-                                    nat.ns_default_options(depth=dep, recluster_every=100))
+                                    nat.ns_default_options(depth=dep, recluster_every=100, bracket=bracket))
             nat.ns_run(h)
             st = nat.ns_get_stats(h)
             res = [nat.ns_summary(h, r) for r in range(n_seeds)]
@@ -404,10 +409,10 @@ def clustering_tests(n_seeds, m=1, n_live=1000):
         out[name] = row
     torch.cuda.synchronize()
     return {"study": "clustering tests (section 2.3, Table 1): N_live=%d, m=%d, %d runs per configuration"
-                     % (n_live, m, n_seeds), "tests": out}
+                     % (n_live, m, n_seeds), "bracket": bracket, "tests": out}
 
 
-def depth_sweep(n_seeds, m=1, n_live=1000, dims=(2, 4, 6, 8, 10), depths=(0, 1, 2, 3, 4, 5, 6)):
+def depth_sweep(n_seeds, m=1, n_live=1000, dims=(2, 4, 6, 8, 10), depths=(0, 1, 2, 3, 4, 5, 6), bracket=0):
     """The depth study of section 2.3 (Fig. 1): Test 2 (two Gaussians of
     weights 1/10 and 1 at -10 and +10 in every coordinate, variances
     alternating 0.1 / 1, prior [-20, 20]^d) truncated to d = 2..10, with the
@@ -427,7 +432,7 @@ def depth_sweep(n_seeds, m=1, n_live=1000, dims=(2, 4, 6, 8, 10), depths=(0, 1, 
     t_all = 0.0
     for dep in depths:
         runs = [(probs[d], n_live, m, 5 * d, 1e-3, 9000 + s) for d in dims for s in range(n_seeds)]
-        h = nat.ns_create_batch(runs, nat.ns_default_options(depth=dep, recluster_every=100,
+        h = nat.ns_create_batch(runs, nat.ns_default_options(depth=dep, recluster_every=100, bracket=bracket,
                                                              walker_mapping=1 if m == 1 else 0))
         nat.ns_run(h)
         t_all += nat.ns_get_stats(h)["run_ms"]
@@ -447,7 +452,7 @@ def depth_sweep(n_seeds, m=1, n_live=1000, dims=(2, 4, 6, 8, 10), depths=(0, 1, 
     torch.cuda.synchronize()
     return {"study": "tree depth sweep (section 2.3, Fig. 1): Test 2 truncated to d, N_live=%d, m=%d, 5 d slice steps, "
                      "re-clustering every 100 iterations, %d runs per point" % (n_live, m, n_seeds),
-            "device_ms": t_all, "dims": table}
+            "bracket": bracket, "device_ms": t_all, "dims": table}
 
 
 # --------------------------------------------------------------------------
@@ -830,11 +835,11 @@ def main():
         return
     if args.clustering_tests > 0:
         if int(os.environ.get("RANK", "0")) == 0:
-            print(json.dumps(clustering_tests(args.clustering_tests)), flush=True)
+            print(json.dumps(clustering_tests(args.clustering_tests, bracket=args.bracket)), flush=True)
         return
     if args.depth_sweep > 0:
         if int(os.environ.get("RANK", "0")) == 0:
-            print(json.dumps(depth_sweep(args.depth_sweep)), flush=True)
+            print(json.dumps(depth_sweep(args.depth_sweep, bracket=args.bracket)), flush=True)
         return
     if args.correction_sweep > 0:
         if int(os.environ.get("RANK", "0")) == 0:

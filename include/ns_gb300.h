@@ -136,6 +136,12 @@ typedef struct {
                            * |threshold| of its threshold (1, default), or goes to FP32 at once (0) */
     double reeval2_margin; /* (0.05) */
     double reeval2_rel;    /* (1e-4) */
+    int bracket;          /* the unit of the initial slice bracket (section 2.2 gives none): 0 (default) the
+                           * walker's cluster Cholesky factor, so the bracket spans `width` standard deviations of
+                           * the cluster; 1 that factor times the cluster's bounding radius (the largest
+                           * Mahalanobis distance of a member from its centre), so it spans `width` radii.  With
+                           * 1 the FP32 factors written to the cluster tables (chol) are the scaled ones; chol64
+                           * stays the unscaled factor */
 } ns_options;
 
 /* One run of a batch. */

@@ -48,6 +48,7 @@ class NsOptions(C.Structure):
         ("reeval_margin", C.c_double), ("reeval_rel", C.c_double), ("reeval_defer", C.c_int),
         ("walker_mapping", C.c_int), ("mlp_batch_cap", C.c_int), ("mlp_cluster", C.c_int),
         ("two_plane", C.c_int), ("reeval2_margin", C.c_double), ("reeval2_rel", C.c_double),
+        ("bracket", C.c_int),
     ]
 
 

@@ -197,7 +197,29 @@ struct TreeIO {
   float* s_chol;    // smem [n_nodes][d][d]
   float* s_cent;    // smem [n_nodes][d]
   int* s_mask;      // smem [n_nodes]
+  int bracket;      // 1: the FP32 factors (the directions') scaled by each node's bounding radius
 };
+
+// This thread's largest squared Mahalanobis distance, over the live points
+// j = tid, tid + blockDim.x, ... < N (live_x [d][n_pad]), from the centre mu
+// in the units of the FP32 factor L (forward substitution), as the bits of a
+// non-negative float (ordered like the values, for atomicMax).
+static __device__ __noinline__ unsigned max_mahalanobis2(const float* __restrict__ live_x, int n_pad, int N, int d,
+                                            const float* L, const float* mu) {
+  float best = 0.f;
+  for (int j = threadIdx.x; j < N; j += blockDim.x) {
+    float r[kMaxDim];
+    float s2 = 0.f;
+    for (int i = 0; i < d; ++i) {
+      float s = live_x[(size_t)i * n_pad + j] - mu[i];
+      for (int k = 0; k < i; ++k) s = fmaf(-L[i * d + k], r[k], s);
+      r[i] = s / L[i * d + i];
+      s2 = fmaf(r[i], r[i], s2);
+    }
+    best = fmaxf(best, s2);
+  }
+  return __float_as_uint(best);
+}
 
 inline __device__ __noinline__ void cluster_tree(const TreeIO& io, const TreeScratch& T, BlockScratch& S, int nw_chol) {
   const int tid = threadIdx.x, B = blockDim.x, lane = tid & 31, wid = tid >> 5;
@@ -541,6 +563,17 @@ inline __device__ __noinline__ void cluster_tree(const TreeIO& io, const TreeScr
     io.logvol[nd] = (float)T.lv[nd];
   }
   __syncthreads();
+  // ---- second bracket reading: each direction factor times its node's radius
+  if (io.bracket == 1) {
+    for (int q = tid; q < n_nodes * d * d; q += B) {
+      const float rad = sqrtf(__uint_as_float(T.node_m2[q / (d * d)]));
+      if (rad > 0.f && isfinite(rad)) {
+        io.s_chol[q] *= rad;
+        io.chol[q] = io.s_chol[q];
+      }
+    }
+    __syncthreads();
+  }
   // ---- each point's accepted leaf --------------------------------------------
   for (int j = tid; j < N; j += B) {
     const int bits = io.side[j];

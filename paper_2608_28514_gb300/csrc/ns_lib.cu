@@ -347,7 +347,7 @@ ns_status check_opts(const ns_options& o, std::string* err) {
       o.mlp_batch_cap < 0 || o.mlp_batch_cap > kMlpNbMax ||
       !(o.mlp_cluster == 0 || o.mlp_cluster == 1 || o.mlp_cluster == 2 || o.mlp_cluster == 4) ||
       o.two_plane < 0 || o.two_plane > 1 || !(o.reeval2_margin >= 0) || !std::isfinite(o.reeval2_margin) ||
-      !(o.reeval2_rel >= 0) || !std::isfinite(o.reeval2_rel)) {
+      !(o.reeval2_rel >= 0) || !std::isfinite(o.reeval2_rel) || o.bracket < 0 || o.bracket > 1) {
     set_err(err, "an option is out of range");
     return NS_ERR_ARG;
   }
@@ -737,6 +737,7 @@ ns_status ns_create_batch(int n_runs, const ns_problem* runs, const ns_options* 
     R.reeval2_rel = (float)opt.reeval2_rel;
     R.walker_warp = (p.lik->kind == NS_LIK_MLP) ? 0 : opt.walker_mapping;
     R.mlp_round_cap = opt.mlp_batch_cap;
+    R.bracket = opt.bracket;
     if (p.lik->kind == NS_LIK_MLP) {
       R.mlp_tiles = reinterpret_cast<const uint8_t*>(base + o.mlp_img);
       R.mlp_desc = reinterpret_cast<const MlpDesc*>(base + o.mlp_desc);
@@ -1559,6 +1560,7 @@ ns_status ns_run_noalloc(const ns_problem* problem, const ns_options* opt_in, fl
   R.split = reinterpret_cast<int*>(base + o_split);
   R.mask = reinterpret_cast<int*>(base + o_mask);
   R.walker_warp = opt.walker_mapping;
+  R.bracket = opt.bracket;
   R.spill = spill ? 1 : 0;
   R.tree_ws = spill ? base + o_tree : nullptr;
   R.st = reinterpret_cast<RunState*>(base + o_state);
@@ -1792,6 +1794,7 @@ ns_status ns_cluster(int N, int n_pad, int d, const float* live_x, const ns_opti
   R.n_min = opt.n_min > 0 ? opt.n_min : d + 1;
   R.kmeans_iters = opt.kmeans_iters;
   R.vol_frac = (float)opt.vol_frac;
+  R.bracket = opt.bracket;
   R.k0 = (uint32_t)(seed & 0xFFFFFFFFull);
   R.k1 = (uint32_t)(seed >> 32);
   R.live_x = const_cast<float*>(live_x);

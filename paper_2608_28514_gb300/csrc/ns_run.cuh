@@ -78,6 +78,7 @@ struct RunDesc {
   float reeval2_rel;      //   reeval2_margin + reeval2_rel |threshold|
   int walker_warp;        // analytic runs: 1 = one walker per warp, 0 = one walker per thread
   int mlp_round_cap;      // BF16 MLP runs: candidates evaluated per round (0 = all, in equal calls)
+  int bracket;            // 1: the direction factors scaled by their cluster's bounding radius
 };
 
 // Shared-memory carve of the run kernel, computed identically on host and
@@ -225,6 +226,25 @@ inline __device__ void cluster_phase(const RunDesc& R, uint32_t t, char* sm, con
     s_cent[i] = (float)acc[i];
     R.centres[i] = (float)acc[i];
   }
+  if (R.n_nodes == 1 && R.bracket == 1) {
+    // the bounding radius of the one cluster: the largest Mahalanobis
+    // distance of a live point from the centre, in the root factor's units
+    // (the tree computes it for every node); the direction factor is then
+    // the Cholesky factor times that radius
+    unsigned* m2u = reinterpret_cast<unsigned*>(&S.iw[0]);
+    if (threadIdx.x == 0) *m2u = 0u;
+    __syncthreads();
+    const unsigned mx = max_mahalanobis2(R.live_x, R.n_pad, R.N, d, s_chol, s_cent);
+    atomicMax(m2u, mx);
+    __syncthreads();
+    const float rad = sqrtf(__uint_as_float(*m2u));
+    __syncthreads();
+    if (rad > 0.f && isfinite(rad))
+      for (int i = threadIdx.x; i < d * d; i += blockDim.x) {
+        s_chol[i] *= rad;
+        R.chol[i] = s_chol[i];
+      }
+  }
   if (R.n_nodes == 1) {
     if (threadIdx.x == 0) {
       s_mask[0] = 1;
@@ -267,6 +287,7 @@ inline __device__ void cluster_phase(const RunDesc& R, uint32_t t, char* sm, con
   io.s_chol = s_chol;
   io.s_cent = s_cent;
   io.s_mask = s_mask;
+  io.bracket = R.bracket;
   cluster_tree(io, T, S, nw_chol);
 }
 
@@ -1115,10 +1136,13 @@ __global__ void NS_RUN_BOUNDS(MLP, DMAX) k_run(const RunDesc* __restrict__ runs,
       walker_phase_mlp<DMAX>(R, SC, s_W, s_seed, s_chol, s_xbuf, s_lbuf, s_rlist, s_mlp, &mlp_ctx, mail, s_list, S, ev,
                              fl, re, werr, cyc_eval, cyc_reeval, RS.mlp_count);
     } else {
-      // every walker's rows of the iteration, spread over the whole block
+      // every walker's rows of the iteration, spread over the whole block;
+      // the walkers' cluster-factor offsets first (the update phase's
+      // scratch), so that a row reads no global memory before its factor
       const long long cd = clock64();
-      draw_directions_block<DMAX>(SC, 0, m, [&](int w) { return s_chol + (size_t)R.live_cid[s_seed[w]] * d * d; },
-                                  R.dirs);
+      for (int w = tid; w < m; w += B) s_stage_cid[w] = R.live_cid[s_seed[w]] * d * d;
+      __syncthreads();
+      draw_directions_block<DMAX>(SC, 0, m, [&](int w) { return s_chol + s_stage_cid[w]; }, R.dirs);
       const long long cd1 = clock64();
       if (R.walker_warp) {
         walker_phase_warp<DMAX>(R, P, SC, s_W, s_seed, ev, fl);
@@ -1157,43 +1181,55 @@ __global__ void NS_RUN_BOUNDS(MLP, DMAX) k_run(const RunDesc* __restrict__ runs,
     const int rel = batch_correct(m, R.K, R.correction, s_W, R.new_l, R.hist_l, R.hist_len, R.t_max, A, Bf, Tm,
                                   s_list, s_vals, s_ctr, S);
     tick(kPhCorrect);
-    // a10: dead append (rejected, ascending) and live update (accepted into S_W's slots)
+    // a10: dead append (rejected, ascending) and live update (accepted into
+    // S_W's slots).  The run's arrays are read into registers first: through
+    // R, every field would be loaded again after each store.
     const long long nd0 = RS.n_dead;
-    for (int q = tid; q < m * d; q += B) {
-      const int j = q / d, i = q - j * d;
-      {
-        const int src = A.src[j], hp = A.hp[j];
-        float val;
-        if (src < m) val = R.live_x[(size_t)i * R.n_pad + s_worst[src]];
-        else if (hp < 0) val = R.new_x[(size_t)(src - m) * d + i];
-        else val = R.hist_x[((size_t)(src - m) * R.t_max + hp) * d + i];
-        R.dead_x[(size_t)(nd0 + j) * d + i] = val;
+    {
+      float* const live_x = R.live_x;
+      const float* const new_x = R.new_x;
+      const float* const hist_x = R.hist_x;
+      float* const dead_x = R.dead_x;
+      float* const stage_x = R.stage_x;
+      float* const live_l = R.live_l;
+      int* const live_cid = R.live_cid;
+      const int n_pad = R.n_pad, t_max = R.t_max, n_nodes = R.n_nodes;
+      for (int q = tid; q < m * d; q += B) {
+        const int j = q / d, i = q - j * d;
+        {
+          const int src = A.src[j], hp = A.hp[j];
+          float val;
+          if (src < m) val = live_x[(size_t)i * n_pad + s_worst[src]];
+          else if (hp < 0) val = new_x[(size_t)(src - m) * d + i];
+          else val = hist_x[((size_t)(src - m) * t_max + hp) * d + i];
+          dead_x[(size_t)(nd0 + j) * d + i] = val;
+        }
+        {
+          const int src = A.src[m + j], hp = A.hp[m + j];
+          float val;
+          if (src < m) val = live_x[(size_t)i * n_pad + s_worst[src]];
+          else if (hp < 0) val = new_x[(size_t)(src - m) * d + i];
+          else val = hist_x[((size_t)(src - m) * t_max + hp) * d + i];
+          stage_x[(size_t)j * d + i] = val;
+        }
       }
-      {
-        const int src = A.src[m + j], hp = A.hp[m + j];
-        float val;
-        if (src < m) val = R.live_x[(size_t)i * R.n_pad + s_worst[src]];
-        else if (hp < 0) val = R.new_x[(size_t)(src - m) * d + i];
-        else val = R.hist_x[((size_t)(src - m) * R.t_max + hp) * d + i];
-        R.stage_x[(size_t)j * d + i] = val;
+      for (int j = tid; j < m; j += B) {
+        R.dead_l[nd0 + j] = A.l[j];
+        const int src = A.src[m + j];
+        s_stage_cid[j] = (src < m) ? live_cid[s_worst[src]] : -1;
       }
-    }
-    for (int j = tid; j < m; j += B) {
-      R.dead_l[nd0 + j] = A.l[j];
-      const int src = A.src[m + j];
-      s_stage_cid[j] = (src < m) ? R.live_cid[s_worst[src]] : -1;
-    }
-    __syncthreads();
-    for (int q = tid; q < m * d; q += B) {
-      const int j = q / d, i = q - j * d;
-      R.live_x[(size_t)i * R.n_pad + s_worst[j]] = R.stage_x[(size_t)j * d + i];
-    }
-    for (int j = tid; j < m; j += B) {
-      const int slot = s_worst[j];
-      R.live_l[slot] = A.l[m + j];
-      int c = s_stage_cid[j];
-      if (c < 0) c = (R.n_nodes > 1) ? nearest_leaf(R.stage_x + (size_t)j * d, d, R.n_nodes, s_cent, s_mask) : 0;
-      R.live_cid[slot] = c;
+      __syncthreads();
+      for (int q = tid; q < m * d; q += B) {
+        const int j = q / d, i = q - j * d;
+        live_x[(size_t)i * n_pad + s_worst[j]] = stage_x[(size_t)j * d + i];
+      }
+      for (int j = tid; j < m; j += B) {
+        const int slot = s_worst[j];
+        live_l[slot] = A.l[m + j];
+        int c = s_stage_cid[j];
+        if (c < 0) c = (n_nodes > 1) ? nearest_leaf(stage_x + (size_t)j * d, d, n_nodes, s_cent, s_mask) : 0;
+        live_cid[slot] = c;
+      }
     }
     __syncthreads();
     tick(kPhUpdate);

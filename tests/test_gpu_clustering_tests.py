@@ -65,15 +65,13 @@ def test_loglike_matches_oracle(nat, oracle, maker):
 CASES = {"array49_d2": (W.array49, 6), "bimodal_d10": (lambda: W.bimodal(10), 1), "shell_d2": (W.shell2d, 4)}
 
 
+@pytest.mark.parametrize("bracket", [0, 1])
 @pytest.mark.parametrize("name", sorted(CASES))
-def test_runs_recover_table1(nat, name):
+def test_runs_recover_table1(nat, name, bracket):
     """16 runs per test, N = 1000, m = 10, 5 d slice steps, re-clustering
     every 100 iterations: the mean log Z within 4 standard errors of Table
-    1's true value, with and without the cluster tree.  (Whether the tree
-    saves evaluations depends on the initial slice bracket, which the paper
-    does not give; with a unit bracket in the cluster's own Cholesky units
-    it does not on Test 2, so evaluation counts are reported by bench.py,
-    not pinned.)"""
+    1's true value, with and without the cluster tree, under both readings
+    of the initial slice bracket."""
     maker, depth = CASES[name]
     p = maker()
     truth = TABLE1[name]["log_z_true"]
@@ -81,7 +79,7 @@ def test_runs_recover_table1(nat, name):
     evals = {}
     for dep in (depth, 0):
         h = nat.ns_create_batch([(p, 1000, 10, 5 * p.d, 1e-3, 900 + s) for s in range(16)],
-                                nat.ns_default_options(depth=dep, recluster_every=100))
+                                nat.ns_default_options(depth=dep, recluster_every=100, bracket=bracket))
         nat.ns_run(h)
         res = [nat.ns_summary(h, r) for r in range(16)]
         nat.ns_destroy(h)

@@ -553,13 +553,13 @@ def test_budget_is_reported_not_hung(nat):
 # --------------------------------------------------------------------------
 # a3 cluster tree (depth >= 1)
 # --------------------------------------------------------------------------
-def _tree_case(nat, oracle, x, depth, seed=3, t=0):
+def _tree_case(nat, oracle, x, depth, seed=3, t=0, bracket=0):
     N, d = x.shape
     n_pad = ((N + 31) // 32) * 32
     live_x = np.zeros((d, n_pad), dtype=np.float32)
     live_x[:, :N] = x.T
     nn = (1 << (depth + 1)) - 1
-    opt = nat.ns_default_options(depth=depth)
+    opt = nat.ns_default_options(depth=depth, bracket=bracket)
     o = dict(centres=torch.zeros(nn, d, device=DEV), chol=torch.zeros(nn, d, d, device=DEV),
              chol64=torch.zeros(nn, d, d, dtype=torch.float64, device=DEV), logvol=torch.zeros(nn, device=DEV),
              count=torch.zeros(nn, dtype=torch.int32, device=DEV), split=torch.zeros(nn, dtype=torch.int32, device=DEV),
@@ -569,6 +569,37 @@ def _tree_case(nat, oracle, x, depth, seed=3, t=0):
     g = {k: v.cpu().numpy() for k, v in o.items()}
     want = oracle.cluster(x.astype(np.float64), oracle.opts(d, 1, depth=depth), seed, t)
     return g, want
+
+
+@pytest.mark.parametrize("case", ["ball_d0", "two_blobs_d1", "four_modes_d3"])
+def test_radius_bracket_scales_the_cluster_factors(nat, oracle, case):
+    """The second bracket reading (options.bracket = 1): the FP32 factors
+    the walkers draw directions with are each node's Cholesky factor times
+    its bounding radius (the oracle's FP64 radius: the largest Mahalanobis
+    distance of a member from the node's centre), at depth 0 (computed
+    apart from the tree) and in the tree; the FP64 factors and the
+    partition are those of the unit reading."""
+    rng = np.random.default_rng(zlib.crc32(case.encode()))
+    if case == "ball_d0":
+        x, depth = rng.uniform(0.2, 0.8, size=(700, 5)).astype(np.float32), 0
+    elif case == "two_blobs_d1":
+        x, depth = _blobs(rng, [[0.25, 0.3, 0.3], [0.75, 0.7, 0.6]], 0.03, 150), 1
+    else:
+        p = W.mixture4_d5(1)
+        th = np.vstack([c + p.sigma * rng.standard_normal((250, 5)) for c in p.centres])
+        x, depth = ((th - p.lo) / (p.hi - p.lo)).astype(np.float32), 3
+    x = rng.permutation(x)
+    g, want = _tree_case(nat, oracle, x, depth, bracket=1)
+    g0, _ = _tree_case(nat, oracle, x, depth, bracket=0)
+    for k in ("split", "mask", "count", "cid", "chol64"):
+        np.testing.assert_array_equal(g[k], g0[k])
+    used = want["count"] > 4 * (x.shape[1] + 1)
+    assert np.all(want["radius"][used] > 1.0)
+    np.testing.assert_allclose(g["chol"][used], want["chol"][used] * want["radius"][used][:, None, None],
+                               rtol=3e-3, atol=2e-6)
+    # and the scale is the radius, not 1: the unit reading's factors differ by it
+    ratio = g["chol"][used][:, 0, 0] / g0["chol"][used][:, 0, 0]
+    np.testing.assert_allclose(ratio, want["radius"][used], rtol=1e-3)
 
 
 def _blobs(rng, centres, sd, n):
