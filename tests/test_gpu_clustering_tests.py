@@ -91,26 +91,35 @@ def test_runs_recover_table1(nat, name, bracket):
     assert all(v > 0 for v in evals.values())
 
 
-def test_tree_evaluation_counts_follow_the_measured_direction(nat):
+@pytest.mark.parametrize("bracket", [0, 1])
+def test_tree_evaluation_counts_follow_the_measured_direction(nat, bracket):
     """Evaluation counts of the sequential sampler (m = 1, N = 1000, 5 d
     slice steps, 10 runs) with and without the tree, at the paper's depths,
-    under this build's bracket reading (a unit width in the slice cluster's
-    Cholesky units, reading r20): the tree saves evaluations on Test 3 (the
-    shell, depth 4: 26 % fewer over 50 runs) and on Test 1 (49 Gaussians,
-    depth 6: 11 % fewer), and costs them on Test 2 (two 10-D Gaussians, depth
-    1: 4-9 % more; the tree-depth study gives 4-24 % more at d = 2..10), where
-    the paper, with a bracket it does not state, reports fewer."""
+    under the two readings of the initial slice bracket, whose width the
+    paper does not give.  A unit width in the slice cluster's Cholesky units
+    (bracket 0): the tree saves evaluations on Test 3 (the shell, depth 4:
+    26 % fewer over 16 runs) and Test 1 (49 Gaussians, depth 6: 11 % fewer)
+    and costs them on Test 2 (two 10-D Gaussians, depth 1: 8 % more).  A
+    width of one bounding radius of the cluster (bracket 1): the tree saves
+    evaluations on all three, as the paper's Table 1 reports (16 runs: 30 %,
+    10 % and 33 % fewer; the paper: 17 %, 26 % and 28 %)."""
     ratio = {}
     for name, (maker, depth) in CASES.items():
         p = maker()
         ev = {}
         for dep in (depth, 0):
             h = nat.ns_create_batch([(p, 1000, 1, 5 * p.d, 1e-3, 700 + s) for s in range(10)],
-                                    nat.ns_default_options(depth=dep, recluster_every=100, walker_mapping=1))
+                                    nat.ns_default_options(depth=dep, recluster_every=100, walker_mapping=1,
+                                                           bracket=bracket))
             nat.ns_run(h)
             ev[dep] = np.mean([nat.ns_summary(h, r)["n_evals"] for r in range(10)])
             nat.ns_destroy(h)
         ratio[name] = ev[depth] / ev[0]
-    assert ratio["shell_d2"] < 0.85, ratio
-    assert ratio["array49_d2"] < 0.97, ratio
-    assert 1.0 < ratio["bimodal_d10"] < 1.2, ratio
+    if bracket == 0:
+        assert ratio["shell_d2"] < 0.85, ratio
+        assert ratio["array49_d2"] < 0.97, ratio
+        assert 1.0 < ratio["bimodal_d10"] < 1.2, ratio
+    else:
+        assert ratio["shell_d2"] < 0.8, ratio
+        assert ratio["array49_d2"] < 0.85, ratio
+        assert ratio["bimodal_d10"] < 0.97, ratio
