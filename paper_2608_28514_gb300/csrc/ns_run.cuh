@@ -126,14 +126,8 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax,
   c.seed = take(sizeof(int) * m);
   c.sel_slot = take(sizeof(int) * m);
   c.sel_key = take(sizeof(uint32_t) * m);
-  if (!mlp) {
-    c.candA = take(cand_bytes);
-    c.candB = take(cand_bytes);
-    c.candT = take(cand_bytes);
-  }
   c.list = take(sizeof(int) * 2 * m);
   c.vals = take(sizeof(float) * m);
-  c.slots = take(mlp ? 0 : sizeof(float) * (size_t)dir_row(dmax) * (m + 31) / 32 * 32);
   c.ctr = take(sizeof(int) * 4);
   c.stage_cid = take(sizeof(int) * m);
   // MLP runs: candidate points (two slots per walker, then FP32 staging
@@ -141,9 +135,10 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax,
   c.xbuf = take(mlp ? sizeof(float) * (size_t)(2 * m + kMlpF32Nb) * mlp_xs(d) : 0);
   c.lbuf = take(mlp ? sizeof(float) * (size_t)(2 * m + kMlpF32Nb) : 0);
   c.rlist = take(mlp ? sizeof(int) * (size_t)(2 * m + kMlpF32Nb) : 0);
-  // from here on, scratch of one phase at a time: the clustering; for MLP
-  // runs also the evaluators (walker phase) and the batch-correction
-  // candidates (Algorithms 1-2 and the update), which never overlap
+  // from here on, scratch of one phase at a time: the clustering, the
+  // walker phase (the analytic walkers' row slots; the MLP evaluators) and
+  // the batch-correction candidates (Algorithms 1-2 and the update), which
+  // never overlap
   const size_t phase0 = o;
   c.tile = take(sizeof(float) * (d * kTileS + d));
   c.acc = take(sizeof(double) * (d + d * d));
@@ -153,7 +148,19 @@ __host__ __device__ inline Carve make_carve(int d, int m, int n_nodes, int dmax,
   // per-warp partials for every warp of the block (MLP blocks have kMlpThreads threads, others <= 256)
   c.tree = take(c.tree_global ? 0 : tree_bytes(d, n_nodes, mlp ? kMlpThreads / 32 : 8, tree_chol_warps(d, 8)));
   c.mlp = phase0;
-  if (mlp) {
+  if (!mlp) {
+    const size_t end_cluster = o;
+    o = phase0;
+    c.slots = take(sizeof(float) * (size_t)dir_row(dmax) * (m + 31) / 32 * 32);
+    const size_t end_slots = o;
+    o = phase0;
+    c.candA = take(cand_bytes);
+    c.candB = take(cand_bytes);
+    c.candT = take(cand_bytes);
+    if (end_cluster > o) o = end_cluster;
+    if (end_slots > o) o = end_slots;
+  } else {
+    c.slots = phase0;
     const size_t end_cluster = o;
     o = phase0;
     c.candA = take(cand_bytes);
