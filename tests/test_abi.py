@@ -86,7 +86,8 @@ def test_validation_without_gpu(native):
     for k, v in [("depth", 9), ("t_max", 0), ("t_max", 65), ("correction", 7), ("width", -1.0),
                  ("precision", 2), ("reeval_margin", -1.0), ("reeval_rel", -1e-3), ("reeval_rel", float("inf")),
                  ("reeval_defer", -1), ("reeval_defer", 65), ("walker_mapping", 2), ("walker_mapping", -1),
-                 ("mlp_batch_cap", -1), ("mlp_batch_cap", 129)]:
+                 ("mlp_batch_cap", -1), ("mlp_batch_cap", 129), ("mlp_cluster", 3), ("two_plane", 2),
+                 ("reeval2_margin", -1.0), ("reeval2_rel", float("nan")), ("bracket", 2), ("bracket", -1)]:
         o = native.ns_default_options(**{k: v})
         with pytest.raises(native.NSError):
             native.ns_create(p, 100, 5, 10, 1e-3, 1, opt=o)
@@ -107,6 +108,8 @@ def test_default_options_match_header(native):
     assert o.width == 1.0 and o.vol_frac == 0.5 and o.kmeans_iters == 10
     assert o.precision == 0 and o.reeval_margin == 2.0 and o.reeval_rel == 4e-3 and o.reeval_defer == 4
     assert o.walker_mapping == 0 and o.mlp_batch_cap == 128
+    assert o.mlp_cluster == 0 and o.two_plane == 1 and o.reeval2_margin == 0.05 and o.reeval2_rel == 1e-4
+    assert o.bracket == 0
 
 
 def test_autotune_and_mapping_arguments_without_gpu(native):
