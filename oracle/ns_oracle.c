@@ -916,7 +916,7 @@ static void live_init(orc_live* s, const orc_lik* L, const uint32_t key[2], long
     *n_evals += s->N;
 }
 
-/* Reading c12 (bracket = 1): the slice bracket's width is counted in units
+/* Reading c18 (bracket = 1): the slice bracket's width is counted in units
  * of the walker's cluster's bounding radius, i.e. the direction factor is the
  * cluster's Cholesky factor times its radius (a node with no positive finite
  * radius keeps its factor).  The unscaled factors stay in the tree itself. */

@@ -77,7 +77,7 @@ typedef struct {
     int bracket;         /* initial slice bracket: 0 = width in units of the cluster's
                             Cholesky factor (reading c3); 1 = width in units of the
                             cluster's bounding radius, the factor scaled by the largest
-                            Mahalanobis distance of a member from the centre (reading c12) */
+                            Mahalanobis distance of a member from the centre (reading c18) */
 } orc_opts;
 
 void orc_default_opts(orc_opts* o, int d, int m);

@@ -536,7 +536,7 @@ def test_node_radius_is_the_largest_mahalanobis_distance(oracle):
 
 
 def test_radius_bracket_is_the_unit_bracket_times_the_radius(oracle):
-    """Reading c12 against its definition: with one cluster, clustered once
+    """Reading c18 against its definition: with one cluster, clustered once
     (at t = 0), a run whose bracket is counted in units of the bounding
     radius r0 takes the same walk as a run with the unit bracket of width r0
     (the direction r0 L z/|z| with bracket [-r, 1 - r] against L z/|z| with
