@@ -111,10 +111,10 @@ def parse():
     return ap.parse_args()
 
 
-def workload_config(args, runs):
+def workload_config(args, runs, note="as many as are resident at once"):
     return {"workload": f"10-D correlated Gaussian, prior [-10,10]^10, N_live={N_LIVE}, m={args.m}, "
                         f"{N_STEPS} slice steps, stop 1e-3; {runs} independent seeded runs per GPU "
-                        f"(as many as are resident at once)",
+                        f"({note})",
             "d": D, "n_live": N_LIVE, "m": args.m, "slice_steps": N_STEPS, "stop_frac": STOP,
             "runs_per_gpu": runs, "correction": "sorting + history (K=1)",
             "l2": "flushed between timed steps (256 MiB write)"}
@@ -775,7 +775,8 @@ def run_reference(args):
     line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(args, n_proc), "impl": "reference",
+            "config": workload_config(args, n_proc, "the reference arm: a bounded sample of the GPU arm's resident "
+                                                    "wave, one run per host process"), "impl": "reference",
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": n_proc, "kind": "oracle", "sample": sample},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
