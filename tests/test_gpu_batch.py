@@ -67,9 +67,8 @@ def test_batch256_against_pins(batch256):
     runs up to d = 10 (180 runs) against their closed forms, with the
     target's statistic: the fraction of runs within twice their reported
     error at least the 1 % point of Binomial(n, 0.9545), per family group,
-    and every run within 5 reported errors (over 180 runs a 4-error bound
-    would fail by chance in about one batch in a hundred even with exact
-    errors)."""
+    and every run within 4 reported errors (the batch's runs are fixed by
+    their seeds; the largest deviation is 3.6 errors, a 9-D Rosenbrock)."""
     from scipy.stats import binom
     runs, res, _ = batch256
     dz = {"gauss": [], "rosenbrock": [], "mixture": []}
@@ -78,7 +77,7 @@ def test_batch256_against_pins(batch256):
         truth = A.logz(p)
         z = (r["log_z"] - truth) / r["log_z_err"]
         if fam == "gauss" or p.d <= 10:
-            assert abs(z) < 5.0, (p.name, N, m, r["log_z"], truth, r["log_z_err"])
+            assert abs(z) < 4.0, (p.name, N, m, r["log_z"], truth, r["log_z_err"])
             dz[fam].append(z)
     g = np.array(dz["gauss"])
     low = np.array(dz["rosenbrock"] + dz["mixture"])
